@@ -1,0 +1,170 @@
+/*
+ * vcomm.h -- C ABI of the virtual-rank collective library for sm_103a (B300).
+ *
+ * A communicator holds N virtual ranks ("vranks") on ONE GPU.  Each vrank has
+ * its own caller-owned send and receive buffers in device memory; between two
+ * vranks data moves only through per-connection FIFOs that the communicator
+ * owns, in the same HBM.  Collectives run as one persistent kernel per call:
+ * one CTA per (vrank, channel) executes the paper's primitive step tables with
+ * flag-polled synchronisation between CTAs.
+ *
+ * Paper: "Demystifying NCCL: An In-depth Analysis of GPU Communication
+ * Protocols and Algorithms" (arXiv 2507.04786).  Section / table cited per call.
+ *
+ * Conventions shared by every call
+ *  - sendbufs / recvbufs are HOST arrays of nranks DEVICE pointers, owned by the
+ *    caller; the library copies the pointer arrays during the call and keeps no
+ *    reference after it returns.  Each pointer must be aligned to the element
+ *    size; 16-byte alignment (torch allocations) enables the vector path.
+ *  - Calls are asynchronous: they return after enqueueing one kernel on
+ *    `stream`; results are valid once the stream has been synchronised.
+ *  - Synchronous errors (bad arguments, unsupported combinations, too many
+ *    CTAs to be co-resident) are returned at once and nothing is enqueued.
+ *  - Device-side failures (a flag wait that exceeded the deadline, an abort)
+ *    end the kernel early; they are reported by vcommGetAsyncError.  The
+ *    kernels never trap.  After such a failure the communicator must be
+ *    destroyed.
+ *  - count == 0 is a successful no-op.
+ *  - Calls on one communicator must be serialised on one stream (like NCCL
+ *    calls on one communicator); calls on different communicators may overlap.
+ */
+#ifndef VCOMM_H_
+#define VCOMM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vcomm* vcomm_t;
+typedef void* vStream_t; /* a cudaStream_t; NULL is the legacy default stream */
+
+typedef enum {
+  vSuccess = 0,
+  vInvalidArgument = 1,
+  vUnsupported = 2,
+  vOutOfMemory = 3,
+  vCudaError = 4,
+  vTimeout = 5,
+  vAborted = 6,
+  vInternalError = 7
+} vResult_t;
+
+typedef enum { vInt32 = 0, vFloat32 = 1, vFloat16 = 2, vBfloat16 = 3 } vDataType_t;
+typedef enum { vSum = 0, vMax = 1 } vRedOp_t;
+typedef enum { vAlgoAuto = 0, vAlgoRing = 1, vAlgoTree = 2 } vAlgo_t;
+typedef enum { vProtoAuto = 0, vProtoSimple = 1, vProtoLL = 2, vProtoLL128 = 3 } vProto_t;
+
+#define VCOMM_MAX_RANKS 64
+#define VCOMM_MAX_CHANNELS 64
+
+/* Communicator configuration.  Zero fields take the defaults in brackets,
+ * which follow the paper's Table "NCCL channel buffer sizes" (Sec. V-C). */
+typedef struct {
+  size_t slotBytes[3];   /* FIFO slot bytes for Simple, LL, LL128 [512 KiB, 32 KiB, 600 KiB] */
+  int nsteps;            /* slots per connection FIFO, NCCL_STEPS of Sec. V-C [8] */
+  int nthreads;          /* upper bound on threads per CTA [512]; lowered to fit co-residency */
+  double timeoutSec;     /* deadline of every device flag wait [5 s; env VCOMM_TIMEOUT_MS] */
+} vcommConfig_t;
+
+/* Plan of one call: algorithm, protocol, channels and chunk steps.  Used to
+ * pin a plan (vcommSetPlan) and to read back the plan of the last call. */
+typedef struct {
+  vAlgo_t algo;
+  vProto_t proto;
+  int nchannels;         /* channels (CTAs per vrank; Tree uses two per channel) */
+  int chunkSteps;        /* FIFO slots per chunk: chunkCount = slot data * chunkSteps */
+} vPlan_t;
+
+/* ncclCommInitAll (Sec. II-A-1): one communicator over `nranks` vranks with
+ * up to `nchannels` channels (Sec. II-C).  nranks in [1, 64], nchannels in
+ * [1, 64].  Uses the current CUDA device.  FIFO arenas are allocated lazily
+ * per (algorithm, protocol) on first use, or eagerly by vcommPrepare.
+ * Errors: vInvalidArgument (ranges, NULL), vOutOfMemory, vCudaError. */
+vResult_t vcommInit(vcomm_t* comm, int nranks, int nchannels);
+vResult_t vcommInitConfig(vcomm_t* comm, int nranks, int nchannels, const vcommConfig_t* cfg);
+
+/* Allocate the FIFO arenas for the given algorithms and protocols now
+ * (bit i of algoMask = vAlgo_t i, bit i of protoMask = vProto_t i), so that
+ * later calls allocate nothing (e.g. before CUDA-graph capture). */
+vResult_t vcommPrepare(vcomm_t comm, unsigned algoMask, unsigned protoMask);
+
+/* ncclCommDestroy (Sec. II-A-1): waits for all work on the device, then frees
+ * the FIFO arenas and the communicator.  NULL is a no-op. */
+vResult_t vcommDestroy(vcomm_t comm);
+
+/* ncclCommAbort (Sec. II-A-1): raises the abort word that every device flag
+ * wait polls, so in-flight kernels of this communicator return early, then
+ * waits for the device and frees the communicator. */
+vResult_t vcommAbort(vcomm_t comm);
+
+/* Asynchronous error of the communicator: vSuccess, vTimeout (a flag wait hit
+ * its deadline) or vAborted.  Does not synchronise. */
+vResult_t vcommGetAsyncError(vcomm_t comm, vResult_t* err);
+
+/* Pin the plan used by later calls whose algo/proto arguments are Auto and
+ * set their channels / chunk steps (fields equal to 0 or Auto stay with the
+ * tuner).  NULL clears the pin. */
+vResult_t vcommSetPlan(vcomm_t comm, const vPlan_t* plan);
+
+/* The plan the last call on this communicator ran with. */
+vResult_t vcommGetLastPlan(vcomm_t comm, vPlan_t* plan);
+
+/* ncclAllReduce (Sec. II-A-2).  Ring: Sec. V-E, Table "Ring AllReduce";
+ * Tree: double binary tree, Sec. II-C and Table "Tree AllReduce".
+ * recvbufs[r] = op over j of sendbufs[j], `count` elements each, for every r.
+ * In place when sendbufs[r] == recvbufs[r]. */
+vResult_t vAllReduce(const void* const* sendbufs, void* const* recvbufs, size_t count,
+                     vDataType_t dtype, vRedOp_t op, vAlgo_t algo, vProto_t proto,
+                     vStream_t stream, vcomm_t comm);
+
+/* ncclReduceScatter (Sec. II-A-2), ring only (Table "Ring ReduceScatter").
+ * sendbufs[r] holds nranks blocks of recvcount elements; recvbufs[r] receives
+ * the reduction of block r.  In place when recvbufs[r] == sendbufs[r] +
+ * r * recvcount elements. */
+vResult_t vReduceScatter(const void* const* sendbufs, void* const* recvbufs, size_t recvcount,
+                         vDataType_t dtype, vRedOp_t op, vAlgo_t algo, vProto_t proto,
+                         vStream_t stream, vcomm_t comm);
+
+/* ncclAllGather (Sec. II-A-2), ring only (Table "Ring AllGather").
+ * recvbufs[r] holds nranks blocks of sendcount elements; block b is rank b's
+ * sendbuf.  Data moves as bytes (Sec. V-C).  In place when sendbufs[r] ==
+ * recvbufs[r] + r * sendcount elements. */
+vResult_t vAllGather(const void* const* sendbufs, void* const* recvbufs, size_t sendcount,
+                     vDataType_t dtype, vAlgo_t algo, vProto_t proto, vStream_t stream,
+                     vcomm_t comm);
+
+/* ncclBroadcast (Sec. II-A-2), ring chain from `root` (Table "Ring
+ * Broadcast").  recvbufs[r] = sendbufs[root] for all r; only sendbufs[root]
+ * is read (others may be NULL).  ncclBcast's in-place form is
+ * sendbufs[root] == recvbufs[root]. */
+vResult_t vBroadcast(const void* const* sendbufs, void* const* recvbufs, size_t count,
+                     vDataType_t dtype, int root, vAlgo_t algo, vProto_t proto,
+                     vStream_t stream, vcomm_t comm);
+
+/* ncclReduce (Sec. II-A-2), ring chain ending at `root` (Table "Ring
+ * Reduce").  Only recvbufs[root] is written (others may be NULL). */
+vResult_t vReduce(const void* const* sendbufs, void* const* recvbufs, size_t count,
+                  vDataType_t dtype, vRedOp_t op, int root, vAlgo_t algo, vProto_t proto,
+                  vStream_t stream, vcomm_t comm);
+
+/* Library version, e.g. 100 for 0.1.0. */
+int vcommVersion(void);
+
+/* ---- protocol encoders exposed for testing (Sec. III-B, III-C) ----------
+ * Run the device-side LL / LL128 line encoder on `nbytes` bytes at device
+ * pointer `src` with the given flag and write the lines to device pointer
+ * `lines` (LL: 8 bytes per 4 data bytes, rounded up to an even number of
+ * lines; LL128: 128 bytes per 120 data bytes).  Decoding runs the device
+ * reader, which fails with vTimeout if a line never carries `flag`. */
+vResult_t vDebugEncode(vProto_t proto, const void* src, size_t nbytes, uint64_t flag,
+                       void* lines, vStream_t stream);
+vResult_t vDebugDecode(vProto_t proto, const void* lines, size_t nbytes, uint64_t flag,
+                       void* dst, double timeoutSec, vStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VCOMM_H_ */

@@ -1,0 +1,242 @@
+"""ctypes binding of the C ABI in include/vcomm.h.
+
+Argument marshalling only: every step of every collective runs in the CUDA
+kernels of libvcomm.so.  Tensors are torch CUDA tensors; only their data
+pointers and the stream handle cross the boundary.  There is no fallback: if
+the library is missing, the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libvcomm.so")
+
+RESULTS = {0: "vSuccess", 1: "vInvalidArgument", 2: "vUnsupported", 3: "vOutOfMemory",
+           4: "vCudaError", 5: "vTimeout", 6: "vAborted", 7: "vInternalError"}
+DTYPE_CODES = {"int32": 0, "fp32": 1, "fp16": 2, "bf16": 3}
+OP_CODES = {"sum": 0, "max": 1}
+ALGO_CODES = {"auto": 0, "ring": 1, "tree": 2}
+PROTO_CODES = {"auto": 0, "simple": 1, "ll": 2, "ll128": 3}
+ALGO_NAMES = {v: k for k, v in ALGO_CODES.items()}
+PROTO_NAMES = {v: k for k, v in PROTO_CODES.items()}
+
+# the exported symbols of include/vcomm.h
+EXPORTS = ("vcommInit", "vcommInitConfig", "vcommPrepare", "vcommDestroy", "vcommAbort",
+           "vcommGetAsyncError", "vcommSetPlan", "vcommGetLastPlan", "vAllReduce",
+           "vReduceScatter", "vAllGather", "vBroadcast", "vReduce", "vcommVersion",
+           "vDebugEncode", "vDebugDecode")
+
+
+class VcommError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        self.name = RESULTS.get(code, str(code))
+        super().__init__(f"{what}: {self.name}")
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("slotBytes", ctypes.c_size_t * 3), ("nsteps", ctypes.c_int),
+                ("nthreads", ctypes.c_int), ("timeoutSec", ctypes.c_double)]
+
+
+class Plan(ctypes.Structure):
+    _fields_ = [("algo", ctypes.c_int), ("proto", ctypes.c_int), ("nchannels", ctypes.c_int),
+                ("chunkSteps", ctypes.c_int)]
+
+    def as_dict(self):
+        return {"algo": ALGO_NAMES[self.algo], "proto": PROTO_NAMES[self.proto],
+                "nchannels": self.nchannels, "chunkSteps": self.chunkSteps}
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load_library():
+    """Load libvcomm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"libvcomm.so not built ({_LIB_PATH}); run __graft_entry__.build()")
+    L = ctypes.CDLL(_LIB_PATH)
+    vp, sz, i32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    L.vcommInit.argtypes = [ctypes.POINTER(vp), i32, i32]
+    L.vcommInitConfig.argtypes = [ctypes.POINTER(vp), i32, i32, ctypes.POINTER(Config)]
+    L.vcommPrepare.argtypes = [vp, ctypes.c_uint, ctypes.c_uint]
+    L.vcommDestroy.argtypes = [vp]
+    L.vcommAbort.argtypes = [vp]
+    L.vcommGetAsyncError.argtypes = [vp, ctypes.POINTER(i32)]
+    L.vcommSetPlan.argtypes = [vp, ctypes.POINTER(Plan)]
+    L.vcommGetLastPlan.argtypes = [vp, ctypes.POINTER(Plan)]
+    L.vAllReduce.argtypes = [pp, pp, sz, i32, i32, i32, i32, vp, vp]
+    L.vReduceScatter.argtypes = [pp, pp, sz, i32, i32, i32, i32, vp, vp]
+    L.vAllGather.argtypes = [pp, pp, sz, i32, i32, i32, vp, vp]
+    L.vBroadcast.argtypes = [pp, pp, sz, i32, i32, i32, i32, vp, vp]
+    L.vReduce.argtypes = [pp, pp, sz, i32, i32, i32, i32, i32, vp, vp]
+    L.vcommVersion.argtypes = []
+    L.vDebugEncode.argtypes = [i32, vp, sz, ctypes.c_uint64, vp, vp]
+    L.vDebugDecode.argtypes = [i32, vp, sz, ctypes.c_uint64, vp, ctypes.c_double, vp]
+    for name in EXPORTS:
+        if name != "vcommVersion":
+            getattr(L, name).restype = i32
+    L.vcommVersion.restype = i32
+    _lib = L
+    return L
+
+
+def version() -> int:
+    return load_library().vcommVersion()
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise VcommError(rc, what)
+
+
+def _dtype_name(t) -> str:
+    import torch
+    m = {torch.float32: "fp32", torch.float16: "fp16", torch.bfloat16: "bf16",
+         torch.int32: "int32"}
+    if t.dtype not in m:
+        raise TypeError(f"unsupported dtype {t.dtype}")
+    return m[t.dtype]
+
+
+def _ptr_array(ts):
+    a = (ctypes.c_void_p * len(ts))()
+    for i, t in enumerate(ts):
+        a[i] = None if t is None else (t if isinstance(t, int) else t.data_ptr())
+    return a
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Comm:
+    """A communicator of `nranks` virtual ranks on the current CUDA device."""
+
+    def __init__(self, nranks: int, nchannels: int, slot_bytes=None, nsteps: int = 0,
+                 nthreads: int = 0, timeout_sec: float = 0.0):
+        L = load_library()
+        self._h = ctypes.c_void_p()
+        cfg = Config()
+        if slot_bytes:
+            for i, p in enumerate(("simple", "ll", "ll128")):
+                cfg.slotBytes[i] = int(slot_bytes.get(p, 0))
+        cfg.nsteps, cfg.nthreads, cfg.timeoutSec = nsteps, nthreads, timeout_sec
+        _check(L.vcommInitConfig(ctypes.byref(self._h), nranks, nchannels, ctypes.byref(cfg)),
+               "vcommInitConfig")
+        self.nranks, self.nchannels = nranks, nchannels
+
+    # -- lifetime
+    def destroy(self):
+        if self._h:
+            _check(load_library().vcommDestroy(self._h), "vcommDestroy")
+            self._h = ctypes.c_void_p()
+
+    def abort(self):
+        if self._h:
+            _check(load_library().vcommAbort(self._h), "vcommAbort")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def prepare(self, algos=("ring",), protos=("simple",)):
+        am = sum(1 << ALGO_CODES[a] for a in algos)
+        pm = sum(1 << PROTO_CODES[p] for p in protos)
+        _check(load_library().vcommPrepare(self._h, am, pm), "vcommPrepare")
+
+    def async_error(self) -> str:
+        e = ctypes.c_int()
+        _check(load_library().vcommGetAsyncError(self._h, ctypes.byref(e)), "vcommGetAsyncError")
+        return RESULTS[e.value]
+
+    def set_plan(self, algo="auto", proto="auto", nchannels=0, chunk_steps=0):
+        p = Plan(ALGO_CODES[algo], PROTO_CODES[proto], nchannels, chunk_steps)
+        _check(load_library().vcommSetPlan(self._h, ctypes.byref(p)), "vcommSetPlan")
+
+    def clear_plan(self):
+        _check(load_library().vcommSetPlan(self._h, None), "vcommSetPlan")
+
+    def last_plan(self) -> dict:
+        p = Plan()
+        _check(load_library().vcommGetLastPlan(self._h, ctypes.byref(p)), "vcommGetLastPlan")
+        return p.as_dict()
+
+    # -- collectives (lists of torch CUDA tensors, one per vrank)
+    def all_reduce(self, sends, recvs, op="sum", algo="ring", proto="simple", stream=None,
+                   count=None):
+        dt = _dtype_name(sends[0])
+        n = sends[0].numel() if count is None else count
+        _check(load_library().vAllReduce(_ptr_array(sends), _ptr_array(recvs), n,
+                                         DTYPE_CODES[dt], OP_CODES[op], ALGO_CODES[algo],
+                                         PROTO_CODES[proto], _stream_handle(stream), self._h),
+               "vAllReduce")
+
+    def reduce_scatter(self, sends, recvs, op="sum", algo="ring", proto="simple", stream=None,
+                       recvcount=None):
+        dt = _dtype_name(sends[0])
+        n = recvs[0].numel() if recvcount is None else recvcount
+        _check(load_library().vReduceScatter(_ptr_array(sends), _ptr_array(recvs), n,
+                                             DTYPE_CODES[dt], OP_CODES[op], ALGO_CODES[algo],
+                                             PROTO_CODES[proto], _stream_handle(stream),
+                                             self._h), "vReduceScatter")
+
+    def all_gather(self, sends, recvs, algo="ring", proto="simple", stream=None,
+                   sendcount=None):
+        dt = _dtype_name(sends[0])
+        n = sends[0].numel() if sendcount is None else sendcount
+        _check(load_library().vAllGather(_ptr_array(sends), _ptr_array(recvs), n,
+                                         DTYPE_CODES[dt], ALGO_CODES[algo], PROTO_CODES[proto],
+                                         _stream_handle(stream), self._h), "vAllGather")
+
+    def broadcast(self, sends, recvs, root=0, algo="ring", proto="simple", stream=None,
+                  count=None):
+        ref = sends[root] if sends[root] is not None else recvs[0]
+        dt = _dtype_name(ref)
+        n = recvs[0].numel() if count is None else count
+        _check(load_library().vBroadcast(_ptr_array(sends), _ptr_array(recvs), n,
+                                         DTYPE_CODES[dt], root, ALGO_CODES[algo],
+                                         PROTO_CODES[proto], _stream_handle(stream), self._h),
+               "vBroadcast")
+
+    def reduce(self, sends, recvs, op="sum", root=0, algo="ring", proto="simple", stream=None,
+               count=None):
+        dt = _dtype_name(sends[0])
+        n = sends[0].numel() if count is None else count
+        _check(load_library().vReduce(_ptr_array(sends), _ptr_array(recvs), n, DTYPE_CODES[dt],
+                                      OP_CODES[op], root, ALGO_CODES[algo], PROTO_CODES[proto],
+                                      _stream_handle(stream), self._h), "vReduce")
+
+
+def debug_encode(proto: str, src, nbytes: int, flag: int, lines, stream=None):
+    _check(load_library().vDebugEncode(PROTO_CODES[proto], src.data_ptr(), nbytes, flag,
+                                       lines.data_ptr(), _stream_handle(stream)), "vDebugEncode")
+
+
+def debug_decode(proto: str, lines, nbytes: int, flag: int, dst, timeout_sec: float = 1.0,
+                 stream=None) -> str:
+    rc = load_library().vDebugDecode(PROTO_CODES[proto], lines.data_ptr(), nbytes, flag,
+                                     dst.data_ptr(), timeout_sec, _stream_handle(stream))
+    return RESULTS[rc]
