@@ -1,0 +1,327 @@
+"""Benchmark: 8-vrank ring AllReduce, 256 MiB per vrank, fp32 sum, on one B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--proto simple|ll128|ll] [--sweep out.jsonl]
+
+One step = one AllReduce over the 8 virtual ranks (one kernel launch).  Prints
+ONE JSON line: bus bandwidth (nccl-tests convention: algbw * 2(k-1)/k) of the
+whole job, the HBM roofline of the kernel (algorithmic bytes 2kS + 4(k-1)S f,
+f = 1 Simple, 2 LL, 128/120 LL128, over the measured HBM copy bandwidth), the
+end-to-end figure through the C ABI with host buffers, the CPU oracle on a
+bounded sample, and the SM clocks sampled during the timed region.
+
+Under torchrun (--gpus N > 1) every rank runs its own replica on its own GPU
+(the collectives never leave one GPU); the value is the total over ranks
+divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2507_04786_b300 import inputs, workloads  # noqa: E402
+
+FIFO_FACTOR = {"simple": 1.0, "ll": 2.0, "ll128": 128.0 / 120.0}
+
+
+def algorithmic_bytes(k, S, proto):
+    """System-wide bytes of a k-vrank ring AllReduce of S bytes per vrank:
+    user 2kS (read inputs, write outputs) + FIFO 2 * 2(k-1)S * f."""
+    return 2 * k * S + 4 * (k - 1) * S * FIFO_FACTOR[proto]
+
+
+def busbw(S, k, seconds):
+    return S / seconds * 2 * (k - 1) / k / 1e9
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2507_04786_b300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload, proto):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    src = kernel_source_hash()
+    with open(p) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            kv = dict(x.split("=", 1) for x in line.split())
+            if kv.get("workload") == workload and kv.get("proto") == proto and kv.get("src") == src:
+                return float(kv["bytes_per_launch"])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons (read only)."""
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout.strip()
+                if out:
+                    self.rows.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if len(r) > 2 + i and r[2 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+
+def cpu_oracle_run(k, S_sample, proto, nch, chunk_steps, seed, reps=1):
+    """Time the CPU oracle (single thread) on a bounded sample of the workload."""
+    import oracle
+    n = S_sample // 4
+    xs = inputs.workload(seed, k, n, "fp32", "normal")
+    chunk = oracle.chunk_units(proto, 4, chunk_steps)
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.all_reduce(xs, "fp32", "sum", nch, chunk)
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def cpu_baseline(k, proto, nch, chunk_steps, seed, target_s=20.0):
+    """Bounded sample: grow the per-vrank size until one oracle run takes a
+    few seconds, then report bus GB/s on that sample."""
+    S = 4 << 20
+    t = cpu_oracle_run(k, S, proto, nch, chunk_steps, seed)[0]
+    while t < target_s / 4 and S < (256 << 20):
+        S *= 2
+        t = cpu_oracle_run(k, S, proto, nch, chunk_steps, seed)[0]
+    return {"value": round(busbw(S, k, t), 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{k} vranks x {S >> 20} MiB fp32 ring AllReduce ({proto}, {nch} channels), "
+                      f"one single-threaded oracle run of {t:.2f} s"}
+
+
+# ------------------------------------------------------------------ GPU leg
+
+def run_gpu(args, rank, world):
+    import torch
+
+    from paper_2507_04786_b300 import Comm
+
+    w = workloads.HEADLINE
+    k, S = w["nranks"], w["bytes_per_rank"]
+    n = S // 4
+    proto = args.proto
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    xs = inputs.workload(w["seed"] + rank, k, n, "fp32", w["dist"])
+    host = [torch.from_numpy(x).pin_memory() for x in xs]
+    sends = [h.to(dev) for h in host]
+    recvs = [torch.empty_like(s) for s in sends]
+    comm = Comm(k, w["nchannels"])
+    comm.set_plan(nchannels=w["nchannels"], chunk_steps=w["chunk_steps"])
+    stream = torch.cuda.current_stream()
+
+    def step():
+        comm.all_reduce(sends, recvs, op="sum", algo="ring", proto=proto, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if comm.async_error() != "vSuccess":
+        raise RuntimeError(comm.async_error())
+
+    barrier(world)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    with ClockSampler(dev.index) as clk:
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for i in range(args.steps):
+            evs[i][0].record(stream)
+            step()
+            evs[i][1].record(stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    total_ms = t0.elapsed_time(t1)
+    launch_ms = [a.elapsed_time(b) for a, b in evs]
+    if comm.async_error() != "vSuccess":
+        raise RuntimeError(comm.async_error())
+
+    # end to end: pinned host inputs -> device, AllReduce, results -> host
+    e2e_steps = max(1, min(args.steps, 5))
+    outs = [torch.empty_like(h).pin_memory() for h in host]
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        for h, s in zip(host, sends):
+            s.copy_(h, non_blocking=True)
+        step()
+        for o, r in zip(outs, recvs):
+            o.copy_(r, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    comm.destroy()
+    return {"ms_per_step": total_ms / args.steps, "launch_ms": float(np.mean(launch_ms)),
+            "e2e_ms": e2e_ms, "clocks": clk.summary(), "launches": args.steps,
+            "S": S, "k": k, "proto": proto}
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(world, x):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--proto", default="simple", choices=["simple", "ll", "ll128"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl")
+
+    w = workloads.HEADLINE
+    k, S = w["nranks"], w["bytes_per_rank"]
+    config = {"workload": w["name"], "nranks": k, "bytes_per_rank": S, "dtype": "fp32",
+              "op": "sum", "algo": "ring", "proto": args.proto, "nchannels": w["nchannels"],
+              "chunk_steps": w["chunk_steps"], "values": "N(0,1)",
+              "l2": "inputs 2 GiB and outputs 2 GiB per step exceed the 126 MB L2 (no flush)",
+              "replicas": world}
+    metric = "8-vrank ring AllReduce bus bandwidth"
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        reps = max(1, args.warmup) + args.steps
+        # bounded sample: 8 MiB per vrank, one oracle AllReduce per step
+        S_s = 8 << 20
+        times = cpu_oracle_run(k, S_s, args.proto, w["nchannels"], w["chunk_steps"], w["seed"],
+                               reps=reps)[args.warmup:]
+        t = float(np.mean(times))
+        v = busbw(S_s, k, t)
+        line = {"metric": metric, "value": round(v, 4), "unit": "GB/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1e3, 3),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic", "impl": "reference", "config": config,
+                "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                                 "sample": f"{k} vranks x {S_s >> 20} MiB per step, single-threaded "
+                                           f"CPU oracle"},
+                "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    r = run_gpu(args, rank, world)
+    ms = reduce_max(world, r["ms_per_step"])
+    launch_ms = reduce_max(world, r["launch_ms"])
+    e2e_ms = reduce_max(world, r["e2e_ms"])
+    if rank != 0:
+        return
+    value = world * busbw(S, k, ms / 1e3)
+    peak, peak_kind = measured_peak()
+    alg = algorithmic_bytes(k, S, args.proto)
+    achieved = alg / (launch_ms / 1e3) / 1e9
+    line = {
+        "metric": metric, "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": config,
+        "algbw_GBps": round(S / (ms / 1e3) / 1e9, 3),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": profiled_traffic(w["name"], args.proto),
+                     "algorithmic_bytes_per_launch": alg, "peak_source": peak_kind},
+        "e2e": {"value": round(world * busbw(S, k, e2e_ms / 1e3), 3), "unit": "GB/s",
+                "h2d_bytes_per_step": k * S, "d2h_bytes_per_step": k * S},
+        "gpu_launches": r["launches"],
+        "clocks": r["clocks"],
+    }
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(k, args.proto, w["nchannels"], w["chunk_steps"],
+                                            w["seed"])
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

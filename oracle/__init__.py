@@ -87,6 +87,8 @@ def lib():
         L.o_ll128_encode.argtypes = [vp, sz, ctypes.c_uint64, vp]
         L.o_ll128_decode.restype = ctypes.c_long
         L.o_ll128_decode.argtypes = [vp, sz, ctypes.c_uint64, vp]
+        for f in ("o_ring_allreduce_point", "o_tree_allreduce_point"):
+            getattr(L, f).argtypes = [i32, i32, sz, i32, i32, sz, sz, vp, vp]
         L.o_f64_to_f16.restype = ctypes.c_uint16
         L.o_f64_to_f16.argtypes = [ctypes.c_double]
         L.o_f64_to_bf16.restype = ctypes.c_uint16
@@ -311,3 +313,23 @@ def ll128_decode(lines: np.ndarray, nbytes: int, flag: int):
     out = np.zeros(nbytes, np.uint8)
     st = lib().o_ll128_decode(lines.ctypes.data, nbytes, flag, out.ctypes.data)
     return int(st), out
+
+
+def all_reduce_points(xs, idx, dtype: str, op: str, nch: int, chunk: int, algo: str = "ring"):
+    """Elements `idx` of the AllReduce result, computed one at a time (for
+    outputs too large to replay whole).  xs: per-rank inputs (numpy arrays of
+    the full length, or equivalently any arrays whose [idx] are the values)."""
+    L = lib()
+    f = L.o_ring_allreduce_point if algo == "ring" else L.o_tree_allreduce_point
+    k = len(xs)
+    n = xs[0].size
+    out = np.empty(len(idx), dtype=xs[0].dtype)
+    vals = np.empty(k, dtype=xs[0].dtype)
+    one = np.empty(1, dtype=xs[0].dtype)
+    for m, i in enumerate(idx):
+        for r in range(k):
+            vals[r] = xs[r][i]
+        rc = f(k, nch, chunk, DTYPES[dtype], OPS[op], n, int(i), vals.ctypes.data, one.ctypes.data)
+        assert rc == 0
+        out[m] = one[0]
+    return out

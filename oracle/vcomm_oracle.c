@@ -659,3 +659,69 @@ long o_ll128_decode(const uint64_t* lines, size_t nbytes, uint64_t flag, uint8_t
   }
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Point queries: the value of ONE output element, for sampled checks of     */
+/* outputs too large to replay whole.  vals[r] is element i of rank r's      */
+/* input (dtype dt).  They follow the same partition and fold orders as the  */
+/* full replays above (which the tests check element by element).            */
+/* ------------------------------------------------------------------------ */
+
+/* ring AllReduce: segment s of the loop holding i is folded x_{s+1}, ..., x_s */
+int o_ring_allreduce_point(int k, int nch, size_t chunk, int dt, int op, size_t count, size_t i,
+                           const void* vals, void* out) {
+  int es = o_dtype_size(dt);
+  if (k < 1 || i >= count) return -1;
+  if (k == 1) { memcpy(out, vals, (size_t)es); return 0; }
+  for (int ch = 0; ch < nch; ch++) {
+    size_t start, len;
+    o_channel_range(count, es, nch, ch, &start, &len);
+    if (i < start || i >= start + len) continue;
+    size_t end = start + len, loop = (size_t)k * chunk;
+    size_t off = start + ((i - start) / loop) * loop;
+    size_t c = o_ring_loop_chunk(off, end, k, chunk, es);
+    int s = (int)((i - off) / c);
+    char acc[8];
+    memcpy(acc, (const char*)vals + (size_t)es * (size_t)o_mod(s + 1, k), (size_t)es);
+    for (int m = 2; m <= k; m++) {
+      int r = o_mod(s + m, k);
+      o_reduce_elem(dt, op, acc, 0, vals, (size_t)r, acc, 0);
+    }
+    memcpy(out, acc, (size_t)es);
+    return 0;
+  }
+  return -1;
+}
+
+/* tree AllReduce: sub-channel j holding i runs tree j % 2 */
+static void o_tree_point_up(int k, int t, int dt, int op, int r, const void* vals, char* out) {
+  int es = o_dtype_size(dt);
+  int p, c0, c1;
+  o_tree_links(k, t, r, &p, &c0, &c1);
+  memcpy(out, (const char*)vals + (size_t)es * (size_t)r, (size_t)es);
+  int kids[2] = {c0, c1};
+  for (int j = 0; j < 2; j++) {
+    if (kids[j] < 0) continue;
+    char sub[8];
+    o_tree_point_up(k, t, dt, op, kids[j], vals, sub);
+    o_reduce_elem(dt, op, sub, 0, out, 0, out, 0);
+  }
+}
+int o_tree_allreduce_point(int k, int nch, size_t chunk, int dt, int op, size_t count, size_t i,
+                           const void* vals, void* out) {
+  int es = o_dtype_size(dt);
+  (void)chunk;
+  if (k < 1 || i >= count) return -1;
+  if (k == 1) { memcpy(out, vals, (size_t)es); return 0; }
+  int nsub = 2 * nch;
+  for (int j = 0; j < nsub; j++) {
+    size_t start, len;
+    o_channel_range(count, es, nsub, j, &start, &len);
+    if (i < start || i >= start + len) continue;
+    char acc[8];
+    o_tree_point_up(k, j % 2, dt, op, o_tree_root(k, j % 2), vals, acc);
+    memcpy(out, acc, (size_t)es);
+    return 0;
+  }
+  return -1;
+}

@@ -1,0 +1,157 @@
+// vcomm_internal.h -- structures shared by the host runtime and the kernels.
+//
+// Layout of a communicator's device state (all in one GPU's HBM):
+//   * per (algorithm, protocol) one FIFO arena: nconn connections, each a ring
+//     of `nsteps` slots of `slotBytes` (Sec. V-C, Table "NCCL channel buffer
+//     sizes"), plus two 128-byte counter lines per connection: `tail` (FIFO
+//     steps the sender has posted) and `head` (steps the receiver has
+//     consumed), the head/tail pair of the paper's P2P transport (Sec. IV-A).
+//   * ring connections: index ch * k + r is the edge r -> r+1 of channel ch.
+//   * tree connections: sub-channel j (two per channel), index j * k + r is the
+//     up edge r -> parent(r); index downOffset + j * k + r the down edge
+//     parent(r) -> r, with downOffset = (2 x the communicator's channels) x k.
+#pragma once
+#include <stddef.h>
+#include <stdint.h>
+
+#include "vcomm.h"
+
+#if defined(__CUDACC__)
+#define VC_HD __host__ __device__ __forceinline__
+#else
+#define VC_HD inline
+#endif
+
+namespace vc {
+
+enum Coll : int { kAllReduce = 0, kReduceScatter = 1, kAllGather = 2, kBroadcast = 3, kReduce = 4,
+                  kCopy = 5 };
+enum Algo : int { kRing = 0, kTree = 1 };
+enum Proto : int { kSimple = 0, kLL = 1, kLL128 = 2 };
+enum DType : int { kI32 = 0, kF32 = 1, kF16 = 2, kBF16 = 3 };
+enum OpKind : int { kSum = 0, kMax = 1 };
+
+constexpr int kCounterStride = 16;  // u64 words between counters (128 bytes)
+
+struct ConnDev {
+  char* buf;                       // nsteps slots of slotBytes
+  unsigned long long* tail;        // written only by the sending CTA
+  unsigned long long* head;        // written only by the receiving CTA
+  unsigned long long unused;
+};
+
+// first device-side failure; lives in host-mapped memory so that the host can
+// read it without synchronising
+struct ErrWord {
+  int code;      // vResult_t
+  int rank;
+  int channel;
+  int where;     // 1 = wait on tail, 2 = wait on head (credit), 3 = LL/LL128 line poll
+};
+
+struct KernArgs {
+  const void* send[VCOMM_MAX_RANKS];
+  void* recv[VCOMM_MAX_RANKS];
+  unsigned long long count;        // units partitioned over channels
+  unsigned long long chunk;        // chunkCount in units (multiple of a 16-byte pack)
+  unsigned long long slotBytes;    // bytes of one FIFO slot
+  unsigned long long slotUnits;    // data units one FIFO slot carries
+  unsigned long long timeoutNs;    // deadline of every flag wait
+  ConnDev* conns;
+  int* errClaim;                   // device word: first failure claims it
+  ErrWord* err;                    // host-mapped report
+  const volatile int* abortFlag;   // host-mapped abort word
+  unsigned long long inplaceMask;  // bit r: rank r runs in place
+  unsigned long long downOffset;   // tree: index of the first down connection
+  int coll;
+  int algo;
+  int nranks;
+  int nsub;                        // CTAs per rank: channels (ring) or 2 x channels (tree)
+  int root;
+  int nsteps;
+  int upThreads;                   // tree: threads of the reduce (up) group on non-root ranks
+};
+
+// ---- channel partition (Sec. V-C): 16-byte packs spread over `nch` ranges,
+// the first (packs % nch) ranges one pack longer, the element tail on the last.
+VC_HD void channelRange(unsigned long long n, int unitBytes, int nch, int ch,
+                        unsigned long long* start, unsigned long long* len) {
+  unsigned long long epp = 16ull / (unsigned long long)unitBytes;
+  unsigned long long npk = n / epp, tail = n % epp;
+  unsigned long long base = npk / (unsigned long long)nch, rem = npk % (unsigned long long)nch;
+  unsigned long long c = (unsigned long long)ch;
+  unsigned long long sp = c * base + (c < rem ? c : rem);
+  unsigned long long lp = base + (c < rem ? 1ull : 0ull);
+  *start = sp * epp;
+  *len = lp * epp + (ch == nch - 1 ? tail : 0ull);
+}
+
+// segment length of a ring-AllReduce loop at `off` in a channel ending at
+// `end`: full loops use chunkCount; the last loop spreads the remainder over
+// the k segments, rounded up to a pack
+VC_HD unsigned long long ringLoopChunk(unsigned long long off, unsigned long long end, int k,
+                                       unsigned long long chunk, int unitBytes) {
+  unsigned long long epp = 16ull / (unsigned long long)unitBytes;
+  unsigned long long loop = (unsigned long long)k * chunk;
+  unsigned long long rem = end - off;
+  if (rem >= loop) return chunk;
+  unsigned long long c = (rem + (unsigned long long)k - 1) / (unsigned long long)k;
+  return (c + epp - 1) / epp * epp;
+}
+
+VC_HD int modk(int a, int k) { return ((a % k) + k) % k; }
+
+// ---- double binary tree (Sec. II-C).  Tree A: node i = rank + 1; odd nodes
+// are leaves; an even node i with lowest set bit b has children i - b/2 and
+// the first of i + b/2, i + b/4, ..., i + 1 not above k; the root is the
+// largest power of two <= k.  Tree B mirrors A (k even) or shifts it by one
+// rank (k odd).
+VC_HD void treeANodeChildren(int k, int i, int* c0, int* c1) {
+  *c0 = 0;
+  *c1 = 0;
+  if (i & 1) return;
+  int b = i & -i;
+  *c0 = i - b / 2;
+  for (int d = b / 2; d >= 1; d >>= 1) {
+    if (i + d <= k) { *c1 = i + d; break; }
+  }
+}
+VC_HD int treeANodeParent(int k, int i) {
+  int root = 1;
+  while (root * 2 <= k) root *= 2;
+  if (i == root) return 0;
+  // walk down from the root: the parent is the node whose child is i
+  int cur = root;
+  while (true) {
+    int c0, c1;
+    treeANodeChildren(k, cur, &c0, &c1);
+    if (c0 == i || c1 == i) return cur;
+    // descend towards i: left subtree of cur holds nodes below cur
+    cur = (i < cur) ? c0 : c1;
+    if (cur == 0) return 0;   // not reachable (cannot happen for 1 <= i <= k)
+  }
+}
+VC_HD int treeNodeOfRank(int k, int t, int r) {
+  if (t == 0) return r + 1;
+  if ((k & 1) == 0) return (k - 1 - r) + 1;
+  return ((r + 1) % k) + 1;
+}
+VC_HD int treeRankOfNode(int k, int t, int i) {
+  int ra = i - 1;
+  if (t == 0) return ra;
+  if ((k & 1) == 0) return k - 1 - ra;
+  return ((ra - 1) % k + k) % k;
+}
+// parent rank (-1 at the root) and children ranks (-1 if absent), children in
+// ascending tree-A node order
+VC_HD void treeLinks(int k, int t, int r, int* parent, int* child0, int* child1) {
+  int i = treeNodeOfRank(k, t, r);
+  int c0, c1;
+  treeANodeChildren(k, i, &c0, &c1);
+  *child0 = c0 ? treeRankOfNode(k, t, c0) : -1;
+  *child1 = c1 ? treeRankOfNode(k, t, c1) : -1;
+  int p = treeANodeParent(k, i);
+  *parent = p ? treeRankOfNode(k, t, p) : -1;
+}
+
+}  // namespace vc

@@ -1,0 +1,12 @@
+// vcomm_kernels.h -- host-visible handles of the kernels in vcomm_kernels.cu.
+#pragma once
+
+namespace vc {
+// persistent collective kernel for (protocol, dtype, op): AllReduce (ring and
+// tree), ReduceScatter, Reduce and the single-rank copy
+const void* reduceKernel(int proto, int dtype, int op);
+// persistent byte-moving kernel for AllGather, Broadcast and the single-rank copy
+const void* copyKernel(int proto);
+const void* debugEncodeKernel();
+const void* debugDecodeKernel();
+}  // namespace vc

@@ -1,0 +1,51 @@
+// vcomm_reduce_inst.cu -- the reducing collective kernel for ONE (protocol,
+// dtype) pair, selected at compile time by -DVC_PROTO=<0..2> -DVC_DTYPE=<0..3>.
+// The build compiles this file once per pair, in parallel.
+#include <cuda_runtime.h>
+
+#include "vcomm_device.cuh"
+
+#ifndef VC_PROTO
+#error "compile with -DVC_PROTO=<0|1|2> -DVC_DTYPE=<0..3>"
+#endif
+
+namespace vc {
+
+template <int P, class T, class Op>
+__global__ void __launch_bounds__(512, 2) kReduceColl(const __grid_constant__ KernArgs a) {
+  __shared__ int sAbort[2];
+  if (threadIdx.x < 2) sAbort[threadIdx.x] = 0;
+  __syncthreads();
+  const int r = blockIdx.x % a.nranks;
+  const int ch = blockIdx.x / a.nranks;
+  volatile int* sa = sAbort;
+  switch (a.coll) {
+    case kAllReduce:
+      if (a.algo == kTree) treeAllReduce<P, T, Op>(a, r, ch, sa);
+      else ringAllReduce<P, T, Op>(a, r, ch, sa);
+      break;
+    case kReduceScatter: ringReduceScatter<P, T, Op>(a, r, ch, sa); break;
+    case kReduce: ringReduce<P, T, Op>(a, r, ch, sa); break;
+    case kCopy: localCopy<T>(a, ch); break;
+    default: break;
+  }
+}
+
+#if VC_DTYPE == 0
+using VcT = int32_t;
+#elif VC_DTYPE == 1
+using VcT = float;
+#elif VC_DTYPE == 2
+using VcT = __half;
+#else
+using VcT = __nv_bfloat16;
+#endif
+
+#define VC_NAME2(P, D) reduceKernel_##P##_##D
+#define VC_NAME(P, D) VC_NAME2(P, D)
+const void* VC_NAME(VC_PROTO, VC_DTYPE)(int op) {
+  return op == kSum ? (const void*)kReduceColl<VC_PROTO, VcT, OpSum>
+                    : (const void*)kReduceColl<VC_PROTO, VcT, OpMax>;
+}
+
+}  // namespace vc

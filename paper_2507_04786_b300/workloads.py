@@ -1,0 +1,39 @@
+"""Named workloads: the shapes the benchmark times and the tests check.
+
+Each workload is a plain dict; sizes are per vrank.  The headline is an
+8-vrank ring AllReduce of 256 MiB per vrank (fp32 sum, N(0, 1) values),
+timed with the Simple and LL128 protocols.
+"""
+MiB = 1 << 20
+KiB = 1 << 10
+
+HEADLINE = {
+    "name": "ring-allreduce-8vr-256MiB",
+    "coll": "allreduce",
+    "algo": "ring",
+    "nranks": 8,
+    "bytes_per_rank": 256 * MiB,
+    "dtype": "fp32",
+    "op": "sum",
+    "dist": "normal",
+    "seed": 1,
+    "protos": ("simple", "ll128"),
+    "nchannels": 32,
+    "chunk_steps": 1,
+}
+
+# the exactly-summable correctness case: 4 vranks, 1,048,576 fp32 integers
+# uniform in [-1000, 1000], Simple, one channel, seed 0
+EXACT = {
+    "name": "ring-allreduce-4vr-1Mi-int-fp32",
+    "nranks": 4,
+    "count": 1 << 20,
+    "dtype": "fp32",
+    "proto": "simple",
+    "nchannels": 1,
+    "seed": 0,
+}
+
+# per-rank message sizes of the protocol sweep: 1 KiB .. 256 MiB in powers of 4
+SWEEP_BYTES = [KiB * 4 ** i for i in range(10)]
+SWEEP_CHANNELS = (1, 4, 16, 32)

@@ -402,3 +402,16 @@ def test_ll128_round_trip(nbytes):
     st, back = oracle.ll128_decode(lines, nbytes, flag)
     assert st == 0 and np.array_equal(back, d)
     assert oracle.ll128_decode(lines, nbytes, flag + 1)[0] == 1
+
+
+@pytest.mark.parametrize("algo", ["ring", "tree"])
+@pytest.mark.parametrize("k,C,chunk,n", [(2, 1, 8, 100), (3, 2, 16, 1003), (8, 3, 64, 20011),
+                                         (5, 4, 32, 4096)])
+@pytest.mark.parametrize("dtype,op", [("fp32", "sum"), ("bf16", "sum"), ("fp16", "max")])
+def test_point_queries_match_replay(algo, k, C, chunk, n, dtype, op):
+    """The one-element queries used for full-size sampled checks agree with
+    the full step-by-step replay on every element."""
+    xs = inputs.workload(21, k, n, dtype, "normal")
+    full = oracle.all_reduce(xs, dtype, op, C, chunk, algo)[0]
+    pts = oracle.all_reduce_points(xs, np.arange(n), dtype, op, C, chunk, algo)
+    assert np.array_equal(pts.view(np.uint8), full.view(np.uint8))
