@@ -81,7 +81,8 @@ def profiled_traffic(workload, proto):
 
 
 class ClockSampler:
-    """nvidia-smi sampling of SM clocks and throttle reasons (read only)."""
+    """Samples SM clocks and throttle reasons with `nvidia-smi -lms 100`
+    (read only) while the timed region runs."""
     FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
@@ -89,41 +90,46 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.rows = []
-        self._stop = threading.Event()
-        self._t = None
-
-    def _run(self):
-        while not self._stop.is_set():
-            try:
-                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                                      "--format=csv,noheader,nounits"], capture_output=True,
-                                     text=True, timeout=5).stdout.strip()
-                if out:
-                    self.rows.append([x.strip() for x in out.split(",")])
-            except Exception:
-                pass
-            self._stop.wait(0.2)
+        self._p = None
 
     def __enter__(self):
-        self._t = threading.Thread(target=self._run, daemon=True)
-        self._t.start()
+        try:
+            self._p = subprocess.Popen(["nvidia-smi", "-i", str(self.index),
+                                        "--query-gpu=" + self.FIELDS,
+                                        "--format=csv,noheader,nounits", "-lms", "100"],
+                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.3)     # first sample lands before the timed region starts
+        except Exception:
+            self._p = None
         return self
 
     def __exit__(self, *a):
-        self._stop.set()
-        self._t.join(timeout=10)
+        if self._p is None:
+            return
+        time.sleep(0.15)
+        self._p.terminate()
+        try:
+            out, _ = self._p.communicate(timeout=5)
+        except Exception:
+            self._p.kill()
+            out, _ = self._p.communicate()
+        self.rows = [[x.strip() for x in l.split(",")] for l in out.splitlines() if l.strip()]
 
     def summary(self):
-        if not self.rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [v for v in (num(r[0]) for r in self.rows) if v is not None]
+        mx = [v for v in (num(r[1]) for r in self.rows if len(r) > 1) if v is not None]
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in self.rows for i in range(4)
                           if len(r) > 2 + i and r[2 + i].lower().startswith("active")})
-        return {"sm_mhz": float(np.median(sm)) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(self.rows)}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
 
 
 # ------------------------------------------------------------------ CPU oracle leg
@@ -163,7 +169,7 @@ def run_gpu(args, rank, world):
     from paper_2507_04786_b300 import Comm
 
     w = workloads.HEADLINE
-    k, S = w["nranks"], w["bytes_per_rank"]
+    k, S = w["nranks"], args.bytes
     n = S // 4
     proto = args.proto
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
@@ -246,11 +252,14 @@ def reduce_max(world, x):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--proto", default="simple", choices=["simple", "ll", "ll128"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
+    ap.add_argument("--bytes", type=int, default=workloads.HEADLINE["bytes_per_rank"],
+                    help="bytes per vrank (default: the headline's 256 MiB; smaller sizes are "
+                         "for profiling captures only)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -262,11 +271,13 @@ def main():
         dist.init_process_group("nccl")
 
     w = workloads.HEADLINE
-    k, S = w["nranks"], w["bytes_per_rank"]
-    config = {"workload": w["name"], "nranks": k, "bytes_per_rank": S, "dtype": "fp32",
+    k, S = w["nranks"], args.bytes
+    wname = w["name"] if S == w["bytes_per_rank"] else f"ring-allreduce-8vr-{S >> 20}MiB"
+    config = {"workload": wname, "nranks": k, "bytes_per_rank": S, "dtype": "fp32",
               "op": "sum", "algo": "ring", "proto": args.proto, "nchannels": w["nchannels"],
               "chunk_steps": w["chunk_steps"], "values": "N(0,1)",
-              "l2": "inputs 2 GiB and outputs 2 GiB per step exceed the 126 MB L2 (no flush)",
+              "l2": f"inputs {k * S >> 20} MiB and outputs {k * S >> 20} MiB per step vs the "
+                    f"126 MB L2 (no flush)",
               "replicas": world}
     metric = "8-vrank ring AllReduce bus bandwidth"
 
@@ -310,7 +321,7 @@ def main():
         "algbw_GBps": round(S / (ms / 1e3) / 1e9, 3),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": profiled_traffic(w["name"], args.proto),
+                     "traffic": profiled_traffic(wname, args.proto),
                      "algorithmic_bytes_per_launch": alg, "peak_source": peak_kind},
         "e2e": {"value": round(world * busbw(S, k, e2e_ms / 1e3), 3), "unit": "GB/s",
                 "h2d_bytes_per_step": k * S, "d2h_bytes_per_step": k * S},

@@ -213,7 +213,7 @@ class Comm:
 
     def broadcast(self, sends, recvs, root=0, algo="ring", proto="simple", stream=None,
                   count=None):
-        ref = sends[root] if sends[root] is not None else recvs[0]
+        ref = sends[root] if 0 <= root < len(sends) and sends[root] is not None else recvs[0]
         dt = _dtype_name(ref)
         n = recvs[0].numel() if count is None else count
         _check(load_library().vBroadcast(_ptr_array(sends), _ptr_array(recvs), n,
