@@ -150,6 +150,36 @@ vResult_t vReduce(const void* const* sendbufs, void* const* recvbufs, size_t cou
                   vDataType_t dtype, vRedOp_t op, int root, vAlgo_t algo, vProto_t proto,
                   vStream_t stream, vcomm_t comm);
 
+/* ---- allocation-free AllReduce -----------------------------------------
+ * The paper has no counterpart to this entry point.  It exists for callers
+ * that cannot call cudaMalloc at the point where they need an AllReduce: code
+ * that must stay inside a fixed memory budget owned by another allocator, and
+ * latency-critical code where cudaMalloc / cudaFree could block or
+ * synchronise the device.  It runs the ring AllReduce with the Simple protocol
+ * (same kernel and same results as vAllReduce with algo Ring, proto Simple,
+ * nchannels channels, 64 KiB Simple slots and chunkSteps 1), but its FIFOs,
+ * counters and error words live in one fixed device array that the library
+ * defines at file scope: VCOMM_NOALLOC_SCRATCH_BYTES (about 8 MiB) on every
+ * GPU that loads the library, held until the process exits.  No
+ * communicator is needed and nothing is allocated.
+ *  - nranks x nchannels must not exceed VCOMM_NOALLOC_MAX_CONNS (32): larger
+ *    requests return vInvalidArgument and enqueue nothing.  count is not
+ *    limited (data streams through the FIFOs).
+ *  - The first call on a device looks up the array's device address (with
+ *    that device current); make that first call before any stream capture.
+ *  - Every call shares the one array and clears its counters first, so calls
+ *    that overlap on the GPU (other streams, other host threads) race and
+ *    corrupt each other: serialise them.
+ *  - deviceStatus: NULL, or caller-owned device memory of 4 ints that the call
+ *    sets to {code, rank, channel, where} of a device-side failure (a flag wait
+ *    past its 5 s deadline), or to zeros on success.
+ * Other arguments and in-place rules as in vAllReduce. */
+#define VCOMM_NOALLOC_MAX_CONNS 32
+#define VCOMM_NOALLOC_SCRATCH_BYTES 8398080
+vResult_t vAllReduceNoAlloc(const void* const* sendbufs, void* const* recvbufs, size_t count,
+                            vDataType_t dtype, vRedOp_t op, int nranks, int nchannels,
+                            int* deviceStatus, vStream_t stream);
+
 /* Library version, e.g. 100 for 0.1.0. */
 int vcommVersion(void);
 

@@ -26,7 +26,7 @@ PROTO_NAMES = {v: k for k, v in PROTO_CODES.items()}
 EXPORTS = ("vcommInit", "vcommInitConfig", "vcommPrepare", "vcommDestroy", "vcommAbort",
            "vcommGetAsyncError", "vcommSetPlan", "vcommGetLastPlan", "vAllReduce",
            "vReduceScatter", "vAllGather", "vBroadcast", "vReduce", "vcommVersion",
-           "vDebugEncode", "vDebugDecode")
+           "vDebugEncode", "vDebugDecode", "vAllReduceNoAlloc")
 
 
 class VcommError(RuntimeError):
@@ -83,6 +83,7 @@ def load_library():
     L.vcommVersion.argtypes = []
     L.vDebugEncode.argtypes = [i32, vp, sz, ctypes.c_uint64, vp, vp]
     L.vDebugDecode.argtypes = [i32, vp, sz, ctypes.c_uint64, vp, ctypes.c_double, vp]
+    L.vAllReduceNoAlloc.argtypes = [pp, pp, sz, i32, i32, i32, i32, vp, vp]
     for name in EXPORTS:
         if name != "vcommVersion":
             getattr(L, name).restype = i32
