@@ -65,7 +65,8 @@ typedef enum { vProtoAuto = 0, vProtoSimple = 1, vProtoLL = 2, vProtoLL128 = 3 }
 typedef struct {
   size_t slotBytes[3];   /* FIFO slot bytes for Simple, LL, LL128 [512 KiB, 32 KiB, 600 KiB] */
   int nsteps;            /* slots per connection FIFO, NCCL_STEPS of Sec. V-C [8] */
-  int nthreads;          /* upper bound on threads per CTA [512]; lowered to fit co-residency */
+  int nthreads;          /* upper bound on threads per CTA [1024; Simple kernels use at most
+                            512]; lowered to fit co-residency */
   double timeoutSec;     /* deadline of every device flag wait [5 s; env VCOMM_TIMEOUT_MS] */
 } vcommConfig_t;
 

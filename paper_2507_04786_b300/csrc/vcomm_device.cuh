@@ -181,53 +181,54 @@ VDEV void storeUser8(char* p, uint64_t v, int valid) {
 
 // ------------------------------------------------------------------ Simple reduce-copy
 // d*[i] = fold over the NSRC sources: v = s0[i]; v = f(s1[i], v); v = f(s2[i], v).
-// 16-byte vectors with UNROLL packs per thread in flight; element-wise tail,
-// and an element-wise path when any pointer is not 16-byte aligned.
+// Warp-contiguous 16-byte vectors: a warp owns 32 x UNROLL consecutive packs
+// per round (lane l takes packs l, l + 32, ...), so every load instruction is
+// one coalesced 512-byte access and all UNROLL x NSRC loads of a round are in
+// flight together.  Element-wise tail, and an element-wise path when any
+// pointer is not 16-byte aligned.  nbytes < 2^32 (one FIFO slot at most).
 template <class T, class Op, int NSRC>
-__device__ __noinline__ void reduceCopy(int tid, int nthr, const char* s0, const char* s1,
-                                        const char* s2, char* d0, char* d1, char* d2, int nd,
-                                        unsigned long long nbytes) {
-  constexpr int UNROLL = (NSRC >= 3) ? 2 : 4;
+VDEV void reduceCopy(int tid, int nthr, const char* s0, const char* s1, const char* s2, char* d0,
+                     char* d1, char* d2, int nd, uint32_t nbytes) {
+  constexpr int UNROLL = (NSRC == 1) ? 8 : (NSRC == 2) ? 4 : 2;
   uintptr_t orall = (uintptr_t)s0 | (uintptr_t)d0;
   if (NSRC > 1) orall |= (uintptr_t)s1;
   if (NSRC > 2) orall |= (uintptr_t)s2;
   if (nd > 1) orall |= (uintptr_t)d1;
   if (nd > 2) orall |= (uintptr_t)d2;
-  unsigned long long done = 0;
+  uint32_t done = 0;
   if ((orall & 15) == 0) {
-    const unsigned long long npk = nbytes / 16;
-    const uint4* a4 = (const uint4*)s0;
-    const uint4* b4 = (const uint4*)s1;
-    const uint4* c4 = (const uint4*)s2;
-    for (unsigned long long p0 = tid; p0 < npk; p0 += (unsigned long long)UNROLL * nthr) {
+    const uint32_t npk = nbytes / 16;
+    const uint32_t lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
+    for (uint32_t base = warp * 32u * UNROLL; base < npk; base += nwarps * 32u * UNROLL) {
+      const uint32_t i0 = base + lane;
+      const uint4* pa = (const uint4*)s0 + i0;
+      const uint4* pb = (const uint4*)s1 + i0;
+      const uint4* pc = (const uint4*)s2 + i0;
       uint4 v[UNROLL], w1[UNROLL], w2[UNROLL];
 #pragma unroll
       for (int u = 0; u < UNROLL; u++) {
-        const unsigned long long i = p0 + (unsigned long long)u * nthr;
-        if (i < npk) {
-          v[u] = ldCG(a4 + i);
-          if (NSRC > 1) w1[u] = ldCG(b4 + i);
-          if (NSRC > 2) w2[u] = ldCG(c4 + i);
+        if (i0 + 32u * u < npk) {
+          v[u] = ldCG(pa + 32 * u);
+          if (NSRC > 1) w1[u] = ldCG(pb + 32 * u);
+          if (NSRC > 2) w2[u] = ldCG(pc + 32 * u);
         }
       }
 #pragma unroll
       for (int u = 0; u < UNROLL; u++) {
-        const unsigned long long i = p0 + (unsigned long long)u * nthr;
-        if (i < npk) {
+        if (i0 + 32u * u < npk) {
           if (NSRC > 1) v[u] = applyWord<T, Op>(w1[u], v[u]);
           if (NSRC > 2) v[u] = applyWord<T, Op>(w2[u], v[u]);
-          st16((uint4*)d0 + i, v[u]);
-          if (nd > 1) st16((uint4*)d1 + i, v[u]);
-          if (nd > 2) st16((uint4*)d2 + i, v[u]);
+          st16((uint4*)d0 + i0 + 32 * u, v[u]);
+          if (nd > 1) st16((uint4*)d1 + i0 + 32 * u, v[u]);
+          if (nd > 2) st16((uint4*)d2 + i0 + 32 * u, v[u]);
         }
       }
     }
     done = npk * 16;
   }
-  // element-wise remainder (or everything when misaligned)
-  const unsigned long long ne = (nbytes - done) / sizeof(T);
-  for (unsigned long long e = tid; e < ne; e += nthr) {
-    const unsigned long long off = done + e * sizeof(T);
+  const uint32_t ne = (nbytes - done) / (uint32_t)sizeof(T);
+  for (uint32_t e = tid; e < ne; e += nthr) {
+    const uint32_t off = done + e * (uint32_t)sizeof(T);
     T v = *(const T*)(s0 + off);
     if (NSRC > 1) v = ElemOp<T, Op>::f(*(const T*)(s1 + off), v);
     if (NSRC > 2) v = ElemOp<T, Op>::f(*(const T*)(s2 + off), v);
@@ -304,35 +305,89 @@ VDEV bool ll128Load(const KernArgs& a, const char* slot, unsigned long long line
   }
 }
 
+// warp-collective: v0/v1 already hold one load of this lane's 16 bytes;
+// re-load until every valid line of the warp carries `flag`.  false on
+// deadline / abort (warp-uniform).
+VDEV bool ll128Ready(const KernArgs& a, const char* slot, unsigned long long line, int lane,
+                     bool lineValid, uint64_t flag, uint64_t& v0, uint64_t& v1,
+                     volatile int* sAbort, int rank, int ch) {
+  const int j = lane & 7;
+  unsigned it = 0;
+  uint64_t t0 = 0;
+  while (true) {
+    bool mine = !lineValid || j != 7 || v1 == flag;
+    bool lineOk = __shfl_sync(0xffffffffu, mine, lane | 7);
+    if (__all_sync(0xffffffffu, lineOk)) return true;
+    if (((++it) & 255u) == 0) {
+      int stop = 0;
+      if (lane == 0) {
+        if (*sAbort) stop = 1;
+        else if (*a.abortFlag) { reportFailure(a, vAborted, rank, ch, 3); *sAbort = 1; stop = 1; }
+        else {
+          uint64_t now = globaltimer();
+          if (t0 == 0) t0 = now;
+          else if (now - t0 > a.timeoutNs) { reportFailure(a, vTimeout, rank, ch, 3); *sAbort = 1; stop = 1; }
+        }
+      }
+      if (__shfl_sync(0xffffffffu, stop, 0)) return false;
+    }
+    if (lineValid) ldVolatile2(slot + 128 * line + 16 * j, v0, v1);
+  }
+}
+
+// poll an LL line pair whose first load is already in x, y
+VDEV bool llReady(const KernArgs& a, const char* slot, unsigned long long p, uint32_t flag,
+                  uint64_t& x, uint64_t& y, volatile int* sAbort, int rank, int ch) {
+  unsigned it = 0;
+  uint64_t t0 = 0;
+  while ((uint32_t)(x >> 32) != flag || (uint32_t)(y >> 32) != flag) {
+    if (((++it) & 255u) == 0) {
+      if (*sAbort) return false;
+      if (*a.abortFlag) { reportFailure(a, vAborted, rank, ch, 3); *sAbort = 1; return false; }
+      uint64_t now = globaltimer();
+      if (t0 == 0) t0 = now;
+      else if (now - t0 > a.timeoutNs) { reportFailure(a, vTimeout, rank, ch, 3); *sAbort = 1; return false; }
+    }
+    ldVolatile2(slot + 16 * p, x, y);
+  }
+  return true;
+}
+
 // ------------------------------------------------------------------ primitives
 // A Prims object is one worker's view of its connections: up to two receive
 // connections (all read by a recv* primitive) and up to two send connections
 // (all written by a *send primitive).  The seven primitives of Sec. V-B are
-// the combinations of (receive?, local input?, send?, user output?).
+// the combinations of (receive?, local input?, send?, user output?).  State
+// is kept in scalars so that it stays in registers.
 template <int PROTO, class T, class Op>
 struct Prims {
   const KernArgs& a;
   int tid, nthr, barId;
   volatile int* sAbort;
   int rank, ch;
-  const ConnDev* rc[2];
-  const ConnDev* sc[2];
+  const ConnDev* rc0;
+  const ConnDev* rc1;
+  const ConnDev* sc0;
+  const ConnDev* sc1;
   int nrc, nsc;
-  uint64_t rstep[2], sstep[2];
+  uint64_t rstep0, rstep1, sstep0, sstep1;
 
   VDEV Prims(const KernArgs& args, int tid_, int nthr_, int barId_, volatile int* sAbort_, int rank_,
              int ch_, const ConnDev* r0, const ConnDev* r1, const ConnDev* s0, const ConnDev* s1)
       : a(args), tid(tid_), nthr(nthr_), barId(barId_), sAbort(sAbort_), rank(rank_), ch(ch_) {
-    nrc = 0;
-    nsc = 0;
-    if (r0) rc[nrc++] = r0;
-    if (r1) rc[nrc++] = r1;
-    if (s0) sc[nsc++] = s0;
-    if (s1) sc[nsc++] = s1;
-    // the step counters: a worker is the only writer of its send conns' tail
-    // and its receive conns' head, so their current values are its position
-    for (int i = 0; i < nrc; i++) rstep[i] = ldAcquire(rc[i]->head);
-    for (int i = 0; i < nsc; i++) sstep[i] = ldAcquire(sc[i]->tail);
+    // compact the connection lists: r0/s0 are filled first
+    rc0 = r0 ? r0 : r1;
+    rc1 = r0 ? r1 : nullptr;
+    sc0 = s0 ? s0 : s1;
+    sc1 = s0 ? s1 : nullptr;
+    nrc = (rc0 ? 1 : 0) + (rc1 ? 1 : 0);
+    nsc = (sc0 ? 1 : 0) + (sc1 ? 1 : 0);
+    // a worker is the only writer of its send conns' tail and its receive
+    // conns' head, so their current values are its position in each FIFO
+    rstep0 = rc0 ? ldAcquire(rc0->head) : 0;
+    rstep1 = rc1 ? ldAcquire(rc1->head) : 0;
+    sstep0 = sc0 ? ldAcquire(sc0->tail) : 0;
+    sstep1 = sc1 ? ldAcquire(sc1->tail) : 0;
   }
 
   VDEV void bar() { groupBar(barId, nthr); }
@@ -344,12 +399,15 @@ struct Prims {
   VDEV bool acquire(bool doRecv, bool doSend) {
     if (tid == 0) {
       bool ok = true;
-      if (PROTO == kSimple && doRecv)
-        for (int i = 0; i < nrc && ok; i++) ok = waitGeq(a, rc[i]->tail, rstep[i] + 1, rank, ch, 1);
-      if (doSend)
-        for (int i = 0; i < nsc && ok; i++)
-          if (sstep[i] + 1 > (uint64_t)a.nsteps)
-            ok = waitGeq(a, sc[i]->head, sstep[i] + 1 - (uint64_t)a.nsteps, rank, ch, 2);
+      if (PROTO == kSimple && doRecv) {
+        ok = waitGeq(a, rc0->tail, rstep0 + 1, rank, ch, 1);
+        if (ok && nrc > 1) ok = waitGeq(a, rc1->tail, rstep1 + 1, rank, ch, 1);
+      }
+      if (doSend && ok) {
+        const uint64_t ns = (uint64_t)a.nsteps;
+        if (sstep0 + 1 > ns) ok = waitGeq(a, sc0->head, sstep0 + 1 - ns, rank, ch, 2);
+        if (ok && nsc > 1 && sstep1 + 1 > ns) ok = waitGeq(a, sc1->head, sstep1 + 1 - ns, rank, ch, 2);
+      }
       if (!ok) *sAbort = 1;
     }
     bar();
@@ -362,116 +420,197 @@ struct Prims {
     bar();
     if (*sAbort) return false;
     if (tid == 0) {
-      if (doSend)
-        for (int i = 0; i < nsc; i++) {
-          if (PROTO == kSimple) stRelease(sc[i]->tail, sstep[i] + 1);
-          else stRelaxed(sc[i]->tail, sstep[i] + 1);
+      if (doSend) {
+        if (PROTO == kSimple) {
+          stRelease(sc0->tail, sstep0 + 1);
+          if (nsc > 1) stRelease(sc1->tail, sstep1 + 1);
+        } else {
+          stRelaxed(sc0->tail, sstep0 + 1);
+          if (nsc > 1) stRelaxed(sc1->tail, sstep1 + 1);
         }
-      if (doRecv)
-        for (int i = 0; i < nrc; i++) stRelease(rc[i]->head, rstep[i] + 1);
+      }
+      if (doRecv) {
+        stRelease(rc0->head, rstep0 + 1);
+        if (nrc > 1) stRelease(rc1->head, rstep1 + 1);
+      }
     }
-    if (doSend)
-      for (int i = 0; i < nsc; i++) sstep[i]++;
-    if (doRecv)
-      for (int i = 0; i < nrc; i++) rstep[i]++;
+    if (doSend) { sstep0++; sstep1++; }
+    if (doRecv) { rstep0++; rstep1++; }
     return true;
   }
 
-  // one FIFO step of m units (m <= slotUnits); out of line to keep the
-  // collectives' code small
-  __device__ __noinline__ bool step(bool doRecv, bool doLocal, bool doSend, bool doOut, const T* local, T* out,
-                 unsigned long long m) {
+  // one FIFO step of m units (m <= slotUnits)
+  VDEV bool step(bool doRecv, bool doLocal, bool doSend, bool doOut, const T* local, T* out,
+                 uint32_t m) {
     if (!acquire(doRecv, doSend)) return false;
-    const unsigned long long nbytes = m * sizeof(T);
+    const uint32_t nbytes = m * (uint32_t)sizeof(T);
     if (PROTO == kSimple) {
-      const char* src[3] = {nullptr, nullptr, nullptr};
-      char* dst[3] = {nullptr, nullptr, nullptr};
-      int ns = 0, nd = 0;
-      if (doLocal) src[ns++] = (const char*)local;
-      if (doRecv)
-        for (int i = 0; i < nrc; i++) src[ns++] = slotOf(rc[i], rstep[i]);
-      if (doOut) dst[nd++] = (char*)out;
-      if (doSend)
-        for (int i = 0; i < nsc; i++) dst[nd++] = slotOf(sc[i], sstep[i]);
-      if (ns == 1) reduceCopy<T, Op, 1>(tid, nthr, src[0], src[1], src[2], dst[0], dst[1], dst[2], nd, nbytes);
-      else if (ns == 2) reduceCopy<T, Op, 2>(tid, nthr, src[0], src[1], src[2], dst[0], dst[1], dst[2], nd, nbytes);
-      else reduceCopy<T, Op, 3>(tid, nthr, src[0], src[1], src[2], dst[0], dst[1], dst[2], nd, nbytes);
-    } else if (PROTO == kLL) {
-      const unsigned long long npairs = (nbytes + 7) / 8;
-      const char* rs[2];
-      char* ss[2];
-      uint32_t rf[2];
-      uint32_t sf[2];
-      for (int i = 0; i < nrc; i++) { rs[i] = slotOf(rc[i], rstep[i]); rf[i] = (uint32_t)(rstep[i] + 1); }
-      for (int i = 0; i < nsc; i++) { ss[i] = slotOf(sc[i], sstep[i]); sf[i] = (uint32_t)(sstep[i] + 1); }
-      for (unsigned long long p = tid; p < npairs; p += nthr) {
-        const int valid = (int)((nbytes - 8 * p) < 8 ? (nbytes - 8 * p) : 8);
-        uint64_t v = 0;
-        int first = 0;
-        if (doLocal) {
-          v = loadUser8<T>((const char*)local + 8 * p, valid);
-        } else {
-          if (!llLoadPair(a, rs[0], p, rf[0], v, sAbort, rank, ch)) break;
-          first = 1;
+      const char* s0;
+      const char* s1 = nullptr;
+      const char* s2 = nullptr;
+      int ns;
+      if (doLocal) {
+        s0 = (const char*)local;
+        ns = 1;
+        if (doRecv) {
+          s1 = slotOf(rc0, rstep0);
+          ns = 2;
+          if (nrc > 1) { s2 = slotOf(rc1, rstep1); ns = 3; }
         }
-        bool fail = false;
-        if (doRecv)
-          for (int i = first; i < nrc; i++) {
-            uint64_t w;
-            if (!llLoadPair(a, rs[i], p, rf[i], w, sAbort, rank, ch)) { fail = true; break; }
-            v = applyWord<T, Op>(w, v);
+      } else {
+        s0 = slotOf(rc0, rstep0);
+        ns = 1;
+        if (nrc > 1) { s1 = slotOf(rc1, rstep1); ns = 2; }
+      }
+      char* d0 = nullptr;
+      char* d1 = nullptr;
+      char* d2 = nullptr;
+      int nd = 0;
+      if (doOut) { d0 = (char*)out; nd = 1; }
+      if (doSend) {
+        char* t0 = slotOf(sc0, sstep0);
+        char* t1 = nsc > 1 ? slotOf(sc1, sstep1) : nullptr;
+        if (nd == 0) { d0 = t0; d1 = t1; } else { d1 = t0; d2 = t1; }
+        nd += nsc;
+      }
+      if (ns == 1) reduceCopy<T, Op, 1>(tid, nthr, s0, s1, s2, d0, d1, d2, nd, nbytes);
+      else if (ns == 2) reduceCopy<T, Op, 2>(tid, nthr, s0, s1, s2, d0, d1, d2, nd, nbytes);
+      else reduceCopy<T, Op, 3>(tid, nthr, s0, s1, s2, d0, d1, d2, nd, nbytes);
+    } else if (PROTO == kLL) {
+      // each thread owns line pairs p = tid + u * nthr (u < U) per round: all
+      // loads of the round are issued before the first flag check
+      constexpr int U = 4;
+      const uint32_t npairs = (nbytes + 7) / 8;
+      const char* rs0 = doRecv ? slotOf(rc0, rstep0) : nullptr;
+      const char* rs1 = (doRecv && nrc > 1) ? slotOf(rc1, rstep1) : nullptr;
+      char* ss0 = doSend ? slotOf(sc0, sstep0) : nullptr;
+      char* ss1 = (doSend && nsc > 1) ? slotOf(sc1, sstep1) : nullptr;
+      const uint32_t rf0 = (uint32_t)(rstep0 + 1), rf1 = (uint32_t)(rstep1 + 1);
+      const uint32_t sf0 = (uint32_t)(sstep0 + 1), sf1 = (uint32_t)(sstep1 + 1);
+      bool fail = false;
+      for (uint32_t p0 = tid; p0 < npairs && !fail; p0 += (uint32_t)U * nthr) {
+        uint64_t v[U], x[U], y[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          const uint32_t p = p0 + (uint32_t)u * nthr;
+          v[u] = 0;
+          if (p < npairs) {
+            if (doLocal) {
+              const int valid = (int)((nbytes - 8 * p) < 8 ? (nbytes - 8 * p) : 8);
+              v[u] = loadUser8<T>((const char*)local + 8ull * p, valid);
+            }
+            if (doRecv) ldVolatile2(rs0 + 16ull * p, x[u], y[u]);
           }
+        }
+        for (int i = 0; i < (doRecv ? nrc : 0) && !fail; i++) {
+          const char* rs = i ? rs1 : rs0;
+          const uint32_t rf = i ? rf1 : rf0;
+          if (i > 0) {
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+              const uint32_t p = p0 + (uint32_t)u * nthr;
+              if (p < npairs) ldVolatile2(rs + 16ull * p, x[u], y[u]);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < U; u++) {
+            const uint32_t p = p0 + (uint32_t)u * nthr;
+            if (p >= npairs || fail) continue;
+            if (!llReady(a, rs, p, rf, x[u], y[u], sAbort, rank, ch)) { fail = true; continue; }
+            const uint64_t w = (x[u] & 0xffffffffull) | (y[u] << 32);
+            v[u] = (doLocal || i > 0) ? applyWord<T, Op>(w, v[u]) : w;
+          }
+        }
         if (fail) break;
-        if (doOut) storeUser8<T>((char*)out + 8 * p, v, valid);
-        if (doSend)
-          for (int i = 0; i < nsc; i++) llStorePair(ss[i], p, v, sf[i]);
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          const uint32_t p = p0 + (uint32_t)u * nthr;
+          if (p >= npairs) continue;
+          const int valid = (int)((nbytes - 8 * p) < 8 ? (nbytes - 8 * p) : 8);
+          if (doOut) storeUser8<T>((char*)out + 8ull * p, v[u], valid);
+          if (doSend) {
+            llStorePair(ss0, p, v[u], sf0);
+            if (nsc > 1) llStorePair(ss1, p, v[u], sf1);
+          }
+        }
       }
     } else {  // LL128
-      const unsigned long long nlines = (nbytes + 119) / 120;
-      const unsigned long long nquads = (nlines + 3) / 4;
+      // a warp owns line quads q = warp + u * nwarps (u < U) per round; all
+      // loads of the round are issued before the first flag check
+      constexpr int U = 2;
+      const uint32_t nlines = (nbytes + 119) / 120;
+      const uint32_t nquads = (nlines + 3) / 4;
       const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
       const int j = lane & 7;
-      const char* rs[2];
-      char* ss[2];
-      uint64_t rf[2], sf[2];
-      for (int i = 0; i < nrc; i++) { rs[i] = slotOf(rc[i], rstep[i]); rf[i] = rstep[i] + 1; }
-      for (int i = 0; i < nsc; i++) { ss[i] = slotOf(sc[i], sstep[i]); sf[i] = sstep[i] + 1; }
-      for (unsigned long long q = warp; q < nquads; q += nwarps) {
-        const unsigned long long line = 4 * q + (lane >> 3);
-        const bool lineValid = line < nlines;
-        const unsigned long long uoff = 120 * line + 16 * (unsigned long long)j;
-        const int cap = (j == 7) ? 8 : 16;
-        long long rem = lineValid ? (long long)nbytes - (long long)uoff : 0;
-        const int valid = rem <= 0 ? 0 : (rem < cap ? (int)rem : cap);
-        const int valid0 = valid < 8 ? valid : 8;
-        const int valid1 = valid > 8 ? valid - 8 : 0;
-        uint64_t v0 = 0, v1 = 0;
-        int first = 0;
-        bool fail = false;
-        if (doLocal) {
-          v0 = loadUser8<T>((const char*)local + uoff, valid0);
-          v1 = loadUser8<T>((const char*)local + uoff + 8, valid1);
-        } else {
-          if (!ll128Load(a, rs[0], line, lane, lineValid, rf[0], v0, v1, sAbort, rank, ch)) fail = true;
-          first = 1;
-        }
-        if (!fail && doRecv)
-          for (int i = first; i < nrc; i++) {
-            uint64_t w0, w1;
-            if (!ll128Load(a, rs[i], line, lane, lineValid, rf[i], w0, w1, sAbort, rank, ch)) {
-              fail = true;
-              break;
-            }
-            v0 = applyWord<T, Op>(w0, v0);
-            v1 = applyWord<T, Op>(w1, v1);
+      const char* rs0 = doRecv ? slotOf(rc0, rstep0) : nullptr;
+      const char* rs1 = (doRecv && nrc > 1) ? slotOf(rc1, rstep1) : nullptr;
+      char* ss0 = doSend ? slotOf(sc0, sstep0) : nullptr;
+      char* ss1 = (doSend && nsc > 1) ? slotOf(sc1, sstep1) : nullptr;
+      const uint64_t rf0 = rstep0 + 1, rf1 = rstep1 + 1, sf0 = sstep0 + 1, sf1 = sstep1 + 1;
+      for (uint32_t q0 = warp; q0 < nquads; q0 += (uint32_t)U * nwarps) {
+        uint64_t v0[U], v1[U], w0[U], w1[U];
+        bool lv[U];
+        int valid[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          const uint32_t line = 4 * (q0 + (uint32_t)u * nwarps) + (lane >> 3);
+          lv[u] = line < nlines;
+          const uint32_t uoff = 120 * line + 16 * j;
+          const int cap = (j == 7) ? 8 : 16;
+          const int rem = lv[u] ? (int)nbytes - (int)uoff : 0;
+          valid[u] = rem <= 0 ? 0 : (rem < cap ? rem : cap);
+          v0[u] = 0;
+          v1[u] = 0;
+          w0[u] = 0;
+          w1[u] = 0;
+          if (doLocal && valid[u] > 0) {
+            v0[u] = loadUser8<T>((const char*)local + uoff, valid[u] < 8 ? valid[u] : 8);
+            v1[u] = loadUser8<T>((const char*)local + uoff + 8, valid[u] > 8 ? valid[u] - 8 : 0);
           }
-        if (fail) break;   // warp-uniform
-        if (doOut && valid > 0) {
-          storeUser8<T>((char*)out + uoff, v0, valid0);
-          storeUser8<T>((char*)out + uoff + 8, v1, valid1);
+          if (doRecv && lv[u]) ldVolatile2(rs0 + 128ull * line + 16 * j, w0[u], w1[u]);
         }
-        if (doSend && lineValid)
-          for (int i = 0; i < nsc; i++) ll128Store(ss[i], line, j, v0, v1, sf[i]);
+        bool fail = false;
+        for (int i = 0; i < (doRecv ? nrc : 0) && !fail; i++) {
+          const char* rs = i ? rs1 : rs0;
+          const uint64_t rf = i ? rf1 : rf0;
+          if (i > 0) {
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+              const uint32_t line = 4 * (q0 + (uint32_t)u * nwarps) + (lane >> 3);
+              if (lv[u]) ldVolatile2(rs + 128ull * line + 16 * j, w0[u], w1[u]);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < U; u++) {
+            const uint32_t line = 4 * (q0 + (uint32_t)u * nwarps) + (lane >> 3);
+            if (fail) continue;   // warp-uniform
+            if (!ll128Ready(a, rs, line, lane, lv[u], rf, w0[u], w1[u], sAbort, rank, ch)) {
+              fail = true;
+              continue;
+            }
+            if (doLocal || i > 0) {
+              v0[u] = applyWord<T, Op>(w0[u], v0[u]);
+              v1[u] = applyWord<T, Op>(w1[u], v1[u]);
+            } else {
+              v0[u] = w0[u];
+              v1[u] = w1[u];
+            }
+          }
+        }
+        if (fail) break;   // warp-uniform
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          const uint32_t line = 4 * (q0 + (uint32_t)u * nwarps) + (lane >> 3);
+          const uint32_t uoff = 120 * line + 16 * j;
+          if (doOut && valid[u] > 0) {
+            storeUser8<T>((char*)out + uoff, v0[u], valid[u] < 8 ? valid[u] : 8);
+            storeUser8<T>((char*)out + uoff + 8, v1[u], valid[u] > 8 ? valid[u] - 8 : 0);
+          }
+          if (doSend && lv[u]) {
+            ll128Store(ss0, line, j, v0[u], v1[u], sf0);
+            if (nsc > 1) ll128Store(ss1, line, j, v0[u], v1[u], sf1);
+          }
+        }
       }
     }
     return release(doRecv, doSend);
@@ -484,208 +623,200 @@ struct Prims {
     while (done < n) {
       unsigned long long m = n - done;
       if (m > a.slotUnits) m = a.slotUnits;
-      if (!step(doRecv, doLocal, doSend, doOut, local ? local + done : nullptr,
-                out ? out + done : nullptr, m))
-        return false;
+      if (!step(doRecv, doLocal, doSend, doOut, local + done, out + done, (uint32_t)m)) return false;
       done += m;
     }
     return true;
   }
-
-  // Sec. V-B primitive names
-  VDEV bool send(const T* x, unsigned long long n) { return run(false, true, true, false, x, nullptr, n); }
-  VDEV bool recv(T* y, unsigned long long n) { return run(true, false, false, true, nullptr, y, n); }
-  VDEV bool recvReduceSend(const T* x, unsigned long long n) { return run(true, true, true, false, x, nullptr, n); }
-  VDEV bool recvCopySend(T* y, unsigned long long n) { return run(true, false, true, true, nullptr, y, n); }
-  VDEV bool recvReduceCopySend(const T* x, T* y, unsigned long long n) { return run(true, true, true, true, x, y, n); }
-  VDEV bool copySend(const T* x, T* y, unsigned long long n) { return run(false, true, true, true, x, y, n); }
-  VDEV bool recvReduceCopy(const T* x, T* y, unsigned long long n) { return run(true, true, false, true, x, y, n); }
 };
 
-// ------------------------------------------------------------------ collectives
-// Ring AllReduce, Table "Steps in one loop iteration of NCCL Ring AllReduce":
-// at step t rank r handles segment (r - t - 1) mod k of the loop.
-template <int P, class T, class Op>
-VDEV void ringAllReduce(const KernArgs& a, int r, int ch, volatile int* sAbort) {
-  const int k = a.nranks;
-  const ConnDev* sc = &a.conns[ch * k + r];
-  const ConnDev* rc = &a.conns[ch * k + modk(r - 1, k)];
-  Prims<P, T, Op> pr(a, threadIdx.x, blockDim.x, 0, sAbort, r, ch, rc, nullptr, sc, nullptr);
-  unsigned long long start, len;
-  channelRange(a.count, sizeof(T), a.nsub, ch, &start, &len);
-  const unsigned long long end = start + len, loop = (unsigned long long)k * a.chunk;
-  const T* x = (const T*)a.send[r];
-  T* y = (T*)a.recv[r];
-  for (unsigned long long off = start; off < end; off += loop) {
-    const unsigned long long c = ringLoopChunk(off, end, k, a.chunk, sizeof(T));
-    for (int t = 0; t <= 2 * k - 2; t++) {
+// ------------------------------------------------------------------ schedules
+// One primitive invocation: which of (receive, local input, send, user
+// output) it uses, and where.  Offsets are in units of the kernel's type.
+struct Desc {
+  bool recv, local, send, out;
+  unsigned long long lo;   // offset into the worker's input buffer
+  unsigned long long oo;   // offset into the worker's output buffer
+  unsigned long long n;
+};
+
+// Worker roles
+enum Role : int { kRoleRing = 0, kRoleTreeRoot = 1, kRoleTreeUp = 2, kRoleTreeDown = 3 };
+
+// The step tables of Sec. V-E as an iterator over primitive invocations.
+struct Sched {
+  int coll, k, r, role, pos;
+  bool leaf, inplace;
+  unsigned long long count, chunk, end, off, c;
+  int t;
+
+  VDEV void init(const KernArgs& a, int r_, int ch, int role_, bool leaf_, int unitBytes) {
+    coll = a.coll;
+    k = a.nranks;
+    r = r_;
+    role = role_;
+    leaf = leaf_;
+    inplace = (a.inplaceMask >> r_) & 1ull;
+    count = a.count;
+    chunk = a.chunk;
+    unsigned long long start, len;
+    channelRange(a.count, unitBytes, a.nsub, ch, &start, &len);
+    off = start;
+    end = start + len;
+    t = 0;
+    c = 0;
+    pos = 0;
+    if (coll == kBroadcast) pos = modk(r - a.root, k);
+    if (coll == kReduce) pos = modk(r - a.root - 1, k);
+  }
+
+  VDEV static void set(Desc& d, bool rv, bool lc, bool sd, bool ot) {
+    d.recv = rv;
+    d.local = lc;
+    d.send = sd;
+    d.out = ot;
+  }
+
+  VDEV bool next(Desc& d, int unitBytes) {
+    if (off >= end) return false;
+    if (role == kRoleRing && coll == kAllReduce) {
+      // Table "Ring AllReduce": rank r handles segment (r - t - 1) mod k
+      if (t == 0) c = ringLoopChunk(off, end, k, chunk, unitBytes);
       const int s = modk(r - t - 1, k);
       unsigned long long sa = off + (unsigned long long)s * c;
       if (sa > end) sa = end;
       unsigned long long sb = sa + c;
       if (sb > end) sb = end;
-      const unsigned long long n = sb - sa;
-      bool ok;
-      if (t == 0) ok = pr.send(x + sa, n);
-      else if (t <= k - 2) ok = pr.recvReduceSend(x + sa, n);
-      else if (t == k - 1) ok = pr.recvReduceCopySend(x + sa, y + sa, n);
-      else if (t <= 2 * k - 3) ok = pr.recvCopySend(y + sa, n);
-      else ok = pr.recv(y + sa, n);
-      if (!ok) return;
+      d.lo = sa;
+      d.oo = sa;
+      d.n = sb - sa;
+      if (t == 0) set(d, false, true, true, false);                 // send
+      else if (t <= k - 2) set(d, true, true, true, false);         // recvReduceSend
+      else if (t == k - 1) set(d, true, true, true, true);          // recvReduceCopySend
+      else if (t <= 2 * k - 3) set(d, true, false, true, true);     // recvCopySend
+      else set(d, true, false, false, true);                        // recv
+      if (++t > 2 * k - 2) { t = 0; off += (unsigned long long)k * chunk; }
+      return true;
     }
+    const unsigned long long n = (end - off < chunk) ? end - off : chunk;
+    d.n = n;
+    if (role == kRoleRing && coll == kReduceScatter) {
+      // Table "Ring ReduceScatter": block (r - t - 1) mod k, lands on rank r at t = k-1
+      d.lo = (unsigned long long)modk(r - t - 1, k) * count + off;
+      d.oo = off;
+      if (t == 0) set(d, false, true, true, false);                 // send
+      else if (t <= k - 2) set(d, true, true, true, false);         // recvReduceSend
+      else set(d, true, true, false, true);                         // recvReduceCopy
+      if (++t > k - 1) { t = 0; off += chunk; }
+      return true;
+    }
+    if (role == kRoleRing && coll == kAllGather) {
+      // Table "Ring AllGather": block (r - t) mod k arrives at step t
+      d.lo = off;
+      d.oo = (unsigned long long)modk(r - t, k) * count + off;
+      if (t == 0) set(d, false, true, true, !inplace);              // send / copySend
+      else if (t <= k - 2) set(d, true, false, true, true);         // recvCopySend
+      else set(d, true, false, false, true);                        // recv
+      if (++t > k - 1) { t = 0; off += chunk; }
+      return true;
+    }
+    d.lo = off;
+    d.oo = off;
+    off += chunk;
+    if (role == kRoleRing && coll == kBroadcast) {
+      // Table "Ring Broadcast": root send / copySend, middle recvCopySend, last recv
+      if (pos == 0) set(d, false, true, true, !inplace);
+      else if (pos < k - 1) set(d, true, false, true, true);
+      else set(d, true, false, false, true);
+    } else if (role == kRoleRing && coll == kReduce) {
+      // Table "Ring Reduce": initiator send, middle recvReduceSend, root recvReduceCopy
+      if (pos == 0) set(d, false, true, true, false);
+      else if (pos < k - 1) set(d, true, true, true, false);
+      else set(d, true, true, false, true);
+    } else if (role == kRoleTreeRoot) {
+      set(d, true, true, true, true);                                // recvReduceCopySend
+    } else if (role == kRoleTreeUp) {
+      if (leaf) set(d, false, true, true, false);                    // send
+      else set(d, true, true, true, false);                          // recvReduceSend
+    } else {
+      if (leaf) set(d, true, false, false, true);                    // recv
+      else set(d, true, false, true, true);                          // recvCopySend
+    }
+    return true;
   }
-}
+};
 
-// Ring ReduceScatter, Table "Steps in one loop iteration of NCCL Ring ReduceScatter"
+// ------------------------------------------------------------------ one worker
+// CTA (r, ch) of a collective launch.  Ring collectives: the whole CTA is one
+// worker on the ring connections (Sec. V-E tables).  Tree AllReduce (Sec. II-C,
+// Table "Tree AllReduce"): sub-channel ch runs tree ch % 2 on its own range;
+// the root runs recvReduceCopySend with all its threads, every other rank
+// splits its threads into a reduce group (send / recvReduceSend towards the
+// root) and a broadcast group (recvCopySend / recv from the root), so the two
+// phases stream concurrently.  The data movement has a single call site.
 template <int P, class T, class Op>
-VDEV void ringReduceScatter(const KernArgs& a, int r, int ch, volatile int* sAbort) {
+VDEV void runWorker(const KernArgs& a, int r, int ch, volatile int* sAbort) {
   const int k = a.nranks;
-  const ConnDev* sc = &a.conns[ch * k + r];
-  const ConnDev* rc = &a.conns[ch * k + modk(r - 1, k)];
-  Prims<P, T, Op> pr(a, threadIdx.x, blockDim.x, 0, sAbort, r, ch, rc, nullptr, sc, nullptr);
-  unsigned long long start, len;
-  channelRange(a.count, sizeof(T), a.nsub, ch, &start, &len);
-  const unsigned long long end = start + len;
-  const T* x = (const T*)a.send[r];
-  T* y = (T*)a.recv[r];
-  for (unsigned long long off = start; off < end; off += a.chunk) {
-    const unsigned long long n = (end - off < a.chunk) ? end - off : a.chunk;
-    for (int t = 0; t <= k - 1; t++) {
-      const int s = modk(r - t - 1, k);
-      const T* src = x + (unsigned long long)s * a.count + off;
-      bool ok;
-      if (t == 0) ok = pr.send(src, n);
-      else if (t <= k - 2) ok = pr.recvReduceSend(src, n);
-      else ok = pr.recvReduceCopy(src, y + off, n);
-      if (!ok) return;
-    }
-  }
-}
-
-// Ring AllGather, Table "Steps in one loop iteration of NCCL Ring AllGather";
-// units are bytes (Sec. V-C), a.count = bytes per rank
-template <int P>
-VDEV void ringAllGather(const KernArgs& a, int r, int ch, volatile int* sAbort) {
-  using T = uint8_t;
-  const int k = a.nranks;
-  const ConnDev* sc = &a.conns[ch * k + r];
-  const ConnDev* rc = &a.conns[ch * k + modk(r - 1, k)];
-  Prims<P, T, OpNone> pr(a, threadIdx.x, blockDim.x, 0, sAbort, r, ch, rc, nullptr, sc, nullptr);
-  unsigned long long start, len;
-  channelRange(a.count, 1, a.nsub, ch, &start, &len);
-  const unsigned long long end = start + len;
-  const T* x = (const T*)a.send[r];
-  T* y = (T*)a.recv[r];
-  for (unsigned long long off = start; off < end; off += a.chunk) {
-    const unsigned long long n = (end - off < a.chunk) ? end - off : a.chunk;
-    for (int t = 0; t <= k - 1; t++) {
-      T* dst = y + (unsigned long long)modk(r - t, k) * a.count + off;
-      bool ok;
-      if (t == 0) ok = ((a.inplaceMask >> r) & 1) ? pr.send(dst, n) : pr.copySend(x + off, dst, n);
-      else if (t <= k - 2) ok = pr.recvCopySend(dst, n);
-      else ok = pr.recv(dst, n);
-      if (!ok) return;
-    }
-  }
-}
-
-// Ring Broadcast chain root -> root+1 -> ... (Table "Ring Broadcast"), bytes
-template <int P>
-VDEV void ringBroadcast(const KernArgs& a, int r, int ch, volatile int* sAbort) {
-  using T = uint8_t;
-  const int k = a.nranks;
-  const int pos = modk(r - a.root, k);
-  const ConnDev* sc = (pos < k - 1) ? &a.conns[ch * k + r] : nullptr;
-  const ConnDev* rc = (pos > 0) ? &a.conns[ch * k + modk(r - 1, k)] : nullptr;
-  Prims<P, T, OpNone> pr(a, threadIdx.x, blockDim.x, 0, sAbort, r, ch, rc, nullptr, sc, nullptr);
-  unsigned long long start, len;
-  channelRange(a.count, 1, a.nsub, ch, &start, &len);
-  const unsigned long long end = start + len;
-  const T* x = (const T*)a.send[r];
-  T* y = (T*)a.recv[r];
-  for (unsigned long long off = start; off < end; off += a.chunk) {
-    const unsigned long long n = (end - off < a.chunk) ? end - off : a.chunk;
-    bool ok;
-    if (pos == 0) ok = ((a.inplaceMask >> r) & 1) ? pr.send(x + off, n) : pr.copySend(x + off, y + off, n);
-    else if (pos < k - 1) ok = pr.recvCopySend(y + off, n);
-    else ok = pr.recv(y + off, n);
-    if (!ok) return;
-  }
-}
-
-// Ring Reduce chain root+1 -> ... -> root (Table "Ring Reduce")
-template <int P, class T, class Op>
-VDEV void ringReduce(const KernArgs& a, int r, int ch, volatile int* sAbort) {
-  const int k = a.nranks;
-  const int pos = modk(r - a.root - 1, k);
-  const ConnDev* sc = (pos < k - 1) ? &a.conns[ch * k + r] : nullptr;
-  const ConnDev* rc = (pos > 0) ? &a.conns[ch * k + modk(r - 1, k)] : nullptr;
-  Prims<P, T, Op> pr(a, threadIdx.x, blockDim.x, 0, sAbort, r, ch, rc, nullptr, sc, nullptr);
-  unsigned long long start, len;
-  channelRange(a.count, sizeof(T), a.nsub, ch, &start, &len);
-  const unsigned long long end = start + len;
-  const T* x = (const T*)a.send[r];
-  T* y = (T*)a.recv[r];
-  for (unsigned long long off = start; off < end; off += a.chunk) {
-    const unsigned long long n = (end - off < a.chunk) ? end - off : a.chunk;
-    bool ok;
-    if (pos == 0) ok = pr.send(x + off, n);
-    else if (pos < k - 1) ok = pr.recvReduceSend(x + off, n);
-    else ok = pr.recvReduceCopy(x + off, y + off, n);
-    if (!ok) return;
-  }
-}
-
-// Tree AllReduce on the double binary tree (Sec. II-C, Table "Steps in one
-// loop iteration of NCCL Tree AllReduce").  Sub-channel j runs tree j % 2 on
-// its own range.  A non-root worker splits its threads into a reduce group
-// (recvReduceSend / send towards the root) and a broadcast group
-// (recvCopySend / recv from the root), so both phases stream concurrently;
-// the root runs recvReduceCopySend with all its threads.
-template <int P, class T, class Op>
-VDEV void treeAllReduce(const KernArgs& a, int r, int j, volatile int* sAbort) {
-  const int k = a.nranks;
-  const int t = j & 1;
-  int parent, c0, c1;
-  treeLinks(k, t, r, &parent, &c0, &c1);
-  const ConnDev* up = a.conns;                                  // [j * k + rank]: rank -> parent
-  const ConnDev* down = a.conns + a.downOffset;                  // [j * k + rank]: parent -> rank
-  const ConnDev* upC0 = c0 >= 0 ? &up[j * k + c0] : nullptr;
-  const ConnDev* upC1 = c1 >= 0 ? &up[j * k + c1] : nullptr;
-  const ConnDev* dnC0 = c0 >= 0 ? &down[j * k + c0] : nullptr;
-  const ConnDev* dnC1 = c1 >= 0 ? &down[j * k + c1] : nullptr;
-  unsigned long long start, len;
-  channelRange(a.count, sizeof(T), a.nsub, j, &start, &len);
-  const unsigned long long end = start + len;
-  const T* x = (const T*)a.send[r];
-  T* y = (T*)a.recv[r];
-  if (parent < 0) {
-    Prims<P, T, Op> pr(a, threadIdx.x, blockDim.x, 0, sAbort, r, j, upC0, upC1, dnC0, dnC1);
-    for (unsigned long long off = start; off < end; off += a.chunk) {
-      const unsigned long long n = (end - off < a.chunk) ? end - off : a.chunk;
-      if (!pr.recvReduceCopySend(x + off, y + off, n)) return;
-    }
-    return;
-  }
-  const int nUp = a.upThreads;
-  const bool isUp = (int)threadIdx.x < nUp;
-  const int gtid = isUp ? threadIdx.x : threadIdx.x - nUp;
-  const int gn = isUp ? nUp : (int)blockDim.x - nUp;
-  volatile int* gAbort = sAbort + (isUp ? 0 : 1);
-  if (isUp) {
-    Prims<P, T, Op> pr(a, gtid, gn, 1, gAbort, r, j, upC0, upC1, &up[j * k + r], nullptr);
-    const bool leaf = (c0 < 0);
-    for (unsigned long long off = start; off < end; off += a.chunk) {
-      const unsigned long long n = (end - off < a.chunk) ? end - off : a.chunk;
-      if (!(leaf ? pr.send(x + off, n) : pr.recvReduceSend(x + off, n))) return;
+  const ConnDev* r0 = nullptr;
+  const ConnDev* r1 = nullptr;
+  const ConnDev* s0 = nullptr;
+  const ConnDev* s1 = nullptr;
+  int tid = threadIdx.x, nthr = blockDim.x, barId = 0, role = kRoleRing;
+  bool leaf = false;
+  volatile int* ab = sAbort;
+  if (a.algo == kTree) {
+    const int t = ch & 1;
+    int parent, c0, c1;
+    treeLinks(k, t, r, &parent, &c0, &c1);
+    const ConnDev* up = a.conns + (unsigned long long)ch * k;                   // rank -> parent
+    const ConnDev* down = a.conns + a.downOffset + (unsigned long long)ch * k;  // parent -> rank
+    leaf = (c0 < 0);
+    if (parent < 0) {
+      role = kRoleTreeRoot;
+      r0 = c0 >= 0 ? &up[c0] : nullptr;
+      r1 = c1 >= 0 ? &up[c1] : nullptr;
+      s0 = c0 >= 0 ? &down[c0] : nullptr;
+      s1 = c1 >= 0 ? &down[c1] : nullptr;
+    } else if ((int)threadIdx.x < a.upThreads) {
+      role = kRoleTreeUp;
+      nthr = a.upThreads;
+      barId = 1;
+      r0 = c0 >= 0 ? &up[c0] : nullptr;
+      r1 = c1 >= 0 ? &up[c1] : nullptr;
+      s0 = &up[r];
+    } else {
+      role = kRoleTreeDown;
+      tid = threadIdx.x - a.upThreads;
+      nthr = blockDim.x - a.upThreads;
+      barId = 2;
+      ab = sAbort + 1;
+      r0 = &down[r];
+      s0 = c0 >= 0 ? &down[c0] : nullptr;
+      s1 = c1 >= 0 ? &down[c1] : nullptr;
     }
   } else {
-    Prims<P, T, Op> pr(a, gtid, gn, 2, gAbort, r, j, &down[j * k + r], nullptr, dnC0, dnC1);
-    const bool leaf = (c0 < 0);
-    for (unsigned long long off = start; off < end; off += a.chunk) {
-      const unsigned long long n = (end - off < a.chunk) ? end - off : a.chunk;
-      if (!(leaf ? pr.recv(y + off, n) : pr.recvCopySend(y + off, n))) return;
+    const ConnDev* ring = a.conns + (unsigned long long)ch * k;
+    bool hasSend = true, hasRecv = true;
+    if (a.coll == kBroadcast) {
+      const int pos = modk(r - a.root, k);
+      hasSend = pos < k - 1;
+      hasRecv = pos > 0;
+    } else if (a.coll == kReduce) {
+      const int pos = modk(r - a.root - 1, k);
+      hasSend = pos < k - 1;
+      hasRecv = pos > 0;
     }
+    s0 = hasSend ? &ring[r] : nullptr;
+    r0 = hasRecv ? &ring[modk(r - 1, k)] : nullptr;
+  }
+  Prims<P, T, Op> pr(a, tid, nthr, barId, ab, r, ch, r0, r1, s0, s1);
+  Sched sc;
+  sc.init(a, r, ch, role, leaf, (int)sizeof(T));
+  const T* x = (const T*)a.send[r];
+  T* y = (T*)a.recv[r];
+  Desc d;
+  while (sc.next(d, (int)sizeof(T))) {
+    if (!pr.run(d.recv, d.local, d.send, d.out, x + d.lo, y + d.oo, d.n)) return;
   }
 }
 
@@ -695,9 +826,15 @@ VDEV void localCopy(const KernArgs& a, int ch) {
   unsigned long long start, len;
   channelRange(a.count, sizeof(T), a.nsub, ch, &start, &len);
   if ((a.inplaceMask & 1) || len == 0) return;
-  reduceCopy<T, OpNone, 1>(threadIdx.x, blockDim.x, (const char*)((const T*)a.send[0] + start),
-                           nullptr, nullptr, (char*)((T*)a.recv[0] + start), nullptr, nullptr, 1,
-                           len * sizeof(T));
+  const char* src = (const char*)((const T*)a.send[0] + start);
+  char* dst = (char*)((T*)a.recv[0] + start);
+  // one slot-sized piece at a time keeps the byte counts within 32 bits
+  const unsigned long long piece = 1ull << 30;
+  for (unsigned long long o = 0; o < len * sizeof(T); o += piece) {
+    const unsigned long long nb = (len * sizeof(T) - o < piece) ? len * sizeof(T) - o : piece;
+    reduceCopy<T, OpNone, 1>(threadIdx.x, blockDim.x, src + o, nullptr, nullptr, dst + o, nullptr,
+                             nullptr, 1, (uint32_t)nb);
+  }
 }
 
 }  // namespace vc

@@ -87,7 +87,7 @@ int residentPerSM(const void* fn, int nthr) {
 struct vcomm {
   int k = 0, nch = 0, dev = 0, nsm = 0;
   size_t slotBytes[3] = {0, 0, 0};
-  int nsteps = 8, nthreads = 512;
+  int nsteps = 8, nthreads = 1024;
   double timeoutSec = 5.0;
   Arena arena[2][3];
   ErrWord* hErr = nullptr;
@@ -161,8 +161,11 @@ vResult_t vcommInitConfig(vcomm_t* comm, int nranks, int nchannels, const vcommC
     c->slotBytes[p] = s;
   }
   c->nsteps = (cfg && cfg->nsteps > 0) ? cfg->nsteps : 8;
-  c->nthreads = (cfg && cfg->nthreads > 0) ? cfg->nthreads : 512;
-  if (c->nthreads % 64 != 0 || c->nthreads > 512 || c->nsteps > 64) { delete c; return vInvalidArgument; }
+  c->nthreads = (cfg && cfg->nthreads > 0) ? cfg->nthreads : 1024;
+  if (c->nthreads % 64 != 0 || c->nthreads > 1024 || c->nsteps < 2 || c->nsteps > 64) {
+    delete c;
+    return vInvalidArgument;
+  }
   c->timeoutSec = (cfg && cfg->timeoutSec > 0) ? cfg->timeoutSec : 5.0;
   if (!(cfg && cfg->timeoutSec > 0)) {
     const char* env = getenv("VCOMM_TIMEOUT_MS");
@@ -334,6 +337,14 @@ static vResult_t collective(int coll, const void* const* sendbufs, void* const* 
     plan.algo = vAlgoRing;
     plan.proto = vProtoSimple;
   }
+  // A ring FIFO step both receives and sends, and a slot is returned only
+  // after the receiver's own send: if one chunk fills every slot of every
+  // ring connection (chunkSteps >= nsteps), each rank waits for a credit from
+  // its successor -- a cycle.  Ring collectives need chunkSteps < nsteps.
+  if (plan.algo == vAlgoRing && k > 1 && plan.chunkSteps >= c->nsteps) {
+    if (c->pinned && c->pin.chunkSteps > 0) return vUnsupported;
+    plan.chunkSteps = c->nsteps - 1;
+  }
   const int al = (plan.algo == vAlgoTree) ? kTree : kRing;
   const int pr = (int)plan.proto - 1;
   const bool bytesUnits = (coll == kAllGather || coll == kBroadcast);
@@ -342,17 +353,18 @@ static vResult_t collective(int coll, const void* const* sendbufs, void* const* 
 
   // co-residency: every CTA of the launch spins on its peers
   int nsub = (al == kTree) ? 2 * plan.nchannels : plan.nchannels;
-  int nthr = c->nthreads;
+  const int nthrMax = std::min(c->nthreads, maxThreadsFor(pr));
+  int nthr = nthrMax;
   while (true) {
     int per = residentPerSM(fn, nthr);
     if ((long long)per * c->nsm >= (long long)k * nsub) break;
-    if (nthr > 128) { nthr /= 2; continue; }
+    if (nthr > 128) { nthr = (nthr / 2) / 64 * 64; continue; }
     // too many CTAs even with small blocks: shrink an automatic channel count
     bool autoCh = !(c->pinned && c->pin.nchannels > 0);
     if (autoCh && plan.nchannels > 1) {
       plan.nchannels--;
       nsub = (al == kTree) ? 2 * plan.nchannels : plan.nchannels;
-      nthr = c->nthreads;
+      nthr = nthrMax;
       continue;
     }
     return vUnsupported;

@@ -31,7 +31,13 @@ enum Proto : int { kSimple = 0, kLL = 1, kLL128 = 2 };
 enum DType : int { kI32 = 0, kF32 = 1, kF16 = 2, kBF16 = 3 };
 enum OpKind : int { kSum = 0, kMax = 1 };
 
-constexpr int kCounterStride = 16;  // u64 words between counters (128 bytes)
+constexpr int kCounterStride = 16;
+
+// Largest CTA each protocol's kernels are compiled for; the register budget
+// per thread is 65536 / that.  Simple streams 16-byte vectors with several
+// loads in flight per thread and wants 128 registers (no spills); LL and
+// LL128 poll flags line by line and want more warps instead.
+constexpr int maxThreadsFor(int proto) { return proto == 0 ? 512 : 1024; }  // u64 words between counters (128 bytes)
 
 struct ConnDev {
   char* buf;                       // nsteps slots of slotBytes

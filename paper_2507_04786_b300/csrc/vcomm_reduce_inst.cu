@@ -12,23 +12,15 @@
 namespace vc {
 
 template <int P, class T, class Op>
-__global__ void __launch_bounds__(512, 2) kReduceColl(const __grid_constant__ KernArgs a) {
+__global__ void __launch_bounds__(maxThreadsFor(P), 1) kReduceColl(const __grid_constant__ KernArgs a) {
   __shared__ int sAbort[2];
   if (threadIdx.x < 2) sAbort[threadIdx.x] = 0;
   __syncthreads();
   const int r = blockIdx.x % a.nranks;
   const int ch = blockIdx.x / a.nranks;
   volatile int* sa = sAbort;
-  switch (a.coll) {
-    case kAllReduce:
-      if (a.algo == kTree) treeAllReduce<P, T, Op>(a, r, ch, sa);
-      else ringAllReduce<P, T, Op>(a, r, ch, sa);
-      break;
-    case kReduceScatter: ringReduceScatter<P, T, Op>(a, r, ch, sa); break;
-    case kReduce: ringReduce<P, T, Op>(a, r, ch, sa); break;
-    case kCopy: localCopy<T>(a, ch); break;
-    default: break;
-  }
+  if (a.coll == kCopy) localCopy<T>(a, ch);
+  else runWorker<P, T, Op>(a, r, ch, sa);
 }
 
 #if VC_DTYPE == 0

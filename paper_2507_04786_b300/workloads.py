@@ -18,7 +18,7 @@ HEADLINE = {
     "dist": "normal",
     "seed": 1,
     "protos": ("simple", "ll128"),
-    "nchannels": 32,
+    "nchannels": 37,          # 8 x 37 = 296 CTAs: two per SM on 148 SMs
     "chunk_steps": 1,
 }
 
