@@ -151,6 +151,43 @@ vResult_t vReduce(const void* const* sendbufs, void* const* recvbufs, size_t cou
                   vDataType_t dtype, vRedOp_t op, int root, vAlgo_t algo, vProto_t proto,
                   vStream_t stream, vcomm_t comm);
 
+/* ---- group calls: many collectives, one launch ---------------------------
+ * ncclGroupStart / ncclGroupEnd (Sec. II-A-4).  Collective calls between
+ * vGroupStart and vGroupEnd (on the calling host thread; groups nest) are
+ * validated and planned immediately but not launched; vGroupEnd launches, per
+ * communicator, ONE persistent batch kernel that runs all of that
+ * communicator's calls: up to 4 gangs of (nranks x nch/G) CTAs run their
+ * share of the calls (longest first) concurrently, each gang's calls one after
+ * another through the same FIFOs.  Each call's result is bit-identical to the
+ * same call launched alone with the plan vcommGetGroupPlans reports.  All
+ * calls of one communicator in a group must use the same stream.  The launch
+ * is capturable in a CUDA graph once the arenas it needs exist (vcommPrepare,
+ * or one uncaptured run); the batch description is a kernel parameter, so a
+ * replay needs no host memory.  Calls within a group return vSuccess after
+ * validation; vGroupEnd returns the first launch error. */
+vResult_t vGroupStart(void);
+vResult_t vGroupEnd(void);
+
+/* Plans of the calls of the last group launched on `comm`, in call order
+ * (channels may be lower than requested: a gang has nch/G channels). */
+vResult_t vcommGetGroupPlans(vcomm_t comm, vPlan_t* plans, int maxPlans, int* nPlans);
+
+/* ---- autotuner ------------------------------------------------------------
+ * Protocol / algorithm / channel selection (Sec. III-D; Sec. II-C: "the tuning
+ * model determines how many channels"): times every candidate plan
+ * (ring/tree x Simple/LL/LL128 x channels 1, 2, 4, ... nch) on this device at
+ * per-rank sizes 1 KiB x 4^i <= maxBytes for each collective whose bit is set
+ * in collMask (bit 0 AllReduce, 1 ReduceScatter, 2 AllGather, 3 Broadcast,
+ * 4 Reduce) and keeps the fastest per size.  Later calls with Auto arguments
+ * take their plan from the table at the nearest size (log scale).  Allocates
+ * 2 x nranks x maxBytes of scratch for the duration of the call; synchronous. */
+vResult_t vcommTune(vcomm_t comm, unsigned collMask, size_t maxBytes, vStream_t stream);
+
+/* The tuned table of one collective (0..4 as in collMask): per size bucket the
+ * chosen plan, the per-rank size in bytes and the measured time in us. */
+vResult_t vcommGetTuneTable(vcomm_t comm, int coll, vPlan_t* plans, size_t* bytes, float* usec,
+                            int maxEntries, int* nEntries);
+
 /* ---- allocation-free AllReduce -----------------------------------------
  * The paper has no counterpart to this entry point.  It exists for callers
  * that cannot call cudaMalloc at the point where they need an AllReduce: code
@@ -194,6 +231,12 @@ vResult_t vDebugEncode(vProto_t proto, const void* src, size_t nbytes, uint64_t 
                        void* lines, vStream_t stream);
 vResult_t vDebugDecode(vProto_t proto, const void* lines, size_t nbytes, uint64_t flag,
                        void* dst, double timeoutSec, vStream_t stream);
+
+/* Fault injection for tests of failure detection: from the next call on,
+ * vrank `rank`'s CTAs return without taking part (-1 turns it off), so the
+ * other vranks' flag waits run into their deadline (vTimeout) or the abort
+ * word (vAborted) -- a lost peer, simulated without any GPU fault. */
+vResult_t vcommDebugSetSkipRank(vcomm_t comm, int rank);
 
 #ifdef __cplusplus
 }

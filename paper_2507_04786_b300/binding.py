@@ -26,7 +26,8 @@ PROTO_NAMES = {v: k for k, v in PROTO_CODES.items()}
 EXPORTS = ("vcommInit", "vcommInitConfig", "vcommPrepare", "vcommDestroy", "vcommAbort",
            "vcommGetAsyncError", "vcommSetPlan", "vcommGetLastPlan", "vAllReduce",
            "vReduceScatter", "vAllGather", "vBroadcast", "vReduce", "vcommVersion",
-           "vDebugEncode", "vDebugDecode", "vAllReduceNoAlloc")
+           "vDebugEncode", "vDebugDecode", "vAllReduceNoAlloc", "vGroupStart", "vGroupEnd",
+           "vcommGetGroupPlans", "vcommTune", "vcommGetTuneTable", "vcommDebugSetSkipRank")
 
 
 class VcommError(RuntimeError):
@@ -84,6 +85,13 @@ def load_library():
     L.vDebugEncode.argtypes = [i32, vp, sz, ctypes.c_uint64, vp, vp]
     L.vDebugDecode.argtypes = [i32, vp, sz, ctypes.c_uint64, vp, ctypes.c_double, vp]
     L.vAllReduceNoAlloc.argtypes = [pp, pp, sz, i32, i32, i32, i32, vp, vp]
+    L.vcommDebugSetSkipRank.argtypes = [vp, i32]
+    L.vGroupStart.argtypes = []
+    L.vGroupEnd.argtypes = []
+    L.vcommGetGroupPlans.argtypes = [vp, ctypes.POINTER(Plan), i32, ctypes.POINTER(i32)]
+    L.vcommTune.argtypes = [vp, ctypes.c_uint, sz, vp]
+    L.vcommGetTuneTable.argtypes = [vp, i32, ctypes.POINTER(Plan), ctypes.POINTER(sz),
+                                    ctypes.POINTER(ctypes.c_float), i32, ctypes.POINTER(i32)]
     for name in EXPORTS:
         if name != "vcommVersion":
             getattr(L, name).restype = i32
@@ -185,6 +193,31 @@ class Comm:
         _check(load_library().vcommGetLastPlan(self._h, ctypes.byref(p)), "vcommGetLastPlan")
         return p.as_dict()
 
+    def debug_skip_rank(self, rank: int):
+        _check(load_library().vcommDebugSetSkipRank(self._h, rank), "vcommDebugSetSkipRank")
+
+    def group_plans(self) -> list:
+        n = ctypes.c_int()
+        arr = (Plan * 256)()
+        _check(load_library().vcommGetGroupPlans(self._h, arr, 256, ctypes.byref(n)),
+               "vcommGetGroupPlans")
+        return [arr[i].as_dict() for i in range(min(n.value, 256))]
+
+    def tune(self, colls=("allreduce",), max_bytes=64 << 20, stream=None):
+        mask = sum(1 << COLL_BITS[c] for c in colls)
+        _check(load_library().vcommTune(self._h, mask, max_bytes, _stream_handle(stream)),
+               "vcommTune")
+
+    def tune_table(self, coll="allreduce") -> list:
+        n = ctypes.c_int()
+        plans = (Plan * 32)()
+        sizes = (ctypes.c_size_t * 32)()
+        us = (ctypes.c_float * 32)()
+        _check(load_library().vcommGetTuneTable(self._h, COLL_BITS[coll], plans, sizes, us, 32,
+                                                ctypes.byref(n)), "vcommGetTuneTable")
+        return [dict(plans[i].as_dict(), bytes=sizes[i], usec=us[i])
+                for i in range(min(n.value, 32))]
+
     # -- collectives (lists of torch CUDA tensors, one per vrank)
     def all_reduce(self, sends, recvs, op="sum", algo="ring", proto="simple", stream=None,
                    count=None):
@@ -229,6 +262,36 @@ class Comm:
         _check(load_library().vReduce(_ptr_array(sends), _ptr_array(recvs), n, DTYPE_CODES[dt],
                                       OP_CODES[op], root, ALGO_CODES[algo], PROTO_CODES[proto],
                                       _stream_handle(stream), self._h), "vReduce")
+
+
+COLL_BITS = {"allreduce": 0, "reducescatter": 1, "allgather": 2, "broadcast": 3, "reduce": 4}
+
+
+def group_start():
+    _check(load_library().vGroupStart(), "vGroupStart")
+
+
+def group_end():
+    _check(load_library().vGroupEnd(), "vGroupEnd")
+
+
+class group:
+    """Context manager: collectives issued inside run as one batched launch
+    per communicator at exit (vGroupStart / vGroupEnd)."""
+
+    def __enter__(self):
+        group_start()
+        return self
+
+    def __exit__(self, exc_type, *a):
+        if exc_type is None:
+            group_end()
+        else:
+            try:
+                group_end()
+            except VcommError:
+                pass
+        return False
 
 
 def debug_encode(proto: str, src, nbytes: int, flag: int, lines, stream=None):

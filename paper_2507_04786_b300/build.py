@@ -25,7 +25,13 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC",
                  "-I", os.path.join(ROOT, "include"), "-I", CSRC]
-INST = "vcomm_reduce_inst.cu"
+# The batch kernel (vcomm_batch.cu) calls per-(protocol, dtype) worker
+# functions compiled in vcomm_batch_inst.cu: those two units are relocatable
+# device code, capped at the batch kernel's 128 registers; every other unit
+# stays whole-program so its kernels keep their own inlining and launch bounds.
+RDC = ["-rdc=true", "-maxrregcount=128"]
+RDC_UNITS = ("vcomm_batch.cu", "vcomm_batch_inst.cu")
+PER_PAIR = ("vcomm_reduce_inst.cu", "vcomm_batch_inst.cu")
 
 
 def units():
@@ -33,13 +39,14 @@ def units():
     out = []
     for src in sorted(glob.glob(os.path.join(CSRC, "*.cu"))):
         base = os.path.splitext(os.path.basename(src))[0]
-        if os.path.basename(src) == INST:
+        extra = RDC if os.path.basename(src) in RDC_UNITS else []
+        if os.path.basename(src) in PER_PAIR:
             for p in range(3):
                 for d in range(4):
                     out.append((src, os.path.join(OBJ, f"{base}_{p}_{d}.o"),
-                                [f"-DVC_PROTO={p}", f"-DVC_DTYPE={d}"]))
+                                extra + [f"-DVC_PROTO={p}", f"-DVC_DTYPE={d}"]))
         else:
-            out.append((src, os.path.join(OBJ, base + ".o"), []))
+            out.append((src, os.path.join(OBJ, base + ".o"), extra))
     return out
 
 
@@ -79,7 +86,7 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
     objs = [o for (_, o, _) in units()]
     if todo or not os.path.exists(OUT) or any(os.path.getmtime(o) > os.path.getmtime(OUT)
                                                for o in objs):
-        cmd = [NVCC] + ARCH + ["-shared", "-cudart", "static", "-o", OUT] + objs
+        cmd = [NVCC] + ARCH + ["-shared", "-rdc=true", "-cudart", "static", "-o", OUT] + objs
         subprocess.run(cmd, check=True)
     return OUT
 

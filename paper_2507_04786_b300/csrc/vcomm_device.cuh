@@ -756,6 +756,7 @@ struct Sched {
 // phases stream concurrently.  The data movement has a single call site.
 template <int P, class T, class Op>
 VDEV void runWorker(const KernArgs& a, int r, int ch, volatile int* sAbort) {
+  if (r == a.skipRank) return;   // injected fault: this vrank never takes part
   const int k = a.nranks;
   const ConnDev* r0 = nullptr;
   const ConnDev* r1 = nullptr;

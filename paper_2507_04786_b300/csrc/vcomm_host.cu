@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
+#include <memory>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -84,6 +86,15 @@ int residentPerSM(const void* fn, int nthr) {
 
 }  // namespace
 
+constexpr int kTuneBuckets = 16;   // message sizes 1 KiB x 4^i
+
+struct TuneEntry {
+  bool valid = false;
+  vPlan_t plan{};
+  size_t bytes = 0;
+  float usec = 0;
+};
+
 struct vcomm {
   int k = 0, nch = 0, dev = 0, nsm = 0;
   size_t slotBytes[3] = {0, 0, 0};
@@ -98,6 +109,10 @@ struct vcomm {
   bool pinned = false;
   vPlan_t pin{};
   vPlan_t last{};
+  TuneEntry tune[5][kTuneBuckets];
+  bool tuned[5] = {false, false, false, false, false};
+  std::vector<vPlan_t> groupPlans;   // plans of the last group's calls, in call order
+  int skipRank = -1;                 // fault injection (vcommDebugSetSkipRank)
 };
 
 static vResult_t freeComm(vcomm* c) {
@@ -249,11 +264,30 @@ vResult_t vcommGetLastPlan(vcomm_t c, vPlan_t* plan) {
 }  // extern "C"
 
 // ------------------------------------------------------------------ planning
-// Default tuning (used where neither the call nor a pin fixes a choice):
-// LL below 64 KiB, LL128 below 2 MiB, Simple above (Sec. III-D: LL/LL128 for
-// small messages, Simple for large); tree AllReduce up to 256 KiB (Sec. V-F:
-// tree best for small, ring for large); about 1 MiB of message per channel.
+// Default tuning (used where neither the call nor a pin fixes a choice and the
+// communicator has not been tuned): LL below 64 KiB, LL128 below 2 MiB,
+// Simple above (Sec. III-D: LL/LL128 for small messages, Simple for large);
+// tree AllReduce up to 256 KiB (Sec. V-F: tree best for small, ring for
+// large); about 1 MiB of message per channel.  A tuned communicator takes
+// each Auto field from its measured table at the nearest size (log scale).
 static void defaultPlan(const vcomm* c, int coll, size_t bytes, vPlan_t* p) {
+  if (coll >= 0 && coll < 5 && c->tuned[coll]) {
+    int best = -1;
+    double bd = 1e30;
+    for (int i = 0; i < kTuneBuckets; i++) {
+      const TuneEntry& e = c->tune[coll][i];
+      if (!e.valid) continue;
+      double d = std::fabs(std::log2((double)e.bytes) - std::log2((double)std::max<size_t>(bytes, 1)));
+      if (d < bd) { bd = d; best = i; }
+    }
+    if (best >= 0) {
+      const vPlan_t& t = c->tune[coll][best].plan;
+      if (p->algo == vAlgoAuto) p->algo = t.algo;
+      if (p->proto == vProtoAuto) p->proto = t.proto;
+      if (p->nchannels <= 0) p->nchannels = std::min(t.nchannels, c->nch);
+      if (p->chunkSteps <= 0) p->chunkSteps = t.chunkSteps;
+    }
+  }
   if (p->proto == vProtoAuto) p->proto = bytes < (64u << 10) ? vProtoLL : bytes < (2u << 20) ? vProtoLL128 : vProtoSimple;
   if (p->algo == vAlgoAuto) p->algo = (coll == kAllReduce && bytes <= (256u << 10) && c->k > 2) ? vAlgoTree : vAlgoRing;
   if (p->nchannels <= 0) {
@@ -265,14 +299,31 @@ static void defaultPlan(const vcomm* c, int coll, size_t bytes, vPlan_t* p) {
   if (p->chunkSteps <= 0) p->chunkSteps = 1;
 }
 
-// ------------------------------------------------------------------ one collective
+// ------------------------------------------------------------------ one call
 static bool overlaps(uintptr_t a, size_t na, uintptr_t b, size_t nb) {
   return na && nb && a < b + nb && b < a + na;
 }
 
-static vResult_t collective(int coll, const void* const* sendbufs, void* const* recvbufs,
-                            size_t count, int dtype, int op, int root, int algo, int proto,
-                            vStream_t stream, vcomm_t c) {
+// everything a launch (single or batched) needs about one collective call
+struct CallSpec {
+  vcomm* c = nullptr;
+  int coll = 0;                 // the user's collective
+  int kcoll = 0;                // the kernel's (kCopy on a single rank)
+  int dtype = 0, redop = 0, root = 0;
+  int al = 0, pr = 0;
+  bool bytesUnits = false;
+  vPlan_t plan{};
+  unsigned long long units = 0; // partitioned units (0: nothing to do)
+  unsigned long long inplace = 0;
+  size_t S = 0;                 // the larger per-rank buffer, bytes
+  cudaStream_t stream = nullptr;
+  const void* send[VCOMM_MAX_RANKS];
+  void* recv[VCOMM_MAX_RANKS];
+};
+
+static vResult_t prepareCall(int coll, const void* const* sendbufs, void* const* recvbufs,
+                             size_t count, int dtype, int op, int root, int algo, int proto,
+                             vStream_t stream, vcomm_t c, CallSpec* cs) {
   if (!c || !sendbufs || !recvbufs) return vInvalidArgument;
   {
     int e = ((volatile ErrWord*)c->hErr)->code;
@@ -286,6 +337,7 @@ static vResult_t collective(int coll, const void* const* sendbufs, void* const* 
   const int k = c->k;
   if ((coll == kBroadcast || coll == kReduce) && (root < 0 || root >= k)) return vInvalidArgument;
   if (algo == vAlgoTree && coll != kAllReduce) return vUnsupported;  // Table "collective support"
+  cs->units = 0;
   if (count == 0) return vSuccess;
   const size_t esz = dtypeSize(dtype);
 
@@ -331,6 +383,7 @@ static vResult_t collective(int coll, const void* const* sendbufs, void* const* 
   }
   if (plan.algo == vAlgoTree && coll != kAllReduce) plan.algo = vAlgoRing;
   defaultPlan(c, coll, std::max(sb, rb), &plan);
+  if (plan.algo == vAlgoTree && (coll != kAllReduce || k < 2)) plan.algo = vAlgoRing;
   int kcoll = coll;
   if (k == 1) {
     kcoll = kCopy;
@@ -345,15 +398,54 @@ static vResult_t collective(int coll, const void* const* sendbufs, void* const* 
     if (c->pinned && c->pin.chunkSteps > 0) return vUnsupported;
     plan.chunkSteps = c->nsteps - 1;
   }
-  const int al = (plan.algo == vAlgoTree) ? kTree : kRing;
-  const int pr = (int)plan.proto - 1;
-  const bool bytesUnits = (coll == kAllGather || coll == kBroadcast);
-  const void* fn = bytesUnits ? copyKernel(pr) : reduceKernel(pr, dtype, op < 0 ? 0 : op);
+  cs->c = c;
+  cs->coll = coll;
+  cs->kcoll = kcoll;
+  cs->dtype = dtype;
+  cs->redop = op < 0 ? 0 : op;
+  cs->root = root;
+  cs->al = (plan.algo == vAlgoTree) ? kTree : kRing;
+  cs->pr = (int)plan.proto - 1;
+  cs->bytesUnits = (coll == kAllGather || coll == kBroadcast);
+  cs->plan = plan;
+  cs->inplace = inplace;
+  cs->S = std::max(sb, rb);
+  cs->stream = (cudaStream_t)stream;
+  if (cs->bytesUnits) cs->units = count * esz;
+  else cs->units = count;
+  for (int r = 0; r < k; r++) {
+    cs->send[r] = sendbufs[r];
+    cs->recv[r] = recvbufs[r];
+  }
+  return vSuccess;
+}
+
+static bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return st != cudaStreamCaptureStatusNone;
+}
+
+// arenas are allocated outside stream capture only (cudaMalloc + sync)
+static vResult_t needArena(vcomm* c, int al, int pr, cudaStream_t s) {
+  if (c->arena[al][pr].ready) return vSuccess;
+  if (capturing(s)) return vUnsupported;   // call vcommPrepare before capturing
+  return ensureArena(c, al, pr);
+}
+
+static vResult_t launchSingle(CallSpec& cs) {
+  vcomm* c = cs.c;
+  const int k = c->k;
+  vPlan_t& plan = cs.plan;
+  const void* fn = cs.bytesUnits ? copyKernel(cs.pr) : reduceKernel(cs.pr, cs.dtype, cs.redop);
   if (!fn) return vInternalError;
 
   // co-residency: every CTA of the launch spins on its peers
-  int nsub = (al == kTree) ? 2 * plan.nchannels : plan.nchannels;
-  const int nthrMax = std::min(c->nthreads, maxThreadsFor(pr));
+  int nsub = (cs.al == kTree) ? 2 * plan.nchannels : plan.nchannels;
+  const int nthrMax = std::min(c->nthreads, maxThreadsFor(cs.pr));
   int nthr = nthrMax;
   while (true) {
     int per = residentPerSM(fn, nthr);
@@ -363,52 +455,255 @@ static vResult_t collective(int coll, const void* const* sendbufs, void* const* 
     bool autoCh = !(c->pinned && c->pin.nchannels > 0);
     if (autoCh && plan.nchannels > 1) {
       plan.nchannels--;
-      nsub = (al == kTree) ? 2 * plan.nchannels : plan.nchannels;
+      nsub = (cs.al == kTree) ? 2 * plan.nchannels : plan.nchannels;
       nthr = nthrMax;
       continue;
     }
     return vUnsupported;
   }
-
-  if (kcoll != kCopy) {
-    vResult_t r = ensureArena(c, al, pr);
+  if (cs.kcoll != kCopy) {
+    vResult_t r = needArena(c, cs.al, cs.pr, cs.stream);
     if (r != vSuccess) return r;
   }
 
   KernArgs a;
   memset(&a, 0, sizeof(a));
   for (int r = 0; r < k; r++) {
-    a.send[r] = sendbufs[r];
-    a.recv[r] = recvbufs[r];
+    a.send[r] = cs.send[r];
+    a.recv[r] = cs.recv[r];
   }
-  const int unitBytes = bytesUnits ? 1 : (int)esz;
-  if (coll == kAllGather || coll == kBroadcast) a.count = count * esz;
-  else a.count = count;
-  if (kcoll == kCopy && coll == kReduceScatter) a.count = count;  // block 0 of rank 0
-  a.slotBytes = c->slotBytes[pr];
-  a.slotUnits = slotDataBytes(pr, c->slotBytes[pr]) / unitBytes;
-  a.chunk = chunkUnits(pr, c->slotBytes[pr], plan.chunkSteps, unitBytes);
+  const int unitBytes = cs.bytesUnits ? 1 : dtypeSize(cs.dtype);
+  a.count = cs.units;
+  a.slotBytes = c->slotBytes[cs.pr];
+  a.slotUnits = slotDataBytes(cs.pr, c->slotBytes[cs.pr]) / unitBytes;
+  a.chunk = chunkUnits(cs.pr, c->slotBytes[cs.pr], plan.chunkSteps, unitBytes);
   a.timeoutNs = (unsigned long long)(c->timeoutSec * 1e9);
-  a.conns = (kcoll == kCopy) ? nullptr : c->arena[al][pr].dConns;
+  a.conns = (cs.kcoll == kCopy) ? nullptr : c->arena[cs.al][cs.pr].dConns;
   a.errClaim = c->dClaim;
   a.err = c->dErr;
   a.abortFlag = c->dAbort;
-  a.inplaceMask = inplace;
+  a.inplaceMask = cs.inplace;
   a.downOffset = (unsigned long long)(2 * c->nch) * k;
-  a.coll = kcoll;
-  a.algo = al;
+  a.coll = cs.kcoll;
+  a.algo = cs.al;
+  a.redop = cs.redop;
   a.nranks = k;
   a.nsub = nsub;
-  a.root = root;
+  a.root = cs.root;
   a.nsteps = c->nsteps;
   a.upThreads = (nthr / 2) / 32 * 32;
+  a.skipRank = c->skipRank;
 
   void* args[] = {(void*)&a};
   cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)(k * nsub)), dim3((unsigned)nthr),
-                                              args, 0, (cudaStream_t)stream);
+                                              args, 0, cs.stream);
   if (e != cudaSuccess) return fromCuda(e);
   c->last = plan;
   return vSuccess;
+}
+
+// ------------------------------------------------------------------ group calls
+// vGroupStart / vGroupEnd (Sec. II-A-4): calls between them are validated and
+// planned at once but launched together at vGroupEnd, one batch kernel per
+// communicator.
+static thread_local int tGroupDepth = 0;
+static thread_local std::vector<CallSpec> tPending;
+
+// launch the batch of one communicator: gangs, LPT assignment, one kernel
+static vResult_t launchGroup(vcomm* c, std::vector<CallSpec>& ops) {
+  if (ops.empty()) return vSuccess;
+  const cudaStream_t stream = ops[0].stream;
+  for (auto& o : ops)
+    if (o.stream != stream) return vInvalidArgument;   // one stream per group and communicator
+  std::vector<vPlan_t> plans;
+  if (ops.size() == 1) {
+    vResult_t r = launchSingle(ops[0]);
+    c->groupPlans.assign(1, ops[0].plan);
+    return r;
+  }
+  const int k = c->k;
+  const void* fn = batchKernel();
+  const int nthr = 256;
+  const int resident = residentPerSM(fn, nthr) * c->nsm;
+  // gangs: up to 4 concurrent op streams, each on nch / G channels
+  int G = std::min<int>(std::min<int>(4, (int)ops.size()), c->nch);
+  int cpg = c->nch / G;
+  while ((long long)G * k * cpg > resident) {
+    if (cpg > 1) cpg--;
+    else if (G > 1) { G--; cpg = c->nch / G; }
+    else return vUnsupported;
+  }
+  // fit each op's plan into a gang
+  for (auto& o : ops) {
+    if (o.kcoll == kCopy) {
+      o.plan.nchannels = std::min(o.plan.nchannels, cpg);
+      continue;
+    }
+    if (o.al == kTree && cpg < 2) { o.al = kRing; o.plan.algo = vAlgoRing; }
+    if (o.al == kTree) o.plan.nchannels = std::min(o.plan.nchannels, cpg / 2);
+    else o.plan.nchannels = std::min(o.plan.nchannels, cpg);
+    if (o.al == kRing && k > 1 && o.plan.chunkSteps >= c->nsteps) o.plan.chunkSteps = c->nsteps - 1;
+    vResult_t r = needArena(c, o.al, o.pr, stream);
+    if (r != vSuccess) return r;
+  }
+  c->groupPlans.clear();
+  for (auto& o : ops) c->groupPlans.push_back(o.plan);
+
+  // launches of at most kMaxBatchOps ops and kMaxBatchPtrs pointers each
+  const int perLaunch = std::min<int>(kMaxBatchOps, kMaxBatchPtrs / (2 * k));
+  for (size_t base = 0; base < ops.size(); base += perLaunch) {
+    const int n = (int)std::min<size_t>(perLaunch, ops.size() - base);
+    // longest-processing-time-first assignment by a bytes-moved cost model
+    std::vector<int> idx(n);
+    std::vector<double> cost(n);
+    for (int i = 0; i < n; i++) {
+      const CallSpec& o = ops[base + i];
+      const double f = (o.pr == kLL) ? 2.0 : (o.pr == kLL128) ? 128.0 / 120.0 : 1.0;
+      cost[i] = (double)o.S * f + 65536.0;   // + a per-op latency in byte-equivalents
+      idx[i] = i;
+    }
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<double> load(G, 0.0);
+    std::vector<int> gangOf(n);
+    for (int i : idx) {
+      int g = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      gangOf[i] = g;
+      load[g] += cost[i];
+    }
+    std::unique_ptr<BatchArgs> b(new BatchArgs());
+    memset(b.get(), 0, sizeof(BatchArgs));
+    b->timeoutNs = (unsigned long long)(c->timeoutSec * 1e9);
+    b->errClaim = c->dClaim;
+    b->err = c->dErr;
+    b->abortFlag = c->dAbort;
+    b->nops = n;
+    b->nranks = k;
+    b->ngangs = G;
+    b->cpg = cpg;
+    b->nsteps = c->nsteps;
+    int pos = 0;
+    for (int g = 0; g < G; g++) {
+      b->gangStart[g] = pos;
+      for (int i = 0; i < n; i++)   // submission order inside a gang
+        if (gangOf[i] == g) b->order[pos++] = (unsigned char)i;
+    }
+    b->gangStart[G] = pos;
+    for (int i = 0; i < n; i++) {
+      const CallSpec& o = ops[base + i];
+      BatchOpDesc& d = b->ops[i];
+      const int unitBytes = o.bytesUnits ? 1 : dtypeSize(o.dtype);
+      d.count = o.units;
+      d.chunk = chunkUnits(o.pr, c->slotBytes[o.pr], o.plan.chunkSteps, unitBytes);
+      d.slotBytes = c->slotBytes[o.pr];
+      d.slotUnits = slotDataBytes(o.pr, c->slotBytes[o.pr]) / unitBytes;
+      d.inplaceMask = o.inplace;
+      d.downOffset = (unsigned long long)(2 * c->nch) * k;
+      d.conns = (o.kcoll == kCopy) ? nullptr : c->arena[o.al][o.pr].dConns;
+      d.coll = o.kcoll;
+      d.algo = o.al;
+      d.proto = o.pr;
+      d.dtype = o.bytesUnits ? -1 : o.dtype;
+      d.redop = o.redop;
+      d.nsub = (o.al == kTree) ? 2 * o.plan.nchannels : o.plan.nchannels;
+      d.root = o.root;
+      d.ptrBase = 2 * k * i;
+      for (int r = 0; r < k; r++) {
+        b->ptrs[2 * k * i + r] = o.send[r];
+        b->ptrs[2 * k * i + k + r] = o.recv[r];
+      }
+    }
+    void* args[] = {(void*)b.get()};
+    cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)(G * k * cpg)), dim3(nthr), args, 0,
+                                                stream);
+    if (e != cudaSuccess) return fromCuda(e);
+  }
+  c->last = ops.back().plan;
+  return vSuccess;
+}
+
+static vResult_t collective(int coll, const void* const* sendbufs, void* const* recvbufs,
+                            size_t count, int dtype, int op, int root, int algo, int proto,
+                            vStream_t stream, vcomm_t c) {
+  CallSpec cs;
+  vResult_t r = prepareCall(coll, sendbufs, recvbufs, count, dtype, op, root, algo, proto, stream,
+                            c, &cs);
+  if (r != vSuccess || cs.units == 0) return r;
+  if (tGroupDepth > 0) {
+    tPending.push_back(cs);
+    c->last = cs.plan;
+    return vSuccess;
+  }
+  return launchSingle(cs);
+}
+
+// ------------------------------------------------------------------ tuner
+// Measures every candidate plan (algorithm, protocol, channels) at message
+// sizes 1 KiB x 4^i up to maxBytes, on scratch buffers, with CUDA events on
+// the caller's stream, and keeps the fastest per size: the table that
+// defaultPlan consults (Sec. III-D / V-F: the choice depends on size).
+static const int kTuneColls[5] = {kAllReduce, kReduceScatter, kAllGather, kBroadcast, kReduce};
+
+static vResult_t tuneOne(vcomm* c, int coll, size_t S, char* sbuf, char* rbuf, size_t stride,
+                         cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+  const int k = c->k;
+  size_t count = S / 4;
+  if (coll == kReduceScatter || coll == kAllGather) count = S / 4 / k;
+  if (count == 0) return vSuccess;
+  std::vector<const void*> sp(k);
+  std::vector<void*> rp(k);
+  for (int r = 0; r < k; r++) {
+    sp[r] = sbuf + (size_t)r * stride;
+    rp[r] = rbuf + (size_t)r * stride;
+  }
+  std::vector<int> chans;
+  for (int ch : {1, 2, 4, 8, 16, 32, 64})
+    if (ch <= c->nch) chans.push_back(ch);
+  if (std::find(chans.begin(), chans.end(), c->nch) == chans.end()) chans.push_back(c->nch);
+  TuneEntry best{};
+  best.usec = 1e30f;
+  const bool savedPinned = c->pinned;
+  const vPlan_t savedPin = c->pin;
+  for (int al = 0; al < ((coll == kAllReduce && k > 2) ? 2 : 1); al++) {
+    for (int pr = 0; pr < 3; pr++) {
+      for (int ch : chans) {
+        vPlan_t p{al ? vAlgoTree : vAlgoRing, (vProto_t)(pr + 1), ch, 1};
+        c->pin = p;
+        c->pinned = true;
+        CallSpec cs;
+        vResult_t r = prepareCall(coll, sp.data(), rp.data(), count, vFloat32, vSum, 0, p.algo,
+                                  p.proto, s, c, &cs);
+        if (r == vSuccess && cs.units) r = launchSingle(cs);   // warm-up (and arena)
+        if (r != vSuccess) { (void)cudaGetLastError(); continue; }
+        const int reps = 3;
+        cudaEventRecord(e0, s);
+        for (int i = 0; i < reps && r == vSuccess; i++) r = launchSingle(cs);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess || r != vSuccess) {
+          (void)cudaGetLastError();
+          continue;
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const float us = ms * 1000.0f / reps;
+        if (us < best.usec) {
+          best.valid = true;
+          best.usec = us;
+          best.bytes = S;
+          best.plan = cs.plan;
+        }
+      }
+    }
+  }
+  c->pinned = savedPinned;
+  c->pin = savedPin;
+  int bucket = 0;
+  while (((size_t)1024 << (2 * bucket)) < S && bucket < kTuneBuckets - 1) bucket++;
+  if (best.valid) {
+    c->tune[coll][bucket] = best;
+    c->tuned[coll] = true;
+  }
+  int e = ((volatile ErrWord*)c->hErr)->code;
+  return e ? (vResult_t)e : vSuccess;
 }
 
 extern "C" {
@@ -444,6 +739,91 @@ vResult_t vReduce(const void* const* sendbufs, void* const* recvbufs, size_t cou
                   vDataType_t dtype, vRedOp_t op, int root, vAlgo_t algo, vProto_t proto,
                   vStream_t stream, vcomm_t comm) {
   return collective(kReduce, sendbufs, recvbufs, count, dtype, op, root, algo, proto, stream, comm);
+}
+
+vResult_t vcommDebugSetSkipRank(vcomm_t c, int rank) {
+  if (!c || rank < -1 || rank >= c->k) return vInvalidArgument;
+  c->skipRank = rank;
+  return vSuccess;
+}
+
+vResult_t vGroupStart(void) {
+  tGroupDepth++;
+  return vSuccess;
+}
+
+vResult_t vGroupEnd(void) {
+  if (tGroupDepth <= 0) return vInvalidArgument;
+  if (--tGroupDepth > 0) return vSuccess;
+  std::vector<CallSpec> pending;
+  pending.swap(tPending);
+  // one batch per communicator, in order of first appearance
+  vResult_t first = vSuccess;
+  std::vector<vcomm*> comms;
+  for (auto& o : pending)
+    if (std::find(comms.begin(), comms.end(), o.c) == comms.end()) comms.push_back(o.c);
+  for (vcomm* c : comms) {
+    std::vector<CallSpec> ops;
+    for (auto& o : pending)
+      if (o.c == c) ops.push_back(o);
+    vResult_t r = launchGroup(c, ops);
+    if (r != vSuccess && first == vSuccess) first = r;
+  }
+  return first;
+}
+
+vResult_t vcommGetGroupPlans(vcomm_t c, vPlan_t* plans, int maxPlans, int* nPlans) {
+  if (!c || !nPlans || maxPlans < 0 || (maxPlans > 0 && !plans)) return vInvalidArgument;
+  const int n = (int)c->groupPlans.size();
+  for (int i = 0; i < n && i < maxPlans; i++) plans[i] = c->groupPlans[i];
+  *nPlans = n;
+  return vSuccess;
+}
+
+vResult_t vcommTune(vcomm_t c, unsigned collMask, size_t maxBytes, vStream_t stream) {
+  if (!c || maxBytes < 1024 || maxBytes > ((size_t)1 << 34)) return vInvalidArgument;
+  if (tGroupDepth > 0) return vInvalidArgument;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (capturing(s)) return vUnsupported;
+  const size_t stride = (maxBytes + 255) / 256 * 256;
+  char* sbuf = nullptr;
+  char* rbuf = nullptr;
+  VC_TRY(cudaMalloc(&sbuf, stride * c->k));
+  vResult_t r = fromCuda(cudaMalloc(&rbuf, stride * c->k));
+  if (r == vSuccess) r = fromCuda(cudaMemset(sbuf, 0, stride * c->k));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (r == vSuccess) r = fromCuda(cudaEventCreate(&e0));
+  if (r == vSuccess) r = fromCuda(cudaEventCreate(&e1));
+  for (int ci = 0; ci < 5 && r == vSuccess; ci++) {
+    if (!(collMask & (1u << ci))) continue;
+    for (size_t S = 1024; S <= maxBytes && r == vSuccess; S *= 4)
+      r = tuneOne(c, kTuneColls[ci], S, sbuf, rbuf, stride, s, e0, e1);
+  }
+  cudaStreamSynchronize(s);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(sbuf);
+  if (rbuf) cudaFree(rbuf);
+  (void)cudaGetLastError();
+  return r;
+}
+
+vResult_t vcommGetTuneTable(vcomm_t c, int coll, vPlan_t* plans, size_t* bytes, float* usec,
+                            int maxEntries, int* nEntries) {
+  if (!c || !nEntries || coll < 0 || coll > 4 || maxEntries < 0) return vInvalidArgument;
+  int n = 0;
+  for (int i = 0; i < kTuneBuckets; i++) {
+    const TuneEntry& e = c->tune[kTuneColls[coll]][i];
+    if (!e.valid) continue;
+    if (n < maxEntries) {
+      if (plans) plans[n] = e.plan;
+      if (bytes) bytes[n] = e.bytes;
+      if (usec) usec[n] = e.usec;
+    }
+    n++;
+  }
+  *nEntries = n;
+  return vSuccess;
 }
 
 // ------------------------------------------------------------------ debug codecs
@@ -486,6 +866,7 @@ vResult_t vDebugDecode(vProto_t proto, const void* lines, size_t nbytes, uint64_
   VC_TRY(cudaMemsetAsync(gDbgClaim, 0, sizeof(int), (cudaStream_t)stream));
   KernArgs a;
   memset(&a, 0, sizeof(a));
+  a.skipRank = -1;
   a.timeoutNs = (unsigned long long)((timeoutSec > 0 ? timeoutSec : 1.0) * 1e9);
   a.errClaim = gDbgClaim;
   a.err = gDbgErrD;

@@ -71,11 +71,41 @@ struct KernArgs {
   unsigned long long downOffset;   // tree: index of the first down connection
   int coll;
   int algo;
+  int redop;                       // OpKind (read by the batch kernel's dispatch)
   int nranks;
   int nsub;                        // CTAs per rank: channels (ring) or 2 x channels (tree)
   int root;
   int nsteps;
   int upThreads;                   // tree: threads of the reduce (up) group on non-root ranks
+  int skipRank;                    // fault injection: this vrank's CTAs return at once (-1: none)
+};
+
+// ---- batched launch: many collectives in one persistent kernel (group calls,
+// Sec. II-A-4).  The grid is `ngangs` gangs of nranks x cpg CTAs; gang g runs
+// its ops one after another on channels [g * cpg, (g + 1) * cpg) of the
+// communicator's arenas.  The whole description travels as one kernel
+// parameter (< 32 KB), so a CUDA graph that captured the launch needs no host
+// buffer at replay time.
+constexpr int kMaxBatchOps = 64;
+constexpr int kMaxBatchPtrs = 2048;   // send + recv pointers of all ops
+constexpr int kMaxGangs = 8;
+
+struct BatchOpDesc {
+  unsigned long long count, chunk, slotBytes, slotUnits, inplaceMask, downOffset;
+  const ConnDev* conns;              // the (algo, proto) arena, before the gang offset
+  int coll, algo, proto, dtype, redop, nsub, root, ptrBase;  // ptrs[ptrBase..+k) send, then recv
+};
+
+struct BatchArgs {
+  unsigned long long timeoutNs;
+  int* errClaim;
+  ErrWord* err;
+  const volatile int* abortFlag;
+  int nops, nranks, ngangs, cpg, nsteps, pad;
+  int gangStart[kMaxGangs + 1];      // gang g runs order[gangStart[g] .. gangStart[g+1])
+  unsigned char order[kMaxBatchOps];
+  BatchOpDesc ops[kMaxBatchOps];
+  const void* ptrs[kMaxBatchPtrs];
 };
 
 // ---- channel partition (Sec. V-C): 16-byte packs spread over `nch` ranges,

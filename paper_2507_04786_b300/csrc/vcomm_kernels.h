@@ -10,3 +10,8 @@ const void* copyKernel(int proto);
 const void* debugEncodeKernel();
 const void* debugDecodeKernel();
 }  // namespace vc
+
+namespace vc {
+// the batched-launch kernel (vcomm_batch.cu); its parameter is a BatchArgs
+const void* batchKernel();
+}  // namespace vc

@@ -134,6 +134,7 @@ extern "C" vResult_t vAllReduceNoAlloc(const void* const* sendbufs, void* const*
   a.root = 0;
   a.nsteps = kNaSlots;
   a.upThreads = 0;
+  a.skipRank = -1;
 
   cudaStream_t s = (cudaStream_t)stream;
   kNoAllocSetup<<<1, 256, 0, s>>>(base, k * nchannels, deviceStatus);
