@@ -233,6 +233,156 @@ def run_gpu(args, rank, world):
             "S": S, "k": k, "proto": proto}
 
 
+# ------------------------------------------------------------------ batched leg
+
+def run_batched(args):
+    """64 AllReduce calls on 8 vranks, per-rank sizes log-uniform in
+    4 KiB..64 MiB, dtypes fp32/bf16/int32, ops sum/max, plans from the
+    autotuner: 64 plain calls per step vs one replay of the captured batch."""
+    import torch
+
+    from paper_2507_04786_b300 import Comm, group
+    w = workloads.BATCHED
+    k, nops = w["nranks"], w["nops"]
+    g = np.random.default_rng(w["seed"])
+    sizes = inputs.log_uniform_sizes(w["seed"], nops, w["lo_bytes"], w["hi_bytes"])
+    tdt = {"fp32": torch.float32, "bf16": torch.bfloat16, "int32": torch.int32}
+    ops = []
+    for i in range(nops):
+        dt = ("fp32", "bf16", "int32")[g.integers(3)]
+        op = ("sum", "max")[g.integers(2)]
+        es = 2 if dt == "bf16" else 4
+        n = int(sizes[i]) // es
+        s_ = [torch.ones(n, dtype=tdt[dt], device="cuda") for _ in range(k)]
+        d_ = [torch.empty_like(t) for t in s_]
+        ops.append((s_, d_, op, n * es))
+    comm = Comm(k, w["nchannels"])
+    t0 = time.time()
+    comm.tune(colls=("allreduce",), max_bytes=w["hi_bytes"])
+    tune_s = time.time() - t0
+    comm.prepare(algos=("ring", "tree"), protos=("simple", "ll", "ll128"))
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+
+    def plain():
+        for s_, d_, op, _ in ops:
+            comm.all_reduce(s_, d_, op=op, algo="auto", proto="auto", stream=stream)
+
+    def batched():
+        with group():
+            for s_, d_, op, _ in ops:
+                comm.all_reduce(s_, d_, op=op, algo="auto", proto="auto", stream=stream)
+
+    steps = max(args.steps // 5, 5)
+
+    def timed(fn):
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    plain_ms = timed(plain)
+    with torch.cuda.stream(stream):
+        batched()                               # fixes the plans before capture
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        batched()
+    batch_ms = timed(graph.replay)
+    err = comm.async_error()
+    comm.destroy()
+    total = sum(o[3] for o in ops)
+    return {"workload": w["name"], "ops": nops, "nranks": k,
+            "bytes_per_rank_total": total, "plain_ms": round(plain_ms, 4),
+            "batched_graph_ms": round(batch_ms, 4), "speedup": round(plain_ms / batch_ms, 3),
+            "plain_algbw_GBps": round(total / (plain_ms / 1e3) / 1e9, 2),
+            "batched_algbw_GBps": round(total / (batch_ms / 1e3) / 1e9, 2),
+            "tune_seconds": round(tune_s, 1), "status": err}
+
+
+# ------------------------------------------------------------------ served leg
+
+def run_served(args):
+    """Poisson arrivals (mean 2000/s) of AllReduce / AllGather / ReduceScatter
+    requests on 2..16 vranks, per-rank sizes log-uniform in 1 KiB..128 MiB,
+    fp32/bf16, admitted under a 40 GB budget: continuous batching vs one
+    launch per request, same request stream."""
+    import torch
+
+    from paper_2507_04786_b300 import Server
+    w = workloads.SERVED
+    nreq = args.serve_requests
+    g = np.random.default_rng(w["seed"])
+    gaps = g.exponential(1.0 / w["rate_per_s"], nreq)
+    arrivals = np.cumsum(gaps)
+    sizes = inputs.log_uniform_sizes(w["seed"], nreq, w["lo_bytes"], w["hi_bytes"])
+    colls = g.integers(0, 3, nreq)
+    ks = g.integers(2, w["max_ranks"] + 1, nreq)
+    dts = g.integers(0, 2, nreq)
+    # resident inputs: every request reads the same pool (one buffer per vrank and dtype)
+    hi = w["hi_bytes"]
+    pool = {"fp32": [torch.ones(hi // 4, dtype=torch.float32, device="cuda") for _ in range(w["max_ranks"])],
+            "bf16": [torch.ones(hi // 2, dtype=torch.bfloat16, device="cuda") for _ in range(w["max_ranks"])]}
+    torch.cuda.synchronize()
+    names = ("allreduce", "reducescatter", "allgather")
+    reqs = []
+    for i in range(nreq):
+        dt = ("fp32", "bf16")[dts[i]]
+        es = 4 if dt == "fp32" else 2
+        k = int(ks[i])
+        coll = names[colls[i]]
+        n = max(16 // es, int(sizes[i]) // es)            # S = the larger per-rank buffer
+        if coll != "allreduce":
+            n = max(1, n // k)
+        reqs.append((coll, dt, k, n, int(sizes[i])))
+    out = {}
+    for mode in ("batch", "plain"):
+        srv = Server(mode=mode, max_ranks=w["max_ranks"], mem_budget=w["budget_bytes"])
+        tickets = []
+        t0 = time.monotonic_ns() + 20_000_000
+        for i, (coll, dt, k, n, S) in enumerate(reqs):
+            due = t0 + int(arrivals[i] * 1e9)
+            while time.monotonic_ns() < due:
+                pass
+            tickets.append(srv.submit(coll, pool[dt][:k], n, dt, "sum", release=True,
+                                      arrival_ns=due))
+        deadline = time.time() + 120
+        while srv.stats()["completed"] + srv.stats()["failed"] < nreq and time.time() < deadline:
+            time.sleep(0.005)
+        st = srv.stats()
+        lats, ends, svc_big, svc_small = [], [], [], []
+        for i, t in enumerate(tickets):
+            state, lat, _, _ = srv.query(t)
+            if state == "done":
+                lats.append(lat / 1e6)
+                ends.append(arrivals[i] + lat / 1e9)
+                if srv.last_service_ns > 0:
+                    (svc_big if reqs[i][4] >= (4 << 20) else svc_small).append(srv.last_service_ns / 1e6)
+            srv.release(t)
+        srv.destroy()
+        lats = np.array(lats, dtype=np.float64)
+        span = (max(ends) - arrivals[0]) if ends else float("nan")
+        total = sum(r[4] * r[2] for r in reqs)
+        out[mode] = {"p50_ms": round(float(np.percentile(lats, 50)), 4) if lats.size else None,
+                     "p99_ms": round(float(np.percentile(lats, 99)), 4) if lats.size else None,
+                     "mean_ms": round(float(lats.mean()), 4) if lats.size else None,
+                     "completed": int(st["completed"]), "failed": int(st["failed"]),
+                     "requests_per_s": round(len(lats) / span, 1),
+                     "GBps": round(total / span / 1e9, 2),
+                     "max_inflight_GB": round(st["maxInflightBytes"] / 1e9, 2),
+                     "mean_service_ms_large": round(float(np.mean(svc_big)), 4) if svc_big else None,
+                     "mean_service_ms_small": round(float(np.mean(svc_small)), 4) if svc_small else None}
+    return {"workload": w["name"], "requests": nreq, "rate_per_s": w["rate_per_s"],
+            "budget_GB": w["budget_bytes"] / 1e9, "continuous_batching": out["batch"],
+            "per_call": out["plain"]}
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -257,6 +407,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--proto", default="simple", choices=["simple", "ll", "ll128"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
+    ap.add_argument("--serve-requests", type=int, default=workloads.SERVED["bench_requests"],
+                    help="requests of the served leg (the full stream is 100000)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and served legs")
     ap.add_argument("--bytes", type=int, default=workloads.HEADLINE["bytes_per_rank"],
                     help="bytes per vrank (default: the headline's 256 MiB; smaller sizes are "
                          "for profiling captures only)")
@@ -328,6 +481,9 @@ def main():
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],
     }
+    if not args.no_extras and world == 1:
+        line["batched"] = run_batched(args)
+        line["served"] = run_served(args)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(k, args.proto, w["nchannels"], w["chunk_steps"],
                                             w["seed"])

@@ -188,6 +188,65 @@ vResult_t vcommTune(vcomm_t comm, unsigned collMask, size_t maxBytes, vStream_t 
 vResult_t vcommGetTuneTable(vcomm_t comm, int coll, vPlan_t* plans, size_t* bytes, float* usec,
                             int maxEntries, int* nEntries);
 
+/* ---- serving: continuous batching of collective requests ------------------
+ * No counterpart in the paper beyond its collectives.  A server runs one
+ * persistent kernel whose gangs each execute one request at a time: one wide
+ * gang (bigGangChannels x maxRanks CTAs) for requests whose per-rank size is
+ * >= bigThreshold, and smallGangs narrow gangs (maxRanks CTAs) for the rest;
+ * a request of k vranks spreads over its gang as (gang CTAs / k) channels.  A host thread admits submitted requests in arrival order --
+ * a request that must wait does not block later ones -- as soon as the bytes
+ * of all admitted, unreleased requests (send + receive, all vranks) fit in
+ * memBudget and a suitable gang is free; it allocates the request's receive
+ * buffers from a pool of memBudget bytes, posts the request to the gang's
+ * host-mapped mailbox, and records its completion time.  A request's plan
+ * depends only on the request (protocol by size unless given; one channel,
+ * or all of the wide gang's channels for large requests; chunkSteps 1), so
+ * its result is bit-identical alone and in any mix, and equal to vAllReduce
+ * (ring) with that plan.  mode 1 ("plain") runs the same requests as one
+ * ordinary launch each on one stream, for comparison.
+ * While a mode-0 server exists its kernel occupies the SMs: do not launch and
+ * wait for other kernels meanwhile (copies are fine). */
+typedef enum { vCollAllReduce = 0, vCollReduceScatter = 1, vCollAllGather = 2 } vColl_t;
+typedef struct vserve* vserve_t;
+typedef struct {
+  int mode;              /* 0 continuous batching [default], 1 one launch per request */
+  int maxRanks;          /* vranks per request, <= 16 [16] */
+  size_t memBudget;      /* bytes of request buffers in flight [40 GiB]; the pool is this size */
+  int bigGangChannels;   /* channels of the wide gang [0: every co-resident CTA the
+                            narrow gangs leave, 8 on a B300 at 512 threads] */
+  int smallGangs;        /* narrow gangs [1] */
+  size_t bigThreshold;   /* per-rank bytes from which a request is large [4 MiB] */
+  size_t slotBytes[3];   /* FIFO slots, Simple / LL / LL128 [256 KiB, 32 KiB, 300 KiB] */
+  double idleTimeoutSec; /* the kernel stops after this long without a request [30 s] */
+  int threads;           /* threads per CTA of the serving kernel, <= 512 [512] */
+} vserveConfig_t;
+typedef struct {
+  uint64_t submitted, completed, failed, queued;
+  size_t inflightBytes, maxInflightBytes;
+} vserveStats_t;
+
+vResult_t vServeCreate(vserve_t* server, const vserveConfig_t* cfg);
+/* Queue one request: sendbufs = nranks device pointers (caller-owned, must stay
+ * valid until completion), count as in the collective (AllReduce count,
+ * ReduceScatter recvcount, AllGather sendcount).  flags bit 0: release the
+ * receive buffers at completion (results are not kept).  arrivalNs: the
+ * request's arrival on the CLOCK_MONOTONIC clock (0: now), the origin of its
+ * latency.  Returns a ticket. */
+vResult_t vServeSubmit(vserve_t server, int coll, const void* const* sendbufs, size_t count,
+                       vDataType_t dtype, vRedOp_t op, int nranks, vProto_t proto, int flags,
+                       int64_t arrivalNs, uint64_t* ticket);
+/* state: 0 queued, 1 running, 2 done, 3 failed; latency = completion - arrival
+ * (ns, -1 until done); service = the request's own run time on the device
+ * (mode 0: the gang's clock; mode 1: events around its launch; ns); plan; recvbufs (nranks pointers into the
+ * pool, valid until vServeRelease).  Any output may be NULL except state. */
+vResult_t vServeQuery(vserve_t server, uint64_t ticket, int* state, int64_t* latencyNs,
+                      int64_t* serviceNs, vPlan_t* plan, void** recvbufs);
+/* Forget a finished request and return its buffers to the budget. */
+vResult_t vServeRelease(vserve_t server, uint64_t ticket);
+vResult_t vServeGetStats(vserve_t server, vserveStats_t* stats);
+/* Stops the kernel after the running requests, then frees everything. */
+vResult_t vServeDestroy(vserve_t server);
+
 /* ---- allocation-free AllReduce -----------------------------------------
  * The paper has no counterpart to this entry point.  It exists for callers
  * that cannot call cudaMalloc at the point where they need an AllReduce: code

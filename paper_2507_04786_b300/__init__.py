@@ -6,5 +6,5 @@ arguments to it with ctypes.  PyTorch is used only for device memory and
 streams.  There is no CPU fallback: a missing library raises at first use.
 """
 from .binding import (  # noqa: F401
-    Comm, VcommError, lib_path, load_library, version,
+    Comm, Server, VcommError, group, lib_path, load_library, version,
 )

@@ -27,7 +27,9 @@ EXPORTS = ("vcommInit", "vcommInitConfig", "vcommPrepare", "vcommDestroy", "vcom
            "vcommGetAsyncError", "vcommSetPlan", "vcommGetLastPlan", "vAllReduce",
            "vReduceScatter", "vAllGather", "vBroadcast", "vReduce", "vcommVersion",
            "vDebugEncode", "vDebugDecode", "vAllReduceNoAlloc", "vGroupStart", "vGroupEnd",
-           "vcommGetGroupPlans", "vcommTune", "vcommGetTuneTable", "vcommDebugSetSkipRank")
+           "vcommGetGroupPlans", "vcommTune", "vcommGetTuneTable", "vcommDebugSetSkipRank",
+           "vServeCreate", "vServeSubmit", "vServeQuery", "vServeRelease", "vServeGetStats",
+           "vServeDestroy")
 
 
 class VcommError(RuntimeError):
@@ -40,6 +42,19 @@ class VcommError(RuntimeError):
 class Config(ctypes.Structure):
     _fields_ = [("slotBytes", ctypes.c_size_t * 3), ("nsteps", ctypes.c_int),
                 ("nthreads", ctypes.c_int), ("timeoutSec", ctypes.c_double)]
+
+
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("maxRanks", ctypes.c_int), ("memBudget", ctypes.c_size_t),
+                ("bigGangChannels", ctypes.c_int), ("smallGangs", ctypes.c_int),
+                ("bigThreshold", ctypes.c_size_t), ("slotBytes", ctypes.c_size_t * 3),
+                ("idleTimeoutSec", ctypes.c_double), ("threads", ctypes.c_int)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("queued", ctypes.c_uint64),
+                ("inflightBytes", ctypes.c_size_t), ("maxInflightBytes", ctypes.c_size_t)]
 
 
 class Plan(ctypes.Structure):
@@ -86,6 +101,15 @@ def load_library():
     L.vDebugDecode.argtypes = [i32, vp, sz, ctypes.c_uint64, vp, ctypes.c_double, vp]
     L.vAllReduceNoAlloc.argtypes = [pp, pp, sz, i32, i32, i32, i32, vp, vp]
     L.vcommDebugSetSkipRank.argtypes = [vp, i32]
+    L.vServeCreate.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ServeConfig)]
+    L.vServeSubmit.argtypes = [vp, i32, pp, sz, i32, i32, i32, i32, i32, ctypes.c_int64,
+                               ctypes.POINTER(ctypes.c_uint64)]
+    L.vServeQuery.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(i32),
+                              ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                              ctypes.POINTER(Plan), pp]
+    L.vServeRelease.argtypes = [vp, ctypes.c_uint64]
+    L.vServeGetStats.argtypes = [vp, ctypes.POINTER(ServeStats)]
+    L.vServeDestroy.argtypes = [vp]
     L.vGroupStart.argtypes = []
     L.vGroupEnd.argtypes = []
     L.vcommGetGroupPlans.argtypes = [vp, ctypes.POINTER(Plan), i32, ctypes.POINTER(i32)]
@@ -292,6 +316,72 @@ class group:
             except VcommError:
                 pass
         return False
+
+
+SERVE_COLLS = {"allreduce": 0, "reducescatter": 1, "allgather": 2}
+SERVE_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
+
+
+class Server:
+    """Continuous-batching server of collective requests (vServe* in vcomm.h)."""
+
+    def __init__(self, mode="batch", max_ranks=16, mem_budget=40 << 30, big_gang_channels=0,
+                 small_gangs=1, big_threshold=4 << 20, slot_bytes=None, idle_timeout_sec=30.0,
+                 threads=512):
+        L = load_library()
+        cfg = ServeConfig()
+        cfg.mode = {"batch": 0, "plain": 1}[mode]
+        cfg.maxRanks = max_ranks
+        cfg.memBudget = mem_budget
+        cfg.bigGangChannels = big_gang_channels
+        cfg.smallGangs = small_gangs
+        cfg.bigThreshold = big_threshold
+        if slot_bytes:
+            for i, p in enumerate(("simple", "ll", "ll128")):
+                cfg.slotBytes[i] = int(slot_bytes.get(p, 0))
+        cfg.idleTimeoutSec = idle_timeout_sec
+        cfg.threads = threads
+        self._h = ctypes.c_void_p()
+        _check(L.vServeCreate(ctypes.byref(self._h), ctypes.byref(cfg)), "vServeCreate")
+
+    def submit(self, coll, sends, count, dtype, op="sum", proto="auto", release=False,
+               arrival_ns=0) -> int:
+        t = ctypes.c_uint64()
+        _check(load_library().vServeSubmit(self._h, SERVE_COLLS[coll], _ptr_array(sends), count,
+                                           DTYPE_CODES[dtype], OP_CODES[op], len(sends),
+                                           PROTO_CODES[proto], 1 if release else 0, arrival_ns,
+                                           ctypes.byref(t)), "vServeSubmit")
+        return t.value
+
+    def query(self, ticket, nranks=16):
+        """(state, latency ns, plan, receive buffers)"""
+        st, lat, svc, plan = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64(), Plan()
+        bufs = (ctypes.c_void_p * nranks)()
+        _check(load_library().vServeQuery(self._h, ticket, ctypes.byref(st), ctypes.byref(lat),
+                                          ctypes.byref(svc), ctypes.byref(plan), bufs),
+               "vServeQuery")
+        self.last_service_ns = svc.value
+        return (SERVE_STATES[st.value], lat.value, plan.as_dict(),
+                [bufs[i] for i in range(nranks)])
+
+    def release(self, ticket):
+        _check(load_library().vServeRelease(self._h, ticket), "vServeRelease")
+
+    def stats(self) -> dict:
+        st = ServeStats()
+        _check(load_library().vServeGetStats(self._h, ctypes.byref(st)), "vServeGetStats")
+        return {f: getattr(st, f) for f, _ in ServeStats._fields_}
+
+    def destroy(self):
+        if self._h:
+            _check(load_library().vServeDestroy(self._h), "vServeDestroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 def debug_encode(proto: str, src, nbytes: int, flag: int, lines, stream=None):

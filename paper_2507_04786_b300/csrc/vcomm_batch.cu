@@ -90,6 +90,141 @@ __global__ void __launch_bounds__(512, 1) kBatch(const __grid_constant__ BatchAr
   }
 }
 
+// ---- serving kernel ---------------------------------------------------------
+// Every gang loops: its leader CTA waits for the host to post request `seq` in
+// the gang's mailbox, copies it to device memory and publishes it; the gang's
+// CTAs that the request uses run it (same workers as the batch kernel); all
+// CTAs of the gang meet at a barrier, after which the leader reports
+// completion to the host.  Waits are bounded: an idle gang stops after
+// idleTimeoutNs, a failed one stops and flags its mailbox.
+__device__ __forceinline__ uint64_t ldVol64(const volatile unsigned long long* p) { return *p; }
+
+__global__ void __launch_bounds__(512, 1) kServe(const __grid_constant__ ServeArgs s) {
+  __shared__ KernArgs sa;
+  __shared__ int sAbort[2];
+  __shared__ int sStop;
+  __shared__ int sUse;
+  __shared__ int sCh;
+  __shared__ int sR;
+  int g = 0;
+  while (g + 1 < s.ngangs && (int)blockIdx.x >= s.gangCta[g + 1]) g++;
+  const int local = blockIdx.x - s.gangCta[g];
+  int ch = 0, r = 0;   // this CTA's (channel, vrank) in the current request
+  const unsigned long long nctas = (unsigned long long)(s.gangCta[g + 1] - s.gangCta[g]);
+  const bool leader = (local == 0);
+  ServeGang* G = &s.gangs[g];
+  volatile ServeSlot* slot = &s.slots[g];
+  if (threadIdx.x < 2) sAbort[threadIdx.x] = 0;
+  for (unsigned long long seq = 1;; seq++) {
+    if (threadIdx.x == 0) {
+      int stop = 0;
+      const uint64_t t0 = globaltimer();
+      if (leader) {
+        while (true) {                                   // idle wait for the host
+          if (ldVol64(&slot->seq) >= seq) break;
+          if (*s.shutdown || *s.abortFlag) { stop = 1; break; }
+          if (globaltimer() - t0 > s.idleTimeoutNs) { stop = 1; break; }
+          __nanosleep(256);
+        }
+        if (!stop) {
+          __threadfence_system();                        // the request was written before seq
+          const volatile unsigned long long* src = (const volatile unsigned long long*)&slot->req;
+          unsigned long long* dst = (unsigned long long*)&G->req;
+          for (int i = 0; i < (int)(sizeof(ServeReq) / 8); i++) dst[i] = src[i];
+          slot->tStart = globaltimer();
+          __threadfence();
+          stRelease(&G->goSeq, seq);
+        } else {
+          stRelease(&G->goSeq, ~0ull);
+        }
+      } else {
+        while (true) {                                   // wait for the leader
+          const uint64_t v = ldAcquire(&G->goSeq);
+          if (v == ~0ull) { stop = 1; break; }
+          if (v >= seq) break;
+          if (globaltimer() - t0 > s.idleTimeoutNs + 2000000000ull) { stop = 1; break; }
+          __nanosleep(256);
+        }
+      }
+      sStop = stop;
+      int use = 0;
+      if (!stop) {
+        const volatile ServeReq* q = (const volatile ServeReq*)&G->req;
+        // a request of k vranks and C channels runs on the gang's first k x C CTAs
+        use = (local < q->nranks * q->nsub) ? 1 : 0;
+        ch = local / q->nranks;
+        r = local % q->nranks;
+        sa.nranks = q->nranks;
+        if (use) {
+          sa.count = q->count;
+          sa.chunk = q->chunk;
+          sa.slotBytes = q->slotBytes;
+          sa.slotUnits = q->slotUnits;
+          sa.timeoutNs = s.timeoutNs;
+          sa.conns = s.conns[q->proto] + s.gangConn[g];
+          sa.errClaim = s.errClaim;
+          sa.err = s.err;
+          sa.abortFlag = s.abortFlag;
+          sa.inplaceMask = q->inplaceMask;
+          sa.downOffset = 0;
+          sa.coll = q->coll;
+          sa.algo = kRing;
+          sa.redop = q->redop;
+          sa.nranks = q->nranks;
+          sa.nsub = q->nsub;
+          sa.root = q->root;
+          sa.nsteps = s.nsteps;
+          sa.upThreads = (blockDim.x / 2) / 32 * 32;
+          sa.skipRank = -1;
+          for (int i = 0; i < q->nranks; i++) {
+            sa.send[i] = (const void*)q->send[i];
+            sa.recv[i] = (void*)q->recv[i];
+          }
+        }
+      }
+      sUse = use;
+      sCh = ch;
+      sR = r;
+    }
+    __syncthreads();
+    if (sStop) return;
+    ch = sCh;
+    r = sR;
+    if (sUse) {
+      const int proto = sa.coll == kCopy ? kSimple : ((const volatile ServeReq*)&G->req)->proto;
+      const int dtype = ((const volatile ServeReq*)&G->req)->dtype;
+      const bool bytes = (sa.coll == kAllGather || sa.coll == kBroadcast ||
+                          (sa.coll == kCopy && dtype < 0));
+      dispatchOp(sa, proto, dtype, bytes, r, ch, sAbort);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(&G->arrive, 1ull);
+      if (leader) {
+        const uint64_t t0 = globaltimer();
+        bool ok = true;
+        while (ldAcquire(&G->arrive) < seq * nctas) {
+          if (globaltimer() - t0 > s.timeoutNs) { ok = false; break; }
+        }
+        const int failed = (!ok || sAbort[0] || sAbort[1] || *s.errClaim) ? 1 : 0;
+        slot->tEnd = globaltimer();
+        if (failed) slot->err = 1;
+        __threadfence_system();
+        slot->done = seq;
+        __threadfence_system();
+        if (failed) stRelease(&G->goSeq, ~0ull);
+        sStop = failed;
+      } else {
+        sStop = (sAbort[0] || sAbort[1]) ? 1 : 0;
+      }
+    }
+    __syncthreads();
+    if (sStop) return;
+  }
+}
+
 const void* batchKernel() { return (const void*)kBatch; }
+const void* serveKernel() { return (const void*)kServe; }
 
 }  // namespace vc

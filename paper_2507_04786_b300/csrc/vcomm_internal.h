@@ -108,6 +108,52 @@ struct BatchArgs {
   const void* ptrs[kMaxBatchPtrs];
 };
 
+// ---- serving: a persistent kernel whose gangs take requests from host-mapped
+// mailboxes (continuous batching).  Gang g owns CTAs [gangCta[g], gangCta[g+1])
+// laid out as gangCpg[g] channels x kmax vranks and ring connections
+// [gangConn[g], gangConn[g] + gangCpg[g] * kmax) of each protocol arena.
+constexpr int kServeMaxRanks = 16;
+constexpr int kMaxServeGangs = 16;
+
+struct ServeReq {
+  int coll, proto, dtype, redop, nranks, nsub, root, pad;
+  unsigned long long count, chunk, slotUnits, slotBytes, inplaceMask;
+  const void* send[kServeMaxRanks];
+  void* recv[kServeMaxRanks];
+};
+
+struct ServeSlot {                   // host-mapped mailbox of one gang
+  unsigned long long seq;            // host: requests posted so far
+  unsigned long long done;           // device: requests completed so far
+  unsigned long long tStart, tEnd;   // device %globaltimer of the last request
+  unsigned long long err;            // device: nonzero once the gang stopped on a failure
+  unsigned long long pad[3];
+  ServeReq req;                      // the posted request (valid while seq > done)
+};
+
+struct ServeGang {                   // device memory, one per gang
+  unsigned long long goSeq;          // leader -> gang: request `goSeq` is in req (~0: stop)
+  unsigned long long pad0[15];
+  unsigned long long arrive;         // gang barrier: CTAs that finished, cumulative
+  unsigned long long pad1[15];
+  ServeReq req;
+};
+
+struct ServeArgs {
+  ServeSlot* slots;
+  ServeGang* gangs;
+  const volatile int* shutdown;      // host-mapped
+  int* errClaim;
+  ErrWord* err;
+  const volatile int* abortFlag;
+  unsigned long long timeoutNs, idleTimeoutNs;
+  ConnDev* conns[3];                 // ring arena per protocol
+  int ngangs, kmax, nsteps, pad;
+  int gangCta[kMaxServeGangs + 1];
+  int gangCpg[kMaxServeGangs];
+  int gangConn[kMaxServeGangs];
+};
+
 // ---- channel partition (Sec. V-C): 16-byte packs spread over `nch` ranges,
 // the first (packs % nch) ranges one pack longer, the element tail on the last.
 VC_HD void channelRange(unsigned long long n, int unitBytes, int nch, int ch,

@@ -14,4 +14,6 @@ const void* debugDecodeKernel();
 namespace vc {
 // the batched-launch kernel (vcomm_batch.cu); its parameter is a BatchArgs
 const void* batchKernel();
+// the persistent serving kernel (vcomm_batch.cu); its parameter is a ServeArgs
+const void* serveKernel();
 }  // namespace vc

@@ -34,6 +34,30 @@ EXACT = {
     "seed": 0,
 }
 
+# 64 concurrent AllReduce calls in one persistent launch (group + CUDA graph)
+BATCHED = {
+    "name": "batched-64-allreduce-8vr-4KiB-64MiB",
+    "nranks": 8,
+    "nops": 64,
+    "lo_bytes": 4 * KiB,
+    "hi_bytes": 64 * MiB,
+    "nchannels": 37,
+    "seed": 3,
+}
+
+# Poisson stream of AllReduce / ReduceScatter / AllGather requests
+SERVED = {
+    "name": "served-poisson-2000rps-2to16vr-1KiB-128MiB",
+    "rate_per_s": 2000.0,
+    "max_ranks": 16,
+    "lo_bytes": 1 * KiB,
+    "hi_bytes": 128 * MiB,
+    "budget_bytes": 40 * (1 << 30),
+    "requests": 100_000,
+    "bench_requests": 20_000,     # default bench run: 10 s of arrivals per mode
+    "seed": 4,
+}
+
 # per-rank message sizes of the protocol sweep: 1 KiB .. 256 MiB in powers of 4
 SWEEP_BYTES = [KiB * 4 ** i for i in range(10)]
 SWEEP_CHANNELS = (1, 4, 16, 32)
