@@ -580,14 +580,21 @@ struct Prims {
               if (lv[u]) ldVolatile2(rs + 128ull * line + 16 * j, w0[u], w1[u]);
             }
           }
+          // one vote for all lines of the round; flag lanes (j == 7) decide
+          bool ok = true;
+#pragma unroll
+          for (int u = 0; u < U; u++) ok = ok && (!lv[u] || j != 7 || w1[u] == rf);
+          if (!__all_sync(0xffffffffu, ok)) {
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+              const uint32_t line = 4 * (q0 + (uint32_t)u * nwarps) + (lane >> 3);
+              if (fail) continue;   // warp-uniform
+              if (!ll128Ready(a, rs, line, lane, lv[u], rf, w0[u], w1[u], sAbort, rank, ch)) fail = true;
+            }
+          }
+          if (fail) break;
 #pragma unroll
           for (int u = 0; u < U; u++) {
-            const uint32_t line = 4 * (q0 + (uint32_t)u * nwarps) + (lane >> 3);
-            if (fail) continue;   // warp-uniform
-            if (!ll128Ready(a, rs, line, lane, lv[u], rf, w0[u], w1[u], sAbort, rank, ch)) {
-              fail = true;
-              continue;
-            }
             if (doLocal || i > 0) {
               v0[u] = applyWord<T, Op>(w0[u], v0[u]);
               v1[u] = applyWord<T, Op>(w1[u], v1[u]);
