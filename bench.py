@@ -383,6 +383,63 @@ def run_served(args):
             "per_call": out["plain"]}
 
 
+# ------------------------------------------------------------------ protocol sweep
+
+def run_sweep(path):
+    """Ring AllReduce on 8 vranks: per-rank sizes 1 KiB..256 MiB (powers of
+    4) x fp32 / bf16 x Simple / LL / LL128 x 1 / 4 / 16 / 32 channels, N(0,1)
+    values; one JSON line per point (median of timed launches)."""
+    import torch
+
+    from paper_2507_04786_b300 import Comm
+    k = 8
+    top = max(workloads.SWEEP_BYTES)
+    base = {dt: [torch.randn(top // es, device="cuda").to(t) for _ in range(k)]
+            for dt, es, t in (("fp32", 4, torch.float32), ("bf16", 2, torch.bfloat16))}
+    outs = {dt: [torch.empty_like(x) for x in xs] for dt, xs in base.items()}
+    comm = Comm(k, max(workloads.SWEEP_CHANNELS))
+    rows = []
+    with open(path, "w") as f:
+        for dt in ("fp32", "bf16"):
+            es = 4 if dt == "fp32" else 2
+            for S in workloads.SWEEP_BYTES:
+                n = S // es
+                xs = [x[:n] for x in base[dt]]
+                ys = [y[:n] for y in outs[dt]]
+                for proto in ("simple", "ll", "ll128"):
+                    for C in workloads.SWEEP_CHANNELS:
+                        comm.set_plan(nchannels=C, chunk_steps=1)
+                        for _ in range(2):
+                            comm.all_reduce(xs, ys, algo="ring", proto=proto)
+                        torch.cuda.synchronize()
+                        reps = 5 if S >= (16 << 20) else 20
+                        ts = []
+                        for _ in range(reps):
+                            e0 = torch.cuda.Event(enable_timing=True)
+                            e1 = torch.cuda.Event(enable_timing=True)
+                            e0.record()
+                            comm.all_reduce(xs, ys, algo="ring", proto=proto)
+                            e1.record()
+                            e1.synchronize()
+                            ts.append(e0.elapsed_time(e1))
+                        ms = float(np.median(ts))
+                        alg = algorithmic_bytes(k, S, proto)
+                        row = {"dtype": dt, "bytes_per_rank": S, "proto": proto, "nchannels": C,
+                               "us": round(ms * 1e3, 2), "busbw_GBps": round(busbw(S, k, ms / 1e3), 2),
+                               "hbm_frac": round(alg / (ms / 1e3) / 1e9 / measured_peak()[0], 4)}
+                        rows.append(row)
+                        f.write(json.dumps(row) + "\n")
+    assert comm.async_error() == "vSuccess"
+    comm.destroy()
+    # best per (dtype, size)
+    best = {}
+    for r in rows:
+        key = (r["dtype"], r["bytes_per_rank"])
+        if key not in best or r["us"] < best[key]["us"]:
+            best[key] = r
+    return [best[k_] for k_ in sorted(best)]
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -410,11 +467,18 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=workloads.SERVED["bench_requests"],
                     help="requests of the served leg (the full stream is 100000)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and served legs")
+    ap.add_argument("--sweep", default=None,
+                    help="run the protocol x size x channel sweep, write JSON lines here, exit")
     ap.add_argument("--bytes", type=int, default=workloads.HEADLINE["bytes_per_rank"],
                     help="bytes per vrank (default: the headline's 256 MiB; smaller sizes are "
                          "for profiling captures only)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+
+    if args.sweep:
+        for r in run_sweep(args.sweep):
+            print(json.dumps(r))
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
