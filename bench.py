@@ -447,13 +447,21 @@ def barrier(world):
 
 
 def reduce_max(world, x):
+    """The slowest replica's value (the job's time is the max over ranks)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(world, S, k, max_ms):
+    """Whole-job bus bandwidth: every replica moved S per vrank; the job took
+    the slowest replica's time."""
+    return world * busbw(S, k, max_ms / 1e3)
 
 
 def main():
@@ -526,7 +534,7 @@ def main():
     e2e_ms = reduce_max(world, r["e2e_ms"])
     if rank != 0:
         return
-    value = world * busbw(S, k, ms / 1e3)
+    value = job_value(world, S, k, ms)
     peak, peak_kind = measured_peak()
     alg = algorithmic_bytes(k, S, args.proto)
     achieved = alg / (launch_ms / 1e3) / 1e9

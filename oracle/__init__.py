@@ -89,6 +89,8 @@ def lib():
         L.o_ll128_decode.argtypes = [vp, sz, ctypes.c_uint64, vp]
         for f in ("o_ring_allreduce_point", "o_tree_allreduce_point"):
             getattr(L, f).argtypes = [i32, i32, sz, i32, i32, sz, sz, vp, vp]
+        L.o_ring_reducescatter_point.argtypes = [i32, i32, i32, i32, vp, vp]
+        L.o_ring_reduce_point.argtypes = [i32, i32, i32, i32, vp, vp]
         L.o_f64_to_f16.restype = ctypes.c_uint16
         L.o_f64_to_f16.argtypes = [ctypes.c_double]
         L.o_f64_to_bf16.restype = ctypes.c_uint16
@@ -333,3 +335,27 @@ def all_reduce_points(xs, idx, dtype: str, op: str, nch: int, chunk: int, algo: 
         assert rc == 0
         out[m] = one[0]
     return out
+
+
+def _fold_points(f, xs, idx, dtype, op, extra, offset=0):
+    k = len(xs)
+    out = np.empty(len(idx), dtype=xs[0].dtype)
+    vals = np.empty(k, dtype=xs[0].dtype)
+    one = np.empty(1, dtype=xs[0].dtype)
+    for m, i in enumerate(idx):
+        for r in range(k):
+            vals[r] = xs[r][offset + i]
+        assert f(k, DTYPES[dtype], OPS[op], extra, vals.ctypes.data, one.ctypes.data) == 0
+        out[m] = one[0]
+    return out
+
+
+def reduce_scatter_points(xs, b, idx, dtype: str, op: str):
+    """Elements `idx` of rank b's ReduceScatter output (block b), one at a time."""
+    n = xs[0].size // len(xs)
+    return _fold_points(lib().o_ring_reducescatter_point, xs, idx, dtype, op, b, offset=b * n)
+
+
+def reduce_points(xs, root: int, idx, dtype: str, op: str):
+    """Elements `idx` of the Reduce result at `root`, one at a time."""
+    return _fold_points(lib().o_ring_reduce_point, xs, idx, dtype, op, root)

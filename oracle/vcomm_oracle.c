@@ -725,3 +725,26 @@ int o_tree_allreduce_point(int k, int nch, size_t chunk, int dt, int op, size_t 
   }
   return -1;
 }
+
+/* ring ReduceScatter: element i of rank b's output folds block b in the
+ * order x_{b+1}, ..., x_b (the partition does not change the order) */
+int o_ring_reducescatter_point(int k, int dt, int op, int b, const void* vals, void* out) {
+  int es = o_dtype_size(dt);
+  if (k < 1 || b < 0 || b >= k) return -1;
+  char acc[8];
+  memcpy(acc, (const char*)vals + (size_t)es * (size_t)o_mod(b + 1, k), (size_t)es);
+  for (int m = 2; m <= k; m++) o_reduce_elem(dt, op, acc, 0, vals, (size_t)o_mod(b + m, k), acc, 0);
+  memcpy(out, acc, (size_t)es);
+  return 0;
+}
+
+/* ring Reduce: the chain root+1, ..., root */
+int o_ring_reduce_point(int k, int dt, int op, int root, const void* vals, void* out) {
+  int es = o_dtype_size(dt);
+  if (k < 1 || root < 0 || root >= k) return -1;
+  char acc[8];
+  memcpy(acc, (const char*)vals + (size_t)es * (size_t)o_mod(root + 1, k), (size_t)es);
+  for (int m = 2; m <= k; m++) o_reduce_elem(dt, op, acc, 0, vals, (size_t)o_mod(root + m, k), acc, 0);
+  memcpy(out, acc, (size_t)es);
+  return 0;
+}

@@ -415,3 +415,20 @@ def test_point_queries_match_replay(algo, k, C, chunk, n, dtype, op):
     full = oracle.all_reduce(xs, dtype, op, C, chunk, algo)[0]
     pts = oracle.all_reduce_points(xs, np.arange(n), dtype, op, C, chunk, algo)
     assert np.array_equal(pts.view(np.uint8), full.view(np.uint8))
+
+
+@pytest.mark.parametrize("k,C,chunk,n", [(2, 1, 8, 40), (3, 2, 16, 333), (8, 3, 64, 4001)])
+@pytest.mark.parametrize("dtype,op", [("fp16", "sum"), ("bf16", "max"), ("int32", "sum")])
+def test_rs_and_reduce_point_queries_match_replay(k, C, chunk, n, dtype, op):
+    dist = "int" if dtype == "int32" else "normal"
+    kw = {"lo": -2 ** 31, "hi": 2 ** 31 - 1} if dtype == "int32" else {}
+    xs = inputs.workload(31, k, k * n, dtype, dist, **kw)
+    rs = oracle.reduce_scatter(xs, dtype, op, C, chunk)
+    for b in range(k):
+        pts = oracle.reduce_scatter_points(xs, b, np.arange(n), dtype, op)
+        assert np.array_equal(pts.view(np.uint8), rs[b].view(np.uint8))
+    ys = [x[:n].copy() for x in xs]
+    for root in (0, k - 1):
+        full = oracle.reduce(ys, dtype, op, root, C, chunk)
+        pts = oracle.reduce_points(ys, root, np.arange(n), dtype, op)
+        assert np.array_equal(pts.view(np.uint8), full.view(np.uint8))
