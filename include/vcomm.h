@@ -55,7 +55,15 @@ typedef enum {
 typedef enum { vInt32 = 0, vFloat32 = 1, vFloat16 = 2, vBfloat16 = 3 } vDataType_t;
 typedef enum { vSum = 0, vMax = 1 } vRedOp_t;
 typedef enum { vAlgoAuto = 0, vAlgoRing = 1, vAlgoTree = 2 } vAlgo_t;
-typedef enum { vProtoAuto = 0, vProtoSimple = 1, vProtoLL = 2, vProtoLL128 = 3 } vProto_t;
+/* vProtoCluster has no counterpart in the paper: the LL line format of
+ * Sec. III-B (4 data bytes + a 4-byte flag per 8-byte store) carried in
+ * distributed shared memory instead of global memory.  Each channel's vranks
+ * run as one thread-block cluster (CTA r = vrank r) and every FIFO lives in
+ * its receiver's shared memory: 4 slots of 8 KiB (4 KiB of data) per
+ * connection.  It needs nranks <= 16 (the largest cluster) and is taken only
+ * when asked for, pinned or chosen by vcommTune; a group of several calls and
+ * the serving API run it as LL. */
+typedef enum { vProtoAuto = 0, vProtoSimple = 1, vProtoLL = 2, vProtoLL128 = 3, vProtoCluster = 4 } vProto_t;
 
 #define VCOMM_MAX_RANKS 64
 #define VCOMM_MAX_CHANNELS 64

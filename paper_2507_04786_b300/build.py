@@ -32,6 +32,7 @@ CFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler",
 RDC = ["-rdc=true", "-maxrregcount=128"]
 RDC_UNITS = ("vcomm_batch.cu", "vcomm_batch_inst.cu")
 PER_PAIR = ("vcomm_reduce_inst.cu", "vcomm_batch_inst.cu")
+PER_DTYPE = ("vcomm_cluster_inst.cu",)
 
 
 def units():
@@ -40,7 +41,10 @@ def units():
     for src in sorted(glob.glob(os.path.join(CSRC, "*.cu"))):
         base = os.path.splitext(os.path.basename(src))[0]
         extra = RDC if os.path.basename(src) in RDC_UNITS else []
-        if os.path.basename(src) in PER_PAIR:
+        if os.path.basename(src) in PER_DTYPE:
+            for d in range(4):
+                out.append((src, os.path.join(OBJ, f"{base}_{d}.o"), extra + [f"-DVC_DTYPE={d}"]))
+        elif os.path.basename(src) in PER_PAIR:
             for p in range(3):
                 for d in range(4):
                     out.append((src, os.path.join(OBJ, f"{base}_{p}_{d}.o"),

@@ -247,7 +247,7 @@ vResult_t vcommSetPlan(vcomm_t c, const vPlan_t* plan) {
   if (!c) return vInvalidArgument;
   if (!plan) { c->pinned = false; return vSuccess; }
   if (plan->algo < vAlgoAuto || plan->algo > vAlgoTree || plan->proto < vProtoAuto ||
-      plan->proto > vProtoLL128 || plan->nchannels < 0 || plan->nchannels > c->nch ||
+      plan->proto > vProtoCluster || plan->nchannels < 0 || plan->nchannels > c->nch ||
       plan->chunkSteps < 0 || plan->chunkSteps > 64)
     return vInvalidArgument;
   c->pin = *plan;
@@ -332,7 +332,7 @@ static vResult_t prepareCall(int coll, const void* const* sendbufs, void* const*
   if (dtype < vInt32 || dtype > vBfloat16) return vInvalidArgument;
   if ((coll == kAllReduce || coll == kReduceScatter || coll == kReduce) && (op < vSum || op > vMax))
     return vInvalidArgument;
-  if (algo < vAlgoAuto || algo > vAlgoTree || proto < vProtoAuto || proto > vProtoLL128)
+  if (algo < vAlgoAuto || algo > vAlgoTree || proto < vProtoAuto || proto > vProtoCluster)
     return vInvalidArgument;
   const int k = c->k;
   if ((coll == kBroadcast || coll == kReduce) && (root < 0 || root >= k)) return vInvalidArgument;
@@ -394,9 +394,13 @@ static vResult_t prepareCall(int coll, const void* const* sendbufs, void* const*
   // after the receiver's own send: if one chunk fills every slot of every
   // ring connection (chunkSteps >= nsteps), each rank waits for a credit from
   // its successor -- a cycle.  Ring collectives need chunkSteps < nsteps.
-  if (plan.algo == vAlgoRing && k > 1 && plan.chunkSteps >= c->nsteps) {
+  // The cluster protocol (one cluster of k CTAs per channel) exists for
+  // clusters of up to 16 CTAs, and its FIFOs have kClusterSlots slots.
+  if (plan.proto == vProtoCluster && k > 16) return vUnsupported;
+  const int fifoSlots = (plan.proto == vProtoCluster) ? kClusterSlots : c->nsteps;
+  if (plan.algo == vAlgoRing && k > 1 && plan.chunkSteps >= fifoSlots) {
     if (c->pinned && c->pin.chunkSteps > 0) return vUnsupported;
-    plan.chunkSteps = c->nsteps - 1;
+    plan.chunkSteps = fifoSlots - 1;
   }
   cs->c = c;
   cs->coll = coll;
@@ -436,7 +440,81 @@ static vResult_t needArena(vcomm* c, int al, int pr, cudaStream_t s) {
   return ensureArena(c, al, pr);
 }
 
+// The cluster protocol: grid k * nsub CTAs in clusters of k (cluster = one
+// channel, CTA r of it = vrank r), each with its FIFOs in dynamic shared
+// memory.  Clusters never wait on one another, so no co-residency is needed
+// beyond one cluster at a time, which the launch itself guarantees.
+static vResult_t launchCluster(CallSpec& cs) {
+  vcomm* c = cs.c;
+  const int k = c->k;
+  vPlan_t& plan = cs.plan;
+  const void* fn = cs.bytesUnits ? clusterCopyKernel() : clusterKernel(cs.dtype, cs.redop);
+  if (!fn) return vInternalError;
+  {
+    // once per kernel: opt in to the dynamic shared memory and to clusters
+    // of more than 8 CTAs
+    static std::mutex mu;
+    static std::vector<const void*> ready;
+    std::lock_guard<std::mutex> g(mu);
+    if (std::find(ready.begin(), ready.end(), fn) == ready.end()) {
+      VC_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kClusterSmemBytes));
+      VC_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+      ready.push_back(fn);
+    }
+  }
+  const int nsub = (cs.al == kTree) ? 2 * plan.nchannels : plan.nchannels;
+  const int nthr = std::min(c->nthreads, maxThreadsFor(kCluster));
+  const int unitBytes = cs.bytesUnits ? 1 : dtypeSize(cs.dtype);
+
+  KernArgs a;
+  memset(&a, 0, sizeof(a));
+  for (int r = 0; r < k; r++) {
+    a.send[r] = cs.send[r];
+    a.recv[r] = cs.recv[r];
+  }
+  a.count = cs.units;
+  a.slotBytes = kClusterSlotBytes;
+  a.slotUnits = (kClusterSlotBytes / 2) / unitBytes;
+  a.chunk = chunkUnits(kLL, kClusterSlotBytes, plan.chunkSteps, unitBytes);
+  a.timeoutNs = (unsigned long long)(c->timeoutSec * 1e9);
+  a.conns = nullptr;
+  a.errClaim = c->dClaim;
+  a.err = c->dErr;
+  a.abortFlag = c->dAbort;
+  a.inplaceMask = cs.inplace;
+  a.coll = cs.kcoll;
+  a.algo = cs.al;
+  a.redop = cs.redop;
+  a.nranks = k;
+  a.nsub = nsub;
+  a.root = cs.root;
+  a.nsteps = kClusterSlots;
+  a.upThreads = (nthr / 2) / 32 * 32;
+  a.skipRank = c->skipRank;
+
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(k * nsub));
+  cfg.blockDim = dim3((unsigned)nthr);
+  cfg.dynamicSmemBytes = kClusterSmemBytes;
+  cfg.stream = cs.stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)k;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int fit = 0;
+  VC_TRY(cudaOccupancyMaxActiveClusters(&fit, fn, &cfg));
+  if (fit < 1) return vUnsupported;
+  void* args[] = {(void*)&a};
+  VC_TRY(cudaLaunchKernelExC(&cfg, fn, args));
+  c->last = plan;
+  return vSuccess;
+}
+
 static vResult_t launchSingle(CallSpec& cs) {
+  if (cs.pr == kCluster) return launchCluster(cs);
   vcomm* c = cs.c;
   const int k = c->k;
   vPlan_t& plan = cs.plan;
@@ -533,8 +611,10 @@ static vResult_t launchGroup(vcomm* c, std::vector<CallSpec>& ops) {
     else if (G > 1) { G--; cpg = c->nch / G; }
     else return vUnsupported;
   }
-  // fit each op's plan into a gang
+  // fit each op's plan into a gang (the batch kernel has no cluster
+  // protocol: such ops run as LL)
   for (auto& o : ops) {
+    if (o.pr == kCluster) { o.pr = kLL; o.plan.proto = vProtoLL; }
     if (o.kcoll == kCopy) {
       o.plan.nchannels = std::min(o.plan.nchannels, cpg);
       continue;
@@ -664,7 +744,9 @@ static vResult_t tuneOne(vcomm* c, int coll, size_t S, char* sbuf, char* rbuf, s
   const bool savedPinned = c->pinned;
   const vPlan_t savedPin = c->pin;
   for (int al = 0; al < ((coll == kAllReduce && k > 2) ? 2 : 1); al++) {
-    for (int pr = 0; pr < 3; pr++) {
+    for (int pr = 0; pr < 4; pr++) {
+      // the cluster protocol is a small-message protocol on <= 16 vranks
+      if (pr == kCluster && (k > 16 || S > ((size_t)4 << 20))) continue;
       for (int ch : chans) {
         vPlan_t p{al ? vAlgoTree : vAlgoRing, (vProto_t)(pr + 1), ch, 1};
         c->pin = p;

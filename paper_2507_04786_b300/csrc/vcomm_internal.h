@@ -27,7 +27,7 @@ namespace vc {
 enum Coll : int { kAllReduce = 0, kReduceScatter = 1, kAllGather = 2, kBroadcast = 3, kReduce = 4,
                   kCopy = 5 };
 enum Algo : int { kRing = 0, kTree = 1 };
-enum Proto : int { kSimple = 0, kLL = 1, kLL128 = 2 };
+enum Proto : int { kSimple = 0, kLL = 1, kLL128 = 2, kCluster = 3 };
 enum DType : int { kI32 = 0, kF32 = 1, kF16 = 2, kBF16 = 3 };
 enum OpKind : int { kSum = 0, kMax = 1 };
 
@@ -36,8 +36,9 @@ constexpr int kCounterStride = 16;
 // Largest CTA each protocol's kernels are compiled for; the register budget
 // per thread is 65536 / that.  Simple streams 16-byte vectors with several
 // loads in flight per thread and wants 128 registers (no spills); LL and
-// LL128 poll flags line by line and want more warps instead.
-constexpr int maxThreadsFor(int proto) { return proto == 0 ? 512 : 1024; }  // u64 words between counters (128 bytes)
+// LL128 poll flags line by line and want more warps instead.  A cluster-
+// protocol FIFO step is at most 512 line pairs: one per thread of 512.
+constexpr int maxThreadsFor(int proto) { return proto == kLL || proto == kLL128 ? 1024 : 512; }
 
 struct ConnDev {
   char* buf;                       // nsteps slots of slotBytes

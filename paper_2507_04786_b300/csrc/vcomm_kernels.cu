@@ -115,6 +115,19 @@ const void* copyKernel(int proto) {
   return nullptr;
 }
 
+#define VC_CDECL(D) const void* clusterKernel_##D(int op);
+VC_CDECL(0) VC_CDECL(1) VC_CDECL(2) VC_CDECL(3)
+#undef VC_CDECL
+const void* clusterKernel(int dtype, int op) {
+  switch (dtype) {
+    case 0: return clusterKernel_0(op);
+    case 1: return clusterKernel_1(op);
+    case 2: return clusterKernel_2(op);
+    case 3: return clusterKernel_3(op);
+  }
+  return nullptr;
+}
+
 const void* debugEncodeKernel() { return (const void*)kDebugEncode; }
 const void* debugDecodeKernel() { return (const void*)kDebugDecode; }
 

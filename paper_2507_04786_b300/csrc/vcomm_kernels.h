@@ -7,6 +7,12 @@ namespace vc {
 const void* reduceKernel(int proto, int dtype, int op);
 // persistent byte-moving kernel for AllGather, Broadcast and the single-rank copy
 const void* copyKernel(int proto);
+// cluster protocol (vcomm_cluster_inst.cu): one cluster of nranks CTAs per channel
+const void* clusterKernel(int dtype, int op);
+const void* clusterCopyKernel();
+constexpr int kClusterSmemBytes = 3 * 4 * 8192 + 256;   // == kCSmemBytes
+constexpr int kClusterSlotBytes = 8192;                 // == kCSlotBytes
+constexpr int kClusterSlots = 4;                        // == kCSlots
 const void* debugEncodeKernel();
 const void* debugDecodeKernel();
 }  // namespace vc
