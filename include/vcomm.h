@@ -60,9 +60,9 @@ typedef enum { vAlgoAuto = 0, vAlgoRing = 1, vAlgoTree = 2 } vAlgo_t;
  * distributed shared memory instead of global memory.  Each channel's vranks
  * run as one thread-block cluster (CTA r = vrank r) and every FIFO lives in
  * its receiver's shared memory: 4 slots of 8 KiB (4 KiB of data) per
- * connection.  It needs nranks <= 16 (the largest cluster) and is taken only
- * when asked for, pinned or chosen by vcommTune; a group of several calls and
- * the serving API run it as LL. */
+ * connection.  It needs nranks <= 16 (the largest cluster); Auto picks it up
+ * to 256 KiB per rank on 2..16 vranks, where its latency is lowest; a group
+ * of several calls and the serving API run it as LL. */
 typedef enum { vProtoAuto = 0, vProtoSimple = 1, vProtoLL = 2, vProtoLL128 = 3, vProtoCluster = 4 } vProto_t;
 
 #define VCOMM_MAX_RANKS 64
@@ -183,7 +183,8 @@ vResult_t vcommGetGroupPlans(vcomm_t comm, vPlan_t* plans, int maxPlans, int* nP
 /* ---- autotuner ------------------------------------------------------------
  * Protocol / algorithm / channel selection (Sec. III-D; Sec. II-C: "the tuning
  * model determines how many channels"): times every candidate plan
- * (ring/tree x Simple/LL/LL128 x channels 1, 2, 4, ... nch) on this device at
+ * (ring/tree x Simple/LL/LL128 x channels 1, 2, 4, ... nch, plus the cluster
+ * protocol up to 4 MiB on <= 16 vranks) on this device at
  * per-rank sizes 1 KiB x 4^i <= maxBytes for each collective whose bit is set
  * in collMask (bit 0 AllReduce, 1 ReduceScatter, 2 AllGather, 3 Broadcast,
  * 4 Reduce) and keeps the fastest per size.  Later calls with Auto arguments

@@ -265,11 +265,13 @@ vResult_t vcommGetLastPlan(vcomm_t c, vPlan_t* plan) {
 
 // ------------------------------------------------------------------ planning
 // Default tuning (used where neither the call nor a pin fixes a choice and the
-// communicator has not been tuned): LL below 64 KiB, LL128 below 2 MiB,
-// Simple above (Sec. III-D: LL/LL128 for small messages, Simple for large);
-// tree AllReduce up to 256 KiB (Sec. V-F: tree best for small, ring for
-// large); about 1 MiB of message per channel.  A tuned communicator takes
-// each Auto field from its measured table at the nearest size (log scale).
+// communicator has not been tuned): up to 256 KiB the cluster protocol on
+// <= 16 vranks (else LL below 64 KiB), LL128 below 2 MiB, Simple above
+// (Sec. III-D: LL/LL128 for small messages, Simple for large); tree AllReduce
+// up to 256 KiB (Sec. V-F: tree best for small, ring for large); about 1 MiB
+// of message per channel, 4 KiB for the cluster protocol (at most 64 / k
+// clusters: a cluster of 16 CTAs takes most of a GPC).  A tuned communicator
+// takes each Auto field from its measured table at the nearest size.
 static void defaultPlan(const vcomm* c, int coll, size_t bytes, vPlan_t* p) {
   if (coll >= 0 && coll < 5 && c->tuned[coll]) {
     int best = -1;
@@ -288,11 +290,16 @@ static void defaultPlan(const vcomm* c, int coll, size_t bytes, vPlan_t* p) {
       if (p->chunkSteps <= 0) p->chunkSteps = t.chunkSteps;
     }
   }
-  if (p->proto == vProtoAuto) p->proto = bytes < (64u << 10) ? vProtoLL : bytes < (2u << 20) ? vProtoLL128 : vProtoSimple;
+  if (p->proto == vProtoAuto) {
+    if (c->k >= 2 && c->k <= 16 && bytes <= (256u << 10)) p->proto = vProtoCluster;
+    else p->proto = bytes < (64u << 10) ? vProtoLL : bytes < (2u << 20) ? vProtoLL128 : vProtoSimple;
+  }
   if (p->algo == vAlgoAuto) p->algo = (coll == kAllReduce && bytes <= (256u << 10) && c->k > 2) ? vAlgoTree : vAlgoRing;
   if (p->nchannels <= 0) {
-    size_t per = (size_t)1 << 20;
+    const bool cl = (p->proto == vProtoCluster);
+    size_t per = cl ? ((size_t)4 << 10) : ((size_t)1 << 20);
     size_t n = (bytes + per - 1) / per;
+    if (cl) n = std::min<size_t>(n, (size_t)std::max(1, 64 / c->k));
     if (p->algo == vAlgoTree) n = (n + 1) / 2;
     p->nchannels = (int)std::max<size_t>(1, std::min<size_t>(n, (size_t)c->nch));
   }
@@ -504,9 +511,20 @@ static vResult_t launchCluster(CallSpec& cs) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  int fit = 0;
-  VC_TRY(cudaOccupancyMaxActiveClusters(&fit, fn, &cfg));
-  if (fit < 1) return vUnsupported;
+  {
+    // does one cluster fit at all (k SMs of one GPC)?  Asked once per shape.
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> fits;
+    std::lock_guard<std::mutex> g(mu);
+    auto key = std::make_pair(fn, k * 2048 + nthr);
+    auto it = fits.find(key);
+    if (it == fits.end()) {
+      int fit = 0;
+      VC_TRY(cudaOccupancyMaxActiveClusters(&fit, fn, &cfg));
+      it = fits.emplace(key, fit).first;
+    }
+    if (it->second < 1) return vUnsupported;
+  }
   void* args[] = {(void*)&a};
   VC_TRY(cudaLaunchKernelExC(&cfg, fn, args));
   c->last = plan;

@@ -3,6 +3,7 @@ every collective through the C ABI against the CPU oracle, bit-exact.
 
 To the oracle the cluster protocol is LL with 8 KiB slots (4 KiB of data per
 FIFO step): the partition, the step tables and the fold order are the same.
+Auto plans pick it on 2..16 vranks up to 256 KiB per rank.
 Sizes span one to many FIFO steps, several chunks and ragged tails, on 2 to
 16 vranks (16 is the largest cluster).
 """
@@ -20,7 +21,6 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-CLUSTER_SLOT = {"ll": 8192}
 DIST = {"fp32": ("normal", {}), "bf16": ("normal", {}), "fp16": ("uniform", {}),
         "int32": ("int", {"lo": -2 ** 20, "hi": 2 ** 20})}
 SIZES = [1, 5, 1023, 1025, 3 * 4096 + 7, 50003]
@@ -49,7 +49,7 @@ def data(seed, k, n, dtype):
 
 
 def chunk(dtype, steps, byte_units=False):
-    return chunk_for("ll", dtype, CLUSTER_SLOT, steps, byte_units=byte_units)
+    return chunk_for("cluster", dtype, None, steps, byte_units=byte_units)
 
 
 def finish(c):
