@@ -32,7 +32,9 @@ sys.path.insert(0, ROOT)
 
 from paper_2507_04786_b300 import inputs, workloads  # noqa: E402
 
-FIFO_FACTOR = {"simple": 1.0, "ll": 2.0, "ll128": 128.0 / 120.0}
+# FIFO bytes in HBM per data byte; the cluster protocol's FIFOs are in shared
+# memory and move no HBM bytes
+FIFO_FACTOR = {"simple": 1.0, "ll": 2.0, "ll128": 128.0 / 120.0, "cluster": 0.0}
 
 
 def algorithmic_bytes(k, S, proto):
@@ -306,6 +308,94 @@ def run_batched(args):
             "tune_seconds": round(tune_s, 1), "status": err}
 
 
+# ------------------------------------------------------------------ small-message leg
+
+def run_small(args):
+    """Latency of small collectives (the flag round-trip bound regime):
+    each collective at 1 KiB and 64 KiB per rank on 8 and 16 vranks, with the
+    library's Auto plan and with the paper's LL / LL128 protocols forced (at
+    their best channel count).  Device time per call: a CUDA graph of 10
+    calls, median of 21 replays."""
+    import torch
+
+    from paper_2507_04786_b300 import Comm
+    w = workloads.SMALL
+    reps_in_graph, replays = 10, 21
+
+    def call(c, coll, a, b, proto, s):
+        algo = "auto" if (coll == "allreduce" and proto == "auto") else (
+            "tree" if coll == "allreduce" else "ring")
+        if coll == "allreduce":
+            c.all_reduce(a, b, algo=algo, proto=proto, stream=s)
+        elif coll == "reducescatter":
+            c.reduce_scatter(a, b, algo="ring", proto=proto, stream=s)
+        elif coll == "allgather":
+            c.all_gather(a, b, algo="ring", proto=proto, stream=s)
+        elif coll == "broadcast":
+            c.broadcast(a, b, root=0, algo="ring", proto=proto, stream=s)
+        else:
+            c.reduce(a, b, root=0, algo="ring", proto=proto, stream=s)
+
+    def graph_us(c, coll, a, b, proto):
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                call(c, coll, a, b, proto, stream)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            for _ in range(reps_in_graph):
+                call(c, coll, a, b, proto, stream)
+        g.replay()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(replays):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.replay()
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e3 / reps_in_graph)
+        return round(float(np.median(ts)), 2)
+
+    rows = []
+    for k in w["nranks"]:
+        big = [torch.randn(max(w["bytes"]) // 4, device="cuda") for _ in range(k)]
+        out = [torch.empty_like(x) for x in big]
+        c = Comm(k, w["nchannels"])
+        c.prepare(algos=("ring", "tree"), protos=("ll", "ll128"))
+        for coll in w["colls"]:
+            for S in w["bytes"]:
+                n = S // 4
+                if coll == "reducescatter":
+                    a, b = [x[:n] for x in big], [y[:n // k] for y in out]
+                elif coll == "allgather":
+                    a, b = [x[:n // k] for x in big], [y[:n] for y in out]
+                else:
+                    a, b = [x[:n] for x in big], [y[:n] for y in out]
+                row = {"coll": coll, "nranks": k, "bytes_per_rank": S}
+                c.clear_plan()
+                row["us_auto"] = graph_us(c, coll, a, b, "auto")
+                p = c.last_plan()
+                row["plan"] = f"{p['algo']}/{p['proto']}/{p['nchannels']}ch"
+                for proto in ("ll", "ll128"):          # the paper's protocols, best channels
+                    best = None
+                    for C in w["ll_channels"]:
+                        c.set_plan(nchannels=C, chunk_steps=1)
+                        t = graph_us(c, coll, a, b, proto)
+                        if best is None or t < best[0]:
+                            best = (t, C)
+                    row["us_" + proto], row[proto + "_channels"] = best
+                c.clear_plan()
+                rows.append(row)
+        err = c.async_error()
+        c.destroy()
+        if err != "vSuccess":
+            return {"workload": w["name"], "status": err}
+    return {"workload": w["name"], "timing": "CUDA graph of 10 calls, median of 21 replays",
+            "rows": rows, "status": "vSuccess"}
+
+
 # ------------------------------------------------------------------ served leg
 
 def run_served(args):
@@ -387,8 +477,9 @@ def run_served(args):
 
 def run_sweep(path):
     """Ring AllReduce on 8 vranks: per-rank sizes 1 KiB..256 MiB (powers of
-    4) x fp32 / bf16 x Simple / LL / LL128 x 1 / 4 / 16 / 32 channels, N(0,1)
-    values; one JSON line per point (median of timed launches)."""
+    4) x fp32 / bf16 x Simple / LL / LL128 (and the cluster protocol up to
+    4 MiB) x 1 / 4 / 16 / 32 channels, N(0,1) values; one JSON line per point
+    (median of timed launches)."""
     import torch
 
     from paper_2507_04786_b300 import Comm
@@ -406,7 +497,9 @@ def run_sweep(path):
                 n = S // es
                 xs = [x[:n] for x in base[dt]]
                 ys = [y[:n] for y in outs[dt]]
-                for proto in ("simple", "ll", "ll128"):
+                for proto in ("simple", "ll", "ll128", "cluster"):
+                    if proto == "cluster" and S > workloads.SWEEP_CLUSTER_MAX:
+                        continue
                     for C in workloads.SWEEP_CHANNELS:
                         comm.set_plan(nchannels=C, chunk_steps=1)
                         for _ in range(2):
@@ -554,6 +647,7 @@ def main():
         "clocks": r["clocks"],
     }
     if not args.no_extras and world == 1:
+        line["small_messages"] = run_small(args)
         line["batched"] = run_batched(args)
         line["served"] = run_served(args)
     if not args.no_cpu:

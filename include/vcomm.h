@@ -63,7 +63,22 @@ typedef enum { vAlgoAuto = 0, vAlgoRing = 1, vAlgoTree = 2 } vAlgo_t;
  * connection.  It needs nranks <= 16 (the largest cluster); Auto picks it up
  * to 256 KiB per rank on 2..16 vranks, where its latency is lowest; a group
  * of several calls and the serving API run it as LL. */
-typedef enum { vProtoAuto = 0, vProtoSimple = 1, vProtoLL = 2, vProtoLL128 = 3, vProtoCluster = 4 } vProto_t;
+/* vProtoDirect follows Sec. IV's P2P_DIRECT (ranks of one process move data
+ * between source and destination buffers directly, with no intermediate
+ * FIFO) to its end on one GPU: a thread reads the k input buffers of a
+ * 16-byte unit and folds them in the ring schedule's order, so a call reads
+ * each input byte once and writes each output byte once.  Ring algorithm
+ * only; for a given plan (channels, chunkSteps) the results are the Simple
+ * protocol's, bit for bit.  A group of several calls and the serving API run
+ * it as Simple. */
+typedef enum {
+  vProtoAuto = 0,
+  vProtoSimple = 1,
+  vProtoLL = 2,
+  vProtoLL128 = 3,
+  vProtoCluster = 4,
+  vProtoDirect = 5
+} vProto_t;
 
 #define VCOMM_MAX_RANKS 64
 #define VCOMM_MAX_CHANNELS 64
@@ -184,7 +199,8 @@ vResult_t vcommGetGroupPlans(vcomm_t comm, vPlan_t* plans, int maxPlans, int* nP
  * Protocol / algorithm / channel selection (Sec. III-D; Sec. II-C: "the tuning
  * model determines how many channels"): times every candidate plan
  * (ring/tree x Simple/LL/LL128 x channels 1, 2, 4, ... nch, plus the cluster
- * protocol up to 4 MiB on <= 16 vranks) on this device at
+ * protocol up to 4 MiB on <= 16 vranks and the direct protocol on the ring)
+ * on this device at
  * per-rank sizes 1 KiB x 4^i <= maxBytes for each collective whose bit is set
  * in collMask (bit 0 AllReduce, 1 ReduceScatter, 2 AllGather, 3 Broadcast,
  * 4 Reduce) and keeps the fastest per size.  Later calls with Auto arguments

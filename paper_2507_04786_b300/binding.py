@@ -18,7 +18,7 @@ RESULTS = {0: "vSuccess", 1: "vInvalidArgument", 2: "vUnsupported", 3: "vOutOfMe
 DTYPE_CODES = {"int32": 0, "fp32": 1, "fp16": 2, "bf16": 3}
 OP_CODES = {"sum": 0, "max": 1}
 ALGO_CODES = {"auto": 0, "ring": 1, "tree": 2}
-PROTO_CODES = {"auto": 0, "simple": 1, "ll": 2, "ll128": 3, "cluster": 4}
+PROTO_CODES = {"auto": 0, "simple": 1, "ll": 2, "ll128": 3, "cluster": 4, "direct": 5}
 ALGO_NAMES = {v: k for k, v in ALGO_CODES.items()}
 PROTO_NAMES = {v: k for k, v in PROTO_CODES.items()}
 

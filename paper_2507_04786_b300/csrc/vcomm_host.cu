@@ -247,7 +247,7 @@ vResult_t vcommSetPlan(vcomm_t c, const vPlan_t* plan) {
   if (!c) return vInvalidArgument;
   if (!plan) { c->pinned = false; return vSuccess; }
   if (plan->algo < vAlgoAuto || plan->algo > vAlgoTree || plan->proto < vProtoAuto ||
-      plan->proto > vProtoCluster || plan->nchannels < 0 || plan->nchannels > c->nch ||
+      plan->proto > vProtoDirect || plan->nchannels < 0 || plan->nchannels > c->nch ||
       plan->chunkSteps < 0 || plan->chunkSteps > 64)
     return vInvalidArgument;
   c->pin = *plan;
@@ -339,7 +339,7 @@ static vResult_t prepareCall(int coll, const void* const* sendbufs, void* const*
   if (dtype < vInt32 || dtype > vBfloat16) return vInvalidArgument;
   if ((coll == kAllReduce || coll == kReduceScatter || coll == kReduce) && (op < vSum || op > vMax))
     return vInvalidArgument;
-  if (algo < vAlgoAuto || algo > vAlgoTree || proto < vProtoAuto || proto > vProtoCluster)
+  if (algo < vAlgoAuto || algo > vAlgoTree || proto < vProtoAuto || proto > vProtoDirect)
     return vInvalidArgument;
   const int k = c->k;
   if ((coll == kBroadcast || coll == kReduce) && (root < 0 || root >= k)) return vInvalidArgument;
@@ -391,6 +391,11 @@ static vResult_t prepareCall(int coll, const void* const* sendbufs, void* const*
   if (plan.algo == vAlgoTree && coll != kAllReduce) plan.algo = vAlgoRing;
   defaultPlan(c, coll, std::max(sb, rb), &plan);
   if (plan.algo == vAlgoTree && (coll != kAllReduce || k < 2)) plan.algo = vAlgoRing;
+  // the direct protocol replays ring fold orders only
+  if (plan.proto == vProtoDirect && plan.algo == vAlgoTree) {
+    if (algo == vAlgoTree || (c->pinned && c->pin.algo == vAlgoTree)) return vUnsupported;
+    plan.algo = vAlgoRing;
+  }
   int kcoll = coll;
   if (k == 1) {
     kcoll = kCopy;
@@ -405,7 +410,7 @@ static vResult_t prepareCall(int coll, const void* const* sendbufs, void* const*
   // clusters of up to 16 CTAs, and its FIFOs have kClusterSlots slots.
   if (plan.proto == vProtoCluster && k > 16) return vUnsupported;
   const int fifoSlots = (plan.proto == vProtoCluster) ? kClusterSlots : c->nsteps;
-  if (plan.algo == vAlgoRing && k > 1 && plan.chunkSteps >= fifoSlots) {
+  if (plan.algo == vAlgoRing && k > 1 && plan.proto != vProtoDirect && plan.chunkSteps >= fifoSlots) {
     if (c->pinned && c->pin.chunkSteps > 0) return vUnsupported;
     plan.chunkSteps = fifoSlots - 1;
   }
@@ -531,8 +536,48 @@ static vResult_t launchCluster(CallSpec& cs) {
   return vSuccess;
 }
 
+// The direct protocol: a plain launch over the data, no FIFO, no waits.
+static vResult_t launchDirect(CallSpec& cs) {
+  vcomm* c = cs.c;
+  const int k = c->k;
+  const void* fn = directKernel(cs.kcoll, cs.dtype, cs.redop);
+  if (!fn) return vInternalError;
+  const int esz = dtypeSize(cs.dtype);
+  DirectArgs a;
+  memset(&a, 0, sizeof(a));
+  bool aligned = true;
+  for (int r = 0; r < k; r++) {
+    a.send[r] = cs.send[r];
+    a.recv[r] = cs.recv[r];
+    if (((uintptr_t)cs.send[r] | (uintptr_t)cs.recv[r]) & 15) aligned = false;
+  }
+  a.count = cs.units;
+  a.chunk = chunkUnits(kSimple, c->slotBytes[kSimple], cs.plan.chunkSteps, esz);
+  a.inplaceMask = cs.inplace;
+  a.coll = cs.kcoll;
+  a.nranks = k;
+  a.nsub = cs.plan.nchannels;
+  a.root = cs.root;
+  // blocks inside a buffer start at multiples of count units
+  if (cs.kcoll == kReduceScatter && (cs.units * esz) % 16) aligned = false;
+  if (cs.kcoll == kAllGather && cs.units % 16) aligned = false;
+  a.vec = aligned ? 1 : 0;
+  const unsigned long long per = aligned ? (cs.bytesUnits ? 16ull : 16ull / esz) : 1ull;
+  unsigned long long units = cs.units / per;
+  if (cs.kcoll == kReduceScatter || cs.kcoll == kAllGather) units *= (unsigned long long)k;
+  const int nthr = 256;
+  const long long resident = (long long)std::max(1, residentPerSM(fn, nthr)) * c->nsm;
+  long long grid = (long long)((units + nthr - 1) / nthr);
+  grid = std::max<long long>(1, std::min<long long>(grid, resident));
+  void* args[] = {(void*)&a};
+  VC_TRY(cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(nthr), args, 0, cs.stream));
+  c->last = cs.plan;
+  return vSuccess;
+}
+
 static vResult_t launchSingle(CallSpec& cs) {
   if (cs.pr == kCluster) return launchCluster(cs);
+  if (cs.pr == kDirect) return launchDirect(cs);
   vcomm* c = cs.c;
   const int k = c->k;
   vPlan_t& plan = cs.plan;
@@ -633,6 +678,7 @@ static vResult_t launchGroup(vcomm* c, std::vector<CallSpec>& ops) {
   // protocol: such ops run as LL)
   for (auto& o : ops) {
     if (o.pr == kCluster) { o.pr = kLL; o.plan.proto = vProtoLL; }
+    if (o.pr == kDirect) { o.pr = kSimple; o.plan.proto = vProtoSimple; }
     if (o.kcoll == kCopy) {
       o.plan.nchannels = std::min(o.plan.nchannels, cpg);
       continue;
@@ -762,9 +808,11 @@ static vResult_t tuneOne(vcomm* c, int coll, size_t S, char* sbuf, char* rbuf, s
   const bool savedPinned = c->pinned;
   const vPlan_t savedPin = c->pin;
   for (int al = 0; al < ((coll == kAllReduce && k > 2) ? 2 : 1); al++) {
-    for (int pr = 0; pr < 4; pr++) {
-      // the cluster protocol is a small-message protocol on <= 16 vranks
+    for (int pr = 0; pr < 5; pr++) {
+      // the cluster protocol is a small-message protocol on <= 16 vranks;
+      // the direct protocol replays ring orders only
       if (pr == kCluster && (k > 16 || S > ((size_t)4 << 20))) continue;
+      if (pr == kDirect && al == 1) continue;
       for (int ch : chans) {
         vPlan_t p{al ? vAlgoTree : vAlgoRing, (vProto_t)(pr + 1), ch, 1};
         c->pin = p;

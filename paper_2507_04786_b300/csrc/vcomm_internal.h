@@ -27,7 +27,7 @@ namespace vc {
 enum Coll : int { kAllReduce = 0, kReduceScatter = 1, kAllGather = 2, kBroadcast = 3, kReduce = 4,
                   kCopy = 5 };
 enum Algo : int { kRing = 0, kTree = 1 };
-enum Proto : int { kSimple = 0, kLL = 1, kLL128 = 2, kCluster = 3 };
+enum Proto : int { kSimple = 0, kLL = 1, kLL128 = 2, kCluster = 3, kDirect = 4 };
 enum DType : int { kI32 = 0, kF32 = 1, kF16 = 2, kBF16 = 3 };
 enum OpKind : int { kSum = 0, kMax = 1 };
 
@@ -153,6 +153,22 @@ struct ServeArgs {
   int gangCta[kMaxServeGangs + 1];
   int gangCpg[kMaxServeGangs];
   int gangConn[kMaxServeGangs];
+};
+
+// ---- the direct protocol (no FIFO): one thread computes a unit's whole
+// ring chain from the k user buffers.  count is in elements (AllReduce,
+// ReduceScatter's recvcount, Reduce) or bytes (AllGather, Broadcast); chunk
+// is the ring AllReduce chunkCount that fixes the segments (and so the fold
+// order), nsub the channel count.
+struct DirectArgs {
+  const void* send[64];
+  void* recv[64];
+  unsigned long long count;
+  unsigned long long chunk;
+  unsigned long long inplaceMask;
+  int coll, nranks, nsub, root;
+  int vec;                         // 1: every access is a 16-byte vector
+  int pad;
 };
 
 // ---- channel partition (Sec. V-C): 16-byte packs spread over `nch` ranges,

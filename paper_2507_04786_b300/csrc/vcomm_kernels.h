@@ -7,6 +7,9 @@ namespace vc {
 const void* reduceKernel(int proto, int dtype, int op);
 // persistent byte-moving kernel for AllGather, Broadcast and the single-rank copy
 const void* copyKernel(int proto);
+// direct protocol (vcomm_direct.cu): AllReduce / ReduceScatter / Reduce per
+// (dtype, op); one byte-copy kernel for AllGather and Broadcast
+const void* directKernel(int coll, int dtype, int op);
 // cluster protocol (vcomm_cluster_inst.cu): one cluster of nranks CTAs per channel
 const void* clusterKernel(int dtype, int op);
 const void* clusterCopyKernel();

@@ -493,7 +493,7 @@ vResult_t vServeSubmit(vserve_t s, int coll, const void* const* sendbufs, size_t
   if (!s || !sendbufs || !ticket || count == 0) return vInvalidArgument;
   if (coll != kAllReduce && coll != kReduceScatter && coll != kAllGather) return vUnsupported;
   if (nranks < 1 || nranks > s->cfg.maxRanks || dtype < vInt32 || dtype > vBfloat16 ||
-      op < vSum || op > vMax || proto < vProtoAuto || proto > vProtoCluster)
+      op < vSum || op > vMax || proto < vProtoAuto || proto > vProtoDirect)
     return vInvalidArgument;
   Request q;
   q.coll = coll;
@@ -501,7 +501,8 @@ vResult_t vServeSubmit(vserve_t s, int coll, const void* const* sendbufs, size_t
   q.redop = op;
   q.nranks = nranks;
   q.flags = flags;
-  q.proto = (proto == vProtoCluster) ? vProtoLL : proto;   // gangs have no cluster protocol
+  // gangs have no cluster or direct protocol
+  q.proto = (proto == vProtoCluster) ? vProtoLL : (proto == vProtoDirect) ? vProtoSimple : proto;
   q.count = count;
   const size_t esz = (dtype == vFloat16 || dtype == vBfloat16) ? 2 : 4;
   q.sb = count * esz;

@@ -61,3 +61,15 @@ SERVED = {
 # per-rank message sizes of the protocol sweep: 1 KiB .. 256 MiB in powers of 4
 SWEEP_BYTES = [KiB * 4 ** i for i in range(10)]
 SWEEP_CHANNELS = (1, 4, 16, 32)
+SWEEP_CLUSTER_MAX = 4 * MiB   # the cluster protocol is swept up to 4 MiB per rank
+
+# small-message latency: every collective at 1 KiB and 64 KiB per rank on 8
+# and 16 vranks, fp32 N(0,1) (the per-hop latency regime)
+SMALL = {
+    "name": "small-messages-8and16vr-1KiB-64KiB",
+    "nranks": (8, 16),
+    "bytes": (1 * KiB, 64 * KiB),
+    "colls": ("allreduce", "reducescatter", "allgather", "broadcast", "reduce"),
+    "nchannels": 8,
+    "ll_channels": (1, 2, 4, 8),   # LL / LL128 are timed at each; the best is kept
+}
