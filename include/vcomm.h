@@ -60,17 +60,19 @@ typedef enum { vAlgoAuto = 0, vAlgoRing = 1, vAlgoTree = 2 } vAlgo_t;
  * distributed shared memory instead of global memory.  Each channel's vranks
  * run as one thread-block cluster (CTA r = vrank r) and every FIFO lives in
  * its receiver's shared memory: 4 slots of 8 KiB (4 KiB of data) per
- * connection.  It needs nranks <= 16 (the largest cluster); Auto picks it up
- * to 256 KiB per rank on 2..16 vranks, where its latency is lowest; a group
- * of several calls and the serving API run it as LL. */
+ * connection.  It needs nranks <= 16 (the largest cluster); Auto picks it for
+ * tree AllReduce up to 256 KiB per rank on 2..16 vranks, where it is the
+ * fastest FIFO protocol; a group of several calls and the serving API run it
+ * as LL. */
 /* vProtoDirect follows Sec. IV's P2P_DIRECT (ranks of one process move data
  * between source and destination buffers directly, with no intermediate
  * FIFO) to its end on one GPU: a thread reads the k input buffers of a
  * 16-byte unit and folds them in the ring schedule's order, so a call reads
  * each input byte once and writes each output byte once.  Ring algorithm
  * only; for a given plan (channels, chunkSteps) the results are the Simple
- * protocol's, bit for bit.  A group of several calls and the serving API run
- * it as Simple. */
+ * protocol's, bit for bit.  Auto picks it on the ring for nranks >= 2; a
+ * group runs all its direct calls in one launch; the serving API runs it as
+ * Simple. */
 typedef enum {
   vProtoAuto = 0,
   vProtoSimple = 1,

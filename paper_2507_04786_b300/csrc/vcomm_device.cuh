@@ -16,6 +16,7 @@
 // Every wait is bounded by %globaltimer; on expiry (or on the host abort word)
 // the worker records the failure and returns -- no trap, no endless loop.
 #pragma once
+#include <type_traits>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
@@ -108,17 +109,45 @@ template <class T> struct ElemOp<T, OpNone> {
   static VDEV T f(T a, T) { return a; }
 };
 
-// apply f lane-wise on raw words (W = uint4 or uint64_t)
+// the sum of two 16-bit lanes per 32-bit word, each lane exactly as
+// ElemOp<T, OpSum> computes it (widen to fp32, one fp32 add, round to T with
+// RNE), with the two roundings done by one packed conversion
+template <class T> VDEV uint32_t sum2(uint32_t a, uint32_t b);
+template <> VDEV uint32_t sum2<__nv_bfloat16>(uint32_t a, uint32_t b) {
+  const float lo = __fadd_rn(__uint_as_float(a << 16), __uint_as_float(b << 16));
+  const float hi = __fadd_rn(__uint_as_float(a & 0xffff0000u), __uint_as_float(b & 0xffff0000u));
+  const __nv_bfloat162 r = __float22bfloat162_rn(make_float2(lo, hi));
+  return *(const uint32_t*)&r;
+}
+template <> VDEV uint32_t sum2<__half>(uint32_t a, uint32_t b) {
+  const float2 fa = __half22float2(*(const __half2*)&a);
+  const float2 fb = __half22float2(*(const __half2*)&b);
+  const __half2 r = __float22half2_rn(make_float2(__fadd_rn(fa.x, fb.x), __fadd_rn(fa.y, fb.y)));
+  return *(const uint32_t*)&r;
+}
+
+// apply f lane-wise on raw words (W = uint4, uint64_t or one element)
 template <class T, class Op, class W>
 VDEV W applyWord(W a, W b) {
-  constexpr int n = sizeof(W) / sizeof(T);
-  union U { W w; T e[n]; };
-  U ua, ub, uo;
-  ua.w = a;
-  ub.w = b;
+  if constexpr (sizeof(T) == 2 && std::is_same<Op, OpSum>::value && sizeof(W) % 4 == 0) {
+    constexpr int n = sizeof(W) / 4;
+    union U { W w; uint32_t u[n]; };
+    U ua, ub, uo;
+    ua.w = a;
+    ub.w = b;
 #pragma unroll
-  for (int i = 0; i < n; i++) uo.e[i] = ElemOp<T, Op>::f(ua.e[i], ub.e[i]);
-  return uo.w;
+    for (int i = 0; i < n; i++) uo.u[i] = sum2<T>(ua.u[i], ub.u[i]);
+    return uo.w;
+  } else {
+    constexpr int n = sizeof(W) / sizeof(T);
+    union U { W w; T e[n]; };
+    U ua, ub, uo;
+    ua.w = a;
+    ub.w = b;
+#pragma unroll
+    for (int i = 0; i < n; i++) uo.e[i] = ElemOp<T, Op>::f(ua.e[i], ub.e[i]);
+    return uo.w;
+  }
 }
 
 // ------------------------------------------------------------------ failure handling

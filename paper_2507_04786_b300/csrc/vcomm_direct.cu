@@ -23,9 +23,18 @@ namespace vc {
 
 namespace {
 
+// one collective as the direct kernels see it (a single launch or one op of
+// a batch): the k send and recv pointers plus DirectArgs' scalars
+struct DirectView {
+  const void* const* send;
+  void* const* recv;
+  unsigned long long count, chunk, inplaceMask;
+  int coll, nranks, nsub, root;
+};
+
 // the ring segment (fold start = s + 1) of element i of a ring AllReduce,
 // and the end (exclusive, in elements) of the run of elements sharing it
-VDEV int arSegment(const DirectArgs& a, unsigned long long i, int esz, unsigned long long* runEnd) {
+VDEV int arSegment(const DirectView& a, unsigned long long i, int esz, unsigned long long* runEnd) {
   const int k = a.nranks;
   const unsigned long long epp = 16ull / (unsigned long long)esz;
   const unsigned long long npk = a.count / epp;
@@ -74,73 +83,113 @@ VDEV W combine(W acc, W x) {
 
 // acc = x_{s+1}; acc = f(acc, x_{s+2}); ... ; acc = f(acc, x_s): the partial
 // sum arriving from the predecessor is the first operand, the local input the
-// second, as in the FIFO kernels
-template <class T, class Op, class U>
-VDEV typename U::W foldChain(const DirectArgs& a, int s, unsigned long long off) {
+// second, as in the FIFO kernels.  NU units at once (offsets off[u], chain
+// starts s[u]): their loads are issued together, B ranks ahead of the combines.
+template <class T, class Op, class U, int NU>
+VDEV void foldChains(const DirectView& a, const int* s, const unsigned long long* off, int nu,
+                     typename U::W* acc) {
   const int k = a.nranks;
-  int r = s + 1 < k ? s + 1 : 0;
-  typename U::W acc = U::load((const char*)a.send[r] + off);
-  constexpr int B = 8;   // loads issued ahead of their combines
-  for (int j = 1; j < k; j += B) {
-    typename U::W v[B];
+  int r[NU];
 #pragma unroll
-    for (int u = 0; u < B; u++) {
-      int rr = r + 1 + u;
-      if (rr >= k) rr -= k;
-      if (j + u < k) v[u] = U::load((const char*)a.send[rr] + off);
+  for (int u = 0; u < NU; u++) {
+    r[u] = s[u] + 1 < k ? s[u] + 1 : 0;
+    if (u < nu) acc[u] = U::load((const char*)a.send[r[u]] + off[u]);
+  }
+  constexpr int B = 8;
+  for (int j = 1; j < k; j += B) {
+    typename U::W v[NU][B];
+#pragma unroll
+    for (int u = 0; u < NU; u++) {
+#pragma unroll
+      for (int b = 0; b < B; b++) {
+        int rr = r[u] + 1 + b;
+        if (rr >= k) rr -= k;
+        if (u < nu && j + b < k) v[u][b] = U::load((const char*)a.send[rr] + off[u]);
+      }
     }
 #pragma unroll
-    for (int u = 0; u < B; u++)
-      if (j + u < k) acc = combine<T, Op, typename U::W>(acc, v[u]);
-    r += B;
-    if (r >= k) r -= k;
+    for (int u = 0; u < NU; u++) {
+#pragma unroll
+      for (int b = 0; b < B; b++)
+        if (u < nu && j + b < k) acc[u] = combine<T, Op, typename U::W>(acc[u], v[u][b]);
+      r[u] += B;
+      if (r[u] >= k) r[u] -= k;
+    }
   }
-  return acc;
 }
 
-// the contiguous range of units [*lo, *hi) of this CTA (consecutive threads
-// take consecutive units, so every warp access is one coalesced 512 bytes)
-VDEV void ctaRange(unsigned long long total, unsigned long long* lo, unsigned long long* hi) {
-  unsigned long long per = (total + gridDim.x - 1) / gridDim.x;
-  per = (per + blockDim.x - 1) / blockDim.x * blockDim.x;
-  *lo = (unsigned long long)blockIdx.x * per;
-  *hi = *lo + per < total ? *lo + per : total;
-}
-
-// AllReduce, ReduceScatter and Reduce; one unit per loop iteration
 template <class T, class Op, class U>
-VDEV void directReduce(const DirectArgs& a) {
+VDEV typename U::W foldChain(const DirectView& a, int s, unsigned long long off) {
+  typename U::W acc[1];
+  foldChains<T, Op, U, 1>(a, &s, &off, 1, acc);
+  return acc[0];
+}
+
+// units of a collective: full units per block x blocks
+VDEV unsigned long long reduceUnits(const DirectView& a, int E) {
+  return (a.count / E) * (a.coll == kReduceScatter ? (unsigned long long)a.nranks : 1ull);
+}
+VDEV unsigned long long copyUnits(const DirectView& a, int E) {
+  return (a.count / E) * (a.coll == kAllGather ? (unsigned long long)a.nranks : 1ull);
+}
+
+// AllReduce, ReduceScatter and Reduce over units [lo, hi) of the collective
+// (consecutive threads take consecutive units, so every warp access is one
+// coalesced 512 bytes), NU units per thread per iteration; `tail`: this CTA
+// also does the element tail of each block
+template <class T, class Op, class U, int NU>
+VDEV void directReduce(const DirectView& a, unsigned long long lo, unsigned long long hi, bool tail) {
   const int k = a.nranks;
   constexpr int E = U::kElems;
   const unsigned long long esz = sizeof(T);
   const unsigned long long nunit = a.count / E;                 // full units per block
-  const unsigned long long nblk = (a.coll == kReduceScatter) ? (unsigned long long)k : 1ull;
-  const unsigned long long total = nunit * nblk;
-  unsigned long long lo, hi;
-  ctaRange(total, &lo, &hi);
   unsigned long long runEnd = 0;   // AllReduce: the current segment's end (elements)
   int seg = 0;
-  for (unsigned long long g = lo + threadIdx.x; g < hi; g += blockDim.x) {
-    if (a.coll == kAllReduce) {
-      const unsigned long long i = g * E;
-      if (i >= runEnd) seg = arSegment(a, i, (int)esz, &runEnd);
-      const unsigned long long off = i * esz;
-      const typename U::W v = foldChain<T, Op, U>(a, seg, off);
-      for (int r = 0; r < k; r++) U::store((char*)a.recv[r] + off, v);
-    } else if (a.coll == kReduceScatter) {
-      const unsigned long long b = g / nunit, u = g % nunit;
-      const typename U::W v = foldChain<T, Op, U>(a, (int)b, (b * a.count + u * E) * esz);
-      U::store((char*)a.recv[b] + u * E * esz, v);
-    } else {
-      const typename U::W v = foldChain<T, Op, U>(a, a.root, g * E * esz);
-      U::store((char*)a.recv[a.root] + g * E * esz, v);
+  for (unsigned long long g0 = lo + threadIdx.x; g0 < hi; g0 += (unsigned long long)NU * blockDim.x) {
+    int s[NU];
+    unsigned long long off[NU];
+    int nu = 0;
+#pragma unroll
+    for (int u = 0; u < NU; u++) {
+      const unsigned long long g = g0 + (unsigned long long)u * blockDim.x;
+      s[u] = 0;
+      off[u] = 0;
+      if (g >= hi) continue;
+      nu = u + 1;
+      if (a.coll == kAllReduce) {
+        const unsigned long long i = g * E;
+        if (i >= runEnd) seg = arSegment(a, i, (int)esz, &runEnd);
+        s[u] = seg;
+        off[u] = i * esz;
+      } else if (a.coll == kReduceScatter) {
+        const unsigned long long b = g / nunit, e = g % nunit;
+        s[u] = (int)b;
+        off[u] = (b * a.count + e * E) * esz;
+      } else {
+        s[u] = a.root;
+        off[u] = g * E * esz;
+      }
+    }
+    typename U::W v[NU];
+    foldChains<T, Op, U, NU>(a, s, off, nu, v);
+#pragma unroll
+    for (int u = 0; u < NU; u++) {
+      if (u >= nu) continue;
+      if (a.coll == kAllReduce) {
+        for (int r = 0; r < k; r++) U::store((char*)a.recv[r] + off[u], v[u]);
+      } else if (a.coll == kReduceScatter) {
+        const unsigned long long g = g0 + (unsigned long long)u * blockDim.x;
+        U::store((char*)a.recv[s[u]] + (g % nunit) * E * esz, v[u]);
+      } else {
+        U::store((char*)a.recv[a.root] + off[u], v[u]);
+      }
     }
   }
-  // the element tail of each block (vector units only)
-  const unsigned long long tail = a.count - nunit * E;
-  if (E > 1 && tail && blockIdx.x == gridDim.x - 1) {
-    for (unsigned long long t = threadIdx.x; t < tail * nblk; t += blockDim.x) {
-      const unsigned long long b = t / tail, i = nunit * E + t % tail;
+  const unsigned long long nt = a.count - nunit * E;   // element tail of each block
+  if (E > 1 && nt && tail) {
+    const unsigned long long nblk = (a.coll == kReduceScatter) ? (unsigned long long)k : 1ull;
+    for (unsigned long long t = threadIdx.x; t < nt * nblk; t += blockDim.x) {
+      const unsigned long long b = t / nt, i = nunit * E + t % nt;
       if (a.coll == kAllReduce) {
         unsigned long long re;
         const int s = arSegment(a, i, (int)esz, &re);
@@ -157,24 +206,14 @@ VDEV void directReduce(const DirectArgs& a) {
   }
 }
 
-template <class T, class Op>
-__global__ void __launch_bounds__(256, 2) kDirectReduce(const __grid_constant__ DirectArgs a) {
-  if (a.vec) directReduce<T, Op, Unit16<T>>(a);
-  else directReduce<T, Op, Unit1<T>>(a);
-}
-
 // AllGather (block b of every output = rank b's input) and Broadcast (every
-// output = the root's input); count in bytes.  A unit is read once and
-// written to every output that is not its own source.
+// output = the root's input) over units [lo, hi); count in bytes.  A unit is
+// read once and written to every output that is not its own source.
 template <class U>
-VDEV void directCopy(const DirectArgs& a) {
+VDEV void directCopy(const DirectView& a, unsigned long long lo, unsigned long long hi, bool tail) {
   const int k = a.nranks;
   constexpr int E = sizeof(typename U::W);
   const unsigned long long nunit = a.count / E;
-  const unsigned long long nblk = (a.coll == kAllGather) ? (unsigned long long)k : 1ull;
-  const unsigned long long total = nunit * nblk;
-  unsigned long long lo, hi;
-  ctaRange(total, &lo, &hi);
   for (unsigned long long g = lo + threadIdx.x; g < hi; g += blockDim.x) {
     const unsigned long long b = (a.coll == kAllGather) ? g / nunit : (unsigned long long)a.root;
     const unsigned long long off = (g % nunit) * E;
@@ -185,33 +224,137 @@ VDEV void directCopy(const DirectArgs& a) {
       U::store((char*)a.recv[r] + dst, v);
     }
   }
+  const unsigned long long nt = a.count - nunit * E;   // byte tail of each block
+  if (E > 1 && nt && tail) {
+    const unsigned long long nblk = (a.coll == kAllGather) ? (unsigned long long)k : 1ull;
+    for (unsigned long long t = threadIdx.x; t < nt * nblk; t += blockDim.x) {
+      const unsigned long long b = (a.coll == kAllGather) ? t / nt : (unsigned long long)a.root;
+      const unsigned long long off = nunit * E + t % nt;
+      const uint8_t v = ((const uint8_t*)a.send[b])[off];
+      const unsigned long long dst = (a.coll == kAllGather) ? b * a.count + off : off;
+      for (int r = 0; r < k; r++) {
+        if ((unsigned long long)r == b && ((a.inplaceMask >> r) & 1ull)) continue;
+        ((uint8_t*)a.recv[r])[dst] = v;
+      }
+    }
+  }
+}
+
+// this CTA's contiguous share [*lo, *hi) of `total` units, in whole blocks
+VDEV void ctaRange(unsigned long long total, unsigned long long* lo, unsigned long long* hi) {
+  unsigned long long per = (total + gridDim.x - 1) / gridDim.x;
+  per = (per + blockDim.x - 1) / blockDim.x * blockDim.x;
+  *lo = (unsigned long long)blockIdx.x * per;
+  if (*lo > total) *lo = total;
+  *hi = *lo + per < total ? *lo + per : total;
+}
+
+VDEV DirectView viewOf(const DirectArgs& a) {
+  return DirectView{a.send, a.recv, a.count, a.chunk, a.inplaceMask, a.coll, a.nranks, a.nsub, a.root};
+}
+
+// Launch shape (measured on 8 x 256 MiB): 4-byte types keep 4 units x 8
+// loads in flight per thread in 256-thread CTAs; 2-byte types, whose packed
+// fp32 arithmetic needs more issue slots, 2 units in 512-thread CTAs.
+template <class T> struct DirectShape {
+  static constexpr int kUnits = sizeof(T) == 4 ? 4 : 2;
+  static constexpr int kThreads = sizeof(T) == 4 ? 256 : 512;
+};
+
+template <class T, class Op>
+__global__ void __launch_bounds__(DirectShape<T>::kThreads, 1)
+    kDirectReduce(const __grid_constant__ DirectArgs a) {
+  const DirectView v = viewOf(a);
+  const bool last = blockIdx.x == gridDim.x - 1;
+  unsigned long long lo, hi;
+  if (a.vec) {
+    ctaRange(reduceUnits(v, Unit16<T>::kElems), &lo, &hi);
+    directReduce<T, Op, Unit16<T>, DirectShape<T>::kUnits>(v, lo, hi, last);
+  } else {
+    ctaRange(reduceUnits(v, 1), &lo, &hi);
+    directReduce<T, Op, Unit1<T>, 1>(v, lo, hi, last);
+  }
 }
 
 __global__ void __launch_bounds__(256) kDirectCopy(const __grid_constant__ DirectArgs a) {
+  const DirectView v = viewOf(a);
+  const bool last = blockIdx.x == gridDim.x - 1;
+  unsigned long long lo, hi;
   if (a.vec) {
-    directCopy<Unit16<uint8_t>>(a);
-    // byte tail of each block
-    const unsigned long long nunit = a.count / 16, tail = a.count - nunit * 16;
-    const int k = a.nranks;
-    const unsigned long long nblk = (a.coll == kAllGather) ? (unsigned long long)k : 1ull;
-    if (tail && blockIdx.x == gridDim.x - 1) {
-      for (unsigned long long t = threadIdx.x; t < tail * nblk; t += blockDim.x) {
-        const unsigned long long b = (a.coll == kAllGather) ? t / tail : (unsigned long long)a.root;
-        const unsigned long long off = nunit * 16 + t % tail;
-        const uint8_t v = ((const uint8_t*)a.send[b])[off];
-        const unsigned long long dst = (a.coll == kAllGather) ? b * a.count + off : off;
-        for (int r = 0; r < k; r++) {
-          if ((unsigned long long)r == b && ((a.inplaceMask >> r) & 1ull)) continue;
-          ((uint8_t*)a.recv[r])[dst] = v;
-        }
-      }
-    }
+    ctaRange(copyUnits(v, 16), &lo, &hi);
+    directCopy<Unit16<uint8_t>>(v, lo, hi, last);
   } else {
-    directCopy<Unit1<uint8_t>>(a);
+    ctaRange(copyUnits(v, 1), &lo, &hi);
+    directCopy<Unit1<uint8_t>>(v, lo, hi, last);
+  }
+}
+
+// ---- many direct collectives of one element type and op in one launch
+// (group calls; the host launches one such kernel per (dtype, op) present,
+// and one for the copies).  The ops' units are laid end to end (op i owns
+// [unitStart[i], unitStart[i + 1])); each CTA takes a contiguous share of
+// that space and runs every op it overlaps on the overlapping units.
+// Nothing waits, so the ops need no ordering.
+VDEV DirectView viewOfOp(const DirectBatchArgs* b, int i) {
+  const DirectOpDesc& o = b->ops[i];
+  return DirectView{(const void* const*)&b->ptrs[o.ptrBase], (void* const*)&b->ptrs[o.ptrBase + o.nranks],
+                    o.count, o.chunk, o.inplaceMask, o.coll, o.nranks, o.nsub, o.root};
+}
+
+// the op-local units [lo, hi) of op i that fall in this CTA's share
+// [glo, ghi), and whether this CTA holds the op's last unit (its tails)
+VDEV void opShare(const DirectBatchArgs* b, int i, unsigned long long glo, unsigned long long ghi,
+                  unsigned long long* lo, unsigned long long* hi, bool* tail) {
+  const unsigned long long s = b->unitStart[i], e = b->unitStart[i + 1];
+  unsigned long long h = (ghi < e ? ghi : e) - s;
+  if (h > b->ops[i].units) h = b->ops[i].units;   // the range may hold one unit more than the op
+  unsigned long long l = (glo > s ? glo : s) - s;
+  *lo = l < h ? l : h;
+  *hi = h;
+  *tail = ghi >= e;
+}
+
+template <class T, class Op>
+__global__ void __launch_bounds__(DirectShape<T>::kThreads, 1)
+    kDirectBatch(const __grid_constant__ DirectBatchArgs b) {
+  const DirectBatchArgs* pb = &b;
+  unsigned long long glo, ghi;
+  ctaRange(pb->unitStart[pb->nops], &glo, &ghi);
+  for (int i = 0; i < pb->nops; i++) {
+    if (pb->unitStart[i + 1] <= glo || pb->unitStart[i] >= ghi) continue;
+    unsigned long long lo, hi;
+    bool tail;
+    opShare(pb, i, glo, ghi, &lo, &hi, &tail);
+    const DirectView v = viewOfOp(pb, i);
+    // (2-byte types: one unit per thread, which the loop over ops leaves
+    // registers for)
+    constexpr int NU = sizeof(T) == 4 ? DirectShape<T>::kUnits : 1;
+    if (pb->ops[i].vec) directReduce<T, Op, Unit16<T>, NU>(v, lo, hi, tail);
+    else directReduce<T, Op, Unit1<T>, 1>(v, lo, hi, tail);
+  }
+}
+
+__global__ void __launch_bounds__(256) kDirectBatchCopy(const __grid_constant__ DirectBatchArgs b) {
+  const DirectBatchArgs* pb = &b;
+  unsigned long long glo, ghi;
+  ctaRange(pb->unitStart[pb->nops], &glo, &ghi);
+  for (int i = 0; i < pb->nops; i++) {
+    if (pb->unitStart[i + 1] <= glo || pb->unitStart[i] >= ghi) continue;
+    unsigned long long lo, hi;
+    bool tail;
+    opShare(pb, i, glo, ghi, &lo, &hi, &tail);
+    const DirectView v = viewOfOp(pb, i);
+    if (pb->ops[i].vec) directCopy<Unit16<uint8_t>>(v, lo, hi, tail);
+    else directCopy<Unit1<uint8_t>>(v, lo, hi, tail);
   }
 }
 
 }  // namespace
+
+int directThreads(int coll, int dtype) {
+  if (coll == kAllGather || coll == kBroadcast) return 256;
+  return (dtype == kF16 || dtype == kBF16) ? DirectShape<__half>::kThreads : DirectShape<float>::kThreads;
+}
 
 const void* directKernel(int coll, int dtype, int op) {
   if (coll == kAllGather || coll == kBroadcast) return (const void*)kDirectCopy;
@@ -222,6 +365,19 @@ const void* directKernel(int coll, int dtype, int op) {
     case kF16: return mx ? (const void*)kDirectReduce<__half, OpMax> : (const void*)kDirectReduce<__half, OpSum>;
     case kBF16:
       return mx ? (const void*)kDirectReduce<__nv_bfloat16, OpMax> : (const void*)kDirectReduce<__nv_bfloat16, OpSum>;
+  }
+  return nullptr;
+}
+
+const void* directBatchKernel(int coll, int dtype, int op) {
+  if (coll == kAllGather || coll == kBroadcast) return (const void*)kDirectBatchCopy;
+  const bool mx = (op == kMax);
+  switch (dtype) {
+    case kI32: return mx ? (const void*)kDirectBatch<int32_t, OpMax> : (const void*)kDirectBatch<int32_t, OpSum>;
+    case kF32: return mx ? (const void*)kDirectBatch<float, OpMax> : (const void*)kDirectBatch<float, OpSum>;
+    case kF16: return mx ? (const void*)kDirectBatch<__half, OpMax> : (const void*)kDirectBatch<__half, OpSum>;
+    case kBF16:
+      return mx ? (const void*)kDirectBatch<__nv_bfloat16, OpMax> : (const void*)kDirectBatch<__nv_bfloat16, OpSum>;
   }
   return nullptr;
 }

@@ -265,13 +265,16 @@ vResult_t vcommGetLastPlan(vcomm_t c, vPlan_t* plan) {
 
 // ------------------------------------------------------------------ planning
 // Default tuning (used where neither the call nor a pin fixes a choice and the
-// communicator has not been tuned): up to 256 KiB the cluster protocol on
-// <= 16 vranks (else LL below 64 KiB), LL128 below 2 MiB, Simple above
-// (Sec. III-D: LL/LL128 for small messages, Simple for large); tree AllReduce
-// up to 256 KiB (Sec. V-F: tree best for small, ring for large); about 1 MiB
-// of message per channel, 4 KiB for the cluster protocol (at most 64 / k
-// clusters: a cluster of 16 CTAs takes most of a GPC).  A tuned communicator
-// takes each Auto field from its measured table at the nearest size.
+// communicator has not been tuned): the direct protocol on the ring (no FIFO
+// at all: on one GPU it is the fastest at every size measured, 1 KiB to
+// 256 MiB).  Where the caller asks for the tree, the FIFO protocols as the
+// paper tunes them: up to 256 KiB the cluster protocol on <= 16 vranks (else
+// LL below 64 KiB), LL128 below 2 MiB, Simple above (Sec. III-D); an Auto
+// algorithm with a FIFO protocol takes the tree for AllReduce up to 256 KiB
+// (Sec. V-F).  About 1 MiB of message per channel, 4 KiB for the cluster
+// protocol (at most 64 / k clusters: a cluster of 16 CTAs takes most of a
+// GPC).  A tuned communicator takes each Auto field from its measured table
+// at the nearest size.
 static void defaultPlan(const vcomm* c, int coll, size_t bytes, vPlan_t* p) {
   if (coll >= 0 && coll < 5 && c->tuned[coll]) {
     int best = -1;
@@ -284,17 +287,22 @@ static void defaultPlan(const vcomm* c, int coll, size_t bytes, vPlan_t* p) {
     }
     if (best >= 0) {
       const vPlan_t& t = c->tune[coll][best].plan;
+      const bool treeAsked = (p->algo == vAlgoTree);
       if (p->algo == vAlgoAuto) p->algo = t.algo;
-      if (p->proto == vProtoAuto) p->proto = t.proto;
+      if (p->proto == vProtoAuto && !(treeAsked && t.proto == vProtoDirect)) p->proto = t.proto;
       if (p->nchannels <= 0) p->nchannels = std::min(t.nchannels, c->nch);
       if (p->chunkSteps <= 0) p->chunkSteps = t.chunkSteps;
     }
   }
   if (p->proto == vProtoAuto) {
-    if (c->k >= 2 && c->k <= 16 && bytes <= (256u << 10)) p->proto = vProtoCluster;
+    if (c->k >= 2 && p->algo != vAlgoTree) p->proto = vProtoDirect;
+    else if (c->k >= 2 && c->k <= 16 && bytes <= (256u << 10)) p->proto = vProtoCluster;
     else p->proto = bytes < (64u << 10) ? vProtoLL : bytes < (2u << 20) ? vProtoLL128 : vProtoSimple;
   }
-  if (p->algo == vAlgoAuto) p->algo = (coll == kAllReduce && bytes <= (256u << 10) && c->k > 2) ? vAlgoTree : vAlgoRing;
+  if (p->algo == vAlgoAuto) {
+    if (p->proto == vProtoDirect) p->algo = vAlgoRing;
+    else p->algo = (coll == kAllReduce && bytes <= (256u << 10) && c->k > 2) ? vAlgoTree : vAlgoRing;
+  }
   if (p->nchannels <= 0) {
     const bool cl = (p->proto == vProtoCluster);
     size_t per = cl ? ((size_t)4 << 10) : ((size_t)1 << 20);
@@ -536,36 +544,51 @@ static vResult_t launchCluster(CallSpec& cs) {
   return vSuccess;
 }
 
+// Geometry of a direct call: whether every access can be a 16-byte vector
+// (all buffers 16-byte aligned, and so the blocks inside them), the units
+// the kernel spreads over its threads, and the Simple chunk that fixes the
+// ring segments.
+struct DirectGeom {
+  bool vec;
+  unsigned long long units, chunk;
+};
+static DirectGeom directGeom(const CallSpec& cs) {
+  const int k = cs.c->k;
+  const int esz = dtypeSize(cs.dtype);
+  bool aligned = true;
+  for (int r = 0; r < k; r++)
+    if (((uintptr_t)cs.send[r] | (uintptr_t)cs.recv[r]) & 15) aligned = false;
+  if (cs.kcoll == kReduceScatter && (cs.units * esz) % 16) aligned = false;
+  if (cs.kcoll == kAllGather && cs.units % 16) aligned = false;
+  const unsigned long long per = aligned ? (cs.bytesUnits ? 16ull : 16ull / esz) : 1ull;
+  unsigned long long units = cs.units / per;
+  if (cs.kcoll == kReduceScatter || cs.kcoll == kAllGather) units *= (unsigned long long)k;
+  return DirectGeom{aligned, units, chunkUnits(kSimple, cs.c->slotBytes[kSimple], cs.plan.chunkSteps, esz)};
+}
+
 // The direct protocol: a plain launch over the data, no FIFO, no waits.
 static vResult_t launchDirect(CallSpec& cs) {
   vcomm* c = cs.c;
   const int k = c->k;
   const void* fn = directKernel(cs.kcoll, cs.dtype, cs.redop);
   if (!fn) return vInternalError;
-  const int esz = dtypeSize(cs.dtype);
+  const DirectGeom g = directGeom(cs);
   DirectArgs a;
   memset(&a, 0, sizeof(a));
-  bool aligned = true;
   for (int r = 0; r < k; r++) {
     a.send[r] = cs.send[r];
     a.recv[r] = cs.recv[r];
-    if (((uintptr_t)cs.send[r] | (uintptr_t)cs.recv[r]) & 15) aligned = false;
   }
   a.count = cs.units;
-  a.chunk = chunkUnits(kSimple, c->slotBytes[kSimple], cs.plan.chunkSteps, esz);
+  a.chunk = g.chunk;
   a.inplaceMask = cs.inplace;
   a.coll = cs.kcoll;
   a.nranks = k;
   a.nsub = cs.plan.nchannels;
   a.root = cs.root;
-  // blocks inside a buffer start at multiples of count units
-  if (cs.kcoll == kReduceScatter && (cs.units * esz) % 16) aligned = false;
-  if (cs.kcoll == kAllGather && cs.units % 16) aligned = false;
-  a.vec = aligned ? 1 : 0;
-  const unsigned long long per = aligned ? (cs.bytesUnits ? 16ull : 16ull / esz) : 1ull;
-  unsigned long long units = cs.units / per;
-  if (cs.kcoll == kReduceScatter || cs.kcoll == kAllGather) units *= (unsigned long long)k;
-  const int nthr = 256;
+  a.vec = g.vec ? 1 : 0;
+  const unsigned long long units = g.units;
+  const int nthr = directThreads(cs.kcoll, cs.dtype);
   const long long resident = (long long)std::max(1, residentPerSM(fn, nthr)) * c->nsm;
   long long grid = (long long)((units + nthr - 1) / nthr);
   grid = std::max<long long>(1, std::min<long long>(grid, resident));
@@ -650,18 +673,102 @@ static vResult_t launchSingle(CallSpec& cs) {
 static thread_local int tGroupDepth = 0;
 static thread_local std::vector<CallSpec> tPending;
 
-// launch the batch of one communicator: gangs, LPT assignment, one kernel
+// the direct calls of a group: one launch per (dtype, op) class present (one
+// for the copies), each over up to kMaxBatchOps calls
+static vResult_t launchDirectGroup(vcomm* c, std::vector<CallSpec>& ops) {
+  const int k = c->k;
+  const cudaStream_t stream = ops[0].stream;
+  const int perLaunch = std::min<int>(kMaxBatchOps, kMaxBatchPtrs / (2 * k));
+  auto classOf = [](const CallSpec& o) {
+    return (o.kcoll == kAllGather || o.kcoll == kBroadcast) ? 8 : o.dtype * 2 + o.redop;
+  };
+  for (int cls = 0; cls <= 8; cls++) {
+    std::vector<const CallSpec*> mine;
+    for (auto& o : ops)
+      if (classOf(o) == cls) mine.push_back(&o);
+    if (mine.empty()) continue;
+    const CallSpec& first = *mine[0];
+    const void* fn = directBatchKernel(first.kcoll, first.dtype, first.redop);
+    const int nthr = directThreads(first.kcoll, first.dtype);
+    const long long resident = (long long)std::max(1, residentPerSM(fn, nthr)) * c->nsm;
+    for (size_t base = 0; base < mine.size(); base += perLaunch) {
+      const int n = (int)std::min<size_t>(perLaunch, mine.size() - base);
+      std::unique_ptr<DirectBatchArgs> b(new DirectBatchArgs());
+      memset(b.get(), 0, sizeof(DirectBatchArgs));
+      b->nops = n;
+      unsigned long long start = 0;
+      for (int i = 0; i < n; i++) {
+        const CallSpec& o = *mine[base + i];
+        const DirectGeom g = directGeom(o);
+        DirectOpDesc& d = b->ops[i];
+        d.count = o.units;
+        d.chunk = g.chunk;
+        d.inplaceMask = o.inplace;
+        d.units = g.units;
+        d.coll = o.kcoll;
+        d.nranks = k;
+        d.nsub = o.plan.nchannels;
+        d.root = o.root;
+        d.dtype = o.dtype;
+        d.redop = o.redop;
+        d.vec = g.vec ? 1 : 0;
+        d.ptrBase = 2 * k * i;
+        for (int r = 0; r < k; r++) {
+          b->ptrs[d.ptrBase + r] = o.send[r];
+          b->ptrs[d.ptrBase + k + r] = o.recv[r];
+        }
+        b->unitStart[i] = start;
+        start += std::max<unsigned long long>(g.units, 1ull);   // a unit range to own the tail
+      }
+      b->unitStart[n] = start;
+      long long grid = (long long)((start + nthr - 1) / nthr);
+      grid = std::max<long long>(1, std::min<long long>(grid, resident));
+      void* args[] = {(void*)b.get()};
+      VC_TRY(cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(nthr), args, 0, stream));
+    }
+  }
+  return vSuccess;
+}
+
+static vResult_t launchFifoGroup(vcomm* c, std::vector<CallSpec>& ops);
+
+// launch a group: its direct calls in one direct batch launch, the FIFO
+// calls in one persistent batch kernel (or a plain launch if alone)
 static vResult_t launchGroup(vcomm* c, std::vector<CallSpec>& ops) {
   if (ops.empty()) return vSuccess;
   const cudaStream_t stream = ops[0].stream;
   for (auto& o : ops)
     if (o.stream != stream) return vInvalidArgument;   // one stream per group and communicator
-  std::vector<vPlan_t> plans;
   if (ops.size() == 1) {
     vResult_t r = launchSingle(ops[0]);
     c->groupPlans.assign(1, ops[0].plan);
     return r;
   }
+  std::vector<CallSpec> direct, fifo;
+  std::vector<std::pair<int, int>> where;   // (0 direct / 1 fifo, index)
+  for (auto& o : ops) {
+    if (o.pr == kDirect && o.kcoll != kCopy) {
+      where.emplace_back(0, (int)direct.size());
+      direct.push_back(o);
+    } else {
+      where.emplace_back(1, (int)fifo.size());
+      fifo.push_back(o);
+    }
+  }
+  vResult_t r = vSuccess;
+  if (!direct.empty()) r = launchDirectGroup(c, direct);
+  if (r == vSuccess && fifo.size() == 1) r = launchSingle(fifo[0]);
+  else if (r == vSuccess && fifo.size() > 1) r = launchFifoGroup(c, fifo);
+  if (r != vSuccess) return r;
+  c->groupPlans.clear();
+  for (auto& w : where) c->groupPlans.push_back(w.first == 0 ? direct[w.second].plan : fifo[w.second].plan);
+  c->last = ops.back().plan;
+  return vSuccess;
+}
+
+// launch the FIFO calls of a group: gangs, LPT assignment, one kernel
+static vResult_t launchFifoGroup(vcomm* c, std::vector<CallSpec>& ops) {
+  const cudaStream_t stream = ops[0].stream;
   const int k = c->k;
   const void* fn = batchKernel();
   const int nthr = 256;
@@ -678,7 +785,7 @@ static vResult_t launchGroup(vcomm* c, std::vector<CallSpec>& ops) {
   // protocol: such ops run as LL)
   for (auto& o : ops) {
     if (o.pr == kCluster) { o.pr = kLL; o.plan.proto = vProtoLL; }
-    if (o.pr == kDirect) { o.pr = kSimple; o.plan.proto = vProtoSimple; }
+    if (o.pr == kDirect) { o.pr = kSimple; o.plan.proto = vProtoSimple; }   // single-rank copies
     if (o.kcoll == kCopy) {
       o.plan.nchannels = std::min(o.plan.nchannels, cpg);
       continue;
@@ -690,8 +797,6 @@ static vResult_t launchGroup(vcomm* c, std::vector<CallSpec>& ops) {
     vResult_t r = needArena(c, o.al, o.pr, stream);
     if (r != vSuccess) return r;
   }
-  c->groupPlans.clear();
-  for (auto& o : ops) c->groupPlans.push_back(o.plan);
 
   // launches of at most kMaxBatchOps ops and kMaxBatchPtrs pointers each
   const int perLaunch = std::min<int>(kMaxBatchOps, kMaxBatchPtrs / (2 * k));

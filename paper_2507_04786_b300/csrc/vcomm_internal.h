@@ -171,6 +171,21 @@ struct DirectArgs {
   int pad;
 };
 
+// ---- direct collectives of one class in one launch: op i owns units
+// [unitStart[i], unitStart[i + 1]) of the concatenated unit space (its
+// `units` real ones, at least one so that some CTA owns its tail); pointers
+// ptrs[ptrBase .. + nranks) send, then recv.
+struct DirectOpDesc {
+  unsigned long long count, chunk, inplaceMask, units;
+  int coll, nranks, nsub, root, dtype, redop, vec, ptrBase;
+};
+struct DirectBatchArgs {
+  int nops, pad;
+  unsigned long long unitStart[kMaxBatchOps + 1];
+  DirectOpDesc ops[kMaxBatchOps];
+  const void* ptrs[kMaxBatchPtrs];
+};
+
 // ---- channel partition (Sec. V-C): 16-byte packs spread over `nch` ranges,
 // the first (packs % nch) ranges one pack longer, the element tail on the last.
 VC_HD void channelRange(unsigned long long n, int unitBytes, int nch, int ch,

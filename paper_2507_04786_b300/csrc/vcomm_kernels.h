@@ -10,6 +10,10 @@ const void* copyKernel(int proto);
 // direct protocol (vcomm_direct.cu): AllReduce / ReduceScatter / Reduce per
 // (dtype, op); one byte-copy kernel for AllGather and Broadcast
 const void* directKernel(int coll, int dtype, int op);
+int directThreads(int coll, int dtype);   // the block size the kernel is compiled for
+// a group's direct calls of one (dtype, op) class (or its copies), DirectBatchArgs;
+// launched with directThreads(coll, dtype) threads
+const void* directBatchKernel(int coll, int dtype, int op);
 // cluster protocol (vcomm_cluster_inst.cu): one cluster of nranks CTAs per channel
 const void* clusterKernel(int dtype, int op);
 const void* clusterCopyKernel();

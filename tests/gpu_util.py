@@ -30,7 +30,8 @@ def bits(a):
 
 
 # The cluster protocol moves LL lines through FIFOs of fixed 8 KiB slots: to
-# the oracle it is LL with that slot size.
+# the oracle it is LL with that slot size.  The direct protocol takes its
+# segments from the Simple protocol's chunk.
 CLUSTER_SLOT_BYTES = 8192
 
 
@@ -38,6 +39,8 @@ def chunk_for(proto, dtype, slots=None, chunk_steps=1, byte_units=False):
     ub = 1 if byte_units else ESZ[dtype]
     if proto == "cluster":
         return oracle.chunk_units("ll", ub, chunk_steps, CLUSTER_SLOT_BYTES)
+    if proto == "direct":
+        proto = "simple"
     sb = None if slots is None else slots[proto]
     return oracle.chunk_units(proto, ub, chunk_steps, sb)
 

@@ -163,7 +163,7 @@ def test_tuner_table_drives_auto_calls():
     assert [e["bytes"] for e in tab] == [1024 * 4 ** i for i in range(6)]
     for e in tab:
         assert e["usec"] > 0 and 1 <= e["nchannels"] <= nch
-        assert e["proto"] in ("simple", "ll", "ll128", "cluster") and e["algo"] in ("ring", "tree")
+        assert e["proto"] in ("simple", "ll", "ll128", "cluster", "direct") and e["algo"] in ("ring", "tree")
     assert len(c.tune_table("allgather")) == 6
     assert c.tune_table("reduce") == []
     # an Auto call takes the table's plan for its size bucket

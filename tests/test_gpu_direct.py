@@ -220,7 +220,7 @@ def test_tree_is_unsupported_and_auto_takes_ring():
     assert float(d[2][5]) == 4.0
 
 
-def test_group_of_several_runs_as_simple():
+def test_group_of_several_direct_calls():
     k, n = 4, 5000
     c = get_comm(k, 4)
     xs = [data(60 + i, k, n, "fp32") for i in range(3)]
@@ -231,7 +231,7 @@ def test_group_of_several_runs_as_simple():
             c.all_reduce(s, d, op="sum", algo="ring", proto="direct")
     finish(c)
     plans = c.group_plans()
-    assert all(p["proto"] == "simple" for p in plans)
+    assert all(p["proto"] == "direct" for p in plans)
     for x3, d, p in zip(xs, dd, plans):
         want = oracle.all_reduce(x3, "fp32", "sum", p["nchannels"], chunk("fp32", p["chunkSteps"]))
         for r in range(k):
@@ -264,3 +264,57 @@ def test_headline_size_sampled():
     assert torch.equal(ref[0].view(torch.int32), d[0].view(torch.int32))
     assert torch.equal(ref[1].view(torch.int32), d[1].view(torch.int32))
     c.destroy()
+
+
+def test_mixed_group_in_one_launch():
+    """40 direct calls of every collective, dtype, op and size (down to a
+    single element, some on unaligned views) in one group: each result equals
+    the oracle's for its own plan."""
+    k = 6
+    c = get_comm(k, 4)
+    rng = np.random.default_rng(11)
+    colls = ("allreduce", "reducescatter", "allgather", "broadcast", "reduce")
+    calls = []
+    with group():
+        for i in range(40):
+            coll = colls[i % 5]
+            dtype = ("fp32", "bf16", "fp16", "int32")[int(rng.integers(4))]
+            op = ("sum", "max")[int(rng.integers(2))]
+            n = int(rng.choice([1, 3, 17, 1000, 4099, 65537]))
+            off = int(rng.integers(2)) if n > 3 else 0
+            root = int(rng.integers(k))
+            m = k * n if coll == "reducescatter" else n
+            xs = data(1000 + i, k, m, dtype)
+            s = offset_views(xs, off)
+            outn = n if coll != "allgather" else k * n
+            d = [torch.empty(outn + off, dtype=s[0].dtype, device="cuda")[off:] for _ in range(k)]
+            if coll == "allreduce":
+                c.all_reduce(s, d, op=op, algo="ring", proto="direct")
+            elif coll == "reducescatter":
+                c.reduce_scatter(s, d, op=op, algo="ring", proto="direct")
+            elif coll == "allgather":
+                c.all_gather(s, d, algo="ring", proto="direct")
+            elif coll == "broadcast":
+                c.broadcast(s, d, root=root, algo="ring", proto="direct")
+            else:
+                d = [t if r == root else None for r, t in enumerate(d)]
+                c.reduce(s, d, op=op, root=root, algo="ring", proto="direct")
+            calls.append((coll, dtype, op, root, xs, s, d))
+    finish(c)
+    plans = c.group_plans()
+    assert len(plans) == 40 and all(p["proto"] == "direct" for p in plans)
+    for (coll, dtype, op, root, xs, s, d), p in zip(calls, plans):
+        C, ch = p["nchannels"], chunk_for("direct", dtype, SMALL_SLOTS, p["chunkSteps"])
+        if coll == "allreduce":
+            want = oracle.all_reduce(xs, dtype, op, C, ch)
+        elif coll == "reducescatter":
+            want = oracle.reduce_scatter(xs, dtype, op, C, ch)
+        elif coll == "allgather":
+            want = [np.concatenate(xs)] * k
+        elif coll == "broadcast":
+            want = [xs[root]] * k
+        else:
+            assert_same(to_np(d[root], dtype), oracle.reduce(xs, dtype, op, root, C, ch), coll)
+            continue
+        for r in range(k):
+            assert_same(to_np(d[r], dtype), want[r], f"{coll} {dtype} {op} rank {r}")
