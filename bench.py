@@ -33,8 +33,8 @@ sys.path.insert(0, ROOT)
 from paper_2507_04786_b300 import inputs, workloads  # noqa: E402
 
 # FIFO bytes in HBM per data byte; the cluster protocol's FIFOs are in shared
-# memory and move no HBM bytes
-FIFO_FACTOR = {"simple": 1.0, "ll": 2.0, "ll128": 128.0 / 120.0, "cluster": 0.0}
+# memory and the direct protocol has none
+FIFO_FACTOR = {"simple": 1.0, "ll": 2.0, "ll128": 128.0 / 120.0, "cluster": 0.0, "direct": 0.0}
 
 
 def algorithmic_bytes(k, S, proto):
@@ -233,6 +233,57 @@ def run_gpu(args, rank, world):
     return {"ms_per_step": total_ms / args.steps, "launch_ms": float(np.mean(launch_ms)),
             "e2e_ms": e2e_ms, "clocks": clk.summary(), "launches": args.steps,
             "S": S, "k": k, "proto": proto}
+
+
+# ------------------------------------------------------------------ direct leg
+
+def run_direct(args):
+    """The headline workload (8 vranks x 256 MiB fp32, 37 channels) with the
+    direct protocol: no FIFO, each unit's ring chain folded from the user
+    buffers; 2kS algorithmic bytes.  Its output is compared bit for bit with
+    a Simple call of the same plan."""
+    import torch
+
+    from paper_2507_04786_b300 import Comm
+    w = workloads.HEADLINE
+    k, S = w["nranks"], args.bytes
+    n = S // 4
+    xs = inputs.workload(w["seed"], k, n, "fp32", w["dist"])
+    sends = [torch.from_numpy(x).cuda() for x in xs]
+    del xs
+    recvs = [torch.empty_like(t) for t in sends]
+    comm = Comm(k, w["nchannels"])
+    comm.set_plan(nchannels=w["nchannels"], chunk_steps=w["chunk_steps"])
+    comm.all_reduce(sends, recvs, op="sum", algo="ring", proto="simple")
+    ref = [r.clone() for r in recvs[:2]]
+    for _ in range(args.warmup):
+        comm.all_reduce(sends, recvs, op="sum", algo="ring", proto="direct")
+    torch.cuda.synchronize()
+    same = all(torch.equal(a.view(torch.int32), b.view(torch.int32)) for a, b in zip(ref, recvs[:2]))
+    del ref
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    stream = torch.cuda.current_stream()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            evs[i][0].record(stream)
+            comm.all_reduce(sends, recvs, op="sum", algo="ring", proto="direct", stream=stream)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    err = comm.async_error()
+    comm.destroy()
+    peak, peak_kind = measured_peak()
+    alg = algorithmic_bytes(k, S, "direct")
+    achieved = alg / (ms / 1e3) / 1e9
+    return {"workload": w["name"], "proto": "direct", "ms_per_step": round(ms, 4),
+            "busbw_GBps": round(busbw(S, k, ms / 1e3), 2),
+            "algbw_GBps": round(S / (ms / 1e3) / 1e9, 2),
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "algorithmic_bytes_per_launch": alg,
+                         "peak_source": peak_kind},
+            "equals_simple": bool(same), "clocks": clk.summary(), "status": err}
 
 
 # ------------------------------------------------------------------ batched leg
@@ -563,7 +614,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--proto", default="simple", choices=["simple", "ll", "ll128"])
+    ap.add_argument("--proto", default="simple", choices=["simple", "ll", "ll128", "direct"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--serve-requests", type=int, default=workloads.SERVED["bench_requests"],
                     help="requests of the served leg (the full stream is 100000)")
@@ -647,6 +698,7 @@ def main():
         "clocks": r["clocks"],
     }
     if not args.no_extras and world == 1:
+        line["direct"] = run_direct(args)
         line["small_messages"] = run_small(args)
         line["batched"] = run_batched(args)
         line["served"] = run_served(args)
