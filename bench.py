@@ -286,6 +286,46 @@ def run_direct(args):
             "equals_simple": bool(same), "clocks": clk.summary(), "status": err}
 
 
+# ------------------------------------------------------------------ all-to-all leg
+
+def run_alltoall(args):
+    """All-to-all (the grouped send / receive pattern) on 8 vranks, 256 MiB
+    per vrank (blocks of 32 MiB), fp32: 2kS bytes (every block read once and
+    written once)."""
+    import torch
+
+    from paper_2507_04786_b300 import Comm
+    k, S = 8, args.bytes
+    n = S // 4
+    sends = [torch.randn(n, device="cuda") for _ in range(k)]
+    recvs = [torch.empty_like(t) for t in sends]
+    comm = Comm(k, 1)
+    for _ in range(args.warmup):
+        comm.all_to_all(sends, recvs)
+    torch.cuda.synchronize()
+    ok = all(torch.equal(recvs[j][r * (n // k):(r + 1) * (n // k)], sends[r][j * (n // k):(j + 1) * (n // k)])
+             for r in (0, k - 1) for j in (0, 3, k - 1))
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    for i in range(args.steps):
+        evs[i][0].record()
+        comm.all_to_all(sends, recvs)
+        evs[i][1].record()
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    err = comm.async_error()
+    comm.destroy()
+    peak, peak_kind = measured_peak()
+    alg = 2 * k * S
+    achieved = alg / (ms / 1e3) / 1e9
+    return {"workload": f"alltoall-8vr-{S >> 20}MiB", "ms_per_step": round(ms, 4),
+            "algbw_GBps": round(S / (ms / 1e3) / 1e9, 2),
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "algorithmic_bytes_per_launch": alg,
+                         "peak_source": peak_kind},
+            "sampled_blocks_exact": bool(ok), "status": err}
+
+
 # ------------------------------------------------------------------ batched leg
 
 def run_batched(args):
@@ -699,6 +739,7 @@ def main():
     }
     if not args.no_extras and world == 1:
         line["direct"] = run_direct(args)
+        line["alltoall"] = run_alltoall(args)
         line["small_messages"] = run_small(args)
         line["batched"] = run_batched(args)
         line["served"] = run_served(args)

@@ -194,8 +194,36 @@ vResult_t vGroupStart(void);
 vResult_t vGroupEnd(void);
 
 /* Plans of the calls of the last group launched on `comm`, in call order
- * (channels may be lower than requested: a gang has nch/G channels). */
+ * (channels may be lower than requested: a gang has nch/G channels).
+ * Point-to-point transfers have no plan and are not listed. */
 vResult_t vcommGetGroupPlans(vcomm_t comm, vPlan_t* plans, int maxPlans, int* nPlans);
+
+/* ---- point-to-point (Sec. II-A-3: ncclSend / ncclRecv) --------------------
+ * vSend: vrank `rank` sends `count` elements from `sendbuf` (device) to vrank
+ * `peer`; vRecv: vrank `rank` receives `count` elements from vrank `peer`
+ * into `recvbuf` (device).  Every vrank lives in this process, so both sides
+ * of a transfer must be issued inside one vGroupStart / vGroupEnd; there the
+ * i-th send from a to b meets the i-th receive at b from a, and their counts
+ * and dtypes must agree (else vGroupEnd returns vInvalidArgument and runs
+ * nothing of the group).  rank == peer is a local copy.  Same-process ranks
+ * copy directly from the source to the destination buffer (Sec. IV,
+ * P2P_DIRECT); each transfer is its own task of one launch, so grouped
+ * transfers run concurrently (Sec. II-C).  Buffers are caller-owned and must
+ * be element-aligned; a receive buffer must not overlap another transfer's
+ * buffers.  Calls outside a group return vInvalidArgument. */
+vResult_t vSend(const void* sendbuf, size_t count, vDataType_t dtype, int rank, int peer,
+                vcomm_t comm, vStream_t stream);
+vResult_t vRecv(void* recvbuf, size_t count, vDataType_t dtype, int rank, int peer,
+                vcomm_t comm, vStream_t stream);
+
+/* All-to-all as the grouped send / receive pattern of Sec. II-A-4: block j
+ * (`count` elements) of sendbufs[r] lands in block r of recvbufs[j], for all
+ * r, j.  Both arrays hold nranks device pointers of nranks x count elements.
+ * Inside a group it adds its nranks^2 transfers to the group; outside, it
+ * launches them at once.  A receive buffer may not overlap any send or other
+ * receive buffer (no in-place form, except on one vrank). */
+vResult_t vAllToAll(const void* const* sendbufs, void* const* recvbufs, size_t count,
+                    vDataType_t dtype, vcomm_t comm, vStream_t stream);
 
 /* ---- autotuner ------------------------------------------------------------
  * Protocol / algorithm / channel selection (Sec. III-D; Sec. II-C: "the tuning

@@ -73,6 +73,7 @@ def lib():
         L.o_ring_reducescatter.argtypes = [i32, i32, sz, i32, i32, sz, pp, pp]
         L.o_ring_allgather.argtypes = [i32, i32, sz, sz, pp, pp]
         L.o_ring_broadcast.argtypes = [i32, i32, sz, sz, i32, pp, pp]
+        L.o_alltoall.argtypes = [i32, sz, pp, pp]
         L.o_ring_reduce.argtypes = [i32, i32, sz, i32, i32, sz, i32, pp, pp]
         L.o_tree_allreduce.argtypes = [i32, i32, sz, i32, i32, sz, pp, pp]
         L.o_encode_array.argtypes = [i32, vp, sz, vp]
@@ -266,6 +267,41 @@ def broadcast(xs, root: int, nch: int, chunk_bytes: int):
     rc = lib().o_ring_broadcast(k, nch, chunk_bytes, xs[0].nbytes, root, _ptrs(xs), _ptrs(outs))
     assert rc == 0
     return outs
+
+
+def all_to_all(xs):
+    """All-to-all (Sec. II-A-4, the grouped Send/Recv pattern): block j of
+    rank r's input (len / k elements) becomes block r of rank j's output."""
+    xs = [np.ascontiguousarray(x) for x in xs]
+    k = len(xs)
+    assert xs[0].size % k == 0
+    outs = [np.empty_like(xs[0]) for _ in range(k)]
+    rc = lib().o_alltoall(k, xs[0].nbytes // k, _ptrs(xs), _ptrs(outs))
+    assert rc == 0
+    return outs
+
+
+def p2p_match(sends, recvs):
+    """Point-to-point transfers of one group (Sec. II-A-3): sends is a list of
+    (rank, peer, array) in issue order, recvs a list of (rank, peer, count);
+    the i-th send from a to b meets the i-th receive at b from a.  Returns the
+    array each receive gets, in recvs order; raises ValueError on an
+    unmatched or mismatched transfer."""
+    from collections import defaultdict, deque
+    q = defaultdict(deque)
+    for a, b, x in sends:
+        q[(a, b)].append(np.ascontiguousarray(x))
+    out = []
+    for b, a, n in recvs:
+        if not q[(a, b)]:
+            raise ValueError(f"receive at {b} from {a} has no send")
+        x = q[(a, b)].popleft()
+        if x.size != n:
+            raise ValueError(f"send {a}->{b} of {x.size} elements meets a receive of {n}")
+        out.append(x.copy())
+    if any(q[key] for key in q):
+        raise ValueError("a send has no receive")
+    return out
 
 
 def reduce(xs, dtype: str, op: str, root: int, nch: int, chunk: int):

@@ -748,3 +748,17 @@ int o_ring_reduce_point(int k, int dt, int op, int root, const void* vals, void*
   memcpy(out, acc, (size_t)es);
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* All-to-all [Sec. II-A-4: a group of Send/Recv calls emulating All-to-All]:
+ * block j (block_bytes) of rank r's input is received by rank j as its
+ * block r.  Byte loops; no arithmetic. */
+/* ------------------------------------------------------------------------ */
+int o_alltoall(int k, size_t block_bytes, const unsigned char* const* in, unsigned char* const* out) {
+  if (k < 1) return -1;
+  for (int r = 0; r < k; r++)
+    for (int j = 0; j < k; j++)
+      for (size_t b = 0; b < block_bytes; b++)
+        out[j][(size_t)r * block_bytes + b] = in[r][(size_t)j * block_bytes + b];
+  return 0;
+}

@@ -29,7 +29,7 @@ EXPORTS = ("vcommInit", "vcommInitConfig", "vcommPrepare", "vcommDestroy", "vcom
            "vDebugEncode", "vDebugDecode", "vAllReduceNoAlloc", "vGroupStart", "vGroupEnd",
            "vcommGetGroupPlans", "vcommTune", "vcommGetTuneTable", "vcommDebugSetSkipRank",
            "vServeCreate", "vServeSubmit", "vServeQuery", "vServeRelease", "vServeGetStats",
-           "vServeDestroy")
+           "vServeDestroy", "vSend", "vRecv", "vAllToAll")
 
 
 class VcommError(RuntimeError):
@@ -278,6 +278,28 @@ class Comm:
                                          DTYPE_CODES[dt], root, ALGO_CODES[algo],
                                          PROTO_CODES[proto], _stream_handle(stream), self._h),
                "vBroadcast")
+
+    def send(self, rank, peer, tensor, count=None, stream=None):
+        """vrank `rank` sends `tensor` to vrank `peer` (inside a group)."""
+        n = tensor.numel() if count is None else count
+        _check(load_library().vSend(ctypes.c_void_p(tensor.data_ptr()), n,
+                                    DTYPE_CODES[_dtype_name(tensor)], rank, peer, self._h,
+                                    _stream_handle(stream)), "vSend")
+
+    def recv(self, rank, peer, tensor, count=None, stream=None):
+        """vrank `rank` receives into `tensor` from vrank `peer` (inside a group)."""
+        n = tensor.numel() if count is None else count
+        _check(load_library().vRecv(ctypes.c_void_p(tensor.data_ptr()), n,
+                                    DTYPE_CODES[_dtype_name(tensor)], rank, peer, self._h,
+                                    _stream_handle(stream)), "vRecv")
+
+    def all_to_all(self, sends, recvs, count=None, stream=None):
+        """Block j of sends[r] lands in block r of recvs[j]."""
+        k = len(sends)
+        n = sends[0].numel() // k if count is None else count
+        _check(load_library().vAllToAll(_ptr_array(sends), _ptr_array(recvs), n,
+                                        DTYPE_CODES[_dtype_name(sends[0])], self._h,
+                                        _stream_handle(stream)), "vAllToAll")
 
     def reduce(self, sends, recvs, op="sum", root=0, algo="ring", proto="simple", stream=None,
                count=None):

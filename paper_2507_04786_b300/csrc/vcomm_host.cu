@@ -673,6 +673,94 @@ static vResult_t launchSingle(CallSpec& cs) {
 static thread_local int tGroupDepth = 0;
 static thread_local std::vector<CallSpec> tPending;
 
+// ---- point-to-point (Sec. II-A-3: ncclSend / ncclRecv).  All vranks live in
+// one process, so a transfer needs both sides inside one group; at
+// vGroupEnd the k-th send from vrank a to b meets the k-th receive at b from
+// a (order per ordered pair).  Same-process ranks move data with direct
+// copies between source and destination buffers (Sec. IV, P2P_DIRECT); each
+// transfer is its own task of one launch (Sec. II-C: grouped sends and
+// receives run in parallel).
+struct P2PSpec {
+  vcomm* c;
+  int rank, peer;
+  bool send;
+  const void* sbuf;
+  void* rbuf;
+  size_t bytes;
+  int dtype;
+  cudaStream_t stream;
+};
+static thread_local std::vector<P2PSpec> tP2P;
+
+struct Transfer {
+  const void* src;
+  void* dst;
+  size_t bytes;
+};
+
+// byte copies, one task each, as kDirectBatchCopy ops over one-rank views
+static vResult_t launchCopies(vcomm* c, const std::vector<Transfer>& xs, cudaStream_t stream) {
+  const void* fn = directBatchKernel(kBroadcast, 0, 0);
+  const int nthr = directThreads(kBroadcast, 0);
+  const long long resident = (long long)std::max(1, residentPerSM(fn, nthr)) * c->nsm;
+  const int perLaunch = std::min<int>(kMaxBatchOps, kMaxBatchPtrs / 2);
+  for (size_t base = 0; base < xs.size(); base += perLaunch) {
+    const int n = (int)std::min<size_t>(perLaunch, xs.size() - base);
+    std::unique_ptr<DirectBatchArgs> b(new DirectBatchArgs());
+    memset(b.get(), 0, sizeof(DirectBatchArgs));
+    b->nops = n;
+    unsigned long long start = 0;
+    for (int i = 0; i < n; i++) {
+      const Transfer& t = xs[base + i];
+      const bool vec = (((uintptr_t)t.src | (uintptr_t)t.dst) & 15) == 0;
+      DirectOpDesc& d = b->ops[i];
+      d.count = t.bytes;
+      d.chunk = 16;
+      d.inplaceMask = (t.src == t.dst) ? 1ull : 0ull;
+      d.units = vec ? t.bytes / 16 : t.bytes;
+      d.coll = kBroadcast;
+      d.nranks = 1;
+      d.nsub = 1;
+      d.root = 0;
+      d.vec = vec ? 1 : 0;
+      d.ptrBase = 2 * i;
+      b->ptrs[2 * i] = t.src;
+      b->ptrs[2 * i + 1] = t.dst;
+      b->unitStart[i] = start;
+      start += std::max<unsigned long long>(d.units, 1ull);
+    }
+    b->unitStart[n] = start;
+    long long grid = (long long)((start + nthr - 1) / nthr);
+    grid = std::max<long long>(1, std::min<long long>(grid, resident));
+    void* args[] = {(void*)b.get()};
+    VC_TRY(cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(nthr), args, 0, stream));
+  }
+  return vSuccess;
+}
+
+// match one communicator's sends and receives of a group into transfers
+static vResult_t matchP2P(vcomm* c, const std::vector<P2PSpec>& ops, std::vector<Transfer>* out,
+                          cudaStream_t* stream) {
+  const int k = c->k;
+  std::vector<std::vector<const P2PSpec*>> sends((size_t)k * k), recvs((size_t)k * k);
+  for (auto& o : ops) {
+    if (o.stream != ops[0].stream) return vInvalidArgument;   // one stream per group and comm
+    if (o.send) sends[(size_t)o.rank * k + o.peer].push_back(&o);
+    else recvs[(size_t)o.peer * k + o.rank].push_back(&o);
+  }
+  *stream = ops[0].stream;
+  for (size_t pr = 0; pr < sends.size(); pr++) {
+    if (sends[pr].size() != recvs[pr].size()) return vInvalidArgument;   // unmatched
+    for (size_t i = 0; i < sends[pr].size(); i++) {
+      const P2PSpec& a = *sends[pr][i];
+      const P2PSpec& b = *recvs[pr][i];
+      if (a.bytes != b.bytes || a.dtype != b.dtype) return vInvalidArgument;
+      if (a.bytes) out->push_back(Transfer{a.sbuf, b.rbuf, a.bytes});
+    }
+  }
+  return vSuccess;
+}
+
 // the direct calls of a group: one launch per (dtype, op) class present (one
 // for the copies), each over up to kMaxBatchOps calls
 static vResult_t launchDirectGroup(vcomm* c, std::vector<CallSpec>& ops) {
@@ -994,6 +1082,73 @@ vResult_t vReduce(const void* const* sendbufs, void* const* recvbufs, size_t cou
   return collective(kReduce, sendbufs, recvbufs, count, dtype, op, root, algo, proto, stream, comm);
 }
 
+static vResult_t p2pCall(bool send, const void* sbuf, void* rbuf, size_t count, vDataType_t dtype,
+                         int rank, int peer, vcomm_t c, vStream_t stream) {
+  if (!c || dtype < vInt32 || dtype > vBfloat16) return vInvalidArgument;
+  if (rank < 0 || rank >= c->k || peer < 0 || peer >= c->k) return vInvalidArgument;
+  const size_t esz = dtypeSize(dtype);
+  const void* p = send ? sbuf : rbuf;
+  if (count && (!p || (uintptr_t)p % esz)) return vInvalidArgument;
+  if (tGroupDepth <= 0) return vInvalidArgument;   // both sides must be in one group
+  {
+    int e = ((volatile ErrWord*)c->hErr)->code;
+    if (e != 0) return (vResult_t)e;
+  }
+  tP2P.push_back(P2PSpec{c, rank, peer, send, sbuf, rbuf, count * esz, (int)dtype, (cudaStream_t)stream});
+  return vSuccess;
+}
+
+vResult_t vSend(const void* sendbuf, size_t count, vDataType_t dtype, int rank, int peer, vcomm_t comm,
+                vStream_t stream) {
+  return p2pCall(true, sendbuf, nullptr, count, dtype, rank, peer, comm, stream);
+}
+
+vResult_t vRecv(void* recvbuf, size_t count, vDataType_t dtype, int rank, int peer, vcomm_t comm,
+                vStream_t stream) {
+  return p2pCall(false, nullptr, recvbuf, count, dtype, rank, peer, comm, stream);
+}
+
+vResult_t vAllToAll(const void* const* sendbufs, void* const* recvbufs, size_t count, vDataType_t dtype,
+                    vcomm_t c, vStream_t stream) {
+  if (!c || !sendbufs || !recvbufs || dtype < vInt32 || dtype > vBfloat16) return vInvalidArgument;
+  const int k = c->k;
+  const size_t esz = dtypeSize(dtype), blk = count * esz;
+  for (int r = 0; r < k; r++) {
+    if (count && (!sendbufs[r] || !recvbufs[r])) return vInvalidArgument;
+    if ((uintptr_t)sendbufs[r] % esz || (uintptr_t)recvbufs[r] % esz) return vInvalidArgument;
+    // a receive buffer may not overlap any buffer but (exactly) its own send buffer
+    for (int q = 0; q < k && count; q++) {
+      if (q != r && overlaps((uintptr_t)recvbufs[r], k * blk, (uintptr_t)recvbufs[q], k * blk))
+        return vInvalidArgument;
+      if (overlaps((uintptr_t)recvbufs[r], k * blk, (uintptr_t)sendbufs[q], k * blk) &&
+          !(q == r && recvbufs[r] == sendbufs[r] && k == 1))
+        return vInvalidArgument;
+    }
+  }
+  {
+    int e = ((volatile ErrWord*)c->hErr)->code;
+    if (e != 0) return (vResult_t)e;
+  }
+  if (count == 0) return vSuccess;
+  // the grouped send / receive pattern of Sec. II-A-4: rank r's block j goes
+  // to block r of rank j
+  if (tGroupDepth > 0) {
+    for (int r = 0; r < k; r++)
+      for (int j = 0; j < k; j++) {
+        const char* s = (const char*)sendbufs[r] + (size_t)j * blk;
+        char* d = (char*)recvbufs[j] + (size_t)r * blk;
+        tP2P.push_back(P2PSpec{c, r, j, true, s, nullptr, blk, (int)dtype, (cudaStream_t)stream});
+        tP2P.push_back(P2PSpec{c, j, r, false, nullptr, d, blk, (int)dtype, (cudaStream_t)stream});
+      }
+    return vSuccess;
+  }
+  std::vector<Transfer> xs;
+  for (int r = 0; r < k; r++)
+    for (int j = 0; j < k; j++)
+      xs.push_back(Transfer{(const char*)sendbufs[r] + (size_t)j * blk, (char*)recvbufs[j] + (size_t)r * blk, blk});
+  return launchCopies(c, xs, (cudaStream_t)stream);
+}
+
 vResult_t vcommDebugSetSkipRank(vcomm_t c, int rank) {
   if (!c || rank < -1 || rank >= c->k) return vInvalidArgument;
   c->skipRank = rank;
@@ -1010,16 +1165,33 @@ vResult_t vGroupEnd(void) {
   if (--tGroupDepth > 0) return vSuccess;
   std::vector<CallSpec> pending;
   pending.swap(tPending);
+  std::vector<P2PSpec> p2p;
+  p2p.swap(tP2P);
   // one batch per communicator, in order of first appearance
   vResult_t first = vSuccess;
   std::vector<vcomm*> comms;
   for (auto& o : pending)
     if (std::find(comms.begin(), comms.end(), o.c) == comms.end()) comms.push_back(o.c);
-  for (vcomm* c : comms) {
+  for (auto& o : p2p)
+    if (std::find(comms.begin(), comms.end(), o.c) == comms.end()) comms.push_back(o.c);
+  // every communicator's sends and receives must match before anything runs
+  std::vector<std::vector<Transfer>> xfers(comms.size());
+  std::vector<cudaStream_t> xstream(comms.size(), nullptr);
+  for (size_t i = 0; i < comms.size(); i++) {
+    std::vector<P2PSpec> mine;
+    for (auto& o : p2p)
+      if (o.c == comms[i]) mine.push_back(o);
+    if (mine.empty()) continue;
+    vResult_t r = matchP2P(comms[i], mine, &xfers[i], &xstream[i]);
+    if (r != vSuccess) return r;
+  }
+  for (size_t i = 0; i < comms.size(); i++) {
+    vcomm* c = comms[i];
     std::vector<CallSpec> ops;
     for (auto& o : pending)
       if (o.c == c) ops.push_back(o);
-    vResult_t r = launchGroup(c, ops);
+    vResult_t r = ops.empty() ? vSuccess : launchGroup(c, ops);
+    if (r == vSuccess && !xfers[i].empty()) r = launchCopies(c, xfers[i], xstream[i]);
     if (r != vSuccess && first == vSuccess) first = r;
   }
   return first;

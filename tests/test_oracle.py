@@ -432,3 +432,45 @@ def test_rs_and_reduce_point_queries_match_replay(k, C, chunk, n, dtype, op):
         full = oracle.reduce(ys, dtype, op, root, C, chunk)
         pts = oracle.reduce_points(ys, root, np.arange(n), dtype, op)
         assert np.array_equal(pts.view(np.uint8), full.view(np.uint8))
+
+
+# ---------------------------------------------------------------- all-to-all and point-to-point
+
+def test_all_to_all_hand_example():
+    """Sec. II-A-4's all-to-all pattern, written out for 3 vranks x 2 elements
+    per block: rank j receives block j of every rank, in rank order."""
+    xs = [np.array([0, 1, 2, 3, 4, 5], dtype=np.int32) + 10 * r for r in range(3)]
+    want = [[0, 1, 10, 11, 20, 21], [2, 3, 12, 13, 22, 23], [4, 5, 14, 15, 24, 25]]
+    got = oracle.all_to_all(xs)
+    for j in range(3):
+        assert got[j].tolist() == want[j]
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 9])
+@pytest.mark.parametrize("dt", [np.float32, np.uint16, np.int32])
+def test_all_to_all_is_an_involution(k, dt):
+    rng = np.random.default_rng(k)
+    n = 7
+    xs = [rng.integers(0, 60000, k * n).astype(dt) for _ in range(k)]
+    once = oracle.all_to_all(xs)
+    twice = oracle.all_to_all(once)
+    for r in range(k):
+        assert np.array_equal(twice[r].view(np.uint8), xs[r].view(np.uint8))
+        for j in range(k):   # block j of rank r's output is block r of rank j's input
+            assert np.array_equal(once[r][j * n:(j + 1) * n], xs[j][r * n:(r + 1) * n])
+    if k == 1:
+        assert np.array_equal(once[0], xs[0])
+
+
+def test_p2p_match_pairs_in_order():
+    a0, a1, b0 = np.arange(3), np.arange(5) + 100, np.arange(2) + 7
+    sends = [(0, 1, a0), (2, 1, b0), (0, 1, a1)]
+    recvs = [(1, 0, 3), (1, 2, 2), (1, 0, 5)]
+    got = oracle.p2p_match(sends, recvs)
+    assert [g.tolist() for g in got] == [a0.tolist(), b0.tolist(), a1.tolist()]
+    with pytest.raises(ValueError):
+        oracle.p2p_match(sends, recvs[:2])                  # a send without its receive
+    with pytest.raises(ValueError):
+        oracle.p2p_match(sends, [(1, 0, 5), (1, 2, 2), (1, 0, 3)])   # counts cross
+    with pytest.raises(ValueError):
+        oracle.p2p_match(sends[:1], [(1, 0, 3), (0, 1, 3)])  # a receive without a send
