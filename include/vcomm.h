@@ -126,6 +126,17 @@ vResult_t vcommDestroy(vcomm_t comm);
  * waits for the device and frees the communicator. */
 vResult_t vcommAbort(vcomm_t comm);
 
+/* Recovery (Sec. II-A-1: abort is "intended for error recovery").
+ * vcommAbortPending raises the abort word like vcommAbort, waits until the
+ * in-flight kernels have returned (their waits end with vAborted), and keeps
+ * the communicator.  vcommReset makes a failed or aborted communicator usable
+ * again: it waits for the device, re-zeroes every FIFO arena and its
+ * counters (a failed call leaves them half written), clears the error and
+ * abort words and the debug fault injection.  It must not be called with
+ * work of this communicator still to be launched (inside a group: error). */
+vResult_t vcommAbortPending(vcomm_t comm);
+vResult_t vcommReset(vcomm_t comm);
+
 /* Asynchronous error of the communicator: vSuccess, vTimeout (a flag wait hit
  * its deadline) or vAborted.  Does not synchronise. */
 vResult_t vcommGetAsyncError(vcomm_t comm, vResult_t* err);

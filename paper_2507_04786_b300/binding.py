@@ -29,7 +29,7 @@ EXPORTS = ("vcommInit", "vcommInitConfig", "vcommPrepare", "vcommDestroy", "vcom
            "vDebugEncode", "vDebugDecode", "vAllReduceNoAlloc", "vGroupStart", "vGroupEnd",
            "vcommGetGroupPlans", "vcommTune", "vcommGetTuneTable", "vcommDebugSetSkipRank",
            "vServeCreate", "vServeSubmit", "vServeQuery", "vServeRelease", "vServeGetStats",
-           "vServeDestroy", "vSend", "vRecv", "vAllToAll")
+           "vServeDestroy", "vSend", "vRecv", "vAllToAll", "vcommAbortPending", "vcommReset")
 
 
 class VcommError(RuntimeError):
@@ -179,6 +179,14 @@ class Comm:
         if self._h:
             _check(load_library().vcommDestroy(self._h), "vcommDestroy")
             self._h = ctypes.c_void_p()
+
+    def abort_pending(self):
+        """Raise the abort word; in-flight calls return early; the comm stays."""
+        _check(load_library().vcommAbortPending(self._h), "vcommAbortPending")
+
+    def reset(self):
+        """Make a failed or aborted communicator usable again."""
+        _check(load_library().vcommReset(self._h), "vcommReset")
 
     def abort(self):
         if self._h:

@@ -158,6 +158,9 @@ static vResult_t ensureArena(vcomm* c, int algo, int proto) {
   return vSuccess;
 }
 
+// nesting depth of vGroupStart / vGroupEnd on this thread
+static thread_local int tGroupDepth = 0;
+
 extern "C" {
 
 int vcommVersion(void) { return 100; }
@@ -235,6 +238,32 @@ vResult_t vcommAbort(vcomm_t c) {
   vResult_t r = fromCuda(cudaDeviceSynchronize());
   freeComm(c);
   return r;
+}
+
+vResult_t vcommAbortPending(vcomm_t c) {
+  if (!c) return vInvalidArgument;
+  *(volatile int*)c->hAbort = 1;
+  return fromCuda(cudaDeviceSynchronize());
+}
+
+vResult_t vcommReset(vcomm_t c) {
+  if (!c) return vInvalidArgument;
+  if (tGroupDepth > 0) return vInvalidArgument;
+  VC_TRY(cudaDeviceSynchronize());   // nothing of this communicator may still run
+  // a failed collective leaves its FIFOs half written and its counters
+  // unequal: start every arena afresh
+  for (auto& row : c->arena)
+    for (auto& a : row) {
+      if (!a.ready) continue;
+      VC_TRY(cudaMemset(a.dBuf, 0, a.bytes));
+      VC_TRY(cudaMemset(a.dCtr, 0, (size_t)a.nconn * 2 * kCounterStride * sizeof(unsigned long long)));
+    }
+  VC_TRY(cudaMemset(c->dClaim, 0, sizeof(int)));
+  VC_TRY(cudaDeviceSynchronize());
+  memset(c->hErr, 0, sizeof(ErrWord));
+  *(volatile int*)c->hAbort = 0;
+  c->skipRank = -1;
+  return vSuccess;
 }
 
 vResult_t vcommGetAsyncError(vcomm_t c, vResult_t* err) {
@@ -670,7 +699,6 @@ static vResult_t launchSingle(CallSpec& cs) {
 // vGroupStart / vGroupEnd (Sec. II-A-4): calls between them are validated and
 // planned at once but launched together at vGroupEnd, one batch kernel per
 // communicator.
-static thread_local int tGroupDepth = 0;
 static thread_local std::vector<CallSpec> tPending;
 
 // ---- point-to-point (Sec. II-A-3: ncclSend / ncclRecv).  All vranks live in
