@@ -9,8 +9,10 @@ Each function cites the passage of "Demystifying NCCL" (arXiv 2507.04786) it
 models; the readings taken where the paper is silent are listed at the top of
 the C file.
 
-Dtypes are named 'int32', 'fp32', 'fp16', 'bf16'.  bf16 arrays are carried as
-numpy uint16 bit patterns; fp16 arrays may be numpy float16 or uint16 bits.
+Dtypes are named 'int8', 'uint8', 'int32', 'uint32', 'int64', 'uint64', 'fp16',
+'bf16', 'fp32', 'fp64'; ops 'sum', 'prod', 'max', 'min', 'avg'.  bf16 arrays
+are carried as numpy uint16 bit patterns; fp16 arrays may be numpy float16 or
+uint16 bits.
 """
 from __future__ import annotations
 
@@ -24,9 +26,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "vcomm_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-DTYPES = {"int32": 0, "fp32": 1, "fp16": 2, "bf16": 3}
-ESIZE = {"int32": 4, "fp32": 4, "fp16": 2, "bf16": 2}
-OPS = {"sum": 0, "max": 1}
+DTYPES = {"int32": 0, "fp32": 1, "fp16": 2, "bf16": 3, "int8": 5, "uint8": 6, "uint32": 7,
+          "int64": 8, "uint64": 9, "fp64": 10}
+ESIZE = {"int32": 4, "fp32": 4, "fp16": 2, "bf16": 2, "int8": 1, "uint8": 1, "uint32": 4,
+         "int64": 8, "uint64": 8, "fp64": 8}
+OPS = {"sum": 0, "max": 1, "prod": 2, "min": 3, "avg": 4}
 PROTOS = {"simple": 0, "ll": 1, "ll128": 2}
 PRIMS = {0: None, 1: "send", 2: "recv", 3: "recvReduceSend", 4: "recvCopySend",
          5: "recvReduceCopySend", 6: "copySend", 7: "recvReduceCopy"}
@@ -219,7 +223,9 @@ def _check(xs, n, dtype):
 
 
 def _np_dtype(dtype):
-    return {"int32": np.int32, "fp32": np.float32, "fp16": np.float16, "bf16": np.uint16}[dtype]
+    return {"int32": np.int32, "fp32": np.float32, "fp16": np.float16, "bf16": np.uint16,
+            "int8": np.int8, "uint8": np.uint8, "uint32": np.uint32, "int64": np.int64,
+            "uint64": np.uint64, "fp64": np.float64}[dtype]
 
 
 def all_reduce(xs, dtype: str, op: str, nch: int, chunk: int, algo: str = "ring"):

@@ -28,6 +28,13 @@
  *   R5 double binary tree: tree A over nodes i = r + 1, tree B by mirror (k
  *      even) or shift by one (k odd); the data of each channel is split into two
  *      halves, the first on tree A and the second on tree B.
+ *   R18 ops and dtypes beyond the paper's examples: prod rounds each hop's
+ *      product to the dtype like sum; min keeps the received operand on ties
+ *      like max; integers (8, 32, 64 bits, signed or not) wrap; avg adds on
+ *      every hop and divides the completed value by the number of ranks in
+ *      the one step that completes it (recvReduceCopy / recvReduceCopySend:
+ *      the ring segment owner, the tree root, the Reduce root), integers
+ *      truncating toward zero, floats rounding once.
  *
  * Arithmetic: values are widened exactly to double, combined in double and
  * rounded once to the user dtype with the encoders below (own implementation
@@ -41,9 +48,13 @@
 #include <math.h>
 
 /* dtype codes (oracle-private) */
-enum { O_INT32 = 0, O_FP32 = 1, O_FP16 = 2, O_BF16 = 3, O_BYTE = 4 };
-/* reduction codes */
-enum { O_SUM = 0, O_MAX = 1 };
+enum {
+  O_INT32 = 0, O_FP32 = 1, O_FP16 = 2, O_BF16 = 3, O_BYTE = 4,
+  O_INT8 = 5, O_UINT8 = 6, O_UINT32 = 7, O_INT64 = 8, O_UINT64 = 9, O_FP64 = 10
+};
+/* reduction codes.  avg is the sum whose final value is divided by the
+ * number of ranks where the schedule completes it (reading R18). */
+enum { O_SUM = 0, O_MAX = 1, O_PROD = 2, O_MIN = 3, O_AVG = 4 };
 /* protocol codes */
 enum { O_SIMPLE = 0, O_LL = 1, O_LL128 = 2 };
 /* primitive codes, named after Sec. V-B */
@@ -54,12 +65,19 @@ enum {
 
 int o_dtype_size(int dt) {
   switch (dt) {
-    case O_INT32: case O_FP32: return 4;
+    case O_INT32: case O_FP32: case O_UINT32: return 4;
     case O_FP16: case O_BF16: return 2;
-    case O_BYTE: return 1;
+    case O_BYTE: case O_INT8: case O_UINT8: return 1;
+    case O_INT64: case O_UINT64: case O_FP64: return 8;
   }
   return 0;
 }
+
+static int o_is_int(int dt) {
+  return dt == O_INT32 || dt == O_INT8 || dt == O_UINT8 || dt == O_UINT32 || dt == O_INT64 ||
+         dt == O_UINT64;
+}
+static int o_is_signed(int dt) { return dt == O_INT32 || dt == O_INT8 || dt == O_INT64; }
 
 /* ------------------------------------------------------------------------ */
 /* IEEE 754 binary formats: exact decode and round-to-nearest-even encode.   */
@@ -156,6 +174,7 @@ void o_decode_array(int dt, const void* in, size_t n, double* x) {
 /* ------------------------------------------------------------------------ */
 static double o_get(int dt, const void* p, size_t i) {
   switch (dt) {
+    case O_FP64: { double v; memcpy(&v, (const char*)p + 8 * i, 8); return v; }
     case O_FP32: { uint32_t b; memcpy(&b, (const char*)p + 4 * i, 4); return o_f32bits_to_f64(b); }
     case O_FP16: return o_f16_to_f64(((const uint16_t*)p)[i]);
     case O_BF16: return o_bf16_to_f64(((const uint16_t*)p)[i]);
@@ -164,30 +183,79 @@ static double o_get(int dt, const void* p, size_t i) {
 }
 static void o_put(int dt, void* p, size_t i, double v) {
   switch (dt) {
+    case O_FP64: memcpy((char*)p + 8 * i, &v, 8); break;
     case O_FP32: { uint32_t b = o_f64_to_f32bits(v); memcpy((char*)p + 4 * i, &b, 4); break; }
     case O_FP16: ((uint16_t*)p)[i] = o_f64_to_f16(v); break;
     case O_BF16: ((uint16_t*)p)[i] = o_f64_to_bf16(v); break;
   }
 }
 
+/* integer element i as a 64-bit pattern: sign-extended for signed types,
+ * zero-extended for unsigned ones */
+static uint64_t o_geti(int dt, const void* p, size_t i) {
+  switch (dt) {
+    case O_INT8: return (uint64_t)(int64_t)((const int8_t*)p)[i];
+    case O_UINT8: return (uint64_t)((const uint8_t*)p)[i];
+    case O_INT32: return (uint64_t)(int64_t)((const int32_t*)p)[i];
+    case O_UINT32: return (uint64_t)((const uint32_t*)p)[i];
+    case O_INT64: case O_UINT64: { uint64_t v; memcpy(&v, (const char*)p + 8 * i, 8); return v; }
+  }
+  return 0;
+}
+/* store the low bits (two's-complement wraparound) */
+static void o_puti(int dt, void* p, size_t i, uint64_t v) {
+  switch (dt) {
+    case O_INT8: case O_UINT8: ((uint8_t*)p)[i] = (uint8_t)v; break;
+    case O_INT32: case O_UINT32: { uint32_t w = (uint32_t)v; memcpy((char*)p + 4 * i, &w, 4); break; }
+    case O_INT64: case O_UINT64: memcpy((char*)p + 8 * i, &v, 8); break;
+  }
+}
+
 static void o_reduce_elem(int dt, int op, const void* a, size_t ia, const void* b, size_t ib,
                           void* out, size_t io) {
-  if (dt == O_INT32) {
-    int32_t x = ((const int32_t*)a)[ia], y = ((const int32_t*)b)[ib], r;
-    if (op == O_SUM) r = (int32_t)((uint32_t)x + (uint32_t)y);   /* two's-complement wrap */
-    else r = (y > x) ? y : x;
-    ((int32_t*)out)[io] = r;
+  const int es = o_dtype_size(dt);
+  if (op == O_AVG) op = O_SUM;   /* the hops of avg add; the final division is o_div_elem */
+  if (o_is_int(dt)) {
+    uint64_t x = o_geti(dt, a, ia), y = o_geti(dt, b, ib), r;
+    int bgt, blt;   /* is the local operand strictly greater / smaller? */
+    if (o_is_signed(dt)) { bgt = (int64_t)y > (int64_t)x; blt = (int64_t)y < (int64_t)x; }
+    else { bgt = y > x; blt = y < x; }
+    switch (op) {
+      case O_SUM: r = x + y; break;                   /* wraps modulo 2^64, then to the width */
+      case O_PROD: r = x * y; break;                  /* low bits of the product */
+      case O_MAX: r = bgt ? y : x; break;             /* ties keep the received operand */
+      default: r = blt ? y : x; break;                /* O_MIN */
+    }
+    o_puti(dt, out, io, r);
     return;
   }
   double x = o_get(dt, a, ia), y = o_get(dt, b, ib);
   if (op == O_SUM) {
     o_put(dt, out, io, x + y);
+  } else if (op == O_PROD) {
+    /* exact in double for fp32 / fp16 / bf16 operands (<= 48 significant
+     * bits), so o_put rounds once; for fp64 the double product is the
+     * correctly rounded one */
+    o_put(dt, out, io, x * y);
   } else {
     /* select a bit pattern, no rounding: ties (including +0 == -0) keep a */
-    int es = o_dtype_size(dt);
-    if (y > x) memcpy((char*)out + es * io, (const char*)b + es * ib, es);
+    int take_b = (op == O_MAX) ? (y > x) : (y < x);
+    if (take_b) memcpy((char*)out + es * io, (const char*)b + es * ib, es);
     else memcpy((char*)out + es * io, (const char*)a + es * ia, es);
   }
+}
+
+/* avg's final step: element i of p divided by k (integers truncate toward
+ * zero; floats round once to the dtype -- a double quotient rounded again is
+ * innocuous, 53 >= 2p + 2) */
+static void o_div_elem(int dt, void* p, size_t i, int k) {
+  if (o_is_int(dt)) {
+    uint64_t v = o_geti(dt, p, i);
+    if (o_is_signed(dt)) o_puti(dt, p, i, (uint64_t)((int64_t)v / (int64_t)k));
+    else o_puti(dt, p, i, v / (uint64_t)k);
+    return;
+  }
+  o_put(dt, p, i, o_get(dt, p, i) / (double)k);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -343,7 +411,7 @@ void o_tree_prims(int k, int t, int r, int* up, int* down) {
 /* recv = FIFO contents from the predecessor, local = user input, out = user */
 /* output, fifo_out = what goes to the successor.                            */
 /* ------------------------------------------------------------------------ */
-static void o_exec(int prim, int dt, int op, size_t n, const void* recv, const void* local,
+static void o_exec(int prim, int dt, int op, int k, size_t n, const void* recv, const void* local,
                    void* out, void* fifo_out) {
   int es = o_dtype_size(dt);
   size_t nb = n * (size_t)es;
@@ -367,9 +435,13 @@ static void o_exec(int prim, int dt, int op, size_t n, const void* recv, const v
       break;
     case P_RECV_REDUCE_COPY:
       for (size_t i = 0; i < n; i++) o_reduce_elem(dt, op, recv, i, local, i, out, i);
+      if (op == O_AVG) for (size_t i = 0; i < n; i++) o_div_elem(dt, out, i, k);
       break;
     case P_RECV_REDUCE_COPY_SEND:
+      /* the step that completes a value writes it and forwards it: avg
+       * divides here, once */
       for (size_t i = 0; i < n; i++) o_reduce_elem(dt, op, recv, i, local, i, out, i);
+      if (op == O_AVG) for (size_t i = 0; i < n; i++) o_div_elem(dt, out, i, k);
       memcpy(fifo_out, out, nb);
       break;
     default:
@@ -410,7 +482,7 @@ int o_ring_allreduce(int k, int nch, size_t chunk, int dt, int op, size_t count,
           size_t b = a + c;
           if (b > end) b = end;
           size_t n = b - a;
-          o_exec(prim, dt, op, n, fprev[o_mod(r - 1, k)], (const char*)send[r] + a * es,
+          o_exec(prim, dt, op, k, n, fprev[o_mod(r - 1, k)], (const char*)send[r] + a * es,
                  (char*)recv[r] + a * es, fnext[r]);
         }
         char** tmp = fprev; fprev = fnext; fnext = tmp;
@@ -448,7 +520,7 @@ int o_ring_reducescatter(int k, int nch, size_t chunk, int dt, int op, size_t re
         for (int r = 0; r < k; r++) {
           int s = o_mod(r - t - 1, k);
           size_t a = (size_t)s * recvcount + off;
-          o_exec(prim, dt, op, n, fprev[o_mod(r - 1, k)], (const char*)send[r] + a * es,
+          o_exec(prim, dt, op, k, n, fprev[o_mod(r - 1, k)], (const char*)send[r] + a * es,
                  (char*)recv[r] + off * es, fnext[r]);
         }
         char** tmp = fprev; fprev = fnext; fnext = tmp;
@@ -481,7 +553,7 @@ int o_ring_allgather(int k, int nch, size_t chunk, size_t nbytes,
         int prim = (k == 1) ? P_COPY_SEND : o_ring_allgather_prim(k, t, 0);
         for (int r = 0; r < k; r++) {
           int blk = o_mod(r - t, k);
-          o_exec(prim, O_BYTE, O_SUM, n, fprev[o_mod(r - 1, k)], (const char*)send[r] + off,
+          o_exec(prim, O_BYTE, O_SUM, k, n, fprev[o_mod(r - 1, k)], (const char*)send[r] + off,
                  (char*)recv[r] + (size_t)blk * nbytes + off, fnext[r]);
         }
         char** tmp = fprev; fprev = fnext; fnext = tmp;
@@ -510,7 +582,7 @@ int o_ring_broadcast(int k, int nch, size_t chunk, size_t nbytes, int root,
       for (int p = 0; p < k; p++) {           /* walk the chain root, root+1, ... */
         int r = o_mod(root + p, k);
         int prim = (k == 1) ? P_COPY_SEND : o_bcast_prim(k, root, r, 0);
-        o_exec(prim, O_BYTE, O_SUM, n, fifo, (const char*)send[r] + off, (char*)recv[r] + off,
+        o_exec(prim, O_BYTE, O_SUM, k, n, fifo, (const char*)send[r] + off, (char*)recv[r] + off,
                fifo2);
         char* tmp = fifo; fifo = fifo2; fifo2 = tmp;
       }
@@ -540,7 +612,7 @@ int o_ring_reduce(int k, int nch, size_t chunk, int dt, int op, size_t count, in
       for (int p = 0; p < k; p++) {           /* walk the chain root+1, ..., root */
         int r = o_mod(root + 1 + p, k);
         int prim = o_reduce_prim(k, root, r);
-        o_exec(prim, dt, op, n, fifo, (const char*)send[r] + off * es,
+        o_exec(prim, dt, op, k, n, fifo, (const char*)send[r] + off * es,
                recv[r] ? (char*)recv[r] + off * es : NULL, fifo2);
         char* tmp = fifo; fifo = fifo2; fifo2 = tmp;
       }
@@ -595,6 +667,8 @@ int o_tree_allreduce(int k, int nch, size_t chunk, int dt, int op, size_t count,
       OTreeCtx c = {k, t, dt, op, n, off, send, val};
       int root = o_tree_root(k, t);
       o_tree_up(&c, root);
+      /* the root's recvReduceCopySend completes the value (avg divides) */
+      if (op == O_AVG) for (size_t i = 0; i < n; i++) o_div_elem(dt, val[root], i, k);
       for (int r = 0; r < k; r++) memcpy((char*)recv[r] + off * es, val[root], n * (size_t)es);
     }
   }
@@ -687,6 +761,7 @@ int o_ring_allreduce_point(int k, int nch, size_t chunk, int dt, int op, size_t 
       int r = o_mod(s + m, k);
       o_reduce_elem(dt, op, acc, 0, vals, (size_t)r, acc, 0);
     }
+    if (op == O_AVG) o_div_elem(dt, acc, 0, k);
     memcpy(out, acc, (size_t)es);
     return 0;
   }
@@ -720,6 +795,7 @@ int o_tree_allreduce_point(int k, int nch, size_t chunk, int dt, int op, size_t 
     if (i < start || i >= start + len) continue;
     char acc[8];
     o_tree_point_up(k, j % 2, dt, op, o_tree_root(k, j % 2), vals, acc);
+    if (op == O_AVG) o_div_elem(dt, acc, 0, k);
     memcpy(out, acc, (size_t)es);
     return 0;
   }
@@ -734,6 +810,7 @@ int o_ring_reducescatter_point(int k, int dt, int op, int b, const void* vals, v
   char acc[8];
   memcpy(acc, (const char*)vals + (size_t)es * (size_t)o_mod(b + 1, k), (size_t)es);
   for (int m = 2; m <= k; m++) o_reduce_elem(dt, op, acc, 0, vals, (size_t)o_mod(b + m, k), acc, 0);
+  if (op == O_AVG && k > 1) o_div_elem(dt, acc, 0, k);
   memcpy(out, acc, (size_t)es);
   return 0;
 }
@@ -745,6 +822,7 @@ int o_ring_reduce_point(int k, int dt, int op, int root, const void* vals, void*
   char acc[8];
   memcpy(acc, (const char*)vals + (size_t)es * (size_t)o_mod(root + 1, k), (size_t)es);
   for (int m = 2; m <= k; m++) o_reduce_elem(dt, op, acc, 0, vals, (size_t)o_mod(root + m, k), acc, 0);
+  if (op == O_AVG && k > 1) o_div_elem(dt, acc, 0, k);
   memcpy(out, acc, (size_t)es);
   return 0;
 }

@@ -17,8 +17,12 @@ import math
 
 import numpy as np
 
-NP_DTYPE = {"int32": np.int32, "fp32": np.float32, "fp16": np.float16, "bf16": np.uint16}
-ESIZE = {"int32": 4, "fp32": 4, "fp16": 2, "bf16": 2}
+NP_DTYPE = {"int32": np.int32, "fp32": np.float32, "fp16": np.float16, "bf16": np.uint16,
+            "int8": np.int8, "uint8": np.uint8, "uint32": np.uint32, "int64": np.int64,
+            "uint64": np.uint64, "fp64": np.float64}
+ESIZE = {"int32": 4, "fp32": 4, "fp16": 2, "bf16": 2, "int8": 1, "uint8": 1, "uint32": 4,
+         "int64": 8, "uint64": 8, "fp64": 8}
+INT_TYPES = ("int8", "uint8", "int32", "uint32", "int64", "uint64")
 
 
 def rng_for(seed: int, rank: int) -> np.random.Generator:
@@ -38,25 +42,33 @@ def cast(x64: np.ndarray, dtype: str) -> np.ndarray:
         return x64.astype(np.float16)
     if dtype == "bf16":
         return _to_bf16_bits(x64)
-    if dtype == "int32":
-        return x64.astype(np.int32)
+    if dtype == "fp64":
+        return np.asarray(x64, dtype=np.float64).copy()
+    if dtype in INT_TYPES:
+        return x64.astype(NP_DTYPE[dtype])
     raise ValueError(dtype)
 
 
 def rank_values(seed: int, rank: int, n: int, dtype: str, dist: str = "normal",
                 lo: int = -1000, hi: int = 1000) -> np.ndarray:
     """n values of one vrank.  dist: 'normal' N(0,1), 'uniform' U[-1,1],
-    'int' integers in [lo, hi] (inclusive), cast to dtype."""
+    'int' integers in [lo, hi] (inclusive), 'pow2' +-2^-1, +-1, +-2; cast to
+    dtype."""
     g = rng_for(seed, rank)
     if dist == "normal":
         return cast(g.standard_normal(n), dtype)
     if dist == "uniform":
         return cast(g.uniform(-1.0, 1.0, n), dtype)
     if dist == "int":
+        if dtype in INT_TYPES:
+            # draw in the type's own width so that full 64-bit ranges work
+            return g.integers(lo, hi, size=n, endpoint=True, dtype=NP_DTYPE[dtype])
         v = g.integers(lo, hi, size=n, endpoint=True)
-        if dtype == "int32":
-            return v.astype(np.int32)
         return cast(v.astype(np.float64), dtype)
+    if dist == "pow2":   # +-2^e, e in [-1, 1]: products of a few are exact in every float type
+        e = g.integers(-1, 1, size=n, endpoint=True).astype(np.float64)
+        sgn = np.where(g.integers(0, 1, size=n, endpoint=True) == 1, 1.0, -1.0)
+        return cast(sgn * np.exp2(e), dtype)
     raise ValueError(dist)
 
 

@@ -474,3 +474,123 @@ def test_p2p_match_pairs_in_order():
         oracle.p2p_match(sends, [(1, 0, 5), (1, 2, 2), (1, 0, 3)])   # counts cross
     with pytest.raises(ValueError):
         oracle.p2p_match(sends[:1], [(1, 0, 3), (0, 1, 3)])  # a receive without a send
+
+
+# ---------------------------------------------------------------- more ops and dtypes (reading R18)
+
+INT_BITS = {"int8": (8, True), "uint8": (8, False), "int32": (32, True), "uint32": (32, False),
+            "int64": (64, True), "uint64": (64, False)}
+
+
+def _wrap(v, dtype):
+    bits, signed = INT_BITS[dtype]
+    v %= 2 ** bits
+    return v - 2 ** bits if signed and v >= 2 ** (bits - 1) else v
+
+
+def _bf16_to_f64(bits):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(bits).view(np.int16)).view(torch.bfloat16).double().numpy()
+
+
+def plain_ext(xs, dtype, op, k):
+    """Order-free definitions for the inputs below: Python integers for the
+    integer types (wrap to the width; avg truncates toward zero), numpy
+    min / max, and exact sums / products for the floats."""
+    if dtype in INT_BITS:
+        cols = zip(*[x.tolist() for x in xs])
+        out = []
+        for col in cols:
+            if op in ("sum", "avg"):
+                v = _wrap(sum(col), dtype)
+                if op == "avg":
+                    v = abs(v) // k * (1 if v >= 0 else -1)
+            elif op == "prod":
+                v = 1
+                for c in col:
+                    v = _wrap(v * c, dtype)
+            else:
+                v = max(col) if op == "max" else min(col)
+            out.append(v)
+        return np.array(out, dtype=xs[0].dtype)
+    a = np.stack([_bf16_to_f64(x) if dtype == "bf16" else x.astype(np.float64) for x in xs])
+    if op == "max":
+        r = a.max(axis=0)
+    elif op == "min":
+        r = a.min(axis=0)
+    elif op == "prod":
+        r = a.prod(axis=0)
+    else:
+        r = a.sum(axis=0) / (k if op == "avg" else 1)
+    return inputs.cast(r, dtype)
+
+
+def ext_inputs(seed, k, n, dtype, op):
+    if dtype in INT_BITS:
+        bits, signed = INT_BITS[dtype]
+        lo, hi = (-2 ** (bits - 1), 2 ** (bits - 1) - 1) if signed else (0, 2 ** bits - 1)
+        return inputs.workload(seed, k, n, dtype, "int", lo=lo, hi=hi)
+    if op == "prod":
+        return inputs.workload(seed, k, n, dtype, "pow2")
+    if op in ("max", "min"):
+        return inputs.workload(seed, k, n, dtype, "normal")
+    # integers whose every partial sum is exact in the type
+    lim = {"fp64": 10 ** 6, "fp32": 1000, "fp16": 200, "bf16": 50}[dtype]
+    return inputs.workload(seed, k, n, dtype, "int", lo=-lim, hi=lim)
+
+
+EXT_TYPES = ["int8", "uint8", "int32", "uint32", "int64", "uint64", "fp16", "bf16", "fp32", "fp64"]
+
+
+@pytest.mark.parametrize("k,n,C,chunk", [(1, 17, 1, 16), (2, 64, 3, 16), (3, 17, 1, 32),
+                                         (5, 64, 3, 16), (4, 33, 2, 32)])
+@pytest.mark.parametrize("dtype", EXT_TYPES)
+@pytest.mark.parametrize("op", ["sum", "prod", "max", "min", "avg"])
+def test_brute_force_ops_and_dtypes(k, n, C, chunk, dtype, op):
+    xs = ext_inputs(977 * k + n, k, n, dtype, op)
+    want = plain_ext(xs, dtype, op, k)
+    for algo in ("ring", "tree"):
+        for o in oracle.all_reduce(xs, dtype, op, C, chunk, algo):
+            assert np.array_equal(o.view(np.uint8), want.view(np.uint8)), algo
+    big = ext_inputs(5 + n, k, k * n, dtype, op)
+    full = plain_ext(big, dtype, op, k)
+    rs = oracle.reduce_scatter(big, dtype, op, C, chunk)
+    for b in range(k):
+        assert np.array_equal(rs[b].view(np.uint8), full[b * n:(b + 1) * n].view(np.uint8))
+    for root in range(k):
+        got = oracle.reduce(xs, dtype, op, root, C, chunk)
+        assert np.array_equal(got.view(np.uint8), want.view(np.uint8))
+
+
+def test_avg_divides_once_at_the_end():
+    """avg is the sum divided by k once: 3 ranks of fp32 1.0 give 1.0 (an avg
+    that divided on every hop would give (1/3 + 1)/3 + 1 ...), and the integer
+    form truncates toward zero."""
+    xs = [np.ones(5, dtype=np.float32) for _ in range(3)]
+    for algo in ("ring", "tree"):
+        for o in oracle.all_reduce(xs, "fp32", "avg", 1, 16, algo):
+            assert o.tolist() == [1.0] * 5
+    ys = [np.array([-7, 7, -8, 8], dtype=np.int32), np.array([0, 0, 0, 0], dtype=np.int32)]
+    assert oracle.all_reduce(ys, "int32", "avg", 1, 16)[0].tolist() == [-3, 3, -4, 4]
+    zs = [np.array([1.0, 2.0], dtype=np.float64) for _ in range(3)]
+    assert oracle.reduce(zs, "fp64", "avg", 1, 1, 2).tolist() == [1.0, 2.0]
+
+
+@pytest.mark.parametrize("dtype,op", [("fp64", "sum"), ("fp32", "prod"), ("bf16", "avg"),
+                                      ("int8", "sum"), ("uint64", "min"), ("fp16", "avg")])
+def test_point_queries_match_replay_new_ops(dtype, op):
+    k, C, chunk, n = 5, 3, 32, 3001
+    dist = "int" if dtype in INT_BITS else ("pow2" if op == "prod" else "normal")
+    kw = {}
+    if dtype in INT_BITS:
+        bits, signed = INT_BITS[dtype]
+        kw = {"lo": -2 ** (bits - 1) if signed else 0, "hi": 2 ** (bits - 1) - 1 if signed else 2 ** bits - 1}
+    xs = inputs.workload(41, k, n, dtype, dist, **kw)
+    for algo in ("ring", "tree"):
+        full = oracle.all_reduce(xs, dtype, op, C, chunk, algo)[0]
+        pts = oracle.all_reduce_points(xs, np.arange(n), dtype, op, C, chunk, algo)
+        assert np.array_equal(pts.view(np.uint8), full.view(np.uint8)), algo
+    for root in (0, k - 1):
+        full = oracle.reduce(xs, dtype, op, root, C, chunk)
+        pts = oracle.reduce_points(xs, root, np.arange(n), dtype, op)
+        assert np.array_equal(pts.view(np.uint8), full.view(np.uint8))
