@@ -52,8 +52,22 @@ typedef enum {
   vInternalError = 7
 } vResult_t;
 
-typedef enum { vInt32 = 0, vFloat32 = 1, vFloat16 = 2, vBfloat16 = 3 } vDataType_t;
-typedef enum { vSum = 0, vMax = 1 } vRedOp_t;
+/* Element types.  The paper names only the element notion (Sec. V-C: the
+ * user type for reductions, bytes for AllGather / Broadcast); the list is
+ * NCCL's.  Integers wrap (two's complement); floats round to nearest even
+ * on every hop; 16-bit floats widen to fp32, combine and round once. */
+typedef enum {
+  vInt32 = 0, vFloat32 = 1, vFloat16 = 2, vBfloat16 = 3,
+  vInt8 = 4, vUint8 = 5, vUint32 = 6, vInt64 = 7, vUint64 = 8, vFloat64 = 9
+} vDataType_t;
+/* Reductions f(received, local), each hop rounded to the element type.  max
+ * and min keep the received operand on ties.  avg adds on every hop and
+ * divides the completed value by nranks once, in the step that completes it
+ * (the ring segment owner's recvReduceCopySend, the tree root, the
+ * ReduceScatter / Reduce final recvReduceCopy): integers truncate toward
+ * zero, floats round once.  The serving API and vAllReduceNoAlloc take
+ * vSum / vMax on the first four types only. */
+typedef enum { vSum = 0, vMax = 1, vProd = 2, vMin = 3, vAvg = 4 } vRedOp_t;
 typedef enum { vAlgoAuto = 0, vAlgoRing = 1, vAlgoTree = 2 } vAlgo_t;
 /* vProtoCluster has no counterpart in the paper: the LL line format of
  * Sec. III-B (4 data bytes + a 4-byte flag per 8-byte store) carried in
@@ -200,7 +214,9 @@ vResult_t vReduce(const void* const* sendbufs, void* const* recvbufs, size_t cou
  * is capturable in a CUDA graph once the arenas it needs exist (vcommPrepare,
  * or one uncaptured run); the batch description is a kernel parameter, so a
  * replay needs no host memory.  Calls within a group return vSuccess after
- * validation; vGroupEnd returns the first launch error. */
+ * validation; vGroupEnd returns the first launch error.  The buffers of
+ * every call must stay allocated until the group's work has completed on
+ * the stream (nothing is read before vGroupEnd). */
 vResult_t vGroupStart(void);
 vResult_t vGroupEnd(void);
 

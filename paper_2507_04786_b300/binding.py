@@ -15,8 +15,9 @@ _LIB_PATH = os.path.join(_HERE, "libvcomm.so")
 
 RESULTS = {0: "vSuccess", 1: "vInvalidArgument", 2: "vUnsupported", 3: "vOutOfMemory",
            4: "vCudaError", 5: "vTimeout", 6: "vAborted", 7: "vInternalError"}
-DTYPE_CODES = {"int32": 0, "fp32": 1, "fp16": 2, "bf16": 3}
-OP_CODES = {"sum": 0, "max": 1}
+DTYPE_CODES = {"int32": 0, "fp32": 1, "fp16": 2, "bf16": 3, "int8": 4, "uint8": 5, "uint32": 6,
+               "int64": 7, "uint64": 8, "fp64": 9}
+OP_CODES = {"sum": 0, "max": 1, "prod": 2, "min": 3, "avg": 4}
 ALGO_CODES = {"auto": 0, "ring": 1, "tree": 2}
 PROTO_CODES = {"auto": 0, "simple": 1, "ll": 2, "ll128": 3, "cluster": 4, "direct": 5}
 ALGO_NAMES = {v: k for k, v in ALGO_CODES.items()}
@@ -136,7 +137,8 @@ def _check(rc: int, what: str):
 def _dtype_name(t) -> str:
     import torch
     m = {torch.float32: "fp32", torch.float16: "fp16", torch.bfloat16: "bf16",
-         torch.int32: "int32"}
+         torch.int32: "int32", torch.int8: "int8", torch.uint8: "uint8", torch.uint32: "uint32",
+         torch.int64: "int64", torch.uint64: "uint64", torch.float64: "fp64"}
     if t.dtype not in m:
         raise TypeError(f"unsupported dtype {t.dtype}")
     return m[t.dtype]

@@ -32,7 +32,8 @@ CFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler",
 RDC = ["-rdc=true", "-maxrregcount=128"]
 RDC_UNITS = ("vcomm_batch.cu", "vcomm_batch_inst.cu")
 PER_PAIR = ("vcomm_reduce_inst.cu", "vcomm_batch_inst.cu")
-PER_DTYPE = ("vcomm_cluster_inst.cu",)
+PER_DTYPE = ("vcomm_cluster_inst.cu", "vcomm_direct_inst.cu")
+NUM_DTYPES = 10   # vDataType_t
 
 
 def units():
@@ -42,11 +43,11 @@ def units():
         base = os.path.splitext(os.path.basename(src))[0]
         extra = RDC if os.path.basename(src) in RDC_UNITS else []
         if os.path.basename(src) in PER_DTYPE:
-            for d in range(4):
+            for d in range(NUM_DTYPES):
                 out.append((src, os.path.join(OBJ, f"{base}_{d}.o"), extra + [f"-DVC_DTYPE={d}"]))
         elif os.path.basename(src) in PER_PAIR:
             for p in range(3):
-                for d in range(4):
+                for d in range(NUM_DTYPES):
                     out.append((src, os.path.join(OBJ, f"{base}_{p}_{d}.o"),
                                 extra + [f"-DVC_PROTO={p}", f"-DVC_DTYPE={d}"]))
         else:

@@ -14,10 +14,9 @@
 
 namespace vc {
 
+#define VC_DTYPES_OF(X, P) X(P, 0) X(P, 1) X(P, 2) X(P, 3) X(P, 4) X(P, 5) X(P, 6) X(P, 7) X(P, 8) X(P, 9)
 #define VC_DECL(P, D) __device__ void batchWorker_##P##_##D(const KernArgs&, int, int, volatile int*);
-VC_DECL(0, 0) VC_DECL(0, 1) VC_DECL(0, 2) VC_DECL(0, 3)
-VC_DECL(1, 0) VC_DECL(1, 1) VC_DECL(1, 2) VC_DECL(1, 3)
-VC_DECL(2, 0) VC_DECL(2, 1) VC_DECL(2, 2) VC_DECL(2, 3)
+VC_DTYPES_OF(VC_DECL, 0) VC_DTYPES_OF(VC_DECL, 1) VC_DTYPES_OF(VC_DECL, 2)
 #undef VC_DECL
 
 template <int P>
@@ -35,9 +34,7 @@ __device__ __forceinline__ void dispatchOp(const KernArgs& a, int proto, int dty
     return;
   }
 #define VC_CASE(P, D) if (proto == P && dtype == D) { batchWorker_##P##_##D(a, r, ch, sAbort); return; }
-  VC_CASE(0, 0) VC_CASE(0, 1) VC_CASE(0, 2) VC_CASE(0, 3)
-  VC_CASE(1, 0) VC_CASE(1, 1) VC_CASE(1, 2) VC_CASE(1, 3)
-  VC_CASE(2, 0) VC_CASE(2, 1) VC_CASE(2, 2) VC_CASE(2, 3)
+  VC_DTYPES_OF(VC_CASE, 0) VC_DTYPES_OF(VC_CASE, 1) VC_DTYPES_OF(VC_CASE, 2)
 #undef VC_CASE
 }
 
@@ -80,6 +77,7 @@ __global__ void __launch_bounds__(512, 1) kBatch(const __grid_constant__ BatchAr
       sa.nsteps = b.nsteps;
       sa.upThreads = (blockDim.x / 2) / 32 * 32;
       sa.skipRank = -1;
+      sa.postDiv = o.postDiv;
     }
     __syncthreads();
     const bool bytes = (o.coll == kAllGather || o.coll == kBroadcast ||
@@ -176,6 +174,7 @@ __global__ void __launch_bounds__(512, 1) kServe(const __grid_constant__ ServeAr
           sa.nsteps = s.nsteps;
           sa.upThreads = (blockDim.x / 2) / 32 * 32;
           sa.skipRank = -1;
+          sa.postDiv = 0;   // serving runs sum and max only
           for (int i = 0; i < q->nranks; i++) {
             sa.send[i] = (const void*)q->send[i];
             sa.recv[i] = (void*)q->recv[i];

@@ -6,30 +6,32 @@
 #include "vcomm_device.cuh"
 
 #ifndef VC_PROTO
-#error "compile with -DVC_PROTO=<0|1|2> -DVC_DTYPE=<0..3>"
+#error "compile with -DVC_PROTO=<0|1|2> -DVC_DTYPE=<0..9>"
 #endif
 
 namespace vc {
 
-#if VC_DTYPE == 0
-using VcT = int32_t;
-#elif VC_DTYPE == 1
-using VcT = float;
-#elif VC_DTYPE == 2
-using VcT = __half;
-#else
-using VcT = __nv_bfloat16;
-#endif
+using VcT = typename DTypeOf<VC_DTYPE>::T;
 
 #define VC_BNAME2(P, D) batchWorker_##P##_##D
 #define VC_BNAME(P, D) VC_BNAME2(P, D)
+
+// one reduction op's worker, not inlined so that each gets its own register
+// allocation (templated on the protocol and type too: this unit is linked as
+// relocatable device code with its siblings, so the name must be unique)
+template <int P, class T, class Op>
+__device__ __noinline__ void opWorker(const KernArgs& a, int r, int ch, volatile int* sAbort) {
+  runWorker<P, T, Op>(a, r, ch, sAbort);
+}
 
 // one op of a batch on CTA (r, ch) of its gang; `a` lives in shared memory
 __device__ __noinline__ void VC_BNAME(VC_PROTO, VC_DTYPE)(const KernArgs& a, int r, int ch,
                                                          volatile int* sAbort) {
   if (a.coll == kCopy) localCopy<VcT>(a, ch);
-  else if (a.redop == kSum) runWorker<VC_PROTO, VcT, OpSum>(a, r, ch, sAbort);
-  else runWorker<VC_PROTO, VcT, OpMax>(a, r, ch, sAbort);
+  else if (a.redop == kSum) opWorker<VC_PROTO, VcT, OpSum>(a, r, ch, sAbort);
+  else if (a.redop == kMax) opWorker<VC_PROTO, VcT, OpMax>(a, r, ch, sAbort);
+  else if (a.redop == kProd) opWorker<VC_PROTO, VcT, OpProd>(a, r, ch, sAbort);
+  else opWorker<VC_PROTO, VcT, OpMin>(a, r, ch, sAbort);
 }
 
 }  // namespace vc

@@ -1,25 +1,17 @@
 // vcomm_cluster_inst.cu -- cluster-protocol kernels for ONE dtype, selected by
-// -DVC_DTYPE=<0..3> (compiled once per dtype); the dtype-0 unit also holds
+// -DVC_DTYPE=<0..9> (compiled once per dtype); the dtype-0 unit also holds
 // the byte-moving kernel for AllGather and Broadcast.
 #include <cuda_runtime.h>
 
 #include "vcomm_cluster.cuh"
 
 #ifndef VC_DTYPE
-#error "compile with -DVC_DTYPE=<0..3>"
+#error "compile with -DVC_DTYPE=<0..9>"
 #endif
 
 namespace vc {
 
-#if VC_DTYPE == 0
-using VcT = int32_t;
-#elif VC_DTYPE == 1
-using VcT = float;
-#elif VC_DTYPE == 2
-using VcT = __half;
-#else
-using VcT = __nv_bfloat16;
-#endif
+using VcT = typename DTypeOf<VC_DTYPE>::T;
 
 // one cluster of nranks CTAs per channel (launched with that cluster shape)
 template <class T, class Op>
@@ -40,7 +32,13 @@ __global__ void __launch_bounds__(maxThreadsFor(kCluster), 1) kClusterColl(const
 #define VC_CNAME2(D) clusterKernel_##D
 #define VC_CNAME(D) VC_CNAME2(D)
 const void* VC_CNAME(VC_DTYPE)(int op) {
-  return op == kSum ? (const void*)kClusterColl<VcT, OpSum> : (const void*)kClusterColl<VcT, OpMax>;
+  switch (op) {
+    case kSum: return (const void*)kClusterColl<VcT, OpSum>;
+    case kMax: return (const void*)kClusterColl<VcT, OpMax>;
+    case kProd: return (const void*)kClusterColl<VcT, OpProd>;
+    case kMin: return (const void*)kClusterColl<VcT, OpMin>;
+  }
+  return nullptr;
 }
 
 #if VC_DTYPE == 0

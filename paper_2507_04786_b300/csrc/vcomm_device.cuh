@@ -72,42 +72,94 @@ VDEV void groupBar(int id, int nthreads) {
 // received operand on ties.
 struct OpSum {};
 struct OpMax {};
+struct OpProd {};
+struct OpMin {};
 struct OpNone {};
 
-template <class T, class Op> struct ElemOp;
-template <> struct ElemOp<float, OpSum> {
-  static VDEV float f(float a, float b) { return __fadd_rn(a, b); }
+// element type of each dtype code (the order of vDataType_t)
+template <int D> struct DTypeOf;
+template <> struct DTypeOf<kI32> { using T = int32_t; };
+template <> struct DTypeOf<kF32> { using T = float; };
+template <> struct DTypeOf<kF16> { using T = __half; };
+template <> struct DTypeOf<kBF16> { using T = __nv_bfloat16; };
+template <> struct DTypeOf<kI8> { using T = int8_t; };
+template <> struct DTypeOf<kU8> { using T = uint8_t; };
+template <> struct DTypeOf<kU32> { using T = uint32_t; };
+template <> struct DTypeOf<kI64> { using T = int64_t; };
+template <> struct DTypeOf<kU64> { using T = uint64_t; };
+template <> struct DTypeOf<kF64> { using T = double; };
+
+// f(a, b), a the received operand, b the local one; every result is rounded
+// to the element type: integers wrap (two's complement), floats round to
+// nearest even, 16-bit floats widen to fp32, combine and round once (exact
+// for sum by double-rounding innocuity, 24 >= 2p + 2, and for prod because the
+// product of two 16-bit values is exact in fp32); max / min keep the received
+// operand on ties.
+template <class T>
+VDEV float widen(T x) {
+  if constexpr (std::is_same<T, __half>::value) return __half2float(x);
+  else return __bfloat162float(x);
+}
+template <class T>
+VDEV T narrow(float x) {
+  if constexpr (std::is_same<T, __half>::value) return __float2half_rn(x);
+  else return __float2bfloat16_rn(x);
+}
+template <class T> struct Is16f {
+  static constexpr bool value = std::is_same<T, __half>::value || std::is_same<T, __nv_bfloat16>::value;
 };
-template <> struct ElemOp<float, OpMax> {
-  static VDEV float f(float a, float b) { return (b > a) ? b : a; }
-};
-template <> struct ElemOp<int32_t, OpSum> {
-  static VDEV int32_t f(int32_t a, int32_t b) { return (int32_t)((uint32_t)a + (uint32_t)b); }
-};
-template <> struct ElemOp<int32_t, OpMax> {
-  static VDEV int32_t f(int32_t a, int32_t b) { return (b > a) ? b : a; }
-};
-template <> struct ElemOp<__half, OpSum> {
-  static VDEV __half f(__half a, __half b) {
-    return __float2half_rn(__fadd_rn(__half2float(a), __half2float(b)));
-  }
-};
-template <> struct ElemOp<__half, OpMax> {
-  static VDEV __half f(__half a, __half b) { return (__half2float(b) > __half2float(a)) ? b : a; }
-};
-template <> struct ElemOp<__nv_bfloat16, OpSum> {
-  static VDEV __nv_bfloat16 f(__nv_bfloat16 a, __nv_bfloat16 b) {
-    return __float2bfloat16_rn(__fadd_rn(__bfloat162float(a), __bfloat162float(b)));
-  }
-};
-template <> struct ElemOp<__nv_bfloat16, OpMax> {
-  static VDEV __nv_bfloat16 f(__nv_bfloat16 a, __nv_bfloat16 b) {
-    return (__bfloat162float(b) > __bfloat162float(a)) ? b : a;
+
+template <class T, class Op>
+struct ElemOp {
+  static VDEV T f(T a, T b) {
+    if constexpr (Is16f<T>::value) {
+      const float x = widen(a), y = widen(b);
+      if constexpr (std::is_same<Op, OpSum>::value) return narrow<T>(__fadd_rn(x, y));
+      else if constexpr (std::is_same<Op, OpProd>::value) return narrow<T>(__fmul_rn(x, y));
+      else if constexpr (std::is_same<Op, OpMax>::value) return (y > x) ? b : a;
+      else return (y < x) ? b : a;
+    } else if constexpr (std::is_same<T, float>::value) {
+      if constexpr (std::is_same<Op, OpSum>::value) return __fadd_rn(a, b);
+      else if constexpr (std::is_same<Op, OpProd>::value) return __fmul_rn(a, b);
+      else if constexpr (std::is_same<Op, OpMax>::value) return (b > a) ? b : a;
+      else return (b < a) ? b : a;
+    } else if constexpr (std::is_same<T, double>::value) {
+      if constexpr (std::is_same<Op, OpSum>::value) return __dadd_rn(a, b);
+      else if constexpr (std::is_same<Op, OpProd>::value) return __dmul_rn(a, b);
+      else if constexpr (std::is_same<Op, OpMax>::value) return (b > a) ? b : a;
+      else return (b < a) ? b : a;
+    } else {   // integers
+      using U = typename std::make_unsigned<T>::type;
+      if constexpr (std::is_same<Op, OpSum>::value) return (T)(U)((U)a + (U)b);
+      else if constexpr (std::is_same<Op, OpProd>::value) return (T)(U)((U)a * (U)b);
+      else if constexpr (std::is_same<Op, OpMax>::value) return (b > a) ? b : a;
+      else return (b < a) ? b : a;
+    }
   }
 };
 template <class T> struct ElemOp<T, OpNone> {
   static VDEV T f(T a, T) { return a; }
 };
+
+// avg's final step: x / k, integers truncating toward zero, floats rounded
+// once to the type (16-bit: an fp32 quotient rounded again, innocuous)
+template <class T>
+VDEV T divElem(T x, int k) {
+  if constexpr (Is16f<T>::value) return narrow<T>(__fdiv_rn(widen(x), (float)k));
+  else if constexpr (std::is_same<T, float>::value) return __fdiv_rn(x, (float)k);
+  else if constexpr (std::is_same<T, double>::value) return __ddiv_rn(x, (double)k);
+  else return (T)(x / (T)k);
+}
+template <class T, class W>
+VDEV W divWord(W w, int k) {
+  constexpr int n = sizeof(W) / sizeof(T);
+  union U { W w; T e[n]; };
+  U u;
+  u.w = w;
+#pragma unroll
+  for (int i = 0; i < n; i++) u.e[i] = divElem<T>(u.e[i], k);
+  return u.w;
+}
 
 // the sum of two 16-bit lanes per 32-bit word, each lane exactly as
 // ElemOp<T, OpSum> computes it (widen to fp32, one fp32 add, round to T with
@@ -189,7 +241,8 @@ VDEV uint64_t loadUser8(const char* p, int valid) {
   uint64_t v = 0;
   for (int b = 0; b < valid; b += (int)sizeof(T)) {
     uint64_t e;
-    if (sizeof(T) == 4) e = *(const uint32_t*)(p + b);
+    if (sizeof(T) == 8) e = *(const uint64_t*)(p + b);
+    else if (sizeof(T) == 4) e = *(const uint32_t*)(p + b);
     else if (sizeof(T) == 2) e = *(const uint16_t*)(p + b);
     else e = *(const uint8_t*)(p + b);
     v |= e << (8 * b);
@@ -201,8 +254,9 @@ VDEV void storeUser8(char* p, uint64_t v, int valid) {
   if (valid <= 0) return;
   if (valid == 8 && (((uintptr_t)p) & 7) == 0) { *(uint64_t*)p = v; return; }
   for (int b = 0; b < valid; b += (int)sizeof(T)) {
-    uint64_t e = v >> (8 * b);
-    if (sizeof(T) == 4) *(uint32_t*)(p + b) = (uint32_t)e;
+    uint64_t e = b < 8 ? v >> (8 * b) : 0;
+    if (sizeof(T) == 8) *(uint64_t*)(p + b) = e;
+    else if (sizeof(T) == 4) *(uint32_t*)(p + b) = (uint32_t)e;
     else if (sizeof(T) == 2) *(uint16_t*)(p + b) = (uint16_t)e;
     else *(uint8_t*)(p + b) = (uint8_t)e;
   }
@@ -215,9 +269,10 @@ VDEV void storeUser8(char* p, uint64_t v, int valid) {
 // one coalesced 512-byte access and all UNROLL x NSRC loads of a round are in
 // flight together.  Element-wise tail, and an element-wise path when any
 // pointer is not 16-byte aligned.  nbytes < 2^32 (one FIFO slot at most).
+// div != 0: the folded value is divided by div before it is stored (avg).
 template <class T, class Op, int NSRC>
 VDEV void reduceCopy(int tid, int nthr, const char* s0, const char* s1, const char* s2, char* d0,
-                     char* d1, char* d2, int nd, uint32_t nbytes) {
+                     char* d1, char* d2, int nd, uint32_t nbytes, int div = 0) {
   constexpr int UNROLL = (NSRC == 1) ? 8 : (NSRC == 2) ? 4 : 2;
   uintptr_t orall = (uintptr_t)s0 | (uintptr_t)d0;
   if (NSRC > 1) orall |= (uintptr_t)s1;
@@ -247,6 +302,7 @@ VDEV void reduceCopy(int tid, int nthr, const char* s0, const char* s1, const ch
         if (i0 + 32u * u < npk) {
           if (NSRC > 1) v[u] = applyWord<T, Op>(w1[u], v[u]);
           if (NSRC > 2) v[u] = applyWord<T, Op>(w2[u], v[u]);
+          if (div) v[u] = divWord<T>(v[u], div);
           st16((uint4*)d0 + i0 + 32 * u, v[u]);
           if (nd > 1) st16((uint4*)d1 + i0 + 32 * u, v[u]);
           if (nd > 2) st16((uint4*)d2 + i0 + 32 * u, v[u]);
@@ -261,6 +317,7 @@ VDEV void reduceCopy(int tid, int nthr, const char* s0, const char* s1, const ch
     T v = *(const T*)(s0 + off);
     if (NSRC > 1) v = ElemOp<T, Op>::f(*(const T*)(s1 + off), v);
     if (NSRC > 2) v = ElemOp<T, Op>::f(*(const T*)(s2 + off), v);
+    if (div) v = divElem<T>(v, div);
     *(T*)(d0 + off) = v;
     if (nd > 1) *(T*)(d1 + off) = v;
     if (nd > 2) *(T*)(d2 + off) = v;
@@ -473,6 +530,9 @@ struct Prims {
                  uint32_t m) {
     if (!acquire(doRecv, doSend)) return false;
     const uint32_t nbytes = m * (uint32_t)sizeof(T);
+    // avg: the step that both reduces and writes the output completes the
+    // value (ring segment owner, tree root, Reduce / ReduceScatter final)
+    const int div = (doRecv && doLocal && doOut) ? a.postDiv : 0;
     if (PROTO == kSimple) {
       const char* s0;
       const char* s1 = nullptr;
@@ -503,8 +563,8 @@ struct Prims {
         nd += nsc;
       }
       if (ns == 1) reduceCopy<T, Op, 1>(tid, nthr, s0, s1, s2, d0, d1, d2, nd, nbytes);
-      else if (ns == 2) reduceCopy<T, Op, 2>(tid, nthr, s0, s1, s2, d0, d1, d2, nd, nbytes);
-      else reduceCopy<T, Op, 3>(tid, nthr, s0, s1, s2, d0, d1, d2, nd, nbytes);
+      else if (ns == 2) reduceCopy<T, Op, 2>(tid, nthr, s0, s1, s2, d0, d1, d2, nd, nbytes, div);
+      else reduceCopy<T, Op, 3>(tid, nthr, s0, s1, s2, d0, d1, d2, nd, nbytes, div);
     } else if (PROTO == kLL) {
       // each thread owns line pairs p = tid + u * nthr (u < U) per round: all
       // loads of the round are issued before the first flag check
@@ -556,6 +616,7 @@ struct Prims {
           const uint32_t p = p0 + (uint32_t)u * nthr;
           if (p >= npairs) continue;
           const int valid = (int)((nbytes - 8 * p) < 8 ? (nbytes - 8 * p) : 8);
+          if (div) v[u] = divWord<T>(v[u], div);
           if (doOut) storeUser8<T>((char*)out + 8ull * p, v[u], valid);
           if (doSend) {
             llStorePair(ss0, p, v[u], sf0);
@@ -638,6 +699,10 @@ struct Prims {
         for (int u = 0; u < U; u++) {
           const uint32_t line = 4 * (q0 + (uint32_t)u * nwarps) + (lane >> 3);
           const uint32_t uoff = 120 * line + 16 * j;
+          if (div) {
+            v0[u] = divWord<T>(v0[u], div);
+            v1[u] = divWord<T>(v1[u], div);
+          }
           if (doOut && valid[u] > 0) {
             storeUser8<T>((char*)out + uoff, v0[u], valid[u] < 8 ? valid[u] : 8);
             storeUser8<T>((char*)out + uoff + 8, v1[u], valid[u] > 8 ? valid[u] - 8 : 0);

@@ -17,264 +17,11 @@
 // No thread waits for another: a plain launch of a grid sized to the data.
 #include <cuda_runtime.h>
 
-#include "vcomm_device.cuh"
+#include "vcomm_direct.cuh"
+#include "vcomm_kernels.h"
 
 namespace vc {
-
-namespace {
-
-// one collective as the direct kernels see it (a single launch or one op of
-// a batch): the k send and recv pointers plus DirectArgs' scalars
-struct DirectView {
-  const void* const* send;
-  void* const* recv;
-  unsigned long long count, chunk, inplaceMask;
-  int coll, nranks, nsub, root;
-};
-
-// the ring segment (fold start = s + 1) of element i of a ring AllReduce,
-// and the end (exclusive, in elements) of the run of elements sharing it
-VDEV int arSegment(const DirectView& a, unsigned long long i, int esz, unsigned long long* runEnd) {
-  const int k = a.nranks;
-  const unsigned long long epp = 16ull / (unsigned long long)esz;
-  const unsigned long long npk = a.count / epp;
-  const unsigned long long nch = (unsigned long long)a.nsub;
-  int ch;
-  const unsigned long long q = i / epp;
-  if (q >= npk) {
-    ch = a.nsub - 1;   // the element tail belongs to the last channel
-  } else {
-    const unsigned long long base = npk / nch, rem = npk % nch;
-    if (q < rem * (base + 1)) ch = (int)(q / (base + 1));
-    else ch = (int)(rem + (q - rem * (base + 1)) / base);
-  }
-  unsigned long long start, len;
-  channelRange(a.count, esz, a.nsub, ch, &start, &len);
-  const unsigned long long end = start + len;
-  const unsigned long long L = (unsigned long long)k * a.chunk;
-  const unsigned long long loopOff = start + (i - start) / L * L;
-  const unsigned long long c = ringLoopChunk(loopOff, end, k, a.chunk, esz);
-  const unsigned long long s = (i - loopOff) / c;
-  unsigned long long e = loopOff + (s + 1) * c;
-  *runEnd = e < end ? e : end;
-  return (int)s;
-}
-
-template <class T>
-struct Unit16 {   // 16-byte unit
-  using W = uint4;
-  static constexpr int kElems = 16 / sizeof(T);
-  static VDEV W load(const char* p) { return __ldcs((const uint4*)p); }
-  static VDEV void store(char* p, W v) { __stcs((uint4*)p, v); }
-};
-template <class T>
-struct Unit1 {    // one element (unaligned buffers)
-  using W = T;
-  static constexpr int kElems = 1;
-  static VDEV W load(const char* p) { return *(const T*)p; }
-  static VDEV void store(char* p, W v) { *(T*)p = v; }
-};
-
-template <class T, class Op, class W>
-VDEV W combine(W acc, W x) {
-  if constexpr (sizeof(W) == sizeof(T)) return ElemOp<T, Op>::f(acc, x);
-  else return applyWord<T, Op>(acc, x);
-}
-
-// acc = x_{s+1}; acc = f(acc, x_{s+2}); ... ; acc = f(acc, x_s): the partial
-// sum arriving from the predecessor is the first operand, the local input the
-// second, as in the FIFO kernels.  NU units at once (offsets off[u], chain
-// starts s[u]): their loads are issued together, B ranks ahead of the combines.
-template <class T, class Op, class U, int NU>
-VDEV void foldChains(const DirectView& a, const int* s, const unsigned long long* off, int nu,
-                     typename U::W* acc) {
-  const int k = a.nranks;
-  int r[NU];
-#pragma unroll
-  for (int u = 0; u < NU; u++) {
-    r[u] = s[u] + 1 < k ? s[u] + 1 : 0;
-    if (u < nu) acc[u] = U::load((const char*)a.send[r[u]] + off[u]);
-  }
-  constexpr int B = 8;
-  for (int j = 1; j < k; j += B) {
-    typename U::W v[NU][B];
-#pragma unroll
-    for (int u = 0; u < NU; u++) {
-#pragma unroll
-      for (int b = 0; b < B; b++) {
-        int rr = r[u] + 1 + b;
-        if (rr >= k) rr -= k;
-        if (u < nu && j + b < k) v[u][b] = U::load((const char*)a.send[rr] + off[u]);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < NU; u++) {
-#pragma unroll
-      for (int b = 0; b < B; b++)
-        if (u < nu && j + b < k) acc[u] = combine<T, Op, typename U::W>(acc[u], v[u][b]);
-      r[u] += B;
-      if (r[u] >= k) r[u] -= k;
-    }
-  }
-}
-
-template <class T, class Op, class U>
-VDEV typename U::W foldChain(const DirectView& a, int s, unsigned long long off) {
-  typename U::W acc[1];
-  foldChains<T, Op, U, 1>(a, &s, &off, 1, acc);
-  return acc[0];
-}
-
-// units of a collective: full units per block x blocks
-VDEV unsigned long long reduceUnits(const DirectView& a, int E) {
-  return (a.count / E) * (a.coll == kReduceScatter ? (unsigned long long)a.nranks : 1ull);
-}
-VDEV unsigned long long copyUnits(const DirectView& a, int E) {
-  return (a.count / E) * (a.coll == kAllGather ? (unsigned long long)a.nranks : 1ull);
-}
-
-// AllReduce, ReduceScatter and Reduce over units [lo, hi) of the collective
-// (consecutive threads take consecutive units, so every warp access is one
-// coalesced 512 bytes), NU units per thread per iteration; `tail`: this CTA
-// also does the element tail of each block
-template <class T, class Op, class U, int NU>
-VDEV void directReduce(const DirectView& a, unsigned long long lo, unsigned long long hi, bool tail) {
-  const int k = a.nranks;
-  constexpr int E = U::kElems;
-  const unsigned long long esz = sizeof(T);
-  const unsigned long long nunit = a.count / E;                 // full units per block
-  unsigned long long runEnd = 0;   // AllReduce: the current segment's end (elements)
-  int seg = 0;
-  for (unsigned long long g0 = lo + threadIdx.x; g0 < hi; g0 += (unsigned long long)NU * blockDim.x) {
-    int s[NU];
-    unsigned long long off[NU];
-    int nu = 0;
-#pragma unroll
-    for (int u = 0; u < NU; u++) {
-      const unsigned long long g = g0 + (unsigned long long)u * blockDim.x;
-      s[u] = 0;
-      off[u] = 0;
-      if (g >= hi) continue;
-      nu = u + 1;
-      if (a.coll == kAllReduce) {
-        const unsigned long long i = g * E;
-        if (i >= runEnd) seg = arSegment(a, i, (int)esz, &runEnd);
-        s[u] = seg;
-        off[u] = i * esz;
-      } else if (a.coll == kReduceScatter) {
-        const unsigned long long b = g / nunit, e = g % nunit;
-        s[u] = (int)b;
-        off[u] = (b * a.count + e * E) * esz;
-      } else {
-        s[u] = a.root;
-        off[u] = g * E * esz;
-      }
-    }
-    typename U::W v[NU];
-    foldChains<T, Op, U, NU>(a, s, off, nu, v);
-#pragma unroll
-    for (int u = 0; u < NU; u++) {
-      if (u >= nu) continue;
-      if (a.coll == kAllReduce) {
-        for (int r = 0; r < k; r++) U::store((char*)a.recv[r] + off[u], v[u]);
-      } else if (a.coll == kReduceScatter) {
-        const unsigned long long g = g0 + (unsigned long long)u * blockDim.x;
-        U::store((char*)a.recv[s[u]] + (g % nunit) * E * esz, v[u]);
-      } else {
-        U::store((char*)a.recv[a.root] + off[u], v[u]);
-      }
-    }
-  }
-  const unsigned long long nt = a.count - nunit * E;   // element tail of each block
-  if (E > 1 && nt && tail) {
-    const unsigned long long nblk = (a.coll == kReduceScatter) ? (unsigned long long)k : 1ull;
-    for (unsigned long long t = threadIdx.x; t < nt * nblk; t += blockDim.x) {
-      const unsigned long long b = t / nt, i = nunit * E + t % nt;
-      if (a.coll == kAllReduce) {
-        unsigned long long re;
-        const int s = arSegment(a, i, (int)esz, &re);
-        const T v = foldChain<T, Op, Unit1<T>>(a, s, i * esz);
-        for (int r = 0; r < k; r++) Unit1<T>::store((char*)a.recv[r] + i * esz, v);
-      } else if (a.coll == kReduceScatter) {
-        const T v = foldChain<T, Op, Unit1<T>>(a, (int)b, (b * a.count + i) * esz);
-        Unit1<T>::store((char*)a.recv[b] + i * esz, v);
-      } else {
-        const T v = foldChain<T, Op, Unit1<T>>(a, a.root, i * esz);
-        Unit1<T>::store((char*)a.recv[a.root] + i * esz, v);
-      }
-    }
-  }
-}
-
-// AllGather (block b of every output = rank b's input) and Broadcast (every
-// output = the root's input) over units [lo, hi); count in bytes.  A unit is
-// read once and written to every output that is not its own source.
-template <class U>
-VDEV void directCopy(const DirectView& a, unsigned long long lo, unsigned long long hi, bool tail) {
-  const int k = a.nranks;
-  constexpr int E = sizeof(typename U::W);
-  const unsigned long long nunit = a.count / E;
-  for (unsigned long long g = lo + threadIdx.x; g < hi; g += blockDim.x) {
-    const unsigned long long b = (a.coll == kAllGather) ? g / nunit : (unsigned long long)a.root;
-    const unsigned long long off = (g % nunit) * E;
-    const typename U::W v = U::load((const char*)a.send[b] + off);
-    const unsigned long long dst = (a.coll == kAllGather) ? b * a.count + off : off;
-    for (int r = 0; r < k; r++) {
-      if ((unsigned long long)r == b && ((a.inplaceMask >> r) & 1ull)) continue;
-      U::store((char*)a.recv[r] + dst, v);
-    }
-  }
-  const unsigned long long nt = a.count - nunit * E;   // byte tail of each block
-  if (E > 1 && nt && tail) {
-    const unsigned long long nblk = (a.coll == kAllGather) ? (unsigned long long)k : 1ull;
-    for (unsigned long long t = threadIdx.x; t < nt * nblk; t += blockDim.x) {
-      const unsigned long long b = (a.coll == kAllGather) ? t / nt : (unsigned long long)a.root;
-      const unsigned long long off = nunit * E + t % nt;
-      const uint8_t v = ((const uint8_t*)a.send[b])[off];
-      const unsigned long long dst = (a.coll == kAllGather) ? b * a.count + off : off;
-      for (int r = 0; r < k; r++) {
-        if ((unsigned long long)r == b && ((a.inplaceMask >> r) & 1ull)) continue;
-        ((uint8_t*)a.recv[r])[dst] = v;
-      }
-    }
-  }
-}
-
-// this CTA's contiguous share [*lo, *hi) of `total` units, in whole blocks
-VDEV void ctaRange(unsigned long long total, unsigned long long* lo, unsigned long long* hi) {
-  unsigned long long per = (total + gridDim.x - 1) / gridDim.x;
-  per = (per + blockDim.x - 1) / blockDim.x * blockDim.x;
-  *lo = (unsigned long long)blockIdx.x * per;
-  if (*lo > total) *lo = total;
-  *hi = *lo + per < total ? *lo + per : total;
-}
-
-VDEV DirectView viewOf(const DirectArgs& a) {
-  return DirectView{a.send, a.recv, a.count, a.chunk, a.inplaceMask, a.coll, a.nranks, a.nsub, a.root};
-}
-
-// Launch shape (measured on 8 x 256 MiB): 4-byte types keep 4 units x 8
-// loads in flight per thread in 256-thread CTAs; 2-byte types, whose packed
-// fp32 arithmetic needs more issue slots, 2 units in 512-thread CTAs.
-template <class T> struct DirectShape {
-  static constexpr int kUnits = sizeof(T) == 4 ? 4 : 2;
-  static constexpr int kThreads = sizeof(T) == 4 ? 256 : 512;
-};
-
-template <class T, class Op>
-__global__ void __launch_bounds__(DirectShape<T>::kThreads, 1)
-    kDirectReduce(const __grid_constant__ DirectArgs a) {
-  const DirectView v = viewOf(a);
-  const bool last = blockIdx.x == gridDim.x - 1;
-  unsigned long long lo, hi;
-  if (a.vec) {
-    ctaRange(reduceUnits(v, Unit16<T>::kElems), &lo, &hi);
-    directReduce<T, Op, Unit16<T>, DirectShape<T>::kUnits>(v, lo, hi, last);
-  } else {
-    ctaRange(reduceUnits(v, 1), &lo, &hi);
-    directReduce<T, Op, Unit1<T>, 1>(v, lo, hi, last);
-  }
-}
+namespace direct {
 
 __global__ void __launch_bounds__(256) kDirectCopy(const __grid_constant__ DirectArgs a) {
   const DirectView v = viewOf(a);
@@ -286,51 +33,6 @@ __global__ void __launch_bounds__(256) kDirectCopy(const __grid_constant__ Direc
   } else {
     ctaRange(copyUnits(v, 1), &lo, &hi);
     directCopy<Unit1<uint8_t>>(v, lo, hi, last);
-  }
-}
-
-// ---- many direct collectives of one element type and op in one launch
-// (group calls; the host launches one such kernel per (dtype, op) present,
-// and one for the copies).  The ops' units are laid end to end (op i owns
-// [unitStart[i], unitStart[i + 1])); each CTA takes a contiguous share of
-// that space and runs every op it overlaps on the overlapping units.
-// Nothing waits, so the ops need no ordering.
-VDEV DirectView viewOfOp(const DirectBatchArgs* b, int i) {
-  const DirectOpDesc& o = b->ops[i];
-  return DirectView{(const void* const*)&b->ptrs[o.ptrBase], (void* const*)&b->ptrs[o.ptrBase + o.nranks],
-                    o.count, o.chunk, o.inplaceMask, o.coll, o.nranks, o.nsub, o.root};
-}
-
-// the op-local units [lo, hi) of op i that fall in this CTA's share
-// [glo, ghi), and whether this CTA holds the op's last unit (its tails)
-VDEV void opShare(const DirectBatchArgs* b, int i, unsigned long long glo, unsigned long long ghi,
-                  unsigned long long* lo, unsigned long long* hi, bool* tail) {
-  const unsigned long long s = b->unitStart[i], e = b->unitStart[i + 1];
-  unsigned long long h = (ghi < e ? ghi : e) - s;
-  if (h > b->ops[i].units) h = b->ops[i].units;   // the range may hold one unit more than the op
-  unsigned long long l = (glo > s ? glo : s) - s;
-  *lo = l < h ? l : h;
-  *hi = h;
-  *tail = ghi >= e;
-}
-
-template <class T, class Op>
-__global__ void __launch_bounds__(DirectShape<T>::kThreads, 1)
-    kDirectBatch(const __grid_constant__ DirectBatchArgs b) {
-  const DirectBatchArgs* pb = &b;
-  unsigned long long glo, ghi;
-  ctaRange(pb->unitStart[pb->nops], &glo, &ghi);
-  for (int i = 0; i < pb->nops; i++) {
-    if (pb->unitStart[i + 1] <= glo || pb->unitStart[i] >= ghi) continue;
-    unsigned long long lo, hi;
-    bool tail;
-    opShare(pb, i, glo, ghi, &lo, &hi, &tail);
-    const DirectView v = viewOfOp(pb, i);
-    // (2-byte types: one unit per thread, which the loop over ops leaves
-    // registers for)
-    constexpr int NU = sizeof(T) == 4 ? DirectShape<T>::kUnits : 1;
-    if (pb->ops[i].vec) directReduce<T, Op, Unit16<T>, NU>(v, lo, hi, tail);
-    else directReduce<T, Op, Unit1<T>, 1>(v, lo, hi, tail);
   }
 }
 
@@ -349,35 +51,45 @@ __global__ void __launch_bounds__(256) kDirectBatchCopy(const __grid_constant__ 
   }
 }
 
-}  // namespace
+}  // namespace direct
+
+#define VC_DDECL(D) const void* directReduceKernel_##D(int op); const void* directBatchKernel_##D(int op);
+VC_DDECL(0) VC_DDECL(1) VC_DDECL(2) VC_DDECL(3) VC_DDECL(4)
+VC_DDECL(5) VC_DDECL(6) VC_DDECL(7) VC_DDECL(8) VC_DDECL(9)
+#undef VC_DDECL
+
+static int dtypeBytes(int dtype) {
+  switch (dtype) {
+    case kI8: case kU8: return 1;
+    case kF16: case kBF16: return 2;
+    case kI64: case kU64: case kF64: return 8;
+  }
+  return 4;
+}
 
 int directThreads(int coll, int dtype) {
   if (coll == kAllGather || coll == kBroadcast) return 256;
-  return (dtype == kF16 || dtype == kBF16) ? DirectShape<__half>::kThreads : DirectShape<float>::kThreads;
+  return direct::directThreadsFor(dtypeBytes(dtype));
 }
 
 const void* directKernel(int coll, int dtype, int op) {
-  if (coll == kAllGather || coll == kBroadcast) return (const void*)kDirectCopy;
-  const bool mx = (op == kMax);
+  if (coll == kAllGather || coll == kBroadcast) return (const void*)direct::kDirectCopy;
   switch (dtype) {
-    case kI32: return mx ? (const void*)kDirectReduce<int32_t, OpMax> : (const void*)kDirectReduce<int32_t, OpSum>;
-    case kF32: return mx ? (const void*)kDirectReduce<float, OpMax> : (const void*)kDirectReduce<float, OpSum>;
-    case kF16: return mx ? (const void*)kDirectReduce<__half, OpMax> : (const void*)kDirectReduce<__half, OpSum>;
-    case kBF16:
-      return mx ? (const void*)kDirectReduce<__nv_bfloat16, OpMax> : (const void*)kDirectReduce<__nv_bfloat16, OpSum>;
+#define VC_DCASE(D) case D: return directReduceKernel_##D(op);
+    VC_DCASE(0) VC_DCASE(1) VC_DCASE(2) VC_DCASE(3) VC_DCASE(4)
+    VC_DCASE(5) VC_DCASE(6) VC_DCASE(7) VC_DCASE(8) VC_DCASE(9)
+#undef VC_DCASE
   }
   return nullptr;
 }
 
 const void* directBatchKernel(int coll, int dtype, int op) {
-  if (coll == kAllGather || coll == kBroadcast) return (const void*)kDirectBatchCopy;
-  const bool mx = (op == kMax);
+  if (coll == kAllGather || coll == kBroadcast) return (const void*)direct::kDirectBatchCopy;
   switch (dtype) {
-    case kI32: return mx ? (const void*)kDirectBatch<int32_t, OpMax> : (const void*)kDirectBatch<int32_t, OpSum>;
-    case kF32: return mx ? (const void*)kDirectBatch<float, OpMax> : (const void*)kDirectBatch<float, OpSum>;
-    case kF16: return mx ? (const void*)kDirectBatch<__half, OpMax> : (const void*)kDirectBatch<__half, OpSum>;
-    case kBF16:
-      return mx ? (const void*)kDirectBatch<__nv_bfloat16, OpMax> : (const void*)kDirectBatch<__nv_bfloat16, OpSum>;
+#define VC_DCASE(D) case D: return directBatchKernel_##D(op);
+    VC_DCASE(0) VC_DCASE(1) VC_DCASE(2) VC_DCASE(3) VC_DCASE(4)
+    VC_DCASE(5) VC_DCASE(6) VC_DCASE(7) VC_DCASE(8) VC_DCASE(9)
+#undef VC_DCASE
   }
   return nullptr;
 }

@@ -50,7 +50,14 @@ vResult_t fromCuda(cudaError_t e) {
     if (r__ != vSuccess) return r__;       \
   } while (0)
 
-int dtypeSize(int dt) { return (dt == kF16 || dt == kBF16) ? 2 : 4; }
+int dtypeSize(int dt) {
+  switch (dt) {
+    case kI8: case kU8: return 1;
+    case kF16: case kBF16: return 2;
+    case kI64: case kU64: case kF64: return 8;
+  }
+  return 4;
+}
 
 size_t slotDataBytes(int proto, size_t slotBytes) {
   if (proto == kLL) return slotBytes / 2;             // 4 data bytes per 8-byte line
@@ -354,6 +361,7 @@ struct CallSpec {
   int coll = 0;                 // the user's collective
   int kcoll = 0;                // the kernel's (kCopy on a single rank)
   int dtype = 0, redop = 0, root = 0;
+  int postDiv = 0;              // avg: k (the kernels add, the completing step divides)
   int al = 0, pr = 0;
   bool bytesUnits = false;
   vPlan_t plan{};
@@ -373,8 +381,8 @@ static vResult_t prepareCall(int coll, const void* const* sendbufs, void* const*
     int e = ((volatile ErrWord*)c->hErr)->code;
     if (e != 0) return (vResult_t)e;   // a failed communicator stays failed
   }
-  if (dtype < vInt32 || dtype > vBfloat16) return vInvalidArgument;
-  if ((coll == kAllReduce || coll == kReduceScatter || coll == kReduce) && (op < vSum || op > vMax))
+  if (dtype < vInt32 || dtype > vFloat64) return vInvalidArgument;
+  if ((coll == kAllReduce || coll == kReduceScatter || coll == kReduce) && (op < vSum || op > vAvg))
     return vInvalidArgument;
   if (algo < vAlgoAuto || algo > vAlgoTree || proto < vProtoAuto || proto > vProtoDirect)
     return vInvalidArgument;
@@ -455,7 +463,8 @@ static vResult_t prepareCall(int coll, const void* const* sendbufs, void* const*
   cs->coll = coll;
   cs->kcoll = kcoll;
   cs->dtype = dtype;
-  cs->redop = op < 0 ? 0 : op;
+  cs->redop = op < 0 ? 0 : (op == vAvg ? kSum : op);
+  cs->postDiv = (op == vAvg && kcoll != kCopy) ? k : 0;
   cs->root = root;
   cs->al = (plan.algo == vAlgoTree) ? kTree : kRing;
   cs->pr = (int)plan.proto - 1;
@@ -540,6 +549,7 @@ static vResult_t launchCluster(CallSpec& cs) {
   a.nsteps = kClusterSlots;
   a.upThreads = (nthr / 2) / 32 * 32;
   a.skipRank = c->skipRank;
+  a.postDiv = cs.postDiv;
 
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(k * nsub));
@@ -616,6 +626,7 @@ static vResult_t launchDirect(CallSpec& cs) {
   a.nsub = cs.plan.nchannels;
   a.root = cs.root;
   a.vec = g.vec ? 1 : 0;
+  a.postDiv = cs.postDiv;
   const unsigned long long units = g.units;
   const int nthr = directThreads(cs.kcoll, cs.dtype);
   const long long resident = (long long)std::max(1, residentPerSM(fn, nthr)) * c->nsm;
@@ -686,6 +697,7 @@ static vResult_t launchSingle(CallSpec& cs) {
   a.nsteps = c->nsteps;
   a.upThreads = (nthr / 2) / 32 * 32;
   a.skipRank = c->skipRank;
+  a.postDiv = cs.postDiv;
 
   void* args[] = {(void*)&a};
   cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)(k * nsub)), dim3((unsigned)nthr),
@@ -795,10 +807,11 @@ static vResult_t launchDirectGroup(vcomm* c, std::vector<CallSpec>& ops) {
   const int k = c->k;
   const cudaStream_t stream = ops[0].stream;
   const int perLaunch = std::min<int>(kMaxBatchOps, kMaxBatchPtrs / (2 * k));
-  auto classOf = [](const CallSpec& o) {
-    return (o.kcoll == kAllGather || o.kcoll == kBroadcast) ? 8 : o.dtype * 2 + o.redop;
+  const int kCopyClass = kNumDtypes * kNumOps;
+  auto classOf = [&](const CallSpec& o) {
+    return (o.kcoll == kAllGather || o.kcoll == kBroadcast) ? kCopyClass : o.dtype * kNumOps + o.redop;
   };
-  for (int cls = 0; cls <= 8; cls++) {
+  for (int cls = 0; cls <= kCopyClass; cls++) {
     std::vector<const CallSpec*> mine;
     for (auto& o : ops)
       if (classOf(o) == cls) mine.push_back(&o);
@@ -828,6 +841,7 @@ static vResult_t launchDirectGroup(vcomm* c, std::vector<CallSpec>& ops) {
         d.dtype = o.dtype;
         d.redop = o.redop;
         d.vec = g.vec ? 1 : 0;
+        d.postDiv = o.postDiv;
         d.ptrBase = 2 * k * i;
         for (int r = 0; r < k; r++) {
           b->ptrs[d.ptrBase + r] = o.send[r];
@@ -971,6 +985,7 @@ static vResult_t launchFifoGroup(vcomm* c, std::vector<CallSpec>& ops) {
       d.redop = o.redop;
       d.nsub = (o.al == kTree) ? 2 * o.plan.nchannels : o.plan.nchannels;
       d.root = o.root;
+      d.postDiv = o.postDiv;
       d.ptrBase = 2 * k * i;
       for (int r = 0; r < k; r++) {
         b->ptrs[2 * k * i + r] = o.send[r];
@@ -1112,7 +1127,7 @@ vResult_t vReduce(const void* const* sendbufs, void* const* recvbufs, size_t cou
 
 static vResult_t p2pCall(bool send, const void* sbuf, void* rbuf, size_t count, vDataType_t dtype,
                          int rank, int peer, vcomm_t c, vStream_t stream) {
-  if (!c || dtype < vInt32 || dtype > vBfloat16) return vInvalidArgument;
+  if (!c || dtype < vInt32 || dtype > vFloat64) return vInvalidArgument;
   if (rank < 0 || rank >= c->k || peer < 0 || peer >= c->k) return vInvalidArgument;
   const size_t esz = dtypeSize(dtype);
   const void* p = send ? sbuf : rbuf;
@@ -1138,7 +1153,7 @@ vResult_t vRecv(void* recvbuf, size_t count, vDataType_t dtype, int rank, int pe
 
 vResult_t vAllToAll(const void* const* sendbufs, void* const* recvbufs, size_t count, vDataType_t dtype,
                     vcomm_t c, vStream_t stream) {
-  if (!c || !sendbufs || !recvbufs || dtype < vInt32 || dtype > vBfloat16) return vInvalidArgument;
+  if (!c || !sendbufs || !recvbufs || dtype < vInt32 || dtype > vFloat64) return vInvalidArgument;
   const int k = c->k;
   const size_t esz = dtypeSize(dtype), blk = count * esz;
   for (int r = 0; r < k; r++) {

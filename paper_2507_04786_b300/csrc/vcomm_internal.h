@@ -28,8 +28,12 @@ enum Coll : int { kAllReduce = 0, kReduceScatter = 1, kAllGather = 2, kBroadcast
                   kCopy = 5 };
 enum Algo : int { kRing = 0, kTree = 1 };
 enum Proto : int { kSimple = 0, kLL = 1, kLL128 = 2, kCluster = 3, kDirect = 4 };
-enum DType : int { kI32 = 0, kF32 = 1, kF16 = 2, kBF16 = 3 };
-enum OpKind : int { kSum = 0, kMax = 1 };
+enum DType : int { kI32 = 0, kF32 = 1, kF16 = 2, kBF16 = 3, kI8 = 4, kU8 = 5, kU32 = 6, kI64 = 7,
+                   kU64 = 8, kF64 = 9 };
+constexpr int kNumDtypes = 10;
+// element-wise ops of the kernels; avg runs as kSum with KernArgs::postDiv
+enum OpKind : int { kSum = 0, kMax = 1, kProd = 2, kMin = 3 };
+constexpr int kNumOps = 4;
 
 constexpr int kCounterStride = 16;
 
@@ -79,6 +83,7 @@ struct KernArgs {
   int nsteps;
   int upThreads;                   // tree: threads of the reduce (up) group on non-root ranks
   int skipRank;                    // fault injection: this vrank's CTAs return at once (-1: none)
+  int postDiv;                     // avg: the step that completes a value divides it by this (0: none)
 };
 
 // ---- batched launch: many collectives in one persistent kernel (group calls,
@@ -95,6 +100,7 @@ struct BatchOpDesc {
   unsigned long long count, chunk, slotBytes, slotUnits, inplaceMask, downOffset;
   const ConnDev* conns;              // the (algo, proto) arena, before the gang offset
   int coll, algo, proto, dtype, redop, nsub, root, ptrBase;  // ptrs[ptrBase..+k) send, then recv
+  int postDiv, pad;
 };
 
 struct BatchArgs {
@@ -168,7 +174,7 @@ struct DirectArgs {
   unsigned long long inplaceMask;
   int coll, nranks, nsub, root;
   int vec;                         // 1: every access is a 16-byte vector
-  int pad;
+  int postDiv;                     // avg: divide the folded value by this (0: none)
 };
 
 // ---- direct collectives of one class in one launch: op i owns units
@@ -178,6 +184,7 @@ struct DirectArgs {
 struct DirectOpDesc {
   unsigned long long count, chunk, inplaceMask, units;
   int coll, nranks, nsub, root, dtype, redop, vec, ptrBase;
+  int postDiv, pad;
 };
 struct DirectBatchArgs {
   int nops, pad;

@@ -91,17 +91,14 @@ __global__ void kDebugDecode(const __grid_constant__ KernArgs a, int proto, cons
 
 // ---- lookup table
 // reduce kernels are instantiated per (protocol, dtype) in vcomm_reduce_inst.cu
+#define VC_DTYPES_OF(X, P) X(P, 0) X(P, 1) X(P, 2) X(P, 3) X(P, 4) X(P, 5) X(P, 6) X(P, 7) X(P, 8) X(P, 9)
 #define VC_DECL(P, D) const void* reduceKernel_##P##_##D(int op);
-VC_DECL(0, 0) VC_DECL(0, 1) VC_DECL(0, 2) VC_DECL(0, 3)
-VC_DECL(1, 0) VC_DECL(1, 1) VC_DECL(1, 2) VC_DECL(1, 3)
-VC_DECL(2, 0) VC_DECL(2, 1) VC_DECL(2, 2) VC_DECL(2, 3)
+VC_DTYPES_OF(VC_DECL, 0) VC_DTYPES_OF(VC_DECL, 1) VC_DTYPES_OF(VC_DECL, 2)
 #undef VC_DECL
 
 const void* reduceKernel(int proto, int dtype, int op) {
 #define VC_CASE(P, D) if (proto == P && dtype == D) return reduceKernel_##P##_##D(op);
-  VC_CASE(0, 0) VC_CASE(0, 1) VC_CASE(0, 2) VC_CASE(0, 3)
-  VC_CASE(1, 0) VC_CASE(1, 1) VC_CASE(1, 2) VC_CASE(1, 3)
-  VC_CASE(2, 0) VC_CASE(2, 1) VC_CASE(2, 2) VC_CASE(2, 3)
+  VC_DTYPES_OF(VC_CASE, 0) VC_DTYPES_OF(VC_CASE, 1) VC_DTYPES_OF(VC_CASE, 2)
 #undef VC_CASE
   return nullptr;
 }
@@ -115,16 +112,13 @@ const void* copyKernel(int proto) {
   return nullptr;
 }
 
-#define VC_CDECL(D) const void* clusterKernel_##D(int op);
-VC_CDECL(0) VC_CDECL(1) VC_CDECL(2) VC_CDECL(3)
+#define VC_CDECL(P, D) const void* clusterKernel_##D(int op);
+VC_DTYPES_OF(VC_CDECL, 0)
 #undef VC_CDECL
 const void* clusterKernel(int dtype, int op) {
-  switch (dtype) {
-    case 0: return clusterKernel_0(op);
-    case 1: return clusterKernel_1(op);
-    case 2: return clusterKernel_2(op);
-    case 3: return clusterKernel_3(op);
-  }
+#define VC_CCASE(P, D) if (dtype == D) return clusterKernel_##D(op);
+  VC_DTYPES_OF(VC_CCASE, 0)
+#undef VC_CCASE
   return nullptr;
 }
 

@@ -1,12 +1,12 @@
 // vcomm_reduce_inst.cu -- the reducing collective kernel for ONE (protocol,
-// dtype) pair, selected at compile time by -DVC_PROTO=<0..2> -DVC_DTYPE=<0..3>.
+// dtype) pair, selected at compile time by -DVC_PROTO=<0..2> -DVC_DTYPE=<0..9>.
 // The build compiles this file once per pair, in parallel.
 #include <cuda_runtime.h>
 
 #include "vcomm_device.cuh"
 
 #ifndef VC_PROTO
-#error "compile with -DVC_PROTO=<0|1|2> -DVC_DTYPE=<0..3>"
+#error "compile with -DVC_PROTO=<0|1|2> -DVC_DTYPE=<0..9>"
 #endif
 
 namespace vc {
@@ -23,21 +23,18 @@ __global__ void __launch_bounds__(maxThreadsFor(P), 1) kReduceColl(const __grid_
   else runWorker<P, T, Op>(a, r, ch, sa);
 }
 
-#if VC_DTYPE == 0
-using VcT = int32_t;
-#elif VC_DTYPE == 1
-using VcT = float;
-#elif VC_DTYPE == 2
-using VcT = __half;
-#else
-using VcT = __nv_bfloat16;
-#endif
+using VcT = typename DTypeOf<VC_DTYPE>::T;
 
 #define VC_NAME2(P, D) reduceKernel_##P##_##D
 #define VC_NAME(P, D) VC_NAME2(P, D)
 const void* VC_NAME(VC_PROTO, VC_DTYPE)(int op) {
-  return op == kSum ? (const void*)kReduceColl<VC_PROTO, VcT, OpSum>
-                    : (const void*)kReduceColl<VC_PROTO, VcT, OpMax>;
+  switch (op) {
+    case kSum: return (const void*)kReduceColl<VC_PROTO, VcT, OpSum>;
+    case kMax: return (const void*)kReduceColl<VC_PROTO, VcT, OpMax>;
+    case kProd: return (const void*)kReduceColl<VC_PROTO, VcT, OpProd>;
+    case kMin: return (const void*)kReduceColl<VC_PROTO, VcT, OpMin>;
+  }
+  return nullptr;
 }
 
 }  // namespace vc

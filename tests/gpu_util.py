@@ -3,7 +3,8 @@ import numpy as np
 
 import oracle
 
-ESZ = {"int32": 4, "fp32": 4, "fp16": 2, "bf16": 2}
+ESZ = {"int32": 4, "fp32": 4, "fp16": 2, "bf16": 2, "int8": 1, "uint8": 1, "uint32": 4, "int64": 8,
+       "uint64": 8, "fp64": 8}
 
 # small FIFO slots so that modest sizes span many loops, chunks and FIFO steps
 SMALL_SLOTS = {"simple": 8192, "ll": 2048, "ll128": 2560}
@@ -21,7 +22,9 @@ def to_np(t, dtype):
     if t.dtype == torch.bfloat16:
         return t.view(torch.int16).cpu().numpy().view(np.uint16)
     out = t.cpu().numpy()
-    want = {"int32": np.int32, "fp32": np.float32, "fp16": np.float16}[dtype]
+    want = {"int32": np.int32, "fp32": np.float32, "fp16": np.float16, "int8": np.int8,
+            "uint8": np.uint8, "uint32": np.uint32, "int64": np.int64, "uint64": np.uint64,
+            "fp64": np.float64}[dtype]
     return out.astype(want, copy=False)
 
 
