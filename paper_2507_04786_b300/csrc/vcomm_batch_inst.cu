@@ -31,7 +31,8 @@ __device__ __noinline__ void VC_BNAME(VC_PROTO, VC_DTYPE)(const KernArgs& a, int
   else if (a.redop == kSum) opWorker<VC_PROTO, VcT, OpSum>(a, r, ch, sAbort);
   else if (a.redop == kMax) opWorker<VC_PROTO, VcT, OpMax>(a, r, ch, sAbort);
   else if (a.redop == kProd) opWorker<VC_PROTO, VcT, OpProd>(a, r, ch, sAbort);
-  else opWorker<VC_PROTO, VcT, OpMin>(a, r, ch, sAbort);
+  else if (a.redop == kMin) opWorker<VC_PROTO, VcT, OpMin>(a, r, ch, sAbort);
+  else opWorker<VC_PROTO, VcT, OpAvg>(a, r, ch, sAbort);
 }
 
 }  // namespace vc

@@ -156,7 +156,7 @@ struct ClusterPrims {
     const uint32_t nbytes = m * (uint32_t)sizeof(T);
     const uint32_t npairs = (nbytes + 7) / 8;
     const int sslot = (int)(sstep % kCSlots);
-    const int div = (doRecv && doLocal && doOut) ? a.postDiv : 0;   // avg completes here
+    const int div = (std::is_same<Op, OpAvg>::value && doRecv && doLocal && doOut) ? a.postDiv : 0;
     const int nw = nthr >> 5;
     int vt = tid - woff * 32;     // my position in this step's rotated map
     if (vt < 0) vt += nthr;

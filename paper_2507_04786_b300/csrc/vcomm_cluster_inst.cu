@@ -37,6 +37,7 @@ const void* VC_CNAME(VC_DTYPE)(int op) {
     case kMax: return (const void*)kClusterColl<VcT, OpMax>;
     case kProd: return (const void*)kClusterColl<VcT, OpProd>;
     case kMin: return (const void*)kClusterColl<VcT, OpMin>;
+    case kAvg: return (const void*)kClusterColl<VcT, OpAvg>;
   }
   return nullptr;
 }

@@ -74,6 +74,7 @@ struct OpSum {};
 struct OpMax {};
 struct OpProd {};
 struct OpMin {};
+struct OpAvg {};   // adds like OpSum; the completing step divides by KernArgs::postDiv
 struct OpNone {};
 
 // element type of each dtype code (the order of vDataType_t)
@@ -140,6 +141,9 @@ struct ElemOp {
 template <class T> struct ElemOp<T, OpNone> {
   static VDEV T f(T a, T) { return a; }
 };
+template <class T> struct ElemOp<T, OpAvg> {
+  static VDEV T f(T a, T b) { return ElemOp<T, OpSum>::f(a, b); }
+};
 
 // avg's final step: x / k, integers truncating toward zero, floats rounded
 // once to the type (16-bit: an fp32 quotient rounded again, innocuous)
@@ -181,7 +185,8 @@ template <> VDEV uint32_t sum2<__half>(uint32_t a, uint32_t b) {
 // apply f lane-wise on raw words (W = uint4, uint64_t or one element)
 template <class T, class Op, class W>
 VDEV W applyWord(W a, W b) {
-  if constexpr (sizeof(T) == 2 && std::is_same<Op, OpSum>::value && sizeof(W) % 4 == 0) {
+  if constexpr (sizeof(T) == 2 && (std::is_same<Op, OpSum>::value || std::is_same<Op, OpAvg>::value) &&
+                sizeof(W) % 4 == 0) {
     constexpr int n = sizeof(W) / 4;
     union U { W w; uint32_t u[n]; };
     U ua, ub, uo;
@@ -532,7 +537,7 @@ struct Prims {
     const uint32_t nbytes = m * (uint32_t)sizeof(T);
     // avg: the step that both reduces and writes the output completes the
     // value (ring segment owner, tree root, Reduce / ReduceScatter final)
-    const int div = (doRecv && doLocal && doOut) ? a.postDiv : 0;
+    const int div = (std::is_same<Op, OpAvg>::value && doRecv && doLocal && doOut) ? a.postDiv : 0;
     if (PROTO == kSimple) {
       const char* s0;
       const char* s1 = nullptr;

@@ -55,7 +55,7 @@ using VcT = typename DTypeOf<VC_DTYPE>::T;
 #define VC_DNAME(N, D) VC_DNAME2(N, D)
 const void* VC_DNAME(directReduceKernel, VC_DTYPE)(int op) {
   switch (op) {
-    case kSum: return (const void*)direct::kDirectReduce<VcT, OpSum>;
+    case kSum: case kAvg: return (const void*)direct::kDirectReduce<VcT, OpSum>;
     case kMax: return (const void*)direct::kDirectReduce<VcT, OpMax>;
     case kProd: return (const void*)direct::kDirectReduce<VcT, OpProd>;
     case kMin: return (const void*)direct::kDirectReduce<VcT, OpMin>;
@@ -64,7 +64,7 @@ const void* VC_DNAME(directReduceKernel, VC_DTYPE)(int op) {
 }
 const void* VC_DNAME(directBatchKernel, VC_DTYPE)(int op) {
   switch (op) {
-    case kSum: return (const void*)direct::kDirectBatch<VcT, OpSum>;
+    case kSum: case kAvg: return (const void*)direct::kDirectBatch<VcT, OpSum>;
     case kMax: return (const void*)direct::kDirectBatch<VcT, OpMax>;
     case kProd: return (const void*)direct::kDirectBatch<VcT, OpProd>;
     case kMin: return (const void*)direct::kDirectBatch<VcT, OpMin>;

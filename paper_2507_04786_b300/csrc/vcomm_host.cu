@@ -463,7 +463,7 @@ static vResult_t prepareCall(int coll, const void* const* sendbufs, void* const*
   cs->coll = coll;
   cs->kcoll = kcoll;
   cs->dtype = dtype;
-  cs->redop = op < 0 ? 0 : (op == vAvg ? kSum : op);
+  cs->redop = op < 0 ? 0 : op;
   cs->postDiv = (op == vAvg && kcoll != kCopy) ? k : 0;
   cs->root = root;
   cs->al = (plan.algo == vAlgoTree) ? kTree : kRing;

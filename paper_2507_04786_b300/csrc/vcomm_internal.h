@@ -31,9 +31,11 @@ enum Proto : int { kSimple = 0, kLL = 1, kLL128 = 2, kCluster = 3, kDirect = 4 }
 enum DType : int { kI32 = 0, kF32 = 1, kF16 = 2, kBF16 = 3, kI8 = 4, kU8 = 5, kU32 = 6, kI64 = 7,
                    kU64 = 8, kF64 = 9 };
 constexpr int kNumDtypes = 10;
-// element-wise ops of the kernels; avg runs as kSum with KernArgs::postDiv
-enum OpKind : int { kSum = 0, kMax = 1, kProd = 2, kMin = 3 };
-constexpr int kNumOps = 4;
+// element-wise ops of the kernels; avg adds like kSum and divides by
+// KernArgs::postDiv in the step that completes a value (its own kernels, so
+// that the other reductions compile without that step)
+enum OpKind : int { kSum = 0, kMax = 1, kProd = 2, kMin = 3, kAvg = 4 };
+constexpr int kNumOps = 5;
 
 constexpr int kCounterStride = 16;
 

@@ -33,6 +33,7 @@ const void* VC_NAME(VC_PROTO, VC_DTYPE)(int op) {
     case kMax: return (const void*)kReduceColl<VC_PROTO, VcT, OpMax>;
     case kProd: return (const void*)kReduceColl<VC_PROTO, VcT, OpProd>;
     case kMin: return (const void*)kReduceColl<VC_PROTO, VcT, OpMin>;
+    case kAvg: return (const void*)kReduceColl<VC_PROTO, VcT, OpAvg>;
   }
   return nullptr;
 }
