@@ -72,6 +72,8 @@ def lib():
         L.o_reduce_prim.argtypes = [i32, i32, i32]
         L.o_tree_links.argtypes = [i32, i32, i32] + [ctypes.POINTER(i32)] * 3
         L.o_tree_root.argtypes = [i32, i32]
+        L.o_htree_links.argtypes = [i32, i32, i32, i32] + [ctypes.POINTER(i32)] * 3
+        L.o_htree_root.argtypes = [i32, i32, i32]
         L.o_tree_prims.argtypes = [i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
         L.o_ring_allreduce.argtypes = [i32, i32, sz, i32, i32, sz, pp, pp]
         L.o_ring_reducescatter.argtypes = [i32, i32, sz, i32, i32, sz, pp, pp]
@@ -80,6 +82,8 @@ def lib():
         L.o_alltoall.argtypes = [i32, sz, pp, pp]
         L.o_ring_reduce.argtypes = [i32, i32, sz, i32, i32, sz, i32, pp, pp]
         L.o_tree_allreduce.argtypes = [i32, i32, sz, i32, i32, sz, pp, pp]
+        L.o_tree_allreduce_m.argtypes = [i32, i32, i32, sz, i32, i32, sz, pp, pp]
+        L.o_tree_allreduce_point_m.argtypes = [i32, i32, i32, sz, i32, i32, sz, sz, vp, vp]
         L.o_encode_array.argtypes = [i32, vp, sz, vp]
         L.o_decode_array.argtypes = [i32, vp, sz, vp]
         L.o_ll_lines.restype = sz
@@ -182,6 +186,18 @@ def tree_root(k: int, t: int) -> int:
     return int(lib().o_tree_root(k, t))
 
 
+def htree_links(k: int, m: int, t: int, r: int):
+    """(parent, child0, child1) of rank r in tree t of the hierarchical tree
+    with nodes of m ranks (Sec. V-E, reading R19); -1 for none."""
+    p, c0, c1 = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    lib().o_htree_links(k, m, t, r, ctypes.byref(p), ctypes.byref(c0), ctypes.byref(c1))
+    return p.value, c0.value, c1.value
+
+
+def htree_root(k: int, m: int, t: int) -> int:
+    return int(lib().o_htree_root(k, m, t))
+
+
 def tree_prims(k: int, t: int, r: int):
     u, d = ctypes.c_int(), ctypes.c_int()
     lib().o_tree_prims(k, t, r, ctypes.byref(u), ctypes.byref(d))
@@ -228,15 +244,20 @@ def _np_dtype(dtype):
             "uint64": np.uint64, "fp64": np.float64}[dtype]
 
 
-def all_reduce(xs, dtype: str, op: str, nch: int, chunk: int, algo: str = "ring"):
+def all_reduce(xs, dtype: str, op: str, nch: int, chunk: int, algo: str = "ring", node: int = 1):
     """Ring AllReduce (Table "Ring AllReduce") or double-binary-tree AllReduce
-    (Table "Tree AllReduce").  `chunk` is chunkCount in elements."""
+    (Table "Tree AllReduce"); `node` > 1: the hierarchical tree with chains of
+    `node` ranks inside each node (Sec. V-E).  `chunk` is chunkCount in
+    elements."""
     xs = [_raw(x) for x in xs]
     k, n = len(xs), xs[0].size
     _check(xs, n, dtype)
     outs = [np.empty_like(xs[0]) for _ in range(k)]
-    f = lib().o_ring_allreduce if algo == "ring" else lib().o_tree_allreduce
-    rc = f(k, nch, chunk, DTYPES[dtype], OPS[op], n, _ptrs(xs), _ptrs(outs))
+    if algo == "ring":
+        rc = lib().o_ring_allreduce(k, nch, chunk, DTYPES[dtype], OPS[op], n, _ptrs(xs), _ptrs(outs))
+    else:
+        rc = lib().o_tree_allreduce_m(k, node, nch, chunk, DTYPES[dtype], OPS[op], n, _ptrs(xs),
+                                      _ptrs(outs))
     assert rc == 0
     return outs
 
@@ -359,13 +380,18 @@ def ll128_decode(lines: np.ndarray, nbytes: int, flag: int):
     return int(st), out
 
 
-def all_reduce_points(xs, idx, dtype: str, op: str, nch: int, chunk: int, algo: str = "ring"):
+def all_reduce_points(xs, idx, dtype: str, op: str, nch: int, chunk: int, algo: str = "ring",
+                      node: int = 1):
     """Elements `idx` of the AllReduce result, computed one at a time (for
     outputs too large to replay whole).  xs: per-rank inputs (numpy arrays of
     the full length, or equivalently any arrays whose [idx] are the values)."""
     L = lib()
-    f = L.o_ring_allreduce_point if algo == "ring" else L.o_tree_allreduce_point
     k = len(xs)
+    if algo == "ring":
+        f = L.o_ring_allreduce_point
+    else:
+        def f(k_, nch_, chunk_, dt_, op_, n_, i_, v_, o_):
+            return L.o_tree_allreduce_point_m(k_, node, nch_, chunk_, dt_, op_, n_, i_, v_, o_)
     n = xs[0].size
     out = np.empty(len(idx), dtype=xs[0].dtype)
     vals = np.empty(k, dtype=xs[0].dtype)

@@ -396,6 +396,31 @@ void o_tree_links(int k, int t, int r, int* parent, int* child0, int* child1) {
 }
 int o_tree_root(int k, int t) { return o_tree_rank_of_node(k, t, o_treeA_root(k)); }
 
+/* ------------------------------------------------------------------------ */
+/* Hierarchical tree [Sec. V-E: the branching structure is built only across */
+/* nodes; inside each node the ranks form a simple chain] (reading R19).     */
+/* The k ranks form k/m nodes of m consecutive ranks; the double binary tree */
+/* above links the nodes.  Inside node n the chain runs n*m -> n*m+1 -> ...  */
+/* -> n*m+m-1 downwards: the first rank of a node hangs from the last rank   */
+/* of its parent node, and the last rank of a node carries the node's child  */
+/* nodes (their first ranks, in tree-A node order), so no rank has more than */
+/* two children.  m = 1 is the flat tree.                                    */
+/* ------------------------------------------------------------------------ */
+void o_htree_links(int k, int m, int t, int r, int* parent, int* child0, int* child1) {
+  if (m <= 1) { o_tree_links(k, t, r, parent, child0, child1); return; }
+  int nn = k / m, node = r / m, i = r % m;
+  int pn = -1, c0 = -1, c1 = -1;
+  if (nn > 1) o_tree_links(nn, t, node, &pn, &c0, &c1);
+  *parent = (i > 0) ? r - 1 : (pn >= 0 ? pn * m + m - 1 : -1);
+  if (i < m - 1) { *child0 = r + 1; *child1 = -1; }
+  else { *child0 = c0 >= 0 ? c0 * m : -1; *child1 = c1 >= 0 ? c1 * m : -1; }
+}
+int o_htree_root(int k, int m, int t) {
+  if (m <= 1) return o_tree_root(k, t);
+  int nn = k / m;
+  return (nn > 1 ? o_tree_root(nn, t) : 0) * m;
+}
+
 /* Tree AllReduce roles, Table "Tree AllReduce": root recvReduceCopySend;
  * middle recvReduceSend then recvCopySend; leaf send then recv */
 void o_tree_prims(int k, int t, int r, int* up, int* down) {
@@ -628,7 +653,7 @@ int o_ring_reduce(int k, int nch, size_t chunk, int dt, int op, size_t count, in
 /* root writes the result; broadcast phase: the result is copied down.       */
 /* ------------------------------------------------------------------------ */
 typedef struct {
-  int k, t, dt, op;
+  int k, m, t, dt, op;
   size_t n, off;
   const void* const* send;
   char** val;               /* per rank: value sent up (n units) */
@@ -637,7 +662,7 @@ typedef struct {
 static void o_tree_up(OTreeCtx* c, int r) {
   int es = o_dtype_size(c->dt);
   int p, c0, c1;
-  o_tree_links(c->k, c->t, r, &p, &c0, &c1);
+  o_htree_links(c->k, c->m, c->t, r, &p, &c0, &c1);
   const char* own = (const char*)c->send[r] + c->off * es;
   memcpy(c->val[r], own, c->n * (size_t)es);
   int kids[2] = {c0, c1};
@@ -649,10 +674,10 @@ static void o_tree_up(OTreeCtx* c, int r) {
   }
 }
 
-int o_tree_allreduce(int k, int nch, size_t chunk, int dt, int op, size_t count,
-                     const void* const* send, void* const* recv) {
+int o_tree_allreduce_m(int k, int m, int nch, size_t chunk, int dt, int op, size_t count,
+                       const void* const* send, void* const* recv) {
   int es = o_dtype_size(dt);
-  if (k < 1 || nch < 1 || es == 0 || chunk == 0) return -1;
+  if (k < 1 || nch < 1 || es == 0 || chunk == 0 || m < 1 || k % m) return -1;
   if (k == 1) { memcpy(recv[0], send[0], count * (size_t)es); return 0; }
   char** val = calloc((size_t)k, sizeof(char*));
   for (int r = 0; r < k; r++) val[r] = malloc(chunk * (size_t)es + 16);
@@ -664,8 +689,8 @@ int o_tree_allreduce(int k, int nch, size_t chunk, int dt, int op, size_t count,
     size_t end = start + len;
     for (size_t off = start; off < end; off += chunk) {
       size_t n = (end - off < chunk) ? end - off : chunk;
-      OTreeCtx c = {k, t, dt, op, n, off, send, val};
-      int root = o_tree_root(k, t);
+      OTreeCtx c = {k, m, t, dt, op, n, off, send, val};
+      int root = o_htree_root(k, m, t);
       o_tree_up(&c, root);
       /* the root's recvReduceCopySend completes the value (avg divides) */
       if (op == O_AVG) for (size_t i = 0; i < n; i++) o_div_elem(dt, val[root], i, k);
@@ -675,6 +700,11 @@ int o_tree_allreduce(int k, int nch, size_t chunk, int dt, int op, size_t count,
   for (int r = 0; r < k; r++) free(val[r]);
   free(val);
   return 0;
+}
+
+int o_tree_allreduce(int k, int nch, size_t chunk, int dt, int op, size_t count,
+                     const void* const* send, void* const* recv) {
+  return o_tree_allreduce_m(k, 1, nch, chunk, dt, op, count, send, recv);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -769,24 +799,24 @@ int o_ring_allreduce_point(int k, int nch, size_t chunk, int dt, int op, size_t 
 }
 
 /* tree AllReduce: sub-channel j holding i runs tree j % 2 */
-static void o_tree_point_up(int k, int t, int dt, int op, int r, const void* vals, char* out) {
+static void o_tree_point_up(int k, int m, int t, int dt, int op, int r, const void* vals, char* out) {
   int es = o_dtype_size(dt);
   int p, c0, c1;
-  o_tree_links(k, t, r, &p, &c0, &c1);
+  o_htree_links(k, m, t, r, &p, &c0, &c1);
   memcpy(out, (const char*)vals + (size_t)es * (size_t)r, (size_t)es);
   int kids[2] = {c0, c1};
   for (int j = 0; j < 2; j++) {
     if (kids[j] < 0) continue;
     char sub[8];
-    o_tree_point_up(k, t, dt, op, kids[j], vals, sub);
+    o_tree_point_up(k, m, t, dt, op, kids[j], vals, sub);
     o_reduce_elem(dt, op, sub, 0, out, 0, out, 0);
   }
 }
-int o_tree_allreduce_point(int k, int nch, size_t chunk, int dt, int op, size_t count, size_t i,
-                           const void* vals, void* out) {
+int o_tree_allreduce_point_m(int k, int m, int nch, size_t chunk, int dt, int op, size_t count,
+                             size_t i, const void* vals, void* out) {
   int es = o_dtype_size(dt);
   (void)chunk;
-  if (k < 1 || i >= count) return -1;
+  if (k < 1 || i >= count || m < 1 || k % m) return -1;
   if (k == 1) { memcpy(out, vals, (size_t)es); return 0; }
   int nsub = 2 * nch;
   for (int j = 0; j < nsub; j++) {
@@ -794,12 +824,16 @@ int o_tree_allreduce_point(int k, int nch, size_t chunk, int dt, int op, size_t 
     o_channel_range(count, es, nsub, j, &start, &len);
     if (i < start || i >= start + len) continue;
     char acc[8];
-    o_tree_point_up(k, j % 2, dt, op, o_tree_root(k, j % 2), vals, acc);
+    o_tree_point_up(k, m, j % 2, dt, op, o_htree_root(k, m, j % 2), vals, acc);
     if (op == O_AVG) o_div_elem(dt, acc, 0, k);
     memcpy(out, acc, (size_t)es);
     return 0;
   }
   return -1;
+}
+int o_tree_allreduce_point(int k, int nch, size_t chunk, int dt, int op, size_t count, size_t i,
+                           const void* vals, void* out) {
+  return o_tree_allreduce_point_m(k, 1, nch, chunk, dt, op, count, i, vals, out);
 }
 
 /* ring ReduceScatter: element i of rank b's output folds block b in the

@@ -315,7 +315,8 @@ def test_fold_order_golden(case):
     xs = [np.full(n, v, np.float16) for v in case["inputs"]]
     hexes = lambda a: [format(int(v), "04x") for v in a.view(np.uint16)]
     if case["coll"] == "allreduce":
-        outs = oracle.all_reduce(xs, "fp16", "sum", case["nch"], case["chunk"], case["algo"])
+        outs = oracle.all_reduce(xs, "fp16", "sum", case["nch"], case["chunk"], case["algo"],
+                                 node=case.get("node", 1))
         for o in outs:
             assert hexes(o) == case["expected_hex"]
     elif case["coll"] == "reducescatter":
@@ -594,3 +595,68 @@ def test_point_queries_match_replay_new_ops(dtype, op):
         full = oracle.reduce(xs, dtype, op, root, C, chunk)
         pts = oracle.reduce_points(xs, root, np.arange(n), dtype, op)
         assert np.array_equal(pts.view(np.uint8), full.view(np.uint8))
+
+
+# ---------------------------------------------------------------- hierarchical tree (reading R19)
+
+HT = [(m, n) for m in (1, 2, 3, 4, 5) for n in range(1, 10)]
+
+
+@pytest.mark.parametrize("m,nn", HT)
+def test_hierarchical_tree_structure(m, nn):
+    """Sec. V-E: branching only across nodes, a chain inside each node; every
+    rank has at most two children; one root; the node graph is the double
+    binary tree over the nodes; m = 1 is the flat tree."""
+    k = m * nn
+    for t in (0, 1):
+        links = [oracle.htree_links(k, m, t, r) for r in range(k)]
+        roots = [r for r in range(k) if links[r][0] < 0]
+        assert roots == [oracle.htree_root(k, m, t)] and roots[0] % m == 0
+        seen, stack = set(), [roots[0]]
+        while stack:                                   # a tree: every rank reached once
+            r = stack.pop()
+            assert r not in seen
+            seen.add(r)
+            for c in links[r][1:]:
+                if c >= 0:
+                    assert links[c][0] == r
+                    stack.append(c)
+        assert seen == set(range(k))
+        for r, (p, c0, c1) in enumerate(links):
+            i = r % m
+            if i > 0:
+                assert p == r - 1                      # chain inside the node
+            if i < m - 1:
+                assert (c0, c1) == (r + 1, -1)
+            else:
+                for c in (c0, c1):                     # branches leave from a node's last rank
+                    assert c < 0 or (c % m == 0 and c // m != r // m)
+            if m == 1:
+                assert (p, c0, c1) == oracle.tree_links(k, t, r)
+        # node graph = the flat double binary tree over the nodes
+        if nn > 1:
+            for node in range(nn):
+                p_node, a, b = oracle.tree_links(nn, t, node)
+                first, last = node * m, node * m + m - 1
+                assert links[first][0] == (p_node * m + m - 1 if p_node >= 0 else -1)
+                assert [c // m for c in links[last][1:] if c >= 0] == [c for c in (a, b) if c >= 0]
+
+
+@pytest.mark.parametrize("m,nn", [(2, 2), (2, 3), (3, 3), (4, 2), (5, 1)])
+@pytest.mark.parametrize("dtype,op", [("int32", "sum"), ("int64", "max"), ("uint8", "prod"),
+                                      ("fp32", "min"), ("int8", "avg")])
+def test_hierarchical_tree_brute_force(m, nn, dtype, op):
+    k, n = m * nn, 37
+    xs = ext_inputs(11 * k + m, k, n, dtype, op)
+    want = plain_ext(xs, dtype, op, k)
+    for o in oracle.all_reduce(xs, dtype, op, 2, 16, "tree", node=m):
+        assert np.array_equal(o.view(np.uint8), want.view(np.uint8))
+
+
+@pytest.mark.parametrize("m,nn", [(2, 4), (4, 2), (3, 5)])
+def test_hierarchical_tree_points_match_replay(m, nn):
+    k, n = m * nn, 2003
+    xs = inputs.workload(3, k, n, "bf16", "normal")
+    full = oracle.all_reduce(xs, "bf16", "sum", 3, 64, "tree", node=m)[0]
+    pts = oracle.all_reduce_points(xs, np.arange(n), "bf16", "sum", 3, 64, "tree", node=m)
+    assert np.array_equal(pts.view(np.uint8), full.view(np.uint8))
