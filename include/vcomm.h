@@ -107,6 +107,9 @@ typedef struct {
   int nthreads;          /* upper bound on threads per CTA [1024; Simple kernels use at most
                             512]; lowered to fit co-residency */
   double timeoutSec;     /* deadline of every device flag wait [5 s; env VCOMM_TIMEOUT_MS] */
+  int treeNodeSize;      /* vranks per node of the tree algorithm [1]: the double binary tree
+                            branches only across nodes of this many consecutive vranks, which
+                            form a chain inside the node (Sec. V-E); must divide nranks */
 } vcommConfig_t;
 
 /* Plan of one call: algorithm, protocol, channels and chunk steps.  Used to

@@ -42,7 +42,8 @@ class VcommError(RuntimeError):
 
 class Config(ctypes.Structure):
     _fields_ = [("slotBytes", ctypes.c_size_t * 3), ("nsteps", ctypes.c_int),
-                ("nthreads", ctypes.c_int), ("timeoutSec", ctypes.c_double)]
+                ("nthreads", ctypes.c_int), ("timeoutSec", ctypes.c_double),
+                ("treeNodeSize", ctypes.c_int)]
 
 
 class ServeConfig(ctypes.Structure):
@@ -164,7 +165,7 @@ class Comm:
     """A communicator of `nranks` virtual ranks on the current CUDA device."""
 
     def __init__(self, nranks: int, nchannels: int, slot_bytes=None, nsteps: int = 0,
-                 nthreads: int = 0, timeout_sec: float = 0.0):
+                 nthreads: int = 0, timeout_sec: float = 0.0, tree_node: int = 0):
         L = load_library()
         self._h = ctypes.c_void_p()
         cfg = Config()
@@ -172,6 +173,7 @@ class Comm:
             for i, p in enumerate(("simple", "ll", "ll128")):
                 cfg.slotBytes[i] = int(slot_bytes.get(p, 0))
         cfg.nsteps, cfg.nthreads, cfg.timeoutSec = nsteps, nthreads, timeout_sec
+        cfg.treeNodeSize = tree_node
         _check(L.vcommInitConfig(ctypes.byref(self._h), nranks, nchannels, ctypes.byref(cfg)),
                "vcommInitConfig")
         self.nranks, self.nchannels = nranks, nchannels

@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(512, 1) kBatch(const __grid_constant__ BatchAr
       sa.upThreads = (blockDim.x / 2) / 32 * 32;
       sa.skipRank = -1;
       sa.postDiv = o.postDiv;
+      sa.treeNode = b.treeNode;
     }
     __syncthreads();
     const bool bytes = (o.coll == kAllGather || o.coll == kBroadcast ||
@@ -175,6 +176,7 @@ __global__ void __launch_bounds__(512, 1) kServe(const __grid_constant__ ServeAr
           sa.upThreads = (blockDim.x / 2) / 32 * 32;
           sa.skipRank = -1;
           sa.postDiv = 0;   // serving runs sum and max only
+          sa.treeNode = 1;  // and the ring only
           for (int i = 0; i < q->nranks; i++) {
             sa.send[i] = (const void*)q->send[i];
             sa.recv[i] = (void*)q->recv[i];

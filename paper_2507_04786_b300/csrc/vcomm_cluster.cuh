@@ -261,7 +261,7 @@ VDEV void runClusterWorker(const KernArgs& a, int r, int ch, volatile int* sAbor
     if (a.algo == kTree) {
       const int t = ch & 1;
       int parent, c0, c1;
-      treeLinks(k, t, r, &parent, &c0, &c1);
+      treeLinksM(k, a.treeNode, t, r, &parent, &c0, &c1);
       leaf = (c0 < 0);
       // credit sets at a sender: 0 = its up link, 1 / 2 = its down links to
       // child0 / child1.  Incoming FIFOs: 0 / 1 = from child0 / child1, 2 =
@@ -277,7 +277,7 @@ VDEV void runClusterWorker(const KernArgs& a, int r, int ch, volatile int* sAbor
           if (c1 >= 0) { (pr.nsc == 0 ? pr.sA : pr.sB) = toC1; pr.nsc++; }
         } else {
           int p0, pc0, pc1;
-          treeLinks(k, t, parent, &p0, &pc0, &pc1);
+          treeLinksM(k, a.treeNode, t, parent, &p0, &pc0, &pc1);
           pr.sA = CLink{parent, (pc0 == r) ? 0 : 1, 0};
           pr.nsc = 1;
           pr.nthr = a.upThreads;
@@ -288,7 +288,7 @@ VDEV void runClusterWorker(const KernArgs& a, int r, int ch, volatile int* sAbor
         pr.nthr = blockDim.x - a.upThreads;
         pr.sAbort = sAbort + 1;
         int p0, pc0, pc1;
-        treeLinks(k, t, parent, &p0, &pc0, &pc1);
+        treeLinksM(k, a.treeNode, t, parent, &p0, &pc0, &pc1);
         pr.rA = CLink{parent, 2, (pc0 == r) ? 1 : 2};
         pr.nrc = 1;
         if (c0 >= 0) { (pr.nsc == 0 ? pr.sA : pr.sB) = toC0; pr.nsc++; }

@@ -874,7 +874,7 @@ VDEV void runWorker(const KernArgs& a, int r, int ch, volatile int* sAbort) {
   if (a.algo == kTree) {
     const int t = ch & 1;
     int parent, c0, c1;
-    treeLinks(k, t, r, &parent, &c0, &c1);
+    treeLinksM(k, a.treeNode, t, r, &parent, &c0, &c1);
     const ConnDev* up = a.conns + (unsigned long long)ch * k;                   // rank -> parent
     const ConnDev* down = a.conns + a.downOffset + (unsigned long long)ch * k;  // parent -> rank
     leaf = (c0 < 0);

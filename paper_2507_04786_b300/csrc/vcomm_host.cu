@@ -107,6 +107,7 @@ struct vcomm {
   size_t slotBytes[3] = {0, 0, 0};
   int nsteps = 8, nthreads = 1024;
   double timeoutSec = 5.0;
+  int treeNode = 1;                  // vranks per node of the hierarchical tree
   Arena arena[2][3];
   ErrWord* hErr = nullptr;
   ErrWord* dErr = nullptr;
@@ -192,6 +193,11 @@ vResult_t vcommInitConfig(vcomm_t* comm, int nranks, int nchannels, const vcommC
     return vInvalidArgument;
   }
   c->timeoutSec = (cfg && cfg->timeoutSec > 0) ? cfg->timeoutSec : 5.0;
+  c->treeNode = (cfg && cfg->treeNodeSize > 0) ? cfg->treeNodeSize : 1;
+  if (nranks % c->treeNode != 0) {
+    delete c;
+    return vInvalidArgument;
+  }
   if (!(cfg && cfg->timeoutSec > 0)) {
     const char* env = getenv("VCOMM_TIMEOUT_MS");
     if (env && atof(env) > 0) c->timeoutSec = atof(env) / 1000.0;
@@ -550,6 +556,7 @@ static vResult_t launchCluster(CallSpec& cs) {
   a.upThreads = (nthr / 2) / 32 * 32;
   a.skipRank = c->skipRank;
   a.postDiv = cs.postDiv;
+  a.treeNode = c->treeNode;
 
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(k * nsub));
@@ -698,6 +705,7 @@ static vResult_t launchSingle(CallSpec& cs) {
   a.upThreads = (nthr / 2) / 32 * 32;
   a.skipRank = c->skipRank;
   a.postDiv = cs.postDiv;
+  a.treeNode = c->treeNode;
 
   void* args[] = {(void*)&a};
   cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)(k * nsub)), dim3((unsigned)nthr),
@@ -960,6 +968,7 @@ static vResult_t launchFifoGroup(vcomm* c, std::vector<CallSpec>& ops) {
     b->ngangs = G;
     b->cpg = cpg;
     b->nsteps = c->nsteps;
+    b->treeNode = c->treeNode;
     int pos = 0;
     for (int g = 0; g < G; g++) {
       b->gangStart[g] = pos;

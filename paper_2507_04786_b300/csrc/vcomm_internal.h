@@ -86,6 +86,7 @@ struct KernArgs {
   int upThreads;                   // tree: threads of the reduce (up) group on non-root ranks
   int skipRank;                    // fault injection: this vrank's CTAs return at once (-1: none)
   int postDiv;                     // avg: the step that completes a value divides it by this (0: none)
+  int treeNode;                    // tree: vranks per node of the hierarchical tree (0 or 1: flat)
 };
 
 // ---- batched launch: many collectives in one persistent kernel (group calls,
@@ -110,7 +111,7 @@ struct BatchArgs {
   int* errClaim;
   ErrWord* err;
   const volatile int* abortFlag;
-  int nops, nranks, ngangs, cpg, nsteps, pad;
+  int nops, nranks, ngangs, cpg, nsteps, treeNode;
   int gangStart[kMaxGangs + 1];      // gang g runs order[gangStart[g] .. gangStart[g+1])
   unsigned char order[kMaxBatchOps];
   BatchOpDesc ops[kMaxBatchOps];
@@ -275,6 +276,28 @@ VC_HD void treeLinks(int k, int t, int r, int* parent, int* child0, int* child1)
   *child1 = c1 ? treeRankOfNode(k, t, c1) : -1;
   int p = treeANodeParent(k, i);
   *parent = p ? treeRankOfNode(k, t, p) : -1;
+}
+
+// ---- hierarchical tree (Sec. V-E: branching only across nodes, a chain
+// inside each node).  The k vranks form k/m nodes of m consecutive vranks;
+// the double binary tree above links the nodes; inside node n the chain runs
+// n*m -> ... -> n*m+m-1 downwards, the node's first vrank hanging from the
+// last vrank of its parent node and the node's last vrank carrying the first
+// vranks of its child nodes, so no vrank has more than two children.
+// m <= 1 is the flat tree.
+VC_HD void treeLinksM(int k, int m, int t, int r, int* parent, int* child0, int* child1) {
+  if (m <= 1) { treeLinks(k, t, r, parent, child0, child1); return; }
+  const int nn = k / m, node = r / m, i = r % m;
+  int pn = -1, c0 = -1, c1 = -1;
+  if (nn > 1) treeLinks(nn, t, node, &pn, &c0, &c1);
+  *parent = (i > 0) ? r - 1 : (pn >= 0 ? pn * m + m - 1 : -1);
+  if (i < m - 1) {
+    *child0 = r + 1;
+    *child1 = -1;
+  } else {
+    *child0 = c0 >= 0 ? c0 * m : -1;
+    *child1 = c1 >= 0 ? c1 * m : -1;
+  }
 }
 
 }  // namespace vc
