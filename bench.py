@@ -489,18 +489,28 @@ def run_small(args):
 
 # ------------------------------------------------------------------ served leg
 
-def run_served(args):
+def fifo_proto(nbytes):
+    """The paper's protocol choice by size (Sec. III-D: LL for small, LL128 for
+    medium, Simple for large messages)."""
+    return "ll" if nbytes < (64 << 10) else ("ll128" if nbytes < (2 << 20) else "simple")
+
+
+def run_served(args, rate=None, nreq=None, modes=("batch", "plain"), protocol="fifo"):
     """Poisson arrivals (mean 2000/s) of AllReduce / AllGather / ReduceScatter
     requests on 2..16 vranks, per-rank sizes log-uniform in 1 KiB..128 MiB,
-    fp32/bf16, admitted under a 40 GB budget: continuous batching vs one
-    launch per request, same request stream."""
+    fp32/bf16, admitted under a 40 GB budget, the same request stream served by
+    continuous batching on resident gangs and by one launch per request on one
+    stream (and, for `modes` with "streams", continuous batching on lanes of
+    streams); `protocol` "fifo": the paper's protocols by size, "auto": the
+    library's choice (the direct protocol)."""
     import torch
 
     from paper_2507_04786_b300 import Server
     w = workloads.SERVED
-    nreq = args.serve_requests
+    nreq = nreq or args.serve_requests
+    rate = rate or w["rate_per_s"]
     g = np.random.default_rng(w["seed"])
-    gaps = g.exponential(1.0 / w["rate_per_s"], nreq)
+    gaps = g.exponential(1.0 / rate, nreq)
     arrivals = np.cumsum(gaps)
     sizes = inputs.log_uniform_sizes(w["seed"], nreq, w["lo_bytes"], w["hi_bytes"])
     colls = g.integers(0, 3, nreq)
@@ -523,15 +533,17 @@ def run_served(args):
             n = max(1, n // k)
         reqs.append((coll, dt, k, n, int(sizes[i])))
     out = {}
-    for mode in ("batch", "plain"):
-        srv = Server(mode=mode, max_ranks=w["max_ranks"], mem_budget=w["budget_bytes"])
+    for mode in modes:
+        srv = Server(mode=mode, max_ranks=w["max_ranks"], mem_budget=w["budget_bytes"],
+                     small_gangs=w["small_lanes"] if mode == "streams" else 1)
         tickets = []
         t0 = time.monotonic_ns() + 20_000_000
         for i, (coll, dt, k, n, S) in enumerate(reqs):
             due = t0 + int(arrivals[i] * 1e9)
             while time.monotonic_ns() < due:
                 pass
-            tickets.append(srv.submit(coll, pool[dt][:k], n, dt, "sum", release=True,
+            proto = fifo_proto(S) if protocol == "fifo" else "auto"
+            tickets.append(srv.submit(coll, pool[dt][:k], n, dt, "sum", proto=proto, release=True,
                                       arrival_ns=due))
         deadline = time.time() + 120
         while srv.stats()["completed"] + srv.stats()["failed"] < nreq and time.time() < deadline:
@@ -559,9 +571,15 @@ def run_served(args):
                      "max_inflight_GB": round(st["maxInflightBytes"] / 1e9, 2),
                      "mean_service_ms_large": round(float(np.mean(svc_big)), 4) if svc_big else None,
                      "mean_service_ms_small": round(float(np.mean(svc_small)), 4) if svc_small else None}
-    return {"workload": w["name"], "requests": nreq, "rate_per_s": w["rate_per_s"],
-            "budget_GB": w["budget_bytes"] / 1e9, "continuous_batching": out["batch"],
-            "per_call": out["plain"]}
+    names = {"streams": "continuous_batching_streams", "batch": "continuous_batching",
+             "plain": "per_call"}
+    res = {"workload": w["name"] if rate == w["rate_per_s"] else f"served-poisson-{int(rate)}rps",
+           "requests": nreq, "rate_per_s": rate, "budget_GB": w["budget_bytes"] / 1e9,
+           "protocol": ("the paper's FIFO protocols by size (LL < 64 KiB <= LL128 < 2 MiB <= Simple)"
+                        if protocol == "fifo" else "auto (direct)")}
+    for m in modes:
+        res[names[m]] = out[m]
+    return res
 
 
 # ------------------------------------------------------------------ protocol sweep
@@ -743,6 +761,7 @@ def main():
         line["small_messages"] = run_small(args)
         line["batched"] = run_batched(args)
         line["served"] = run_served(args)
+        line["served_direct"] = run_served(args, modes=("plain", "streams", "batch"), protocol="auto")
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(k, args.proto, w["nchannels"], w["chunk_steps"],
                                             w["seed"])

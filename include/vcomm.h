@@ -288,13 +288,20 @@ vResult_t vcommGetTuneTable(vcomm_t comm, int coll, vPlan_t* plans, size_t* byte
  * or all of the wide gang's channels for large requests; chunkSteps 1), so
  * its result is bit-identical alone and in any mix, and equal to vAllReduce
  * (ring) with that plan.  mode 1 ("plain") runs the same requests as one
- * ordinary launch each on one stream, for comparison.
+ * ordinary launch each on one stream, for comparison.  mode 2 ("streams")
+ * is continuous batching without a resident kernel: each admitted request is
+ * one launch on a lane -- a stream for large requests (>= bigThreshold) and
+ * max(1, smallGangs) streams for the others -- whose grid is capped (the
+ * large lane leaves 16 SMs; a small lane takes one CTA per 256 KiB of the
+ * request's traffic, 4 to 32), so that requests on different lanes run side
+ * by side; at most two launches per lane are in flight.  Plans as in mode 1, so results are bit-identical across modes.
  * While a mode-0 server exists its kernel occupies the SMs: do not launch and
  * wait for other kernels meanwhile (copies are fine). */
 typedef enum { vCollAllReduce = 0, vCollReduceScatter = 1, vCollAllGather = 2 } vColl_t;
 typedef struct vserve* vserve_t;
 typedef struct {
-  int mode;              /* 0 continuous batching [default], 1 one launch per request */
+  int mode;              /* 0 continuous batching on resident gangs [default], 1 one launch
+                            per request, 2 continuous batching on lanes of streams */
   int maxRanks;          /* vranks per request, <= 16 [16] */
   size_t memBudget;      /* bytes of request buffers in flight [40 GiB]; the pool is this size */
   int bigGangChannels;   /* channels of the wide gang [0: every co-resident CTA the
@@ -322,7 +329,7 @@ vResult_t vServeSubmit(vserve_t server, int coll, const void* const* sendbufs, s
                        int64_t arrivalNs, uint64_t* ticket);
 /* state: 0 queued, 1 running, 2 done, 3 failed; latency = completion - arrival
  * (ns, -1 until done); service = the request's own run time on the device
- * (mode 0: the gang's clock; mode 1: events around its launch; ns); plan; recvbufs (nranks pointers into the
+ * (mode 0: the gang's clock; modes 1, 2: events around its launch; ns); plan; recvbufs (nranks pointers into the
  * pool, valid until vServeRelease).  Any output may be NULL except state. */
 vResult_t vServeQuery(vserve_t server, uint64_t ticket, int* state, int64_t* latencyNs,
                       int64_t* serviceNs, vPlan_t* plan, void** recvbufs);

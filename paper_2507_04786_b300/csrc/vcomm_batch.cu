@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include "vcomm_device.cuh"
+#include "vcomm_direct.cuh"
 #include "vcomm_kernels.h"
 
 namespace vc {
@@ -98,6 +99,49 @@ __global__ void __launch_bounds__(512, 1) kBatch(const __grid_constant__ BatchAr
 // idleTimeoutNs, a failed one stops and flags its mailbox.
 __device__ __forceinline__ uint64_t ldVol64(const volatile unsigned long long* p) { return *p; }
 
+// A request with the direct protocol (no FIFO) spreads its units over all of
+// the gang's CTAs: CTA `local` of `nctas` takes a contiguous share.  One body
+// per (dtype, op), not inlined, so that each keeps its own registers.
+__device__ void shareRange(unsigned long long total, unsigned long long local, unsigned long long nctas,
+                           unsigned long long* lo, unsigned long long* hi) {
+  unsigned long long per = (total + nctas - 1) / nctas;
+  per = (per + blockDim.x - 1) / blockDim.x * blockDim.x;
+  *lo = local * per < total ? local * per : total;
+  *hi = *lo + per < total ? *lo + per : total;
+}
+
+template <class T, class Op>
+__device__ __noinline__ void serveDirect(const ServeReq* q, unsigned long long local, unsigned long long nctas) {
+  using namespace direct;
+  const DirectView v{(const void* const*)q->send, (void* const*)q->recv, q->count, q->chunk, q->inplaceMask,
+                     q->coll, q->nranks, q->nsub, q->root, 0};
+  unsigned long long lo, hi;
+  if (q->coll == kAllGather || q->coll == kBroadcast) {
+    if (q->vec) {
+      shareRange(copyUnits(v, 16), local, nctas, &lo, &hi);
+      directCopy<Unit16<uint8_t>>(v, lo, hi, local + 1 == nctas);
+    } else {
+      shareRange(copyUnits(v, 1), local, nctas, &lo, &hi);
+      directCopy<Unit1<uint8_t>>(v, lo, hi, local + 1 == nctas);
+    }
+  } else if (q->vec) {
+    shareRange(reduceUnits(v, Unit16<T>::kElems), local, nctas, &lo, &hi);
+    directReduce<T, Op, Unit16<T>, 1>(v, lo, hi, local + 1 == nctas);
+  } else {
+    shareRange(reduceUnits(v, 1), local, nctas, &lo, &hi);
+    directReduce<T, Op, Unit1<T>, 1>(v, lo, hi, local + 1 == nctas);
+  }
+}
+
+__device__ void dispatchDirect(const ServeReq* q, unsigned long long local, unsigned long long nctas) {
+  const bool mx = q->redop == kMax;
+  if (q->coll == kAllGather || q->coll == kBroadcast) serveDirect<uint8_t, OpNone>(q, local, nctas);
+  else if (q->dtype == kI32) mx ? serveDirect<int32_t, OpMax>(q, local, nctas) : serveDirect<int32_t, OpSum>(q, local, nctas);
+  else if (q->dtype == kF32) mx ? serveDirect<float, OpMax>(q, local, nctas) : serveDirect<float, OpSum>(q, local, nctas);
+  else if (q->dtype == kF16) mx ? serveDirect<__half, OpMax>(q, local, nctas) : serveDirect<__half, OpSum>(q, local, nctas);
+  else mx ? serveDirect<__nv_bfloat16, OpMax>(q, local, nctas) : serveDirect<__nv_bfloat16, OpSum>(q, local, nctas);
+}
+
 __global__ void __launch_bounds__(512, 1) kServe(const __grid_constant__ ServeArgs s) {
   __shared__ KernArgs sa;
   __shared__ int sAbort[2];
@@ -147,7 +191,9 @@ __global__ void __launch_bounds__(512, 1) kServe(const __grid_constant__ ServeAr
       }
       sStop = stop;
       int use = 0;
-      if (!stop) {
+      if (!stop && ((const volatile ServeReq*)&G->req)->proto == kDirect) {
+        use = 2;   // the direct protocol: every CTA of the gang takes a share
+      } else if (!stop) {
         const volatile ServeReq* q = (const volatile ServeReq*)&G->req;
         // a request of k vranks and C channels runs on the gang's first k x C CTAs
         use = (local < q->nranks * q->nsub) ? 1 : 0;
@@ -191,7 +237,9 @@ __global__ void __launch_bounds__(512, 1) kServe(const __grid_constant__ ServeAr
     if (sStop) return;
     ch = sCh;
     r = sR;
-    if (sUse) {
+    if (sUse == 2) {
+      dispatchDirect(&G->req, (unsigned long long)local, nctas);
+    } else if (sUse) {
       const int proto = sa.coll == kCopy ? kSimple : ((const volatile ServeReq*)&G->req)->proto;
       const int dtype = ((const volatile ServeReq*)&G->req)->dtype;
       const bool bytes = (sa.coll == kAllGather || sa.coll == kBroadcast ||

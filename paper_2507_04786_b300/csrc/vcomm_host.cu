@@ -374,6 +374,7 @@ struct CallSpec {
   unsigned long long units = 0; // partitioned units (0: nothing to do)
   unsigned long long inplace = 0;
   size_t S = 0;                 // the larger per-rank buffer, bytes
+  int maxCtas = 0;              // direct protocol: cap on the grid (0: the whole GPU)
   cudaStream_t stream = nullptr;
   const void* send[VCOMM_MAX_RANKS];
   void* recv[VCOMM_MAX_RANKS];
@@ -639,6 +640,7 @@ static vResult_t launchDirect(CallSpec& cs) {
   const long long resident = (long long)std::max(1, residentPerSM(fn, nthr)) * c->nsm;
   long long grid = (long long)((units + nthr - 1) / nthr);
   grid = std::max<long long>(1, std::min<long long>(grid, resident));
+  if (cs.maxCtas > 0) grid = std::min<long long>(grid, cs.maxCtas);
   void* args[] = {(void*)&a};
   VC_TRY(cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(nthr), args, 0, cs.stream));
   c->last = cs.plan;
@@ -1008,6 +1010,21 @@ static vResult_t launchFifoGroup(vcomm* c, std::vector<CallSpec>& ops) {
   }
   c->last = ops.back().plan;
   return vSuccess;
+}
+
+// the serving layer's launch: a ring collective whose direct-protocol grid
+// is capped at maxCtas, so that concurrent requests on other streams keep
+// SMs (other protocols ignore the cap); returns the plan it ran
+vResult_t vc::serveCollective(int coll, const void* const* sendbufs, void* const* recvbufs, size_t count,
+                              int dtype, int op, int proto, void* stream, vcomm_t c, int maxCtas,
+                              vPlan_t* plan) {
+  CallSpec cs;
+  vResult_t r = prepareCall(coll, sendbufs, recvbufs, count, dtype, op, 0, vAlgoRing, proto, stream, c, &cs);
+  if (r != vSuccess) return r;
+  if (plan) *plan = cs.plan;
+  if (cs.units == 0) return vSuccess;
+  cs.maxCtas = maxCtas;
+  return launchSingle(cs);
 }
 
 static vResult_t collective(int coll, const void* const* sendbufs, void* const* recvbufs,

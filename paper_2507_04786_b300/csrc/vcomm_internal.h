@@ -126,7 +126,8 @@ constexpr int kServeMaxRanks = 16;
 constexpr int kMaxServeGangs = 16;
 
 struct ServeReq {
-  int coll, proto, dtype, redop, nranks, nsub, root, pad;
+  int coll, proto, dtype, redop, nranks, nsub, root;
+  int vec;                           // direct protocol: every access a 16-byte vector
   unsigned long long count, chunk, slotUnits, slotBytes, inplaceMask;
   const void* send[kServeMaxRanks];
   void* recv[kServeMaxRanks];

@@ -7,6 +7,11 @@ namespace vc {
 const void* reduceKernel(int proto, int dtype, int op);
 // persistent byte-moving kernel for AllGather, Broadcast and the single-rank copy
 const void* copyKernel(int proto);
+// the serving layer's capped launch (vcomm_host.cu)
+vResult_t serveCollective(int coll, const void* const* sendbufs, void* const* recvbufs, size_t count,
+                          int dtype, int op, int proto, void* stream, vcomm_t c, int maxCtas,
+                          vPlan_t* plan);
+
 // direct protocol (vcomm_direct.cu): AllReduce / ReduceScatter / Reduce per
 // (dtype, op); one byte-copy kernel for AllGather and Broadcast
 const void* directKernel(int coll, int dtype, int op);

@@ -100,8 +100,9 @@ struct Request {
   int gang = -1;
   bool big = false;
   vPlan_t plan{};
-  cudaEvent_t ev = nullptr;           // plain mode: end of the request's launch
-  cudaEvent_t ev0 = nullptr;          // plain mode: start of the request's launch
+  cudaEvent_t ev = nullptr;           // modes 1, 2: end of the request's launch
+  cudaEvent_t ev0 = nullptr;          // modes 1, 2: start of the request's launch
+  int lane = -1;                      // mode 2: the stream it runs on
 };
 
 }  // namespace
@@ -132,9 +133,14 @@ struct vserve {
   std::vector<uint64_t> posted;       // per gang: requests posted
   std::vector<uint64_t> running;      // per gang: ticket running (0: free)
   bool kernelUp = false;
-  // plain mode
+  // plain mode (and the communicators of mode 2)
   vcomm_t comms[kServeMaxRanks + 1] = {};
   std::deque<uint64_t> plainInflight;
+  // stream mode: lane 0 for large requests, lanes 1.. for the others; each
+  // lane's launches are capped at laneCtas[l] CTAs so that the lanes overlap
+  std::vector<cudaStream_t> lanes;
+  std::vector<int> laneCtas;
+  std::vector<std::deque<uint64_t>> laneInflight;
   // requests
   std::mutex mu;
   std::deque<uint64_t> incoming;      // submitted, not yet seen by the dispatcher
@@ -154,7 +160,8 @@ namespace {
 void planFor(const vserve* s, Request& q) {
   const size_t S = std::max(q.sb, q.rb);
   vProto_t p = q.proto;
-  if (p == vProtoAuto) p = S < (64u << 10) ? vProtoLL : S < (2u << 20) ? vProtoLL128 : vProtoSimple;
+  // Auto: the direct protocol (no FIFO), the fastest at every size on one GPU
+  if (p == vProtoAuto) p = vProtoDirect;
   q.big = S >= s->cfg.bigThreshold;
   // a request spreads over its whole gang: channels = gang CTAs / vranks
   // (mode 1: over up to 2 CTAs per SM), at most ~1 MiB of message per channel
@@ -203,6 +210,28 @@ void postToGang(vserve* s, Request& q, int g) {
   sr.coll = (q.nranks == 1) ? kCopy : q.coll;
   sr.proto = (q.nranks == 1) ? kSimple : pr;
   sr.dtype = bytes ? -1 : q.dtype;
+  if (sr.proto == kDirect) {
+    // no FIFO: the gang's CTAs fold the units from the user buffers; the
+    // segments (fold order) come from the Simple slot's chunk, as in a plain call
+    sr.dtype = q.dtype;
+    sr.redop = q.redop;
+    sr.nranks = q.nranks;
+    sr.nsub = q.plan.nchannels;
+    sr.count = bytes ? q.count * esz : q.count;
+    unsigned long long epp = 16 / unitBytes;
+    unsigned long long ch = s->cfg.slotBytes[kSimple] * (unsigned long long)q.plan.chunkSteps / unitBytes;
+    ch = ch / epp * epp;
+    sr.chunk = ch < epp ? epp : ch;
+    bool aligned = true;
+    for (int r = 0; r < q.nranks; r++) {
+      sr.send[r] = q.send[r];
+      sr.recv[r] = q.recv[r];
+      if (((uintptr_t)q.send[r] | (uintptr_t)q.recv[r]) & 15) aligned = false;
+    }
+    if (q.coll == kReduceScatter && (q.count * esz) % 16) aligned = false;
+    if (q.coll == kAllGather && (q.count * esz) % 16) aligned = false;
+    sr.vec = aligned ? 1 : 0;
+  } else {
   sr.redop = q.redop;
   sr.nranks = q.nranks;
   sr.nsub = q.plan.nchannels;
@@ -219,6 +248,7 @@ void postToGang(vserve* s, Request& q, int g) {
   for (int r = 0; r < q.nranks; r++) {
     sr.send[r] = q.send[r];
     sr.recv[r] = q.recv[r];
+  }
   }
   volatile ServeSlot* slot = &s->hSlots[g];
   memcpy((void*)&slot->req, &sr, sizeof(sr));
@@ -255,6 +285,34 @@ vResult_t launchPlain(vserve* s, Request& q) {
   return vSuccess;
 }
 
+// mode 2: the request as one launch on its lane's stream, grid capped so
+// that the lanes run side by side (continuous batching without a resident
+// kernel: each admitted request starts at once on free SMs)
+vResult_t launchLane(vserve* s, Request& q, int lane) {
+  vcomm_t c = s->comms[q.nranks];
+  cudaStream_t st = s->lanes[lane];
+  if (!q.ev0) cudaEventCreate(&q.ev0);
+  cudaEventRecord(q.ev0, st);
+  vcommSetPlan(c, &q.plan);
+  // a small lane's grid grows with the request (about 256 KiB of traffic per
+  // CTA, 4..laneCtas CTAs): tiny requests stay on a few SMs, mid-size ones
+  // are not starved
+  int cap = s->laneCtas[lane];
+  if (lane > 0) {
+    const size_t bytes = (q.sb + q.rb) * (size_t)q.nranks;
+    cap = (int)std::min<size_t>((size_t)cap, std::max<size_t>(4, bytes / (256u << 10)));
+  }
+  vResult_t r = serveCollective(q.coll, q.send, q.recv, q.count, q.dtype, q.redop, q.plan.proto, st, c,
+                                cap, &q.plan);
+  if (r != vSuccess) return r;
+  if (!q.ev) cudaEventCreate(&q.ev);
+  cudaEventRecord(q.ev, st);
+  q.state = 1;
+  q.lane = lane;
+  s->laneInflight[lane].push_back(q.ticket);
+  return vSuccess;
+}
+
 // try to start the request at the head of `q` on gang g (-1: plain launch);
 // false if the budget or the pool cannot take it yet
 bool tryStart(vserve* s, std::deque<uint64_t>& q, int g) {
@@ -264,7 +322,13 @@ bool tryStart(vserve* s, std::deque<uint64_t>& q, int g) {
   if (!allocOutputs(s, r)) return false;
   s->inflight += bytes;
   s->maxInflight = std::max(s->maxInflight, s->inflight);
-  if (g >= 0) {
+  if (s->cfg.mode == 2) {
+    vResult_t e = launchLane(s, r, g);
+    if (e != vSuccess) {
+      s->threadErr = e;
+      completeReq(s, r, false);
+    }
+  } else if (g >= 0) {
     postToGang(s, r, g);
   } else {
     vResult_t e = launchPlain(s, r);
@@ -301,6 +365,24 @@ void dispatcher(vserve* s) {
           progress = true;
         }
       }
+    } else if (s->cfg.mode == 2) {
+      for (size_t l = 0; l < s->lanes.size(); l++) {
+        while (!s->laneInflight[l].empty()) {
+          Request& q = s->reqs[s->laneInflight[l].front()];
+          cudaError_t e = cudaEventQuery(q.ev);
+          if (e == cudaErrorNotReady) break;
+          (void)cudaGetLastError();
+          vResult_t ae = vSuccess;
+          vcommGetAsyncError(s->comms[q.nranks], &ae);
+          float ms = 0;
+          if (e == cudaSuccess && cudaEventElapsedTime(&ms, q.ev0, q.ev) == cudaSuccess)
+            q.serviceNs = (int64_t)(ms * 1e6);
+          (void)cudaGetLastError();
+          completeReq(s, q, e == cudaSuccess && ae == vSuccess);
+          s->laneInflight[l].pop_front();
+          progress = true;
+        }
+      }
     } else {
       while (!s->plainInflight.empty()) {
         Request& q = s->reqs[s->plainInflight.front()];
@@ -328,6 +410,20 @@ void dispatcher(vserve* s) {
           if (!s->running[i]) g = i;
         if (g < 0 && !s->running[0] && s->bigQ.empty()) g = 0;
         if (g < 0 || !tryStart(s, s->smallQ, g)) break;
+        progress = true;
+      }
+    } else if (s->cfg.mode == 2) {
+      // large requests on lane 0, the others on the least busy small lane;
+      // at most two launches in flight per lane
+      const size_t depth = 2;
+      while (!s->bigQ.empty() && s->laneInflight[0].size() < depth && tryStart(s, s->bigQ, 0)) progress = true;
+      while (!s->smallQ.empty()) {
+        int best = -1;
+        for (int l = 1; l < (int)s->lanes.size(); l++)
+          if (s->laneInflight[l].size() < depth &&
+              (best < 0 || s->laneInflight[l].size() < s->laneInflight[best].size()))
+            best = l;
+        if (best < 0 || !tryStart(s, s->smallQ, best)) break;
         progress = true;
       }
     } else {
@@ -366,7 +462,7 @@ vResult_t vServeCreate(vserve_t* out, const vserveConfig_t* cfgIn) {
   for (int p = 0; p < 3; p++)
     if (cfg.slotBytes[p] == 0) cfg.slotBytes[p] = defSlot[p];
   if (cfg.idleTimeoutSec <= 0) cfg.idleTimeoutSec = 30.0;
-  if (cfg.mode < 0 || cfg.mode > 1 || cfg.maxRanks > kServeMaxRanks ||
+  if (cfg.mode < 0 || cfg.mode > 2 || cfg.maxRanks > kServeMaxRanks ||
       1 + cfg.smallGangs > kMaxServeGangs || cfg.threads % 64 || cfg.threads > 512)
     return vInvalidArgument;
   for (int p = 0; p < 3; p++)
@@ -469,7 +565,18 @@ vResult_t vServeCreate(vserve_t* out, const vserveConfig_t* cfgIn) {
     s->posted.assign(s->ngangs, 0);
     s->running.assign(s->ngangs, 0);
   }
-  if (r == vSuccess && cfg.mode == 1) {
+  if (r == vSuccess && cfg.mode == 2) {
+    // one stream per lane; small lanes get a few SMs each, the large lane the rest
+    const int nSmall = std::max(1, cfg.smallGangs);
+    const int reserve = 16;   // SMs the large lane leaves to the small lanes
+    s->lanes.assign(1 + nSmall, nullptr);
+    s->laneCtas.assign(1 + nSmall, 32);
+    s->laneCtas[0] = std::max(4, s->nsm - reserve);
+    s->laneInflight.assign(1 + nSmall, std::deque<uint64_t>());
+    for (auto& st : s->lanes)
+      if (r == vSuccess) r = fromCudaS(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  }
+  if (r == vSuccess && cfg.mode >= 1) {
     // one communicator per vrank count, arenas allocated now (not mid-stream)
     vcommConfig_t cc{};
     for (int p = 0; p < 3; p++) cc.slotBytes[p] = cfg.slotBytes[p];
@@ -501,8 +608,8 @@ vResult_t vServeSubmit(vserve_t s, int coll, const void* const* sendbufs, size_t
   q.redop = op;
   q.nranks = nranks;
   q.flags = flags;
-  // gangs have no cluster or direct protocol
-  q.proto = (proto == vProtoCluster) ? vProtoLL : (proto == vProtoDirect) ? vProtoSimple : proto;
+  // gangs have no cluster protocol
+  q.proto = (proto == vProtoCluster) ? vProtoLL : proto;
   q.count = count;
   const size_t esz = (dtype == vFloat16 || dtype == vBfloat16) ? 2 : 4;
   q.sb = count * esz;
@@ -576,6 +683,8 @@ vResult_t vServeDestroy(vserve_t s) {
   if (s->th.joinable()) s->th.join();
   if (s->hShutdown) *(volatile int*)s->hShutdown = 1;
   if (s->stream) cudaStreamSynchronize(s->stream);
+  for (auto st : s->lanes)
+    if (st) cudaStreamSynchronize(st);
   for (auto& kv : s->reqs) {
     if (kv.second.ev) cudaEventDestroy(kv.second.ev);
     if (kv.second.ev0) cudaEventDestroy(kv.second.ev0);
@@ -595,6 +704,8 @@ vResult_t vServeDestroy(vserve_t s) {
   if (s->hAbort) cudaFreeHost(s->hAbort);
   if (s->pool) cudaFree(s->pool);
   if (s->stream) cudaStreamDestroy(s->stream);
+  for (auto st : s->lanes)
+    if (st) cudaStreamDestroy(st);
   (void)cudaGetLastError();
   delete s;
   return vSuccess;

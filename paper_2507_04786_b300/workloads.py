@@ -55,6 +55,7 @@ SERVED = {
     "budget_bytes": 40 * (1 << 30),
     "requests": 100_000,
     "bench_requests": 20_000,     # default bench run: 10 s of arrivals per mode
+    "small_lanes": 4,             # continuous batching on streams: lanes for small requests
     "seed": 4,
 }
 

@@ -102,29 +102,31 @@ CFG = dict(max_ranks=8, mem_budget=256 << 20, big_gang_channels=4, small_gangs=4
            big_threshold=256 << 10, slot_bytes=SMALL_SLOTS, idle_timeout_sec=20.0)
 
 
-def test_serving_results_exact_and_same_alone():
+@pytest.mark.parametrize("mode", ["batch", "streams"])
+def test_serving_results_exact_and_same_alone(mode):
     reqs = make_requests(5, 48, 8, 1024, 2 << 20)
-    outs, plans, stats = run_server(reqs, mode="batch", **CFG)
+    outs, plans, stats = run_server(reqs, mode=mode, **CFG)
     assert stats["completed"] == len(reqs) and stats["failed"] == 0
     assert stats["maxInflightBytes"] <= CFG["mem_budget"]
-    assert any(p["nchannels"] > 1 for p in plans)   # large requests spread over the wide gang
+    assert any(p["nchannels"] > 1 for p in plans)   # large requests spread over several channels
     for r, o, p in zip(reqs, outs, plans):
         want = oracle_for(r, p)
         for q in range(r["k"]):
             assert_same(o[q], want[q], f"{r['coll']} k={r['k']} n={r['n']} rank {q}")
     # the same requests alone, each on a fresh server, give the same bits
     for i in (0, 7, 19, 33):
-        o1, p1, _ = run_server([reqs[i]], mode="batch", **CFG)
+        o1, p1, _ = run_server([reqs[i]], mode=mode, **CFG)
         assert p1[0] == plans[i]
         for q in range(reqs[i]["k"]):
             assert_same(o1[0][q], outs[i][q], f"request {i} alone vs in the mix, rank {q}")
 
 
-def test_serving_respects_memory_budget():
+@pytest.mark.parametrize("mode", ["batch", "streams"])
+def test_serving_respects_memory_budget(mode):
     reqs = make_requests(9, 24, 8, 256 << 10, 1 << 20)
     budget = 24 << 20
     cfg = dict(CFG, mem_budget=budget)
-    outs, plans, stats = run_server(reqs, mode="batch", **cfg)
+    outs, plans, stats = run_server(reqs, mode=mode, **cfg)
     assert stats["completed"] == len(reqs)
     assert 0 < stats["maxInflightBytes"] <= budget
 
@@ -137,3 +139,15 @@ def test_plain_mode_exact():
         want = oracle_for(r, p)
         for q in range(r["k"]):
             assert_same(o[q], want[q], f"plain {r['coll']} k={r['k']} rank {q}")
+
+
+def test_streams_and_plain_give_the_same_bits():
+    """Plans depend on the request alone: the lanes of the streams mode and
+    one launch per request produce identical results."""
+    reqs = make_requests(13, 20, 8, 1024, 4 << 20)
+    o1, p1, _ = run_server(reqs, mode="streams", **CFG)
+    o2, p2, _ = run_server(reqs, mode="plain", **CFG)
+    assert p1 == p2
+    for i in range(len(reqs)):
+        for q in range(reqs[i]["k"]):
+            assert_same(o1[i][q], o2[i][q], f"request {i} rank {q}")
