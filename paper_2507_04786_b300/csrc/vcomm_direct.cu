@@ -53,7 +53,8 @@ __global__ void __launch_bounds__(256) kDirectBatchCopy(const __grid_constant__ 
 
 }  // namespace direct
 
-#define VC_DDECL(D) const void* directReduceKernel_##D(int op); const void* directBatchKernel_##D(int op);
+#define VC_DDECL(D) const void* directReduceKernel_##D(int op); const void* directBatchKernel_##D(int op); \
+  const void* directStagedKernel_##D(int op);
 VC_DDECL(0) VC_DDECL(1) VC_DDECL(2) VC_DDECL(3) VC_DDECL(4)
 VC_DDECL(5) VC_DDECL(6) VC_DDECL(7) VC_DDECL(8) VC_DDECL(9)
 #undef VC_DDECL
@@ -92,6 +93,22 @@ const void* directBatchKernel(int coll, int dtype, int op) {
 #undef VC_DCASE
   }
   return nullptr;
+}
+
+const void* directStagedKernel(int dtype, int op) {
+  switch (dtype) {
+#define VC_DCASE(D) case D: return directStagedKernel_##D(op);
+    VC_DCASE(0) VC_DCASE(1) VC_DCASE(2) VC_DCASE(3) VC_DCASE(4)
+    VC_DCASE(5) VC_DCASE(6) VC_DCASE(7) VC_DCASE(8) VC_DCASE(9)
+#undef VC_DCASE
+  }
+  return nullptr;
+}
+
+int directStagedThreads() { return 256; }
+
+size_t directStagedSmem(int nranks, unsigned tileBytes) {
+  return (size_t)direct::kStages * nranks * tileBytes + 2 * (size_t)tileBytes + 8 * direct::kStages;
 }
 
 }  // namespace vc

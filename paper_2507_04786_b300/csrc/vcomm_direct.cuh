@@ -290,5 +290,190 @@ VDEV void opShare(const DirectBatchArgs* b, int i, unsigned long long glo, unsig
   *tail = ghi >= e;
 }
 
+
+// ---- the AllReduce staged through shared memory.
+//
+// Same arithmetic as directReduce (each 16-byte unit's ring chain folded in
+// the order of its segment), but the data moves by bulk asynchronous copies:
+// one thread loads tile i of every rank's input into shared memory (k copies
+// that complete one mbarrier), kStages tiles ahead of the fold, and stores
+// the folded tile to every rank's output with k bulk stores, so the loads in
+// flight never drain while the CTA folds.  Each CTA takes tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ...  Shared memory: in[kStages][k][tile],
+// out[2][tile] (the folded tile, double buffered so the stores of one tile
+// overlap the fold of the next), then kStages mbarriers.
+constexpr int kStages = 3;
+
+VDEV unsigned smemU32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+VDEV void mbarInit(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smemU32(bar)), "r"(count) : "memory");
+}
+// the initialised barriers become visible to the bulk-copy (async) proxy
+VDEV void fenceBarrierInit() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// arrive once, expecting `bytes` of bulk copies to complete this phase
+VDEV void mbarExpect(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smemU32(bar)), "r"(bytes)
+               : "memory");
+}
+VDEV bool mbarTryWait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smemU32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// global -> shared, `bytes` (a multiple of 16, both addresses 16-byte aligned)
+VDEV void bulkLoad(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smemU32(dst)),
+      "l"(src), "r"(bytes), "r"(smemU32(bar))
+      : "memory");
+}
+// shared -> global, same rules
+VDEV void bulkStore(void* dst, const void* src, unsigned bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smemU32(src)),
+               "r"(bytes)
+               : "memory");
+}
+VDEV void bulkCommit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// every group but the newest has finished reading its shared memory
+VDEV void bulkWaitRead1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+// every group has completed
+VDEV void bulkWaitAll() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// this thread's generic-proxy writes to shared memory become visible to bulk copies
+VDEV void fenceProxyAsync() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+VDEV void stagedFailure(const DirectArgs& a, int where) {
+  if (atomicCAS(a.errClaim, 0, (int)vTimeout) == 0) {
+    volatile ErrWord* e = a.err;
+    e->rank = -1;
+    e->channel = (int)blockIdx.x;
+    e->where = where;
+    __threadfence_system();
+    e->code = (int)vTimeout;
+    __threadfence_system();
+  }
+}
+
+// wait for phase `parity` of *bar, at most timeoutNs
+VDEV bool stageWait(uint64_t* bar, unsigned parity, unsigned long long timeoutNs) {
+  if (mbarTryWait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  while (true) {
+    if (mbarTryWait(bar, parity)) return true;
+    if (globaltimer() - t0 > timeoutNs) return false;
+  }
+}
+
+template <class T, class Op>
+VDEV void directAllReduceStaged(const DirectArgs& a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const DirectView v = viewOf(a);
+  const int k = a.nranks;
+  constexpr int E = Unit16<T>::kElems;
+  constexpr unsigned long long esz = sizeof(T);
+  const unsigned long long fullBytes = (a.count / E) * 16ull;   // the 16-byte units of a buffer
+  const unsigned tile = (unsigned)a.tileBytes;
+  const unsigned long long ntiles = (fullBytes + tile - 1) / tile;
+  unsigned char* in = smem;
+  unsigned char* out = smem + (size_t)kStages * k * tile;
+  uint64_t* bar = (uint64_t*)(out + 2 * (size_t)tile);
+
+  // self-check of what the bulk copies need: 16-byte aligned buffers, tiles
+  // and shared memory, and one phase's bytes within an mbarrier's count
+  bool bad = (smemU32(smem) & 15u) || (tile & 127u) || tile == 0 ||
+             (unsigned long long)k * tile >= (1ull << 20);
+  for (int r = 0; r < k; r++)
+    if (((uintptr_t)v.send[r] | (uintptr_t)v.recv[r]) & 15u) bad = true;
+  if (bad) {
+    if (threadIdx.x == 0) stagedFailure(a, 5);
+    return;
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; s++) mbarInit(&bar[s], 1);
+    fenceBarrierInit();
+  }
+  __syncthreads();
+
+  const unsigned long long G = gridDim.x;
+  const unsigned long long mine = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / G + 1 : 0;
+  auto tileOff = [&](unsigned long long i) { return (blockIdx.x + i * G) * (unsigned long long)tile; };
+  auto tileLen = [&](unsigned long long off) {
+    return (unsigned)(fullBytes - off < tile ? fullBytes - off : tile);
+  };
+  auto issue = [&](unsigned long long i) {   // thread 0: the k input tiles of my i-th tile
+    const int st = (int)(i % kStages);
+    const unsigned long long off = tileOff(i);
+    const unsigned len = tileLen(off);
+    mbarExpect(&bar[st], len * (unsigned)k);
+    for (int r = 0; r < k; r++)
+      bulkLoad(in + ((size_t)st * k + r) * tile, (const char*)v.send[r] + off, len, &bar[st]);
+  };
+  if (threadIdx.x == 0)
+    for (unsigned long long i = 0; i < mine && i < (unsigned long long)kStages; i++) issue(i);
+
+  unsigned long long runEnd = 0;   // the current segment's end (elements); offsets only grow
+  int seg = 0;
+  unsigned long long i = 0;
+  bool failed = false;
+  for (; i < mine; i++) {
+    const int st = (int)(i % kStages);
+    const bool ok = stageWait(&bar[st], (unsigned)((i / kStages) & 1ull), a.timeoutNs);
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    const int ob = (int)(i & 1ull);
+    if (threadIdx.x == 0) bulkWaitRead1();   // the stores of tile i - 2 no longer read out[ob]
+    __syncthreads();
+    const unsigned long long off = tileOff(i);
+    const unsigned len = tileLen(off);
+    const unsigned char* src = in + (size_t)st * k * tile;
+    unsigned char* o = out + (size_t)ob * tile;
+    for (unsigned u = threadIdx.x * 16u; u < len; u += blockDim.x * 16u) {
+      const unsigned long long e0 = (off + u) / esz;
+      if (e0 >= runEnd) seg = arSegment(v, e0, (int)esz, &runEnd);
+      int r = seg + 1 < k ? seg + 1 : 0;
+      uint4 acc = *(const uint4*)(src + (size_t)r * tile + u);
+      for (int j = 1; j < k; j++) {
+        if (++r == k) r = 0;
+        acc = combine<T, Op, uint4>(acc, *(const uint4*)(src + (size_t)r * tile + u));
+      }
+      if (a.postDiv) acc = divide<T, Unit16<T>>(acc, a.postDiv);
+      *(uint4*)(o + u) = acc;
+    }
+    fenceProxyAsync();
+    __syncthreads();   // out[ob] written; in[st] read by every thread
+    if (threadIdx.x == 0) {
+      for (int r = 0; r < k; r++) bulkStore((char*)v.recv[r] + off, o, len);
+      bulkCommit();
+      if (i + kStages < mine) issue(i + kStages);
+    }
+  }
+  if (threadIdx.x == 0) {
+    bulkWaitAll();
+    if (failed) {
+      stagedFailure(a, 4);
+      // loads still in flight (tiles i .. i + kStages - 1) must land before
+      // the CTA's shared memory is released
+      for (unsigned long long j = i; j < mine && j < i + kStages; j++)
+        (void)stageWait(&bar[j % kStages], (unsigned)((j / kStages) & 1ull), a.timeoutNs);
+    }
+  }
+  if (failed) return;
+  // the element tail after the last full unit
+  if (blockIdx.x == gridDim.x - 1) {
+    const unsigned long long nunit = a.count / E;
+    directReduce<T, Op, Unit16<T>, 1>(v, nunit, nunit, true);
+  }
+}
+
 }  // namespace direct
 }  // namespace vc

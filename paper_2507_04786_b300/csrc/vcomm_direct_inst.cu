@@ -47,6 +47,13 @@ __global__ void __launch_bounds__(DirectShape<T>::kThreads, 1)
   }
 }
 
+// AllReduce of 16-byte aligned buffers staged through shared memory by bulk
+// copies (one CTA per SM; dynamic shared memory from directStagedSmem)
+template <class T, class Op>
+__global__ void __launch_bounds__(256, 1) kDirectAllReduceStaged(const __grid_constant__ DirectArgs a) {
+  directAllReduceStaged<T, Op>(a);
+}
+
 }  // namespace direct
 
 using VcT = typename DTypeOf<VC_DTYPE>::T;
@@ -72,4 +79,16 @@ const void* VC_DNAME(directBatchKernel, VC_DTYPE)(int op) {
   return nullptr;
 }
 
+}  // namespace vc
+
+namespace vc {
+const void* VC_DNAME(directStagedKernel, VC_DTYPE)(int op) {
+  switch (op) {
+    case kSum: case kAvg: return (const void*)direct::kDirectAllReduceStaged<VcT, OpSum>;
+    case kMax: return (const void*)direct::kDirectAllReduceStaged<VcT, OpMax>;
+    case kProd: return (const void*)direct::kDirectAllReduceStaged<VcT, OpProd>;
+    case kMin: return (const void*)direct::kDirectAllReduceStaged<VcT, OpMin>;
+  }
+  return nullptr;
+}
 }  // namespace vc

@@ -108,6 +108,8 @@ struct vcomm {
   int nsteps = 8, nthreads = 1024;
   double timeoutSec = 5.0;
   int treeNode = 1;                  // vranks per node of the hierarchical tree
+  // direct AllReduce: bytes per rank from which the staged kernel runs
+  unsigned long long stagedMinBytes = 1ull << 20;
   Arena arena[2][3];
   ErrWord* hErr = nullptr;
   ErrWord* dErr = nullptr;
@@ -201,6 +203,11 @@ vResult_t vcommInitConfig(vcomm_t* comm, int nranks, int nchannels, const vcommC
   if (!(cfg && cfg->timeoutSec > 0)) {
     const char* env = getenv("VCOMM_TIMEOUT_MS");
     if (env && atof(env) > 0) c->timeoutSec = atof(env) / 1000.0;
+  }
+  if (const char* env = getenv("VCOMM_STAGED_MIN_BYTES")) {
+    char* end = nullptr;
+    const unsigned long long v = strtoull(env, &end, 10);
+    if (end && end != env && *end == 0) c->stagedMinBytes = v;
   }
   vResult_t r = fromCuda(cudaGetDevice(&c->dev));
   if (r == vSuccess) r = fromCuda(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->dev));
@@ -613,6 +620,52 @@ static DirectGeom directGeom(const CallSpec& cs) {
   return DirectGeom{aligned, units, chunkUnits(kSimple, cs.c->slotBytes[kSimple], cs.plan.chunkSteps, esz)};
 }
 
+// The staged direct AllReduce (bulk copies through shared memory) takes
+// 16-byte aligned AllReduce calls of at least stagedMinBytes per rank (1 MiB,
+// env VCOMM_STAGED_MIN_BYTES) on the whole GPU; smaller calls keep the
+// register kernel, whose first loads leave without a pipeline to fill.  Its
+// tile is the largest multiple of 128 bytes (at most 16 KiB) whose kStages x k
+// input tiles and two output tiles fit kStagedSmemMax bytes of shared memory.
+constexpr int kStagedSmemMax = 205 * 1024;
+static bool useStaged(const CallSpec& cs, const DirectGeom& g) {
+  return cs.kcoll == kAllReduce && g.vec && cs.c->k >= 2 && cs.maxCtas == 0 &&
+         g.units * 16ull >= cs.c->stagedMinBytes;
+}
+static unsigned stagedTile(int k) {
+  unsigned t = (unsigned)((kStagedSmemMax - 64) / (3 * k + 2)) / 128u * 128u;
+  return std::min(16384u, std::max(128u, t));
+}
+
+static vResult_t launchStaged(CallSpec& cs, const DirectGeom& g, DirectArgs& a) {
+  vcomm* c = cs.c;
+  const int k = c->k;
+  const void* fn = directStagedKernel(cs.dtype, cs.redop);
+  if (!fn) return vInternalError;
+  {
+    // once per kernel: opt in to the dynamic shared memory
+    static std::mutex mu;
+    static std::vector<const void*> ready;
+    std::lock_guard<std::mutex> lk(mu);
+    if (std::find(ready.begin(), ready.end(), fn) == ready.end()) {
+      VC_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmemMax));
+      ready.push_back(fn);
+    }
+  }
+  const unsigned tile = stagedTile(k);
+  const size_t smem = directStagedSmem(k, tile);
+  if (smem > (size_t)kStagedSmemMax) return vInternalError;
+  a.tileBytes = tile;
+  a.timeoutNs = (unsigned long long)(c->timeoutSec * 1e9);
+  a.errClaim = c->dClaim;
+  a.err = c->dErr;
+  const unsigned long long ntiles = (g.units * 16ull + tile - 1) / tile;
+  const long long grid = std::max<long long>(1, std::min<long long>((long long)ntiles, c->nsm));
+  void* args[] = {(void*)&a};
+  VC_TRY(cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(directStagedThreads()), args, smem, cs.stream));
+  c->last = cs.plan;
+  return vSuccess;
+}
+
 // The direct protocol: a plain launch over the data, no FIFO, no waits.
 static vResult_t launchDirect(CallSpec& cs) {
   vcomm* c = cs.c;
@@ -635,6 +688,7 @@ static vResult_t launchDirect(CallSpec& cs) {
   a.root = cs.root;
   a.vec = g.vec ? 1 : 0;
   a.postDiv = cs.postDiv;
+  if (useStaged(cs, g)) return launchStaged(cs, g, a);
   const unsigned long long units = g.units;
   const int nthr = directThreads(cs.kcoll, cs.dtype);
   const long long resident = (long long)std::max(1, residentPerSM(fn, nthr)) * c->nsm;

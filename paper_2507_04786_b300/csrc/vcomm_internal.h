@@ -59,7 +59,8 @@ struct ErrWord {
   int code;      // vResult_t
   int rank;
   int channel;
-  int where;     // 1 = wait on tail, 2 = wait on head (credit), 3 = LL/LL128 line poll
+  int where;     // 1 = wait on tail, 2 = wait on head (credit), 3 = LL/LL128 line poll,
+                 // 4 = a bulk copy into shared memory, 5 = a misaligned staged buffer
 };
 
 struct KernArgs {
@@ -179,6 +180,11 @@ struct DirectArgs {
   int coll, nranks, nsub, root;
   int vec;                         // 1: every access is a 16-byte vector
   int postDiv;                     // avg: divide the folded value by this (0: none)
+  // the AllReduce staged through shared memory (kDirectAllReduceStaged) only:
+  unsigned long long tileBytes;    // bytes of one rank's tile (multiple of 128)
+  unsigned long long timeoutNs;    // deadline of every wait for a bulk copy
+  int* errClaim;                   // device word: first failure claims it
+  ErrWord* err;                    // host-mapped report
 };
 
 // ---- direct collectives of one class in one launch: op i owns units

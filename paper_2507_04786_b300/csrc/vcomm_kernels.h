@@ -19,6 +19,13 @@ int directThreads(int coll, int dtype);   // the block size the kernel is compil
 // a group's direct calls of one (dtype, op) class (or its copies), DirectBatchArgs;
 // launched with directThreads(coll, dtype) threads
 const void* directBatchKernel(int coll, int dtype, int op);
+// AllReduce of 16-byte aligned buffers staged through shared memory by bulk
+// copies (DirectArgs with tileBytes, timeoutNs, errClaim, err); one CTA per SM
+// of directStagedThreads() threads and directStagedSmem(nranks, tileBytes)
+// bytes of dynamic shared memory
+const void* directStagedKernel(int dtype, int op);
+int directStagedThreads();
+size_t directStagedSmem(int nranks, unsigned tileBytes);
 // cluster protocol (vcomm_cluster_inst.cu): one cluster of nranks CTAs per channel
 const void* clusterKernel(int dtype, int op);
 const void* clusterCopyKernel();
