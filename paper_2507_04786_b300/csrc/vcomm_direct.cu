@@ -111,4 +111,10 @@ size_t directStagedSmem(int nranks, unsigned tileBytes) {
   return (size_t)direct::kStages * nranks * tileBytes + 2 * (size_t)tileBytes + 8 * direct::kStages;
 }
 
+unsigned directStagedTile(int nranks, size_t smemMax) {
+  const size_t per = (size_t)direct::kStages * nranks + 2;   // tiles held in shared memory
+  const size_t t = (smemMax - 8 * direct::kStages) / per / 128 * 128;
+  return (unsigned)(t < 128 ? 128 : t > 16384 ? 16384 : t);
+}
+
 }  // namespace vc

@@ -624,16 +624,11 @@ static DirectGeom directGeom(const CallSpec& cs) {
 // 16-byte aligned AllReduce calls of at least stagedMinBytes per rank (1 MiB,
 // env VCOMM_STAGED_MIN_BYTES) on the whole GPU; smaller calls keep the
 // register kernel, whose first loads leave without a pipeline to fill.  Its
-// tile is the largest multiple of 128 bytes (at most 16 KiB) whose kStages x k
-// input tiles and two output tiles fit kStagedSmemMax bytes of shared memory.
+// tile comes from directStagedTile for kStagedSmemMax bytes of shared memory.
 constexpr int kStagedSmemMax = 205 * 1024;
 static bool useStaged(const CallSpec& cs, const DirectGeom& g) {
   return cs.kcoll == kAllReduce && g.vec && cs.c->k >= 2 && cs.maxCtas == 0 &&
          g.units * 16ull >= cs.c->stagedMinBytes;
-}
-static unsigned stagedTile(int k) {
-  unsigned t = (unsigned)((kStagedSmemMax - 64) / (3 * k + 2)) / 128u * 128u;
-  return std::min(16384u, std::max(128u, t));
 }
 
 static vResult_t launchStaged(CallSpec& cs, const DirectGeom& g, DirectArgs& a) {
@@ -651,7 +646,7 @@ static vResult_t launchStaged(CallSpec& cs, const DirectGeom& g, DirectArgs& a) 
       ready.push_back(fn);
     }
   }
-  const unsigned tile = stagedTile(k);
+  const unsigned tile = directStagedTile(k, kStagedSmemMax);
   const size_t smem = directStagedSmem(k, tile);
   if (smem > (size_t)kStagedSmemMax) return vInternalError;
   a.tileBytes = tile;

@@ -26,6 +26,9 @@ const void* directBatchKernel(int coll, int dtype, int op);
 const void* directStagedKernel(int dtype, int op);
 int directStagedThreads();
 size_t directStagedSmem(int nranks, unsigned tileBytes);
+// the largest tile (a multiple of 128 bytes, at most 16 KiB) whose staged
+// shared memory fits smemMax bytes
+unsigned directStagedTile(int nranks, size_t smemMax);
 // cluster protocol (vcomm_cluster_inst.cu): one cluster of nranks CTAs per channel
 const void* clusterKernel(int dtype, int op);
 const void* clusterCopyKernel();
