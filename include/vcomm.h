@@ -86,11 +86,11 @@ typedef enum { vAlgoAuto = 0, vAlgoRing = 1, vAlgoTree = 2 } vAlgo_t;
  * only; for a given plan (channels, chunkSteps) the results are the Simple
  * protocol's, bit for bit.  Auto picks it on the ring for nranks >= 2; a
  * group runs all its direct calls in one launch; the serving API runs it as
- * Simple.  An AllReduce of 16-byte aligned buffers of at least 1 MiB per rank
- * (env VCOMM_STAGED_MIN_BYTES, read at vcommInit) moves its data by bulk
- * asynchronous copies through shared memory (same fold, same bits); a
- * bulk copy that does not complete within timeoutSec fails the call with
- * vTimeout like a flag wait. */
+ * Simple.  An AllReduce of 16-byte aligned buffers on 2..16 vranks (fp64: up
+ * to 8) of at least 8 MiB per rank (env VCOMM_STAGED_MIN_BYTES, read at
+ * vcommInit) moves its data by bulk asynchronous copies through shared memory
+ * (same fold, same bits); a bulk copy that does not complete within
+ * timeoutSec fails the call with vTimeout like a flag wait. */
 typedef enum {
   vProtoAuto = 0,
   vProtoSimple = 1,

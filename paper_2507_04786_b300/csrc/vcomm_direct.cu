@@ -107,13 +107,15 @@ const void* directStagedKernel(int dtype, int op) {
 
 int directStagedThreads() { return 256; }
 
-size_t directStagedSmem(int nranks, unsigned tileBytes) {
-  return (size_t)direct::kStages * nranks * tileBytes + 2 * (size_t)tileBytes + 8 * direct::kStages;
+int directStagedMaxStages() { return direct::kMaxStages; }
+
+size_t directStagedSmem(int nranks, int stages, unsigned tileBytes) {
+  return (size_t)stages * nranks * tileBytes + 2 * (size_t)tileBytes + 8 * (size_t)stages;
 }
 
-unsigned directStagedTile(int nranks, size_t smemMax) {
-  const size_t per = (size_t)direct::kStages * nranks + 2;   // tiles held in shared memory
-  const size_t t = (smemMax - 8 * direct::kStages) / per / 128 * 128;
+unsigned directStagedTile(int nranks, int stages, size_t smemMax) {
+  const size_t per = (size_t)stages * nranks + 2;   // tiles held in shared memory
+  const size_t t = (smemMax - 8 * (size_t)stages) / per / 128 * 128;
   return (unsigned)(t < 128 ? 128 : t > 16384 ? 16384 : t);
 }
 

@@ -296,13 +296,13 @@ VDEV void opShare(const DirectBatchArgs* b, int i, unsigned long long glo, unsig
 // Same arithmetic as directReduce (each 16-byte unit's ring chain folded in
 // the order of its segment), but the data moves by bulk asynchronous copies:
 // one thread loads tile i of every rank's input into shared memory (k copies
-// that complete one mbarrier), kStages tiles ahead of the fold, and stores
-// the folded tile to every rank's output with k bulk stores, so the loads in
-// flight never drain while the CTA folds.  Each CTA takes tiles blockIdx.x,
-// blockIdx.x + gridDim.x, ...  Shared memory: in[kStages][k][tile],
+// that complete one mbarrier), S = a.stages tiles ahead of the fold, and
+// stores the folded tile to every rank's output with k bulk stores, so the
+// loads in flight never drain while the CTA folds.  Each CTA takes tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...  Shared memory: in[S][k][tile],
 // out[2][tile] (the folded tile, double buffered so the stores of one tile
-// overlap the fold of the next), then kStages mbarriers.
-constexpr int kStages = 3;
+// overlap the fold of the next), then S mbarriers.
+constexpr int kMaxStages = 3;
 
 VDEV unsigned smemU32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -381,14 +381,15 @@ VDEV void directAllReduceStaged(const DirectArgs& a) {
   constexpr unsigned long long esz = sizeof(T);
   const unsigned long long fullBytes = (a.count / E) * 16ull;   // the 16-byte units of a buffer
   const unsigned tile = (unsigned)a.tileBytes;
+  const int S = a.stages;
   const unsigned long long ntiles = (fullBytes + tile - 1) / tile;
   unsigned char* in = smem;
-  unsigned char* out = smem + (size_t)kStages * k * tile;
+  unsigned char* out = smem + (size_t)S * k * tile;
   uint64_t* bar = (uint64_t*)(out + 2 * (size_t)tile);
 
   // self-check of what the bulk copies need: 16-byte aligned buffers, tiles
   // and shared memory, and one phase's bytes within an mbarrier's count
-  bool bad = (smemU32(smem) & 15u) || (tile & 127u) || tile == 0 ||
+  bool bad = (smemU32(smem) & 15u) || (tile & 127u) || tile == 0 || S < 2 || S > kMaxStages ||
              (unsigned long long)k * tile >= (1ull << 20);
   for (int r = 0; r < k; r++)
     if (((uintptr_t)v.send[r] | (uintptr_t)v.recv[r]) & 15u) bad = true;
@@ -397,7 +398,7 @@ VDEV void directAllReduceStaged(const DirectArgs& a) {
     return;
   }
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; s++) mbarInit(&bar[s], 1);
+    for (int s = 0; s < S; s++) mbarInit(&bar[s], 1);
     fenceBarrierInit();
   }
   __syncthreads();
@@ -409,7 +410,7 @@ VDEV void directAllReduceStaged(const DirectArgs& a) {
     return (unsigned)(fullBytes - off < tile ? fullBytes - off : tile);
   };
   auto issue = [&](unsigned long long i) {   // thread 0: the k input tiles of my i-th tile
-    const int st = (int)(i % kStages);
+    const int st = (int)(i % S);
     const unsigned long long off = tileOff(i);
     const unsigned len = tileLen(off);
     mbarExpect(&bar[st], len * (unsigned)k);
@@ -417,15 +418,15 @@ VDEV void directAllReduceStaged(const DirectArgs& a) {
       bulkLoad(in + ((size_t)st * k + r) * tile, (const char*)v.send[r] + off, len, &bar[st]);
   };
   if (threadIdx.x == 0)
-    for (unsigned long long i = 0; i < mine && i < (unsigned long long)kStages; i++) issue(i);
+    for (unsigned long long i = 0; i < mine && i < (unsigned long long)S; i++) issue(i);
 
   unsigned long long runEnd = 0;   // the current segment's end (elements); offsets only grow
   int seg = 0;
   unsigned long long i = 0;
   bool failed = false;
   for (; i < mine; i++) {
-    const int st = (int)(i % kStages);
-    const bool ok = stageWait(&bar[st], (unsigned)((i / kStages) & 1ull), a.timeoutNs);
+    const int st = (int)(i % S);
+    const bool ok = stageWait(&bar[st], (unsigned)((i / S) & 1ull), a.timeoutNs);
     if (__syncthreads_or(!ok)) {
       failed = true;
       break;
@@ -454,17 +455,17 @@ VDEV void directAllReduceStaged(const DirectArgs& a) {
     if (threadIdx.x == 0) {
       for (int r = 0; r < k; r++) bulkStore((char*)v.recv[r] + off, o, len);
       bulkCommit();
-      if (i + kStages < mine) issue(i + kStages);
+      if (i + S < mine) issue(i + S);
     }
   }
   if (threadIdx.x == 0) {
     bulkWaitAll();
     if (failed) {
       stagedFailure(a, 4);
-      // loads still in flight (tiles i .. i + kStages - 1) must land before
-      // the CTA's shared memory is released
-      for (unsigned long long j = i; j < mine && j < i + kStages; j++)
-        (void)stageWait(&bar[j % kStages], (unsigned)((j / kStages) & 1ull), a.timeoutNs);
+      // loads still in flight (tiles i .. i + S - 1) must land before the
+      // CTA's shared memory is released
+      for (unsigned long long j = i; j < mine && j < i + S; j++)
+        (void)stageWait(&bar[j % S], (unsigned)((j / S) & 1ull), a.timeoutNs);
     }
   }
   if (failed) return;

@@ -109,7 +109,7 @@ struct vcomm {
   double timeoutSec = 5.0;
   int treeNode = 1;                  // vranks per node of the hierarchical tree
   // direct AllReduce: bytes per rank from which the staged kernel runs
-  unsigned long long stagedMinBytes = 1ull << 20;
+  unsigned long long stagedMinBytes = 8ull << 20;
   Arena arena[2][3];
   ErrWord* hErr = nullptr;
   ErrWord* dErr = nullptr;
@@ -621,15 +621,22 @@ static DirectGeom directGeom(const CallSpec& cs) {
 }
 
 // The staged direct AllReduce (bulk copies through shared memory) takes
-// 16-byte aligned AllReduce calls of at least stagedMinBytes per rank (1 MiB,
-// env VCOMM_STAGED_MIN_BYTES) on the whole GPU; smaller calls keep the
-// register kernel, whose first loads leave without a pipeline to fill.  Its
-// tile comes from directStagedTile for kStagedSmemMax bytes of shared memory.
+// 16-byte aligned AllReduce calls on the whole GPU on 2..16 vranks from
+// stagedMinBytes per rank (8 MiB, env VCOMM_STAGED_MIN_BYTES), fp64 only up to
+// 8 vranks.  Measured against the register kernel: smaller calls give a CTA
+// too few tiles to fill the pipeline; beyond 16 vranks a tile holds fewer
+// 16-byte units than the CTA has threads; fp64 folds of 16 vranks are bound
+// by the fp64 pipe, where the register kernel's independent chains issue
+// better.  Two stages of loads in flight suit up to 4 vranks, three more.
+// The tile comes from directStagedTile for kStagedSmemMax bytes of shared
+// memory.
 constexpr int kStagedSmemMax = 205 * 1024;
 static bool useStaged(const CallSpec& cs, const DirectGeom& g) {
-  return cs.kcoll == kAllReduce && g.vec && cs.c->k >= 2 && cs.maxCtas == 0 &&
-         g.units * 16ull >= cs.c->stagedMinBytes;
+  const int k = cs.c->k;
+  return cs.kcoll == kAllReduce && g.vec && k >= 2 && k <= 16 && cs.maxCtas == 0 &&
+         !(cs.dtype == kF64 && k > 8) && g.units * 16ull >= cs.c->stagedMinBytes;
 }
+static int stagedStages(int k) { return std::min(k <= 4 ? 2 : 3, directStagedMaxStages()); }
 
 static vResult_t launchStaged(CallSpec& cs, const DirectGeom& g, DirectArgs& a) {
   vcomm* c = cs.c;
@@ -646,9 +653,11 @@ static vResult_t launchStaged(CallSpec& cs, const DirectGeom& g, DirectArgs& a) 
       ready.push_back(fn);
     }
   }
-  const unsigned tile = directStagedTile(k, kStagedSmemMax);
-  const size_t smem = directStagedSmem(k, tile);
+  const int stages = stagedStages(k);
+  const unsigned tile = directStagedTile(k, stages, kStagedSmemMax);
+  const size_t smem = directStagedSmem(k, stages, tile);
   if (smem > (size_t)kStagedSmemMax) return vInternalError;
+  a.stages = stages;
   a.tileBytes = tile;
   a.timeoutNs = (unsigned long long)(c->timeoutSec * 1e9);
   a.errClaim = c->dClaim;

@@ -20,15 +20,16 @@ int directThreads(int coll, int dtype);   // the block size the kernel is compil
 // launched with directThreads(coll, dtype) threads
 const void* directBatchKernel(int coll, int dtype, int op);
 // AllReduce of 16-byte aligned buffers staged through shared memory by bulk
-// copies (DirectArgs with tileBytes, timeoutNs, errClaim, err); one CTA per SM
-// of directStagedThreads() threads and directStagedSmem(nranks, tileBytes)
-// bytes of dynamic shared memory
+// copies (DirectArgs with stages, tileBytes, timeoutNs, errClaim, err); one
+// CTA per SM of directStagedThreads() threads and
+// directStagedSmem(nranks, stages, tileBytes) bytes of dynamic shared memory
 const void* directStagedKernel(int dtype, int op);
 int directStagedThreads();
-size_t directStagedSmem(int nranks, unsigned tileBytes);
+int directStagedMaxStages();
+size_t directStagedSmem(int nranks, int stages, unsigned tileBytes);
 // the largest tile (a multiple of 128 bytes, at most 16 KiB) whose staged
 // shared memory fits smemMax bytes
-unsigned directStagedTile(int nranks, size_t smemMax);
+unsigned directStagedTile(int nranks, int stages, size_t smemMax);
 // cluster protocol (vcomm_cluster_inst.cu): one cluster of nranks CTAs per channel
 const void* clusterKernel(int dtype, int op);
 const void* clusterCopyKernel();

@@ -2,13 +2,15 @@
 asynchronous copies, kDirectAllReduceStaged) against the CPU oracle,
 bit-exact.
 
-The staged kernel takes aligned AllReduce calls from VCOMM_STAGED_MIN_BYTES
-per rank (read when a communicator is created).  These tests create their
-communicators with that threshold at 16 bytes, so sizes the oracle replays in
-seconds already run staged and span many tiles, several CTAs, segments that
-straddle tiles, a ragged last tile and an element tail; small Simple slots
-make segments short.  Its results must equal the oracle's ring results for
-Simple's chunk, the register kernel's bit for bit, and a Simple call's.
+The staged kernel takes aligned AllReduce calls on 2..16 vranks (fp64: up to
+8) from VCOMM_STAGED_MIN_BYTES per rank (read when a communicator is
+created).  These tests create their communicators with that threshold at 16
+bytes, so sizes the oracle replays in seconds already run staged and span
+many tiles, several CTAs, segments that straddle tiles, a ragged last tile
+and an element tail, with two stages (up to 4 vranks) and three; small
+Simple slots make segments short.  Its results must equal the oracle's ring
+results for Simple's chunk, the register kernel's bit for bit, and a Simple
+call's.  Beyond the rule's limits the register kernel runs.
 """
 import os
 
@@ -81,8 +83,8 @@ CASES = [("fp32", "sum"), ("bf16", "sum"), ("fp16", "max"), ("int32", "sum"), ("
 
 
 @pytest.mark.parametrize("dtype,op", CASES)
-@pytest.mark.parametrize("k,C,steps", [(2, 1, 1), (3, 3, 2), (8, 8, 1), (16, 3, 3), (33, 2, 1),
-                                       (64, 2, 1)])
+@pytest.mark.parametrize("k,C,steps", [(2, 1, 1), (3, 3, 2), (4, 2, 1), (5, 2, 2), (8, 8, 1),
+                                       (16, 3, 3), (33, 2, 1)])
 def test_staged_allreduce(dtype, op, k, C, steps):
     c = get_comm(k, C)
     c.set_plan(nchannels=C, chunk_steps=steps)
@@ -177,25 +179,40 @@ def test_headline_size_default_threshold():
     c.destroy()
 
 
-def test_threshold_picks_the_kernel():
-    """The launch list shows which kernel ran: staged at or above the
-    threshold, the register kernel below it."""
+def kernels_of(c, k, n, dtype=torch.float32):
+    """Names of the kernels one direct AllReduce of n elements launches."""
     prof = pytest.importorskip("torch.profiler")
-    k, C = 4, 2
-    c = make_comm(k, C, 1 << 20)
-    names = {}
-    for label, n in (("small", (1 << 20) // 4 - 4), ("large", (1 << 20) // 4)):
-        s = [torch.ones(n, device="cuda") for _ in range(k)]
-        d = [torch.empty_like(t) for t in s]
+    s = [torch.ones(n, device="cuda", dtype=dtype) for _ in range(k)]
+    d = [torch.empty_like(t) for t in s]
+    torch.cuda.synchronize()
+    with prof.profile(activities=[prof.ProfilerActivity.CUDA]) as p:
+        c.all_reduce(s, d, algo="ring", proto="direct")
         torch.cuda.synchronize()
-        with prof.profile(activities=[prof.ProfilerActivity.CUDA]) as p:
-            c.all_reduce(s, d, algo="ring", proto="direct")
-            torch.cuda.synchronize()
-        names[label] = [e.name for e in p.events()]
-        assert float(d[1][-1]) == float(k)
-    c.destroy()
-    if not names["large"]:
+    assert c.async_error() == "vSuccess"
+    assert float(d[k - 1][-1]) == float(k)
+    return [e.name for e in p.events()]
+
+
+def test_threshold_and_rule_pick_the_kernel():
+    """The launch list shows which kernel ran: staged at or above the
+    threshold on 2..16 vranks, the register kernel below it, beyond 16
+    vranks, and for fp64 beyond 8 vranks."""
+    c4 = make_comm(4, 2, 1 << 20)
+    large = kernels_of(c4, 4, (1 << 20) // 4)
+    small = kernels_of(c4, 4, (1 << 20) // 4 - 4)
+    c4.destroy()
+    if not large:
         pytest.skip("the profiler recorded no CUDA kernels")
-    assert any("kDirectAllReduceStaged" in x for x in names["large"])
-    assert not any("kDirectAllReduceStaged" in x for x in names["small"])
-    assert any("kDirectReduce" in x for x in names["small"])
+    assert any("kDirectAllReduceStaged" in x for x in large)
+    assert not any("kDirectAllReduceStaged" in x for x in small)
+    assert any("kDirectReduce" in x for x in small)
+    c17 = make_comm(17, 1, 16)
+    beyond = kernels_of(c17, 17, 100000)
+    c17.destroy()
+    assert not any("kDirectAllReduceStaged" in x for x in beyond)
+    c16 = make_comm(16, 1, 16)
+    f64 = kernels_of(c16, 16, 100000, torch.float64)
+    f32 = kernels_of(c16, 16, 100000)
+    c16.destroy()
+    assert not any("kDirectAllReduceStaged" in x for x in f64)
+    assert any("kDirectAllReduceStaged" in x for x in f32)
