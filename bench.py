@@ -200,6 +200,7 @@ def run_gpu(args, rank, world):
         torch.cuda.synchronize()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
+        step()   # untimed: the GPU sat idle while the sampler started
         t0.record(stream)
         for i in range(args.steps):
             evs[i][0].record(stream)
@@ -266,6 +267,8 @@ def run_direct(args):
     stream = torch.cuda.current_stream()
     with ClockSampler(torch.cuda.current_device()) as clk:
         torch.cuda.synchronize()
+        # untimed: the GPU sat idle while the sampler started
+        comm.all_reduce(sends, recvs, op="sum", algo="ring", proto="direct", stream=stream)
         for i in range(args.steps):
             evs[i][0].record(stream)
             comm.all_reduce(sends, recvs, op="sum", algo="ring", proto="direct", stream=stream)
