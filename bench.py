@@ -213,23 +213,52 @@ def run_gpu(args, rank, world):
     if comm.async_error() != "vSuccess":
         raise RuntimeError(comm.async_error())
 
-    # end to end: pinned host inputs -> device, AllReduce, results -> host
-    e2e_steps = max(1, min(args.steps, 5))
+    # end to end: pinned host inputs -> device, AllReduce, results -> host.
+    # Every step copies its own inputs in and its own result out inside the
+    # timed region.  Two device buffer sets on three streams let the upload
+    # of step i + 1 (one copy engine) run while step i's result comes back
+    # (the other engine); a set is reused only after step i - 2 has read its
+    # inputs and its result has left the device.
+    e2e_steps = max(2, min(args.steps, 10))
     outs = [torch.empty_like(h).pin_memory() for h in host]
+    sets = [(sends, recvs), ([torch.empty_like(x) for x in sends], [torch.empty_like(x) for x in sends])]
+    s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    ev_in, ev_red, ev_out = ([torch.cuda.Event() for _ in range(2)] for _ in range(3))
     barrier(world)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(e2e_steps):
-        for h, s in zip(host, sends):
-            s.copy_(h, non_blocking=True)
-        step()
-        for o, r in zip(outs, recvs):
-            o.copy_(r, non_blocking=True)
+    s_in.wait_event(e0)
+    for i in range(e2e_steps):
+        b = i % 2
+        sb, rb = sets[b]
+        with torch.cuda.stream(s_in):
+            if i >= 2:
+                s_in.wait_event(ev_red[b])
+            for h, x in zip(host, sb):
+                x.copy_(h, non_blocking=True)
+            ev_in[b].record(s_in)
+        stream.wait_event(ev_in[b])
+        if i >= 2:
+            stream.wait_event(ev_out[b])
+        comm.all_reduce(sb, rb, op="sum", algo="ring", proto=proto, stream=stream)
+        ev_red[b].record(stream)
+        with torch.cuda.stream(s_out):
+            s_out.wait_event(ev_red[b])
+            for o, r in zip(outs, rb):
+                o.copy_(r, non_blocking=True)
+            ev_out[b].record(s_out)
+    stream.wait_stream(s_in)
+    stream.wait_stream(s_out)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    if comm.async_error() != "vSuccess":
+        raise RuntimeError(comm.async_error())
+    want = [r.cpu() for r in sets[(e2e_steps - 1) % 2][1][:1]]
+    if not torch.equal(outs[0].view(torch.int32), want[0].view(torch.int32)):
+        raise RuntimeError("end-to-end result differs from the device result")
     comm.destroy()
     return {"ms_per_step": total_ms / args.steps, "launch_ms": float(np.mean(launch_ms)),
             "e2e_ms": e2e_ms, "clocks": clk.summary(), "launches": args.steps,
