@@ -51,6 +51,11 @@ __global__ void __launch_bounds__(256) kDirectBatchCopy(const __grid_constant__ 
   }
 }
 
+// AllGather, Broadcast and point-to-point transfers of 16-byte aligned
+// buffers staged through shared memory by bulk copies; one thread of the
+// CTA drives them
+__global__ void __launch_bounds__(32) kCopyStaged(const __grid_constant__ CopyArgs a) { copyStaged(a); }
+
 }  // namespace direct
 
 #define VC_DDECL(D) const void* directReduceKernel_##D(int op); const void* directBatchKernel_##D(int op); \
@@ -108,6 +113,9 @@ const void* directStagedKernel(int dtype, int op) {
 int directStagedThreads() { return 256; }
 
 int directStagedMaxStages() { return direct::kMaxStages; }
+
+const void* copyStagedKernel() { return (const void*)direct::kCopyStaged; }
+int copyStagedMaxStages() { return direct::kMaxCopyStages; }
 
 size_t directStagedSmem(int nranks, int stages, unsigned tileBytes) {
   return (size_t)stages * nranks * tileBytes + 2 * (size_t)tileBytes + 8 * (size_t)stages;

@@ -476,5 +476,105 @@ VDEV void directAllReduceStaged(const DirectArgs& a) {
   }
 }
 
+
+// ---- copies staged through shared memory (AllGather, Broadcast, point to
+// point).  A copy needs no arithmetic, so one thread per CTA moves the data
+// with bulk copies alone: tile i of its share goes global -> shared (one
+// mbarrier per stage) and shared -> every destination (bulk stores); the
+// load of tile i + S - 1 is issued as soon as the stores of tile i - 1 have
+// read their stage, so S - 1 tiles of loads stay in flight.
+constexpr int kMaxCopyStages = 4;
+
+VDEV void copyFailure(const CopyArgs& a, int where) {
+  if (atomicCAS(a.errClaim, 0, (int)vTimeout) == 0) {
+    volatile ErrWord* e = a.err;
+    e->rank = -1;
+    e->channel = (int)blockIdx.x;
+    e->where = where;
+    __threadfence_system();
+    e->code = (int)vTimeout;
+    __threadfence_system();
+  }
+}
+
+// the task holding global tile t, searching up from task `from` (<= it)
+VDEV int copyTaskOf(const CopyArgs& a, unsigned long long t, int from) {
+  while (from + 1 < a.ntasks && a.tasks[from + 1].tileStart <= t) from++;
+  return from;
+}
+
+VDEV void copyStaged(const CopyArgs& a) {
+  if (threadIdx.x != 0) return;   // one thread drives the bulk copies
+  extern __shared__ __align__(128) unsigned char smem[];
+  const unsigned tile = (unsigned)a.tile;
+  const int S = a.stages;
+  uint64_t* bar = (uint64_t*)(smem + (size_t)S * tile);
+
+  // self-check of what the bulk copies need: 16-byte aligned sources,
+  // destinations, offsets and sizes, tiles within an mbarrier's count
+  bool bad = (smemU32(smem) & 15u) || (tile & 127u) || tile == 0 || tile >= (1u << 20) || S < 2 ||
+             S > kMaxCopyStages || a.ntasks < 1 || a.ntasks > kMaxCopyTasks;
+  for (int t = 0; !bad && t < a.ntasks; t++) {
+    const CopyTask& c = a.tasks[t];
+    if (((uintptr_t)c.src | c.bytes | c.dstOff) & 15u) bad = true;
+    if (c.dstBase < 0 || c.ndst < 0 || c.dstBase + c.ndst > kMaxCopyTasks) bad = true;
+    for (int d = 0; !bad && d < c.ndst; d++)
+      if ((uintptr_t)a.dsts[c.dstBase + d] & 15u) bad = true;
+  }
+  if (bad) {
+    copyFailure(a, 5);
+    return;
+  }
+  for (int s = 0; s < S; s++) mbarInit(&bar[s], 1);
+  fenceBarrierInit();
+
+  const unsigned long long G = gridDim.x;
+  const unsigned long long mine = blockIdx.x < a.ntiles ? (a.ntiles - 1 - blockIdx.x) / G + 1 : 0;
+  // my i-th tile is global tile blockIdx.x + i * G; loads and stores each
+  // walk their tiles in increasing order, so each keeps its own task hint
+  int loadTask = 0, storeTask = 0;
+  auto issue = [&](unsigned long long i) {
+    const unsigned long long t = blockIdx.x + i * G;
+    loadTask = copyTaskOf(a, t, loadTask);
+    const CopyTask& c = a.tasks[loadTask];
+    const unsigned long long off = (t - c.tileStart) * (unsigned long long)tile;
+    const unsigned len = (unsigned)(c.bytes - off < tile ? c.bytes - off : tile);
+    const int st = (int)(i % S);
+    mbarExpect(&bar[st], len);
+    bulkLoad(smem + (size_t)st * tile, (const char*)c.src + off, len, &bar[st]);
+  };
+  unsigned long long issued = 0;
+  for (; issued < mine && issued + 1 < (unsigned long long)S; issued++) issue(issued);
+
+  unsigned long long i = 0;
+  bool failed = false;
+  for (; i < mine; i++) {
+    const int st = (int)(i % S);
+    if (!stageWait(&bar[st], (unsigned)((i / S) & 1ull), a.timeoutNs)) {
+      failed = true;
+      break;
+    }
+    const unsigned long long t = blockIdx.x + i * G;
+    storeTask = copyTaskOf(a, t, storeTask);
+    const CopyTask& c = a.tasks[storeTask];
+    const unsigned long long off = (t - c.tileStart) * (unsigned long long)tile;
+    const unsigned len = (unsigned)(c.bytes - off < tile ? c.bytes - off : tile);
+    for (int d = 0; d < c.ndst; d++)
+      if (!((c.skipMask >> d) & 1ull))
+        bulkStore((char*)a.dsts[c.dstBase + d] + c.dstOff + off, smem + (size_t)st * tile, len);
+    bulkCommit();
+    bulkWaitRead1();   // the stores of tile i - 1 have read their stage
+    if (issued < mine) issue(issued++);
+  }
+  bulkWaitAll();
+  if (failed) {
+    copyFailure(a, 4);
+    // loads still in flight (tiles i .. issued - 1) must land before the
+    // CTA's shared memory is released
+    for (unsigned long long j = i; j < issued; j++)
+      (void)stageWait(&bar[j % S], (unsigned)((j / S) & 1ull), a.timeoutNs);
+  }
+}
+
 }  // namespace direct
 }  // namespace vc

@@ -670,6 +670,82 @@ static vResult_t launchStaged(CallSpec& cs, const DirectGeom& g, DirectArgs& a) 
   return vSuccess;
 }
 
+// Copies staged through shared memory (AllGather, Broadcast and grouped
+// point-to-point transfers): 16-byte aligned tasks whose sizes are multiples
+// of 16 bytes, from stagedMinBytes per rank (AllGather, Broadcast) or in
+// total (transfers), on the whole GPU.  Four stages of 32 KiB tiles, one CTA
+// per SM.
+constexpr unsigned kCopyTile = 32768;
+constexpr int kCopyStages = 4;
+
+static vResult_t launchCopyStaged(vcomm* c, CopyArgs& a, cudaStream_t stream) {
+  const void* fn = copyStagedKernel();
+  const int stages = std::min(kCopyStages, copyStagedMaxStages());
+  const size_t smem = (size_t)stages * kCopyTile + 8 * (size_t)stages;
+  {
+    // once: opt in to the dynamic shared memory
+    static std::mutex mu;
+    static bool ready = false;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!ready) {
+      VC_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      ready = true;
+    }
+  }
+  unsigned long long t = 0;
+  for (int i = 0; i < a.ntasks; i++) {
+    a.tasks[i].tileStart = t;
+    t += (a.tasks[i].bytes + kCopyTile - 1) / kCopyTile;
+  }
+  a.ntiles = t;
+  if (t == 0) return vSuccess;
+  a.tile = (int)kCopyTile;
+  a.stages = stages;
+  a.timeoutNs = (unsigned long long)(c->timeoutSec * 1e9);
+  a.errClaim = c->dClaim;
+  a.err = c->dErr;
+  const long long grid = std::max<long long>(1, std::min<long long>((long long)t, c->nsm));
+  void* args[] = {(void*)&a};
+  VC_TRY(cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(32), args, smem, stream));
+  return vSuccess;
+}
+
+// AllGather (one task per source rank) or Broadcast (one task) as staged
+// copies, if the call qualifies
+static bool useCopyStaged(const CallSpec& cs, const DirectGeom& g) {
+  return (cs.kcoll == kAllGather || cs.kcoll == kBroadcast) && g.vec && cs.c->k >= 2 &&
+         cs.maxCtas == 0 && cs.units % 16 == 0 && cs.units >= cs.c->stagedMinBytes;
+}
+static vResult_t launchCopyCollStaged(CallSpec& cs) {
+  const int k = cs.c->k;
+  CopyArgs a;
+  memset(&a, 0, sizeof(a));
+  for (int r = 0; r < k; r++) a.dsts[r] = cs.recv[r];
+  if (cs.kcoll == kAllGather) {
+    a.ntasks = k;
+    for (int b = 0; b < k; b++) {
+      CopyTask& t = a.tasks[b];
+      t.src = cs.send[b];
+      t.bytes = cs.units;
+      t.dstOff = (unsigned long long)b * cs.units;
+      t.skipMask = ((cs.inplace >> b) & 1ull) << b;
+      t.dstBase = 0;
+      t.ndst = k;
+    }
+  } else {
+    a.ntasks = 1;
+    CopyTask& t = a.tasks[0];
+    t.src = cs.send[cs.root];
+    t.bytes = cs.units;
+    t.skipMask = ((cs.inplace >> cs.root) & 1ull) << cs.root;
+    t.ndst = k;
+  }
+  const vResult_t r = launchCopyStaged(cs.c, a, cs.stream);
+  if (r != vSuccess) return r;
+  cs.c->last = cs.plan;
+  return vSuccess;
+}
+
 // The direct protocol: a plain launch over the data, no FIFO, no waits.
 static vResult_t launchDirect(CallSpec& cs) {
   vcomm* c = cs.c;
@@ -693,6 +769,7 @@ static vResult_t launchDirect(CallSpec& cs) {
   a.vec = g.vec ? 1 : 0;
   a.postDiv = cs.postDiv;
   if (useStaged(cs, g)) return launchStaged(cs, g, a);
+  if (useCopyStaged(cs, g)) return launchCopyCollStaged(cs);
   const unsigned long long units = g.units;
   const int nthr = directThreads(cs.kcoll, cs.dtype);
   const long long resident = (long long)std::max(1, residentPerSM(fn, nthr)) * c->nsm;
@@ -808,6 +885,35 @@ struct Transfer {
 
 // byte copies, one task each, as kDirectBatchCopy ops over one-rank views
 static vResult_t launchCopies(vcomm* c, const std::vector<Transfer>& xs, cudaStream_t stream) {
+  // staged copies when every transfer is 16-byte aligned and whole 16-byte
+  // units and the group moves at least stagedMinBytes
+  bool staged = !xs.empty();
+  unsigned long long total = 0;
+  for (const Transfer& t : xs) {
+    if ((((uintptr_t)t.src | (uintptr_t)t.dst | t.bytes) & 15) != 0) staged = false;
+    total += t.bytes;
+  }
+  if (staged && total >= c->stagedMinBytes) {
+    for (size_t base = 0; base < xs.size(); base += kMaxCopyTasks) {
+      const int n = (int)std::min<size_t>(kMaxCopyTasks, xs.size() - base);
+      CopyArgs a;
+      memset(&a, 0, sizeof(a));
+      a.ntasks = n;
+      for (int i = 0; i < n; i++) {
+        const Transfer& x = xs[base + i];
+        CopyTask& t = a.tasks[i];
+        t.src = x.src;
+        t.bytes = x.bytes;
+        t.skipMask = x.src == x.dst ? 1ull : 0ull;
+        t.dstBase = i;
+        t.ndst = 1;
+        a.dsts[i] = x.dst;
+      }
+      const vResult_t r = launchCopyStaged(c, a, stream);
+      if (r != vSuccess) return r;
+    }
+    return vSuccess;
+  }
   const void* fn = directBatchKernel(kBroadcast, 0, 0);
   const int nthr = directThreads(kBroadcast, 0);
   const long long resident = (long long)std::max(1, residentPerSM(fn, nthr)) * c->nsm;

@@ -188,6 +188,27 @@ struct DirectArgs {
   ErrWord* err;                    // host-mapped report
 };
 
+// ---- copies staged through shared memory (kCopyStaged): AllGather,
+// Broadcast and point-to-point transfers as tasks.  Task i copies `bytes`
+// (a multiple of 16) from `src` to dsts[dstBase + d] + dstOff for d < ndst,
+// skipping the destinations whose bit is set in skipMask; its tiles are the
+// global tiles [tileStart, tileStart + ceil(bytes / tile)).
+constexpr int kMaxCopyTasks = 64;
+struct CopyTask {
+  const void* src;
+  unsigned long long bytes, tileStart, dstOff, skipMask;
+  int dstBase, ndst;
+};
+struct CopyArgs {
+  CopyTask tasks[kMaxCopyTasks];
+  void* dsts[kMaxCopyTasks];
+  unsigned long long ntiles;       // tiles of all tasks
+  unsigned long long timeoutNs;    // deadline of every wait for a bulk copy
+  int* errClaim;
+  ErrWord* err;
+  int ntasks, tile, stages, pad;
+};
+
 // ---- direct collectives of one class in one launch: op i owns units
 // [unitStart[i], unitStart[i + 1]) of the concatenated unit space (its
 // `units` real ones, at least one so that some CTA owns its tail); pointers

@@ -30,6 +30,10 @@ size_t directStagedSmem(int nranks, int stages, unsigned tileBytes);
 // the largest tile (a multiple of 128 bytes, at most 16 KiB) whose staged
 // shared memory fits smemMax bytes
 unsigned directStagedTile(int nranks, int stages, size_t smemMax);
+// copies staged through shared memory (CopyArgs); 32 threads per CTA,
+// stages x tile + 8 x stages bytes of dynamic shared memory
+const void* copyStagedKernel();
+int copyStagedMaxStages();
 // cluster protocol (vcomm_cluster_inst.cu): one cluster of nranks CTAs per channel
 const void* clusterKernel(int dtype, int op);
 const void* clusterCopyKernel();
