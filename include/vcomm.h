@@ -89,8 +89,10 @@ typedef enum { vAlgoAuto = 0, vAlgoRing = 1, vAlgoTree = 2 } vAlgo_t;
  * Simple.  An AllReduce of 16-byte aligned buffers on 2..16 vranks (fp64: up
  * to 8) of at least 8 MiB per rank (env VCOMM_STAGED_MIN_BYTES, read at
  * vcommInit) moves its data by bulk asynchronous copies through shared memory
- * (same fold, same bits); a bulk copy that does not complete within
- * timeoutSec fails the call with vTimeout like a flag wait. */
+ * (same fold, same bits); so do an AllGather or Broadcast of 16-byte aligned
+ * buffers whose per-rank size is whole 16-byte units and at least that
+ * threshold.  A bulk copy that does not complete within timeoutSec fails the
+ * call with vTimeout like a flag wait. */
 typedef enum {
   vProtoAuto = 0,
   vProtoSimple = 1,
@@ -242,7 +244,10 @@ vResult_t vcommGetGroupPlans(vcomm_t comm, vPlan_t* plans, int maxPlans, int* nP
  * nothing of the group).  rank == peer is a local copy.  Same-process ranks
  * copy directly from the source to the destination buffer (Sec. IV,
  * P2P_DIRECT); each transfer is its own task of one launch, so grouped
- * transfers run concurrently (Sec. II-C).  Buffers are caller-owned and must
+ * transfers run concurrently (Sec. II-C).  When every transfer of the group
+ * is 16-byte aligned and whole 16-byte units and the group moves at least
+ * VCOMM_STAGED_MIN_BYTES (8 MiB), the tasks move by bulk copies through
+ * shared memory, up to 64 per launch.  Buffers are caller-owned and must
  * be element-aligned; a receive buffer must not overlap another transfer's
  * buffers.  Calls outside a group return vInvalidArgument. */
 vResult_t vSend(const void* sendbuf, size_t count, vDataType_t dtype, int rank, int peer,
