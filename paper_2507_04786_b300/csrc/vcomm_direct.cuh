@@ -291,10 +291,10 @@ VDEV void opShare(const DirectBatchArgs* b, int i, unsigned long long glo, unsig
 }
 
 
-// ---- the AllReduce staged through shared memory.
+// ---- the reducing collectives staged through shared memory.
 //
-// Same arithmetic as directReduce (each 16-byte unit's ring chain folded in
-// the order of its segment), but the data moves by bulk asynchronous copies:
+// Same arithmetic as directReduce (each 16-byte unit's chain folded in its
+// ring order), but the data moves by bulk asynchronous copies:
 // one thread loads tile i of every rank's input into shared memory (k copies
 // that complete one mbarrier), S = a.stages tiles ahead of the fold, and
 // stores the folded tile to every rank's output with k bulk stores, so the
@@ -372,17 +372,25 @@ VDEV bool stageWait(uint64_t* bar, unsigned parity, unsigned long long timeoutNs
   }
 }
 
+// AllReduce, ReduceScatter and Reduce staged through shared memory.  A
+// tile is a range of one block: the whole buffer (AllReduce, Reduce) or
+// block b of the k ReduceScatter blocks (b's chain starts at rank b + 1 and
+// ends in recvbuf b); AllReduce units take their segment's chain and go to
+// every output, Reduce units the chain ending at the root.
 template <class T, class Op>
-VDEV void directAllReduceStaged(const DirectArgs& a) {
+VDEV void directReduceStaged(const DirectArgs& a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const DirectView v = viewOf(a);
   const int k = a.nranks;
   constexpr int E = Unit16<T>::kElems;
   constexpr unsigned long long esz = sizeof(T);
-  const unsigned long long fullBytes = (a.count / E) * 16ull;   // the 16-byte units of a buffer
+  const unsigned long long fullBytes = (a.count / E) * 16ull;   // the 16-byte units of a block
   const unsigned tile = (unsigned)a.tileBytes;
   const int S = a.stages;
-  const unsigned long long ntiles = (fullBytes + tile - 1) / tile;
+  const bool rs = a.coll == kReduceScatter;
+  const unsigned long long blockStride = rs ? a.count * esz : 0ull;   // between send blocks
+  const unsigned long long perBlock = (fullBytes + tile - 1) / tile;
+  const unsigned long long ntiles = (rs ? (unsigned long long)k : 1ull) * perBlock;
   unsigned char* in = smem;
   unsigned char* out = smem + (size_t)S * k * tile;
   uint64_t* bar = (uint64_t*)(out + 2 * (size_t)tile);
@@ -390,7 +398,8 @@ VDEV void directAllReduceStaged(const DirectArgs& a) {
   // self-check of what the bulk copies need: 16-byte aligned buffers, tiles
   // and shared memory, and one phase's bytes within an mbarrier's count
   bool bad = (smemU32(smem) & 15u) || (tile & 127u) || tile == 0 || S < 2 || S > kMaxStages ||
-             (unsigned long long)k * tile >= (1ull << 20);
+             (unsigned long long)k * tile >= (1ull << 20) || (blockStride & 15u) ||
+             !(a.coll == kAllReduce || rs || a.coll == kReduce);
   for (int r = 0; r < k; r++)
     if (((uintptr_t)v.send[r] | (uintptr_t)v.recv[r]) & 15u) bad = true;
   if (bad) {
@@ -405,17 +414,23 @@ VDEV void directAllReduceStaged(const DirectArgs& a) {
 
   const unsigned long long G = gridDim.x;
   const unsigned long long mine = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / G + 1 : 0;
-  auto tileOff = [&](unsigned long long i) { return (blockIdx.x + i * G) * (unsigned long long)tile; };
-  auto tileLen = [&](unsigned long long off) {
-    return (unsigned)(fullBytes - off < tile ? fullBytes - off : tile);
+  // my i-th tile: global tile blockIdx.x + i * G = block b, offset off in it
+  auto tileAt = [&](unsigned long long i, int* b, unsigned long long* off, unsigned* len) {
+    const unsigned long long t = blockIdx.x + i * G;
+    *b = (int)(t / perBlock);
+    *off = (t % perBlock) * (unsigned long long)tile;
+    *len = (unsigned)(fullBytes - *off < tile ? fullBytes - *off : tile);
   };
   auto issue = [&](unsigned long long i) {   // thread 0: the k input tiles of my i-th tile
     const int st = (int)(i % S);
-    const unsigned long long off = tileOff(i);
-    const unsigned len = tileLen(off);
+    int b;
+    unsigned long long off;
+    unsigned len;
+    tileAt(i, &b, &off, &len);
+    const unsigned long long src = (unsigned long long)b * blockStride + off;
     mbarExpect(&bar[st], len * (unsigned)k);
     for (int r = 0; r < k; r++)
-      bulkLoad(in + ((size_t)st * k + r) * tile, (const char*)v.send[r] + off, len, &bar[st]);
+      bulkLoad(in + ((size_t)st * k + r) * tile, (const char*)v.send[r] + src, len, &bar[st]);
   };
   if (threadIdx.x == 0)
     for (unsigned long long i = 0; i < mine && i < (unsigned long long)S; i++) issue(i);
@@ -434,13 +449,19 @@ VDEV void directAllReduceStaged(const DirectArgs& a) {
     const int ob = (int)(i & 1ull);
     if (threadIdx.x == 0) bulkWaitRead1();   // the stores of tile i - 2 no longer read out[ob]
     __syncthreads();
-    const unsigned long long off = tileOff(i);
-    const unsigned len = tileLen(off);
+    int b;
+    unsigned long long off;
+    unsigned len;
+    tileAt(i, &b, &off, &len);
     const unsigned char* src = in + (size_t)st * k * tile;
     unsigned char* o = out + (size_t)ob * tile;
     for (unsigned u = threadIdx.x * 16u; u < len; u += blockDim.x * 16u) {
-      const unsigned long long e0 = (off + u) / esz;
-      if (e0 >= runEnd) seg = arSegment(v, e0, (int)esz, &runEnd);
+      if (a.coll == kAllReduce) {
+        const unsigned long long e0 = (off + u) / esz;
+        if (e0 >= runEnd) seg = arSegment(v, e0, (int)esz, &runEnd);
+      } else {
+        seg = rs ? b : a.root;
+      }
       int r = seg + 1 < k ? seg + 1 : 0;
       uint4 acc = *(const uint4*)(src + (size_t)r * tile + u);
       for (int j = 1; j < k; j++) {
@@ -453,7 +474,11 @@ VDEV void directAllReduceStaged(const DirectArgs& a) {
     fenceProxyAsync();
     __syncthreads();   // out[ob] written; in[st] read by every thread
     if (threadIdx.x == 0) {
-      for (int r = 0; r < k; r++) bulkStore((char*)v.recv[r] + off, o, len);
+      if (a.coll == kAllReduce) {
+        for (int r = 0; r < k; r++) bulkStore((char*)v.recv[r] + off, o, len);
+      } else {
+        bulkStore((char*)v.recv[rs ? b : a.root] + off, o, len);
+      }
       bulkCommit();
       if (i + S < mine) issue(i + S);
     }
@@ -469,8 +494,9 @@ VDEV void directAllReduceStaged(const DirectArgs& a) {
     }
   }
   if (failed) return;
-  // the element tail after the last full unit
-  if (blockIdx.x == gridDim.x - 1) {
+  // the element tail after the last full unit (ReduceScatter blocks of
+  // whole units have none)
+  if (blockIdx.x == gridDim.x - 1 && !rs) {
     const unsigned long long nunit = a.count / E;
     directReduce<T, Op, Unit16<T>, 1>(v, nunit, nunit, true);
   }

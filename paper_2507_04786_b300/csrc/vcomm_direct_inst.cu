@@ -47,11 +47,12 @@ __global__ void __launch_bounds__(DirectShape<T>::kThreads, 1)
   }
 }
 
-// AllReduce of 16-byte aligned buffers staged through shared memory by bulk
-// copies (one CTA per SM; dynamic shared memory from directStagedSmem)
+// AllReduce, ReduceScatter and Reduce of 16-byte aligned buffers staged
+// through shared memory by bulk copies (one CTA per SM; dynamic shared memory
+// from directStagedSmem)
 template <class T, class Op>
-__global__ void __launch_bounds__(256, 1) kDirectAllReduceStaged(const __grid_constant__ DirectArgs a) {
-  directAllReduceStaged<T, Op>(a);
+__global__ void __launch_bounds__(256, 1) kDirectReduceStaged(const __grid_constant__ DirectArgs a) {
+  directReduceStaged<T, Op>(a);
 }
 
 }  // namespace direct
@@ -84,10 +85,10 @@ const void* VC_DNAME(directBatchKernel, VC_DTYPE)(int op) {
 namespace vc {
 const void* VC_DNAME(directStagedKernel, VC_DTYPE)(int op) {
   switch (op) {
-    case kSum: case kAvg: return (const void*)direct::kDirectAllReduceStaged<VcT, OpSum>;
-    case kMax: return (const void*)direct::kDirectAllReduceStaged<VcT, OpMax>;
-    case kProd: return (const void*)direct::kDirectAllReduceStaged<VcT, OpProd>;
-    case kMin: return (const void*)direct::kDirectAllReduceStaged<VcT, OpMin>;
+    case kSum: case kAvg: return (const void*)direct::kDirectReduceStaged<VcT, OpSum>;
+    case kMax: return (const void*)direct::kDirectReduceStaged<VcT, OpMax>;
+    case kProd: return (const void*)direct::kDirectReduceStaged<VcT, OpProd>;
+    case kMin: return (const void*)direct::kDirectReduceStaged<VcT, OpMin>;
   }
   return nullptr;
 }

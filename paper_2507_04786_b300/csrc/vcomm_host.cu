@@ -620,10 +620,10 @@ static DirectGeom directGeom(const CallSpec& cs) {
   return DirectGeom{aligned, units, chunkUnits(kSimple, cs.c->slotBytes[kSimple], cs.plan.chunkSteps, esz)};
 }
 
-// The staged direct AllReduce (bulk copies through shared memory) takes
-// 16-byte aligned AllReduce calls on the whole GPU on 2..16 vranks from
-// stagedMinBytes per rank (8 MiB, env VCOMM_STAGED_MIN_BYTES), fp64 only up to
-// 8 vranks.  Measured against the register kernel: smaller calls give a CTA
+// The staged direct reducing kernel (bulk copies through shared memory)
+// takes 16-byte aligned AllReduce, ReduceScatter and Reduce calls on the
+// whole GPU on 2..16 vranks from stagedMinBytes per rank (send buffer; 8 MiB,
+// env VCOMM_STAGED_MIN_BYTES), fp64 only up to 8 vranks.  Measured against the register kernel: smaller calls give a CTA
 // too few tiles to fill the pipeline; beyond 16 vranks a tile holds fewer
 // 16-byte units than the CTA has threads; fp64 folds of 16 vranks are bound
 // by the fp64 pipe, where the register kernel's independent chains issue
@@ -633,8 +633,9 @@ static DirectGeom directGeom(const CallSpec& cs) {
 constexpr int kStagedSmemMax = 205 * 1024;
 static bool useStaged(const CallSpec& cs, const DirectGeom& g) {
   const int k = cs.c->k;
-  return cs.kcoll == kAllReduce && g.vec && k >= 2 && k <= 16 && cs.maxCtas == 0 &&
-         !(cs.dtype == kF64 && k > 8) && g.units * 16ull >= cs.c->stagedMinBytes;
+  const bool coll = cs.kcoll == kAllReduce || cs.kcoll == kReduceScatter || cs.kcoll == kReduce;
+  return coll && g.vec && k >= 2 && k <= 16 && cs.maxCtas == 0 && !(cs.dtype == kF64 && k > 8) &&
+         g.units * 16ull >= cs.c->stagedMinBytes;
 }
 static int stagedStages(int k) { return std::min(k <= 4 ? 2 : 3, directStagedMaxStages()); }
 
@@ -662,7 +663,9 @@ static vResult_t launchStaged(CallSpec& cs, const DirectGeom& g, DirectArgs& a) 
   a.timeoutNs = (unsigned long long)(c->timeoutSec * 1e9);
   a.errClaim = c->dClaim;
   a.err = c->dErr;
-  const unsigned long long ntiles = (g.units * 16ull + tile - 1) / tile;
+  // tiles never straddle ReduceScatter blocks (g.units counts all k blocks)
+  const unsigned long long nblk = cs.kcoll == kReduceScatter ? (unsigned long long)k : 1ull;
+  const unsigned long long ntiles = nblk * ((g.units / nblk * 16ull + tile - 1) / tile);
   const long long grid = std::max<long long>(1, std::min<long long>((long long)ntiles, c->nsm));
   void* args[] = {(void*)&a};
   VC_TRY(cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(directStagedThreads()), args, smem, cs.stream));

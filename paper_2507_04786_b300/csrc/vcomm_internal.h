@@ -180,7 +180,7 @@ struct DirectArgs {
   int coll, nranks, nsub, root;
   int vec;                         // 1: every access is a 16-byte vector
   int postDiv;                     // avg: divide the folded value by this (0: none)
-  // the AllReduce staged through shared memory (kDirectAllReduceStaged) only:
+  // the staged reducing kernel (kDirectReduceStaged) only:
   int stages;                      // tiles of loads in flight (2 or 3)
   unsigned long long tileBytes;    // bytes of one rank's tile (multiple of 128)
   unsigned long long timeoutNs;    // deadline of every wait for a bulk copy

@@ -19,8 +19,9 @@ int directThreads(int coll, int dtype);   // the block size the kernel is compil
 // a group's direct calls of one (dtype, op) class (or its copies), DirectBatchArgs;
 // launched with directThreads(coll, dtype) threads
 const void* directBatchKernel(int coll, int dtype, int op);
-// AllReduce of 16-byte aligned buffers staged through shared memory by bulk
-// copies (DirectArgs with stages, tileBytes, timeoutNs, errClaim, err); one
+// AllReduce, ReduceScatter and Reduce of 16-byte aligned buffers staged
+// through shared memory by bulk copies (DirectArgs with stages, tileBytes,
+// timeoutNs, errClaim, err); one
 // CTA per SM of directStagedThreads() threads and
 // directStagedSmem(nranks, stages, tileBytes) bytes of dynamic shared memory
 const void* directStagedKernel(int dtype, int op);

@@ -1,10 +1,10 @@
-"""GPU parity of the direct AllReduce staged through shared memory (bulk
-asynchronous copies, kDirectAllReduceStaged) against the CPU oracle,
-bit-exact.
+"""GPU parity of the direct reducing collectives staged through shared
+memory (bulk asynchronous copies, kDirectReduceStaged) against the CPU
+oracle, bit-exact.
 
-The staged kernel takes aligned AllReduce calls on 2..16 vranks (fp64: up to
-8) from VCOMM_STAGED_MIN_BYTES per rank (read when a communicator is
-created).  These tests create their communicators with that threshold at 16
+The staged kernel takes aligned AllReduce, ReduceScatter and Reduce calls on
+2..16 vranks (fp64: up to 8) from VCOMM_STAGED_MIN_BYTES per rank (read when
+a communicator is created).  These tests create their communicators with that threshold at 16
 bytes, so sizes the oracle replays in seconds already run staged and span
 many tiles, several CTAs, segments that straddle tiles, a ragged last tile
 and an element tail, with two stages (up to 4 vranks) and three; small
@@ -127,6 +127,56 @@ def test_equals_register_kernel_and_simple(dtype, k, C):
         c.clear_plan()
 
 
+@pytest.mark.parametrize("dtype,op", [("fp32", "sum"), ("bf16", "sum"), ("int32", "max"),
+                                      ("fp16", "avg"), ("int8", "prod")])
+@pytest.mark.parametrize("k", [2, 5, 16])
+def test_staged_reduce_scatter(dtype, op, k):
+    """ReduceScatter blocks of whole 16-byte units run staged (tiles never
+    straddle blocks); other block sizes take the register kernel."""
+    c = get_comm(k, 2)
+    c.set_plan(nchannels=2, chunk_steps=1)
+    for m in (16, 4096, 50000, 777):              # 777: not whole units for 2- and 4-byte types
+        xs = data(m + 11 * k + len(op), k, k * m, dtype, op)
+        s = [to_dev(x) for x in xs]
+        d = [torch.empty(m, dtype=s[0].dtype, device="cuda") for _ in range(k)]
+        c.reduce_scatter(s, d, op=op, algo="ring", proto="direct")
+        finish(c)
+        want = oracle.reduce_scatter(xs, dtype, op, 2, chunk_for("simple", dtype, SMALL_SLOTS, 1))
+        for r in sorted({0, k // 2, k - 1}):
+            assert_same(to_np(d[r], dtype), want[r], f"m={m} rank {r}")
+    m = 20000                                      # in place: recvbuf r is block r of sendbuf r
+    xs = data(9 * k, k, k * m, dtype, op)
+    s = [to_dev(x) for x in xs]
+    c.reduce_scatter(s, [t[r * m:(r + 1) * m] for r, t in enumerate(s)], op=op, algo="ring",
+                     proto="direct")
+    finish(c)
+    want = oracle.reduce_scatter(xs, dtype, op, 2, chunk_for("simple", dtype, SMALL_SLOTS, 1))
+    for r in range(k):
+        assert_same(to_np(s[r][r * m:(r + 1) * m], dtype), want[r], f"in place rank {r}")
+    c.clear_plan()
+
+
+@pytest.mark.parametrize("dtype,op", [("fp32", "sum"), ("bf16", "max"), ("int32", "sum"),
+                                      ("fp64", "min")])
+@pytest.mark.parametrize("k,root", [(2, 1), (5, 3), (16, 0)])
+def test_staged_reduce(dtype, op, k, root):
+    c = get_comm(k, 1)
+    c.set_plan(nchannels=1, chunk_steps=1)
+    for n in (5, 2049, 30011, 100003):
+        xs = data(n + 7 * root, k, n, dtype, op)
+        s = [to_dev(x) for x in xs]
+        d = [torch.empty_like(s[0]) if r == root else None for r in range(k)]
+        c.reduce(s, d, op=op, root=root, algo="ring", proto="direct")
+        finish(c)
+        want = oracle.reduce(xs, dtype, op, root, 1, chunk_for("simple", dtype, SMALL_SLOTS, 1))
+        assert_same(to_np(d[root], dtype), want, f"n={n}")
+        d = [s[root] if r == root else None for r in range(k)]     # the root in place
+        c.reduce(s, d, op=op, root=root, algo="ring", proto="direct")
+        finish(c)
+        assert_same(to_np(s[root], dtype), want, f"in place n={n}")
+    c.clear_plan()
+
+
 def test_in_place_and_unaligned_fallback():
     """In place (recvbuf = sendbuf) runs staged; a view at an odd element
     offset is not 16-byte aligned and takes the element-wise kernel; both
@@ -203,16 +253,27 @@ def test_threshold_and_rule_pick_the_kernel():
     c4.destroy()
     if not large:
         pytest.skip("the profiler recorded no CUDA kernels")
-    assert any("kDirectAllReduceStaged" in x for x in large)
-    assert not any("kDirectAllReduceStaged" in x for x in small)
+    assert any("kDirectReduceStaged" in x for x in large)
+    assert not any("kDirectReduceStaged" in x for x in small)
     assert any("kDirectReduce" in x for x in small)
     c17 = make_comm(17, 1, 16)
     beyond = kernels_of(c17, 17, 100000)
     c17.destroy()
-    assert not any("kDirectAllReduceStaged" in x for x in beyond)
+    assert not any("kDirectReduceStaged" in x for x in beyond)
     c16 = make_comm(16, 1, 16)
     f64 = kernels_of(c16, 16, 100000, torch.float64)
     f32 = kernels_of(c16, 16, 100000)
     c16.destroy()
-    assert not any("kDirectAllReduceStaged" in x for x in f64)
-    assert any("kDirectAllReduceStaged" in x for x in f32)
+    assert not any("kDirectReduceStaged" in x for x in f64)
+    assert any("kDirectReduceStaged" in x for x in f32)
+    c3 = make_comm(3, 1, 16)
+    prof = pytest.importorskip("torch.profiler")
+    s = [torch.ones(3 * 4096, device="cuda") for _ in range(3)]
+    d = [torch.empty(4096, device="cuda") for _ in range(3)]
+    torch.cuda.synchronize()
+    with prof.profile(activities=[prof.ProfilerActivity.CUDA]) as p:
+        c3.reduce_scatter(s, d, algo="ring", proto="direct")
+        torch.cuda.synchronize()
+    assert c3.async_error() == "vSuccess" and float(d[2][-1]) == 3.0
+    c3.destroy()
+    assert any("kDirectReduceStaged" in e.name for e in p.events())
