@@ -86,9 +86,10 @@ typedef enum { vAlgoAuto = 0, vAlgoRing = 1, vAlgoTree = 2 } vAlgo_t;
  * only; for a given plan (channels, chunkSteps) the results are the Simple
  * protocol's, bit for bit.  Auto picks it on the ring for nranks >= 2; a
  * group runs all its direct calls in one launch; the serving API runs it as
- * Simple.  An AllReduce, ReduceScatter or Reduce of 16-byte aligned buffers
- * on 2..16 vranks (fp64: up to 8) of at least 8 MiB per rank (send buffer;
- * env VCOMM_STAGED_MIN_BYTES, read at vcommInit) moves its data by bulk
+ * Simple.  An AllReduce on 2..16 vranks (fp64: up to 8), or a ReduceScatter
+ * or Reduce on 2..4 vranks, of 16-byte aligned buffers of at least 8 MiB per
+ * rank (send buffer; env VCOMM_STAGED_MIN_BYTES, read at vcommInit) moves its
+ * data by bulk
  * asynchronous copies through shared memory (same fold, same bits); so do an AllGather or Broadcast of 16-byte aligned
  * buffers whose per-rank size is whole 16-byte units and at least that
  * threshold.  A bulk copy that does not complete within timeoutSec fails the

@@ -621,9 +621,11 @@ static DirectGeom directGeom(const CallSpec& cs) {
 }
 
 // The staged direct reducing kernel (bulk copies through shared memory)
-// takes 16-byte aligned AllReduce, ReduceScatter and Reduce calls on the
-// whole GPU on 2..16 vranks from stagedMinBytes per rank (send buffer; 8 MiB,
-// env VCOMM_STAGED_MIN_BYTES), fp64 only up to 8 vranks.  Measured against the register kernel: smaller calls give a CTA
+// takes 16-byte aligned calls on the whole GPU from stagedMinBytes per rank
+// (send buffer; 8 MiB, env VCOMM_STAGED_MIN_BYTES): AllReduce on 2..16
+// vranks (fp64 up to 8), ReduceScatter and Reduce on 2..4 vranks, where a
+// tile's one output leaves the register kernel ahead once the fold of more
+// inputs, between two block barriers, outlasts the tile's loads.  Measured against the register kernel: smaller calls give a CTA
 // too few tiles to fill the pipeline; beyond 16 vranks a tile holds fewer
 // 16-byte units than the CTA has threads; fp64 folds of 16 vranks are bound
 // by the fp64 pipe, where the register kernel's independent chains issue
@@ -633,8 +635,8 @@ static DirectGeom directGeom(const CallSpec& cs) {
 constexpr int kStagedSmemMax = 205 * 1024;
 static bool useStaged(const CallSpec& cs, const DirectGeom& g) {
   const int k = cs.c->k;
-  const bool coll = cs.kcoll == kAllReduce || cs.kcoll == kReduceScatter || cs.kcoll == kReduce;
-  return coll && g.vec && k >= 2 && k <= 16 && cs.maxCtas == 0 && !(cs.dtype == kF64 && k > 8) &&
+  const int kmax = cs.kcoll == kAllReduce ? 16 : (cs.kcoll == kReduceScatter || cs.kcoll == kReduce) ? 4 : 0;
+  return g.vec && k >= 2 && k <= kmax && cs.maxCtas == 0 && !(cs.dtype == kF64 && k > 8) &&
          g.units * 16ull >= cs.c->stagedMinBytes;
 }
 static int stagedStages(int k) { return std::min(k <= 4 ? 2 : 3, directStagedMaxStages()); }

@@ -2,9 +2,9 @@
 memory (bulk asynchronous copies, kDirectReduceStaged) against the CPU
 oracle, bit-exact.
 
-The staged kernel takes aligned AllReduce, ReduceScatter and Reduce calls on
-2..16 vranks (fp64: up to 8) from VCOMM_STAGED_MIN_BYTES per rank (read when
-a communicator is created).  These tests create their communicators with that threshold at 16
+The staged kernel takes aligned AllReduce calls on 2..16 vranks (fp64: up to
+8) and ReduceScatter / Reduce calls on 2..4 vranks from
+VCOMM_STAGED_MIN_BYTES per rank (read when a communicator is created).  These tests create their communicators with that threshold at 16
 bytes, so sizes the oracle replays in seconds already run staged and span
 many tiles, several CTAs, segments that straddle tiles, a ragged last tile
 and an element tail, with two stages (up to 4 vranks) and three; small
@@ -129,10 +129,11 @@ def test_equals_register_kernel_and_simple(dtype, k, C):
 
 @pytest.mark.parametrize("dtype,op", [("fp32", "sum"), ("bf16", "sum"), ("int32", "max"),
                                       ("fp16", "avg"), ("int8", "prod")])
-@pytest.mark.parametrize("k", [2, 5, 16])
+@pytest.mark.parametrize("k", [2, 3, 4, 16])
 def test_staged_reduce_scatter(dtype, op, k):
-    """ReduceScatter blocks of whole 16-byte units run staged (tiles never
-    straddle blocks); other block sizes take the register kernel."""
+    """ReduceScatter blocks of whole 16-byte units run staged on up to 4
+    vranks (tiles never straddle blocks); other block sizes and 16 vranks
+    take the register kernel."""
     c = get_comm(k, 2)
     c.set_plan(nchannels=2, chunk_steps=1)
     for m in (16, 4096, 50000, 777):              # 777: not whole units for 2- and 4-byte types
@@ -158,7 +159,7 @@ def test_staged_reduce_scatter(dtype, op, k):
 
 @pytest.mark.parametrize("dtype,op", [("fp32", "sum"), ("bf16", "max"), ("int32", "sum"),
                                       ("fp64", "min")])
-@pytest.mark.parametrize("k,root", [(2, 1), (5, 3), (16, 0)])
+@pytest.mark.parametrize("k,root", [(2, 1), (3, 0), (4, 3), (16, 0)])
 def test_staged_reduce(dtype, op, k, root):
     c = get_comm(k, 1)
     c.set_plan(nchannels=1, chunk_steps=1)
