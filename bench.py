@@ -709,6 +709,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=workloads.SERVED["bench_requests"],
                     help="requests of the served leg (the full stream is 100000)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and served legs")
+    ap.add_argument("--extras", default="direct,alltoall,small,batched,served",
+                    help="the extra legs to run, comma separated (profiling captures run one)")
     ap.add_argument("--sweep", default=None,
                     help="run the protocol x size x channel sweep, write JSON lines here, exit")
     ap.add_argument("--bytes", type=int, default=workloads.HEADLINE["bytes_per_rank"],
@@ -787,13 +789,19 @@ def main():
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],
     }
+    legs = set(args.extras.split(","))
     if not args.no_extras and world == 1:
-        line["direct"] = run_direct(args)
-        line["alltoall"] = run_alltoall(args)
-        line["small_messages"] = run_small(args)
-        line["batched"] = run_batched(args)
-        line["served"] = run_served(args)
-        line["served_direct"] = run_served(args, modes=("plain", "streams", "batch"), protocol="auto")
+        if "direct" in legs:
+            line["direct"] = run_direct(args)
+        if "alltoall" in legs:
+            line["alltoall"] = run_alltoall(args)
+        if "small" in legs:
+            line["small_messages"] = run_small(args)
+        if "batched" in legs:
+            line["batched"] = run_batched(args)
+        if "served" in legs:
+            line["served"] = run_served(args)
+            line["served_direct"] = run_served(args, modes=("plain", "streams", "batch"), protocol="auto")
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(k, args.proto, w["nchannels"], w["chunk_steps"],
                                             w["seed"])
