@@ -640,6 +640,10 @@ static bool useStaged(const CallSpec& cs, const DirectGeom& g) {
          g.units * 16ull >= cs.c->stagedMinBytes;
 }
 static int stagedStages(int k) { return std::min(k <= 4 ? 2 : 3, directStagedMaxStages()); }
+// Up to 3 vranks a tile's loads are too few bytes to keep HBM busy from one
+// CTA per SM (k = 2: 3.3 TB/s); two CTAs per SM, each with half the shared
+// memory, double them (k = 2: 5.2 TB/s).
+static int stagedCtasPerSM(int k) { return k <= 3 ? 2 : 1; }
 
 static vResult_t launchStaged(CallSpec& cs, const DirectGeom& g, DirectArgs& a) {
   vcomm* c = cs.c;
@@ -657,7 +661,8 @@ static vResult_t launchStaged(CallSpec& cs, const DirectGeom& g, DirectArgs& a) 
     }
   }
   const int stages = stagedStages(k);
-  const unsigned tile = directStagedTile(k, stages, kStagedSmemMax);
+  const int perSM = stagedCtasPerSM(k);
+  const unsigned tile = directStagedTile(k, stages, kStagedSmemMax / perSM);
   const size_t smem = directStagedSmem(k, stages, tile);
   if (smem > (size_t)kStagedSmemMax) return vInternalError;
   a.stages = stages;
@@ -668,7 +673,7 @@ static vResult_t launchStaged(CallSpec& cs, const DirectGeom& g, DirectArgs& a) 
   // tiles never straddle ReduceScatter blocks (g.units counts all k blocks)
   const unsigned long long nblk = cs.kcoll == kReduceScatter ? (unsigned long long)k : 1ull;
   const unsigned long long ntiles = nblk * ((g.units / nblk * 16ull + tile - 1) / tile);
-  const long long grid = std::max<long long>(1, std::min<long long>((long long)ntiles, c->nsm));
+  const long long grid = std::max<long long>(1, std::min<long long>((long long)ntiles, (long long)perSM * c->nsm));
   void* args[] = {(void*)&a};
   VC_TRY(cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(directStagedThreads()), args, smem, cs.stream));
   c->last = cs.plan;
