@@ -616,11 +616,11 @@ def run_served(args, rate=None, nreq=None, modes=("batch", "plain"), protocol="f
 
 # ------------------------------------------------------------------ protocol sweep
 
-def run_sweep(path):
+def run_sweep(path, protos=("simple", "ll", "ll128", "cluster")):
     """Ring AllReduce on 8 vranks: per-rank sizes 1 KiB..256 MiB (powers of
-    4) x fp32 / bf16 x Simple / LL / LL128 (and the cluster protocol up to
-    4 MiB) x 1 / 4 / 16 / 32 channels, N(0,1) values; one JSON line per point
-    (median of timed launches)."""
+    4) x fp32 / bf16 x the given protocols (default Simple / LL / LL128 and
+    the cluster protocol up to 4 MiB) x 1 / 4 / 16 / 32 channels, N(0,1)
+    values; one JSON line per point (median of timed launches)."""
     import torch
 
     from paper_2507_04786_b300 import Comm
@@ -638,7 +638,7 @@ def run_sweep(path):
                 n = S // es
                 xs = [x[:n] for x in base[dt]]
                 ys = [y[:n] for y in outs[dt]]
-                for proto in ("simple", "ll", "ll128", "cluster"):
+                for proto in protos:
                     if proto == "cluster" and S > workloads.SWEEP_CLUSTER_MAX:
                         continue
                     for C in workloads.SWEEP_CHANNELS:
@@ -713,6 +713,8 @@ def main():
                     help="the extra legs to run, comma separated (profiling captures run one)")
     ap.add_argument("--sweep", default=None,
                     help="run the protocol x size x channel sweep, write JSON lines here, exit")
+    ap.add_argument("--sweep-protos", default="simple,ll,ll128,cluster",
+                    help="protocols of the sweep, comma separated (direct too)")
     ap.add_argument("--bytes", type=int, default=workloads.HEADLINE["bytes_per_rank"],
                     help="bytes per vrank (default: the headline's 256 MiB; smaller sizes are "
                          "for profiling captures only)")
@@ -720,7 +722,7 @@ def main():
     args.warmup = max(args.warmup, 3)
 
     if args.sweep:
-        for r in run_sweep(args.sweep):
+        for r in run_sweep(args.sweep, tuple(args.sweep_protos.split(","))):
             print(json.dumps(r))
         return
 
