@@ -47,6 +47,10 @@ def busbw(S, k, seconds):
     return S / seconds * 2 * (k - 1) / k / 1e9
 
 
+# B300 nominal HBM3e bandwidth (GB/s), reported beside the measured peak
+NOMINAL_HBM_GBS = 7700.0
+
+
 def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -314,7 +318,8 @@ def run_direct(args):
             "algbw_GBps": round(S / (ms / 1e3) / 1e9, 2),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "algorithmic_bytes_per_launch": alg,
-                         "peak_source": peak_kind},
+                         "peak_source": peak_kind,
+                         "nominal_frac": round(achieved / NOMINAL_HBM_GBS, 4)},
             "equals_simple": bool(same), "clocks": clk.summary(), "status": err}
 
 
@@ -354,7 +359,8 @@ def run_alltoall(args):
             "algbw_GBps": round(S / (ms / 1e3) / 1e9, 2),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "algorithmic_bytes_per_launch": alg,
-                         "peak_source": peak_kind},
+                         "peak_source": peak_kind,
+                         "nominal_frac": round(achieved / NOMINAL_HBM_GBS, 4)},
             "sampled_blocks_exact": bool(ok), "status": err}
 
 
@@ -785,7 +791,8 @@ def main():
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": profiled_traffic(wname, args.proto),
-                     "algorithmic_bytes_per_launch": alg, "peak_source": peak_kind},
+                     "algorithmic_bytes_per_launch": alg, "peak_source": peak_kind,
+                     "nominal_frac": round(achieved / NOMINAL_HBM_GBS, 4)},
         "e2e": {"value": round(world * busbw(S, k, e2e_ms / 1e3), 3), "unit": "GB/s",
                 "h2d_bytes_per_step": k * S, "d2h_bytes_per_step": k * S},
         "gpu_launches": r["launches"],
