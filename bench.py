@@ -622,14 +622,14 @@ def run_served(args, rate=None, nreq=None, modes=("batch", "plain"), protocol="f
 
 # ------------------------------------------------------------------ protocol sweep
 
-def run_sweep(path, protos=("simple", "ll", "ll128", "cluster")):
-    """Ring AllReduce on 8 vranks: per-rank sizes 1 KiB..256 MiB (powers of
+def run_sweep(path, protos=("simple", "ll", "ll128", "cluster"), algo="ring"):
+    """AllReduce on 8 vranks (ring, or the double binary tree): per-rank sizes 1 KiB..256 MiB (powers of
     4) x fp32 / bf16 x the given protocols (default Simple / LL / LL128 and
     the cluster protocol up to 4 MiB) x 1 / 4 / 16 / 32 channels, N(0,1)
     values; one JSON line per point (median of timed launches)."""
     import torch
 
-    from paper_2507_04786_b300 import Comm
+    from paper_2507_04786_b300 import Comm, VcommError
     k = 8
     top = max(workloads.SWEEP_BYTES)
     base = {dt: [torch.randn(top // es, device="cuda").to(t) for _ in range(k)]
@@ -649,8 +649,13 @@ def run_sweep(path, protos=("simple", "ll", "ll128", "cluster")):
                         continue
                     for C in workloads.SWEEP_CHANNELS:
                         comm.set_plan(nchannels=C, chunk_steps=1)
-                        for _ in range(2):
-                            comm.all_reduce(xs, ys, algo="ring", proto=proto)
+                        try:
+                            for _ in range(2):
+                                comm.all_reduce(xs, ys, algo=algo, proto=proto)
+                        except VcommError as e:      # e.g. more CTAs than can be co-resident
+                            f.write(json.dumps({"dtype": dt, "bytes_per_rank": S, "algo": algo, "proto": proto,
+                                                "nchannels": C, "refused": e.name}) + "\n")
+                            continue
                         torch.cuda.synchronize()
                         reps = 5 if S >= (16 << 20) else 20
                         ts = []
@@ -658,13 +663,13 @@ def run_sweep(path, protos=("simple", "ll", "ll128", "cluster")):
                             e0 = torch.cuda.Event(enable_timing=True)
                             e1 = torch.cuda.Event(enable_timing=True)
                             e0.record()
-                            comm.all_reduce(xs, ys, algo="ring", proto=proto)
+                            comm.all_reduce(xs, ys, algo=algo, proto=proto)
                             e1.record()
                             e1.synchronize()
                             ts.append(e0.elapsed_time(e1))
                         ms = float(np.median(ts))
                         alg = algorithmic_bytes(k, S, proto)
-                        row = {"dtype": dt, "bytes_per_rank": S, "proto": proto, "nchannels": C,
+                        row = {"dtype": dt, "bytes_per_rank": S, "algo": algo, "proto": proto, "nchannels": C,
                                "us": round(ms * 1e3, 2), "busbw_GBps": round(busbw(S, k, ms / 1e3), 2),
                                "hbm_frac": round(alg / (ms / 1e3) / 1e9 / measured_peak()[0], 4)}
                         rows.append(row)
@@ -721,6 +726,8 @@ def main():
                     help="run the protocol x size x channel sweep, write JSON lines here, exit")
     ap.add_argument("--sweep-protos", default="simple,ll,ll128,cluster",
                     help="protocols of the sweep, comma separated (direct too)")
+    ap.add_argument("--sweep-algo", default="ring", choices=["ring", "tree"],
+                    help="algorithm of the sweep")
     ap.add_argument("--bytes", type=int, default=workloads.HEADLINE["bytes_per_rank"],
                     help="bytes per vrank (default: the headline's 256 MiB; smaller sizes are "
                          "for profiling captures only)")
@@ -728,7 +735,7 @@ def main():
     args.warmup = max(args.warmup, 3)
 
     if args.sweep:
-        for r in run_sweep(args.sweep, tuple(args.sweep_protos.split(","))):
+        for r in run_sweep(args.sweep, tuple(args.sweep_protos.split(",")), args.sweep_algo):
             print(json.dumps(r))
         return
 
