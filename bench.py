@@ -685,6 +685,78 @@ def run_sweep(path, protos=("simple", "ll", "ll128", "cluster"), algo="ring"):
     return [best[k_] for k_ in sorted(best)]
 
 
+COLL_SWEEP_BYTES = [workloads.KiB * 4 ** i for i in range(1, 9)] + [128 << 20]
+
+
+def coll_bytes(coll, k, S, proto):
+    """System-wide algorithmic bytes of one collective, S = the larger
+    per-rank buffer (ReduceScatter sendbuf, AllGather recvbuf): user bytes
+    plus 2(k-1)S x f of FIFO writes and reads (f = 0 without a FIFO)."""
+    f = FIFO_FACTOR[proto]
+    user = {"allreduce": 2 * k * S, "reducescatter": k * S + S, "allgather": S + k * S,
+            "broadcast": S + k * S, "reduce": k * S + S}[coll]
+    return user + (4 if coll == "allreduce" else 2) * (k - 1) * S * f
+
+
+def run_coll_sweep(path, protos=("direct", "simple"), nchannels=16):
+    """ReduceScatter, AllGather, Broadcast (root 0) and Reduce (root 0) on 8
+    and 16 vranks, fp16 and int32 (sum), per-rank sizes 4 KiB..64 MiB
+    (powers of 4) and 128 MiB, ring, the given protocols at `nchannels`
+    channels; one JSON line per point (median of launches timed alone)."""
+    import torch
+
+    from paper_2507_04786_b300 import Comm
+    top = max(COLL_SWEEP_BYTES)
+    rows = []
+    with open(path, "w") as f:
+        for k in (8, 16):
+            comm = Comm(k, nchannels)
+            comm.set_plan(nchannels=nchannels, chunk_steps=1)
+            for dt, t in (("fp16", torch.float16), ("int32", torch.int32)):
+                es = torch.tensor([], dtype=t).element_size()
+                big = [torch.ones(top // es, device="cuda", dtype=t) for _ in range(k)]
+                out = [torch.empty(top // es, device="cuda", dtype=t) for _ in range(k)]
+                for S in COLL_SWEEP_BYTES:
+                    n = S // es
+                    xs, ys = [x[:n] for x in big], [y[:n] for y in out]
+                    blk = [y[:n // k] for y in out]
+                    for coll in ("reducescatter", "allgather", "broadcast", "reduce"):
+                        for proto in protos:
+                            if coll == "reducescatter":
+                                call = lambda: comm.reduce_scatter(xs, blk, algo="ring", proto=proto)
+                            elif coll == "allgather":
+                                call = lambda: comm.all_gather([x[:n // k] for x in xs], ys, algo="ring",
+                                                               proto=proto)
+                            elif coll == "broadcast":
+                                call = lambda: comm.broadcast(xs, ys, root=0, algo="ring", proto=proto)
+                            else:
+                                call = lambda: comm.reduce(xs, [ys[0]] + [None] * (k - 1), root=0,
+                                                           algo="ring", proto=proto)
+                            for _ in range(2):
+                                call()
+                            torch.cuda.synchronize()
+                            ts = []
+                            for _ in range(5 if S >= (16 << 20) else 20):
+                                e0 = torch.cuda.Event(enable_timing=True)
+                                e1 = torch.cuda.Event(enable_timing=True)
+                                e0.record()
+                                call()
+                                e1.record()
+                                e1.synchronize()
+                                ts.append(e0.elapsed_time(e1))
+                            ms = float(np.median(ts))
+                            alg = coll_bytes(coll, k, S, proto)
+                            row = {"coll": coll, "nranks": k, "dtype": dt, "bytes_per_rank": S, "proto": proto,
+                                   "nchannels": nchannels, "us": round(ms * 1e3, 2),
+                                   "hbm_frac": round(alg / (ms / 1e3) / 1e9 / measured_peak()[0], 4)}
+                            rows.append(row)
+                            f.write(json.dumps(row) + "\n")
+                del big, out
+            assert comm.async_error() == "vSuccess"
+            comm.destroy()
+    return rows
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -728,6 +800,9 @@ def main():
                     help="protocols of the sweep, comma separated (direct too)")
     ap.add_argument("--sweep-algo", default="ring", choices=["ring", "tree"],
                     help="algorithm of the sweep")
+    ap.add_argument("--sweep-colls", default=None,
+                    help="sweep ReduceScatter / AllGather / Broadcast / Reduce (direct and Simple), "
+                         "write JSON lines here, exit")
     ap.add_argument("--bytes", type=int, default=workloads.HEADLINE["bytes_per_rank"],
                     help="bytes per vrank (default: the headline's 256 MiB; smaller sizes are "
                          "for profiling captures only)")
@@ -737,6 +812,9 @@ def main():
     if args.sweep:
         for r in run_sweep(args.sweep, tuple(args.sweep_protos.split(",")), args.sweep_algo):
             print(json.dumps(r))
+        return
+    if args.sweep_colls:
+        run_coll_sweep(args.sweep_colls)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
