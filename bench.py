@@ -47,8 +47,9 @@ def busbw(S, k, seconds):
     return S / seconds * 2 * (k - 1) / k / 1e9
 
 
-# B300 nominal HBM3e bandwidth (GB/s), reported beside the measured peak
-NOMINAL_HBM_GBS = 7700.0
+# B300 nominal HBM3e bandwidth (GB/s): the ~8 TB/s the part is quoted at,
+# reported beside the measured copy bandwidth as a second denominator
+NOMINAL_HBM_GBS = 8000.0
 
 
 def measured_peak():
@@ -60,13 +61,23 @@ def measured_peak():
     return 6400.0, "fallback"
 
 
+# the sources the reducing collective kernel (kReduceColl) is compiled from
+KERNEL_SOURCES = ("include/vcomm.h", "paper_2507_04786_b300/csrc/vcomm_device.cuh",
+                  "paper_2507_04786_b300/csrc/vcomm_internal.h",
+                  "paper_2507_04786_b300/csrc/vcomm_reduce_inst.cu")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2507_04786_b300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, name), "rb") as f:
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, name), "rb") as f:
             h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
+
+
+TRAFFIC_SOURCE = ("dram__bytes_read.sum + dram__bytes_write.sum per launch from a committed one-pass "
+                  "ncu capture of the full-size launch (profiles/dram_traffic.txt), used only while "
+                  "the kernel's sources are unchanged since; null otherwise")
 
 
 def profiled_traffic(workload, proto):
@@ -140,36 +151,94 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ CPU oracle leg
 
-def cpu_oracle_run(k, S_sample, proto, nch, chunk_steps, seed, reps=1):
-    """Time the CPU oracle (single thread) on a bounded sample of the workload."""
+def oracle_all_reduce(xs, dtype, op, nch, chunk, threads=1):
+    """The CPU oracle's ring AllReduce of the whole buffers.  threads > 1:
+    the same oracle function on every channel's slice, one host thread per
+    slice (channels are independent and a slice run on one channel replays
+    exactly that channel's loops, so the result is bit-identical; the oracle
+    releases the interpreter lock while it runs)."""
+    import oracle
+    if threads <= 1:
+        return oracle.all_reduce(xs, dtype, op, nch, chunk)
+    from concurrent.futures import ThreadPoolExecutor
+    n = xs[0].size
+    es = oracle.ESIZE[dtype]
+    outs = [np.empty_like(x) for x in xs]
+
+    def one(ch):
+        lo, ln = oracle.channel_range(n, es, nch, ch)
+        if ln == 0:
+            return
+        part = oracle.all_reduce([x[lo:lo + ln] for x in xs], dtype, op, 1, chunk)
+        for o, p_ in zip(outs, part):
+            o[lo:lo + ln] = p_
+
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(one, range(nch)))
+    return outs
+
+
+def oracle_threads(nch):
+    return max(1, min(os.cpu_count() or 1, nch))
+
+
+def cpu_oracle_run(k, S_sample, proto, nch, chunk_steps, seed, reps=1, threads=1, xs=None):
+    """Time the CPU oracle on a bounded sample of the workload (fp32 sum)."""
     import oracle
     n = S_sample // 4
-    xs = inputs.workload(seed, k, n, "fp32", "normal")
+    if xs is None:
+        xs = inputs.workload(seed, k, n, "fp32", "normal")
     chunk = oracle.chunk_units(proto, 4, chunk_steps)
     times = []
     for _ in range(reps):
         t0 = time.perf_counter()
-        oracle.all_reduce(xs, "fp32", "sum", nch, chunk)
+        oracle_all_reduce(xs, "fp32", "sum", nch, chunk, threads)
         times.append(time.perf_counter() - t0)
     return times
 
 
-def cpu_baseline(k, proto, nch, chunk_steps, seed, target_s=20.0):
-    """Bounded sample: grow the per-vrank size until one oracle run takes a
-    few seconds, then report bus GB/s on that sample."""
-    S = 4 << 20
-    t = cpu_oracle_run(k, S, proto, nch, chunk_steps, seed)[0]
-    while t < target_s / 4 and S < (256 << 20):
-        S *= 2
-        t = cpu_oracle_run(k, S, proto, nch, chunk_steps, seed)[0]
-    return {"value": round(busbw(S, k, t), 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+def cpu_baseline(k, proto, nch, chunk_steps, seed):
+    """The CPU oracle on the host cores, on a bounded sample: the headline
+    AllReduce (k vranks, 37 channels) at 64 MiB per vrank, once with one
+    thread per channel slice on all cores and once single-threaded (the same
+    fold order, the same bits), plus the exactly-summable 4-vrank case
+    (1,048,576 fp32 integers per vrank, Simple, one channel), reported as bus
+    GB/s."""
+    S = 64 << 20
+    xs = inputs.workload(seed, k, S // 4, "fp32", "normal")
+    thr = oracle_threads(nch)
+    t_all = min(cpu_oracle_run(k, S, proto, nch, chunk_steps, seed, reps=2, threads=thr, xs=xs))
+    t_one = cpu_oracle_run(k, S, proto, nch, chunk_steps, seed, reps=1, threads=1, xs=xs)[0]
+    del xs
+    import oracle
+    e = workloads.EXACT
+    n1 = e["count"]
+    x1 = inputs.workload(e["seed"], e["nranks"], n1, "fp32", "int", lo=-1000, hi=1000)
+    ch1 = oracle.chunk_units(e["proto"], 4, 1)
+    t1 = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        oracle.all_reduce(x1, "fp32", "sum", e["nchannels"], ch1)
+        t1.append(time.perf_counter() - t0)
+    t1 = min(t1)
+    return {"value": round(busbw(S, k, t_all), 4), "unit": "GB/s", "cores": thr,
+            "host_cores": os.cpu_count(), "kind": "oracle",
             "sample": f"{k} vranks x {S >> 20} MiB fp32 ring AllReduce ({proto}, {nch} channels), "
-                      f"one single-threaded oracle run of {t:.2f} s"}
+                      f"one oracle thread per channel slice on {thr} of {os.cpu_count()} host "
+                      f"cores, best of 2 runs ({t_all:.2f} s)",
+            "single_thread": {"value": round(busbw(S, k, t_one), 4), "unit": "GB/s", "cores": 1,
+                              "seconds": round(t_one, 3)},
+            "exact_4vr_1Mi": {"workload": e["name"], "seconds": round(t1, 4), "cores": 1,
+                              "algbw_GBps": round(n1 * 4 / t1 / 1e9, 4),
+                              "busbw_GBps": round(busbw(n1 * 4, e["nranks"], t1), 4)}}
 
 
 # ------------------------------------------------------------------ GPU leg
 
-def run_gpu(args, rank, world):
+_HEADLINE_INPUTS = {}   # the headline's inputs, drawn once per process
+
+
+def run_gpu(args, rank, world, proto=None, steps=None, e2e=True):
     import torch
 
     from paper_2507_04786_b300 import Comm
@@ -177,10 +246,15 @@ def run_gpu(args, rank, world):
     w = workloads.HEADLINE
     k, S = w["nranks"], args.bytes
     n = S // 4
-    proto = args.proto
+    proto = proto or args.proto
+    steps = steps or args.steps
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    xs = inputs.workload(w["seed"] + rank, k, n, "fp32", w["dist"])
+    key = (w["seed"] + rank, k, n)
+    if key not in _HEADLINE_INPUTS:
+        _HEADLINE_INPUTS.clear()
+        _HEADLINE_INPUTS[key] = inputs.workload(w["seed"] + rank, k, n, "fp32", w["dist"])
+    xs = _HEADLINE_INPUTS[key]
     host = [torch.from_numpy(x).pin_memory() for x in xs]
     sends = [h.to(dev) for h in host]
     recvs = [torch.empty_like(s) for s in sends]
@@ -199,14 +273,14 @@ def run_gpu(args, rank, world):
 
     barrier(world)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
+           for _ in range(steps)]
     with ClockSampler(dev.index) as clk:
         torch.cuda.synchronize()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         step()   # untimed: the GPU sat idle while the sampler started
         t0.record(stream)
-        for i in range(args.steps):
+        for i in range(steps):
             evs[i][0].record(stream)
             step()
             evs[i][1].record(stream)
@@ -216,6 +290,11 @@ def run_gpu(args, rank, world):
     launch_ms = [a.elapsed_time(b) for a, b in evs]
     if comm.async_error() != "vSuccess":
         raise RuntimeError(comm.async_error())
+    res = {"ms_per_step": total_ms / steps, "launch_ms": float(np.mean(launch_ms)),
+           "clocks": clk.summary(), "launches": steps, "S": S, "k": k, "proto": proto}
+    if not e2e:
+        comm.destroy()
+        return res
 
     # end to end: pinned host inputs -> device, AllReduce, results -> host.
     # Every step copies its own inputs in and its own result out inside the
@@ -223,7 +302,7 @@ def run_gpu(args, rank, world):
     # of step i + 1 (one copy engine) run while step i's result comes back
     # (the other engine); a set is reused only after step i - 2 has read its
     # inputs and its result has left the device.
-    e2e_steps = max(2, min(args.steps, 10))
+    e2e_steps = max(2, min(steps, 10))
     outs = [torch.empty_like(h).pin_memory() for h in host]
     sets = [(sends, recvs), ([torch.empty_like(x) for x in sends], [torch.empty_like(x) for x in sends])]
     s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
@@ -264,9 +343,8 @@ def run_gpu(args, rank, world):
     if not torch.equal(outs[0].view(torch.int32), want[0].view(torch.int32)):
         raise RuntimeError("end-to-end result differs from the device result")
     comm.destroy()
-    return {"ms_per_step": total_ms / args.steps, "launch_ms": float(np.mean(launch_ms)),
-            "e2e_ms": e2e_ms, "clocks": clk.summary(), "launches": args.steps,
-            "S": S, "k": k, "proto": proto}
+    res["e2e_ms"] = e2e_ms
+    return res
 
 
 # ------------------------------------------------------------------ direct leg
@@ -757,6 +835,28 @@ def run_coll_sweep(path, protos=("direct", "simple"), nchannels=16):
     return rows
 
 
+def headline_leg(args, rank, world, proto, wname):
+    """The headline workload with another FIFO protocol (same channels, same
+    chunk), timed the same way on the launching stream: its own roofline
+    against the bytes that protocol must move."""
+    r = run_gpu(args, rank, world, proto=proto, steps=max(5, args.steps // 2), e2e=False)
+    ms = reduce_max(world, r["ms_per_step"])
+    launch_ms = reduce_max(world, r["launch_ms"])
+    k, S = r["k"], r["S"]
+    peak, peak_kind = measured_peak()
+    alg = algorithmic_bytes(k, S, proto)
+    achieved = alg / (launch_ms / 1e3) / 1e9
+    return {"proto": proto, "value": round(job_value(world, S, k, ms), 3), "unit": "GB/s",
+            "ms_per_step": round(ms, 4), "steps": r["launches"],
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4),
+                         "traffic": profiled_traffic(wname, proto), "traffic_source": TRAFFIC_SOURCE,
+                         "algorithmic_bytes_per_launch": alg, "peak_source": peak_kind,
+                         "nominal_peak": NOMINAL_HBM_GBS,
+                         "nominal_frac": round(achieved / NOMINAL_HBM_GBS, 4)},
+            "clocks": r["clocks"]}
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -789,6 +889,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--proto", default="simple", choices=["simple", "ll", "ll128", "direct"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
+    ap.add_argument("--no-ll128", action="store_true",
+                    help="skip the LL128 leg of the headline workload")
     ap.add_argument("--serve-requests", type=int, default=workloads.SERVED["bench_requests"],
                     help="requests of the served leg (the full stream is 100000)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and served legs")
@@ -839,19 +941,22 @@ def main():
         if rank != 0:
             return
         reps = max(1, args.warmup) + args.steps
-        # bounded sample: 8 MiB per vrank, one oracle AllReduce per step
+        # bounded sample: 8 MiB per vrank, one oracle AllReduce per step, one
+        # oracle thread per channel slice on the host cores
         S_s = 8 << 20
+        thr = oracle_threads(w["nchannels"])
         times = cpu_oracle_run(k, S_s, args.proto, w["nchannels"], w["chunk_steps"], w["seed"],
-                               reps=reps)[args.warmup:]
+                               reps=reps, threads=thr)[args.warmup:]
         t = float(np.mean(times))
         v = busbw(S_s, k, t)
         line = {"metric": metric, "value": round(v, 4), "unit": "GB/s", "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1e3, 3),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic", "impl": "reference", "config": config,
-                "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                                 "sample": f"{k} vranks x {S_s >> 20} MiB per step, single-threaded "
-                                           f"CPU oracle"},
+                "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": thr,
+                                 "host_cores": os.cpu_count(), "kind": "oracle",
+                                 "sample": f"{k} vranks x {S_s >> 20} MiB per step, CPU oracle with "
+                                           f"one thread per channel slice on {thr} host cores"},
                 "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -876,13 +981,17 @@ def main():
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": profiled_traffic(wname, args.proto),
+                     "traffic_source": TRAFFIC_SOURCE,
                      "algorithmic_bytes_per_launch": alg, "peak_source": peak_kind,
+                     "nominal_peak": NOMINAL_HBM_GBS,
                      "nominal_frac": round(achieved / NOMINAL_HBM_GBS, 4)},
         "e2e": {"value": round(world * busbw(S, k, e2e_ms / 1e3), 3), "unit": "GB/s",
                 "h2d_bytes_per_step": k * S, "d2h_bytes_per_step": k * S},
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],
     }
+    if args.proto == "simple" and not args.no_ll128:
+        line["ll128"] = headline_leg(args, rank, world, "ll128", wname)
     legs = set(args.extras.split(","))
     if not args.no_extras and world == 1:
         if "direct" in legs:

@@ -4,9 +4,13 @@
  * A communicator holds N virtual ranks ("vranks") on ONE GPU.  Each vrank has
  * its own caller-owned send and receive buffers in device memory; between two
  * vranks data moves only through per-connection FIFOs that the communicator
- * owns, in the same HBM.  Collectives run as one persistent kernel per call:
- * one CTA per (vrank, channel) executes the paper's primitive step tables with
- * flag-polled synchronisation between CTAs.
+ * owns, in the same HBM.  With the paper's protocols (Simple, LL, LL128) a
+ * collective runs as one persistent kernel per call: one CTA per (vrank,
+ * channel) executes the paper's primitive step tables with flag-polled
+ * synchronisation between CTAs.  Auto picks, on the ring, the direct protocol
+ * (vProtoDirect below): a plain kernel with no FIFO and no flags that folds
+ * each 16-byte unit's whole ring chain in the same order, so its results are
+ * the Simple protocol's bit for bit.
  *
  * Paper: "Demystifying NCCL: An In-depth Analysis of GPU Communication
  * Protocols and Algorithms" (arXiv 2507.04786).  Section / table cited per call.
@@ -22,8 +26,9 @@
  *    CTAs to be co-resident) are returned at once and nothing is enqueued.
  *  - Device-side failures (a flag wait that exceeded the deadline, an abort)
  *    end the kernel early; they are reported by vcommGetAsyncError.  The
- *    kernels never trap.  After such a failure the communicator must be
- *    destroyed.
+ *    kernels never trap.  After such a failure the communicator returns the
+ *    error from every later call until it is reset (vcommReset, which makes it
+ *    usable again) or destroyed; vcommAbortPending ends in-flight calls first.
  *  - count == 0 is a successful no-op.
  *  - Calls on one communicator must be serialised on one stream (like NCCL
  *    calls on one communicator); calls on different communicators may overlap.
@@ -366,12 +371,16 @@ vResult_t vServeDestroy(vserve_t server);
  *    limited (data streams through the FIFOs).
  *  - The first call on a device looks up the array's device address (with
  *    that device current); make that first call before any stream capture.
+ *    The address is kept for the life of the process, so calls must not span
+ *    a cudaDeviceReset of the device.  Device ordinals up to 63.
  *  - Every call shares the one array and clears its counters first, so calls
  *    that overlap on the GPU (other streams, other host threads) race and
  *    corrupt each other: serialise them.
  *  - deviceStatus: NULL, or caller-owned device memory of 4 ints that the call
  *    sets to {code, rank, channel, where} of a device-side failure (a flag wait
- *    past its 5 s deadline), or to zeros on success.
+ *    past its 5 s deadline), or to zeros on success.  With NULL a device-side
+ *    failure is recorded only inside the library's array, where the caller
+ *    cannot read it: pass a status buffer to observe timeouts.
  * Other arguments and in-place rules as in vAllReduce. */
 #define VCOMM_NOALLOC_MAX_CONNS 32
 #define VCOMM_NOALLOC_SCRATCH_BYTES 8398080

@@ -41,8 +41,13 @@ static __device__ __align__(256) unsigned char gNoAllocScratch[kNaTotal];
 
 namespace {
 
+// The device address of gNoAllocScratch, looked up once per device ordinal and
+// kept for the life of the process.  cudaDeviceReset destroys the context
+// that holds it (the module is loaded again, maybe elsewhere), so calls must
+// not span a reset of the device.
+constexpr int kNaMaxDevices = 64;
 std::mutex gNaMu;
-void* gNaBase[VCOMM_MAX_RANKS];   // per device ordinal: device address of gNoAllocScratch
+void* gNaBase[kNaMaxDevices];
 
 // every call clears what must start at zero (counters, error words) and
 // rebuilds the connection table: the previous call's contents are stale
@@ -89,10 +94,11 @@ extern "C" vResult_t vAllReduceNoAlloc(const void* const* sendbufs, void* const*
 
   // set-up, once per device, with that device current: the scratch's address
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= VCOMM_MAX_RANKS) {
+  if (cudaGetDevice(&dev) != cudaSuccess) {
     (void)cudaGetLastError();
     return vCudaError;
   }
+  if (dev < 0 || dev >= kNaMaxDevices) return vUnsupported;
   unsigned char* base = nullptr;
   {
     std::lock_guard<std::mutex> lk(gNaMu);

@@ -48,3 +48,21 @@ def test_reference_arm_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+@pytest.mark.parametrize("dtype,nch,n,proto", [("fp32", 37, 300_007, "simple"), ("bf16", 5, 123_457, "ll128"),
+                                               ("fp32", 3, 70_001, "ll")])
+def test_all_cores_oracle_equals_single_thread(dtype, nch, n, proto):
+    """The CPU baseline's all-cores form (one oracle run per channel slice, on
+    its own thread) gives the oracle's single-threaded bits."""
+    import numpy as np
+
+    import oracle
+    from paper_2507_04786_b300 import inputs
+    xs = inputs.workload(3, 8, n, dtype, "normal")
+    es = oracle.ESIZE[dtype]
+    chunk = oracle.chunk_units(proto, es, 1, {"simple": 8192, "ll": 2048, "ll128": 2560}[proto])
+    one = bench.oracle_all_reduce(xs, dtype, "sum", nch, chunk, threads=1)
+    many = bench.oracle_all_reduce(xs, dtype, "sum", nch, chunk, threads=4)
+    for a, b in zip(one, many):
+        assert np.array_equal(a.view(np.uint8), b.view(np.uint8))

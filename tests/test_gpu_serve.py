@@ -1,11 +1,14 @@
-"""Serving (continuous batching) on the GPU.
+"""Serving (continuous batching) on the GPU, for every protocol.
 
-Requests of different collectives, vrank counts, dtypes and sizes are queued
-at once; the server admits them as gangs and budget free up.  Every result
-must equal the oracle for the plan the server reports, and requests re-run
-alone must give the same bits as in the mix.  While a batching server runs its
-kernel occupies the SMs, so inputs are prepared before it starts and outputs
-are read back with copies only.
+Requests of different collectives, vrank counts (2..16), dtypes and sizes are
+queued at once; the server admits them as gangs, lanes and budget free up.
+Every result must equal the oracle for the plan the server reports, and
+requests re-run alone must give the same bits as in the mix.  Each test runs
+with the paper's FIFO protocols (Simple, LL, LL128: the resident gangs'
+flag-polled path) and with Auto (the direct protocol), in the three modes
+(resident gangs, lanes of streams, one launch per request).  While a batching
+server runs its kernel occupies the SMs, so inputs are prepared before it
+starts and outputs are read back with copies only.
 """
 import time
 
@@ -23,6 +26,8 @@ torch = pytest.importorskip("torch")
 
 TYPESTR = {"fp32": "<f4", "bf16": "<i2", "fp16": "<f2", "int32": "<i4"}
 NPDT = {"fp32": np.float32, "bf16": np.uint16, "fp16": np.float16, "int32": np.int32}
+PROTOS = ["simple", "ll", "ll128", "auto"]
+MODES = ["batch", "streams", "plain"]
 
 
 class _Dev:
@@ -33,8 +38,10 @@ class _Dev:
                                          "data": (ptr, False), "version": 3}
 
 
-def read_back(ptr, n, dtype):
+def read_back(ptr, n, dtype, idx=None):
     t = torch.as_tensor(_Dev(ptr, n, dtype), device="cuda")
+    if idx is not None:
+        t = t[torch.from_numpy(idx).cuda()]
     return t.cpu().numpy().view(NPDT[dtype]).copy()
 
 
@@ -56,28 +63,34 @@ def make_requests(seed, nreq, kmax, lo, hi):
     return reqs
 
 
-def run_server(reqs, **cfg):
-    """Submit all requests at once, wait, return (outputs, plans, stats)."""
+def out_len(r):
+    return r["k"] * r["n"] if r["coll"] == "allgather" else r["n"]
+
+
+def run_server(reqs, proto="auto", sample=None, **cfg):
+    """Submit all requests at once, wait, return (outputs, plans, stats).
+    sample: per request None (read the whole output) or the indices to read."""
     sends = [[to_dev(x) for x in r["xs"]] for r in reqs]
     torch.cuda.synchronize()
+    sample = sample or [None] * len(reqs)
     srv = Server(**cfg)
     try:
-        tickets = [srv.submit(r["coll"], s, r["n"], r["dtype"], r["op"])
+        tickets = [srv.submit(r["coll"], s, r["n"], r["dtype"], r["op"], proto=proto)
                    for r, s in zip(reqs, sends)]
         t0 = time.time()
         results = {}
         while len(results) < len(tickets):
-            for r, t in zip(reqs, tickets):
+            for i, (r, t) in enumerate(zip(reqs, tickets)):
                 if t in results:
                     continue
                 st, lat, plan, bufs = srv.query(t)
                 if st in ("done", "failed"):
                     assert st == "done", (r["coll"], r["k"], st)
                     assert lat > 0
-                    rn = r["k"] * r["n"] if r["coll"] == "allgather" else r["n"]
-                    results[t] = ([read_back(bufs[q], rn, r["dtype"]) for q in range(r["k"])], plan)
+                    results[t] = ([read_back(bufs[q], out_len(r), r["dtype"], sample[i])
+                                   for q in range(r["k"])], plan)
                     srv.release(t)          # return the buffers to the budget at once
-            assert time.time() - t0 < 120, "requests did not finish"
+            assert time.time() - t0 < 180, "requests did not finish"
             time.sleep(0.001)
         outs = [results[t][0] for t in tickets]
         plans = [results[t][1] for t in tickets]
@@ -88,66 +101,174 @@ def run_server(reqs, **cfg):
     return outs, plans, stats
 
 
-def oracle_for(r, plan):
-    dt, C = r["dtype"], plan["nchannels"]
+_oracle_cache = {}
+
+
+def oracle_for(r, plan, slots=SMALL_SLOTS):
+    """The oracle's outputs for request r under `plan` (cached per request and
+    plan: the same request recurs across modes and protocols)."""
+    key = (id(r), plan["proto"], plan["nchannels"], plan["chunkSteps"],
+           None if slots is None else tuple(sorted(slots.items())))
+    if key in _oracle_cache:
+        return _oracle_cache[key]
+    dt, C, cs = r["dtype"], plan["nchannels"], plan["chunkSteps"]
     if r["coll"] == "allgather":
-        return oracle.all_gather(r["xs"], C, chunk_for(plan["proto"], dt, SMALL_SLOTS, 1, True))
-    ch = chunk_for(plan["proto"], dt, SMALL_SLOTS, 1)
-    if r["coll"] == "allreduce":
-        return oracle.all_reduce(r["xs"], dt, r["op"], C, ch)
-    return oracle.reduce_scatter(r["xs"], dt, r["op"], C, ch)
+        want = oracle.all_gather(r["xs"], C, chunk_for(plan["proto"], dt, slots, cs, True))
+    else:
+        ch = chunk_for(plan["proto"], dt, slots, cs)
+        if r["coll"] == "allreduce":
+            want = oracle.all_reduce(r["xs"], dt, r["op"], C, ch)
+        else:
+            want = oracle.reduce_scatter(r["xs"], dt, r["op"], C, ch)
+    _oracle_cache[key] = want
+    return want
 
 
-CFG = dict(max_ranks=8, mem_budget=256 << 20, big_gang_channels=4, small_gangs=4,
+CFG = dict(max_ranks=16, mem_budget=512 << 20, big_gang_channels=4, small_gangs=4,
            big_threshold=256 << 10, slot_bytes=SMALL_SLOTS, idle_timeout_sec=20.0)
 
+_reqs = {}
 
+
+def requests(name):
+    """The request sets, built once per session (their oracle results are cached)."""
+    if name not in _reqs:
+        _reqs[name] = {"mix": lambda: make_requests(5, 40, 16, 1024, 2 << 20),
+                       "budget": lambda: make_requests(9, 24, 16, 256 << 10, 1 << 20),
+                       "plain": lambda: make_requests(13, 20, 16, 1024, 4 << 20)}[name]()
+    return _reqs[name]
+
+
+def wanted_proto(plan_proto, asked):
+    """The protocol a request must run with: the one asked for, and Auto runs
+    the direct protocol."""
+    return ("direct" if asked == "auto" else asked) == plan_proto
+
+
+@pytest.mark.parametrize("proto", PROTOS)
 @pytest.mark.parametrize("mode", ["batch", "streams"])
-def test_serving_results_exact_and_same_alone(mode):
-    reqs = make_requests(5, 48, 8, 1024, 2 << 20)
-    outs, plans, stats = run_server(reqs, mode=mode, **CFG)
+def test_serving_results_exact_and_same_alone(mode, proto):
+    reqs = requests("mix")
+    outs, plans, stats = run_server(reqs, proto=proto, mode=mode, **CFG)
     assert stats["completed"] == len(reqs) and stats["failed"] == 0
     assert stats["maxInflightBytes"] <= CFG["mem_budget"]
     assert any(p["nchannels"] > 1 for p in plans)   # large requests spread over several channels
     for r, o, p in zip(reqs, outs, plans):
+        assert wanted_proto(p["proto"], proto), p
         want = oracle_for(r, p)
         for q in range(r["k"]):
-            assert_same(o[q], want[q], f"{r['coll']} k={r['k']} n={r['n']} rank {q}")
+            assert_same(o[q], want[q], f"{proto} {r['coll']} k={r['k']} n={r['n']} rank {q}")
     # the same requests alone, each on a fresh server, give the same bits
     for i in (0, 7, 19, 33):
-        o1, p1, _ = run_server([reqs[i]], mode=mode, **CFG)
+        o1, p1, _ = run_server([reqs[i]], proto=proto, mode=mode, **CFG)
         assert p1[0] == plans[i]
         for q in range(reqs[i]["k"]):
-            assert_same(o1[0][q], outs[i][q], f"request {i} alone vs in the mix, rank {q}")
+            assert_same(o1[0][q], outs[i][q], f"{proto} request {i} alone vs in the mix, rank {q}")
 
 
+@pytest.mark.parametrize("proto", PROTOS)
 @pytest.mark.parametrize("mode", ["batch", "streams"])
-def test_serving_respects_memory_budget(mode):
-    reqs = make_requests(9, 24, 8, 256 << 10, 1 << 20)
-    budget = 24 << 20
+def test_serving_respects_memory_budget(mode, proto):
+    reqs = requests("budget")
+    budget = 40 << 20
     cfg = dict(CFG, mem_budget=budget)
-    outs, plans, stats = run_server(reqs, mode=mode, **cfg)
+    outs, plans, stats = run_server(reqs, proto=proto, mode=mode, **cfg)
     assert stats["completed"] == len(reqs)
     assert 0 < stats["maxInflightBytes"] <= budget
-
-
-def test_plain_mode_exact():
-    reqs = make_requests(11, 16, 8, 1024, 1 << 20)
-    outs, plans, stats = run_server(reqs, mode="plain", **CFG)
-    assert stats["completed"] == len(reqs)
-    for r, o, p in zip(reqs, outs, plans):
+    for r, o, p in zip(reqs[:6], outs[:6], plans[:6]):
         want = oracle_for(r, p)
         for q in range(r["k"]):
-            assert_same(o[q], want[q], f"plain {r['coll']} k={r['k']} rank {q}")
+            assert_same(o[q], want[q], f"{proto} budget {r['coll']} k={r['k']} rank {q}")
 
 
-def test_streams_and_plain_give_the_same_bits():
+@pytest.mark.parametrize("proto", PROTOS)
+def test_plain_mode_exact(proto):
+    reqs = requests("plain")
+    outs, plans, stats = run_server(reqs, proto=proto, mode="plain", **CFG)
+    assert stats["completed"] == len(reqs)
+    for r, o, p in zip(reqs, outs, plans):
+        assert wanted_proto(p["proto"], proto), p
+        want = oracle_for(r, p)
+        for q in range(r["k"]):
+            assert_same(o[q], want[q], f"{proto} plain {r['coll']} k={r['k']} rank {q}")
+
+
+@pytest.mark.parametrize("proto", PROTOS)
+def test_streams_and_plain_give_the_same_bits(proto):
     """Plans depend on the request alone: the lanes of the streams mode and
     one launch per request produce identical results."""
-    reqs = make_requests(13, 20, 8, 1024, 4 << 20)
-    o1, p1, _ = run_server(reqs, mode="streams", **CFG)
-    o2, p2, _ = run_server(reqs, mode="plain", **CFG)
+    reqs = requests("plain")
+    o1, p1, _ = run_server(reqs, proto=proto, mode="streams", **CFG)
+    o2, p2, _ = run_server(reqs, proto=proto, mode="plain", **CFG)
     assert p1 == p2
     for i in range(len(reqs)):
         for q in range(reqs[i]["k"]):
-            assert_same(o1[i][q], o2[i][q], f"request {i} rank {q}")
+            assert_same(o1[i][q], o2[i][q], f"{proto} request {i} rank {q}")
+
+
+# ------------------------------------------------------------ the largest requests
+
+LARGE = [  # (collective, vranks, dtype, per-rank bytes S = the larger buffer)
+    ("allreduce", 16, "fp32", 128 << 20),
+    ("reducescatter", 13, "bf16", 64 << 20),
+    ("allgather", 16, "fp32", 128 << 20),
+    ("allreduce", 2, "bf16", 96 << 20),
+]
+
+
+@pytest.fixture(scope="module")
+def large_requests():
+    reqs = []
+    for i, (coll, k, dt, S) in enumerate(LARGE):
+        es = 4 if dt == "fp32" else 2
+        n = S // es if coll == "allreduce" else S // es // k
+        nin = k * n if coll == "reducescatter" else n
+        xs = inputs.workload(4000 + i, k, nin, dt, "normal")
+        reqs.append(dict(coll=coll, k=k, dtype=dt, n=n, xs=xs, op="sum"))
+    g = np.random.default_rng(17)
+    sample = []
+    for r in reqs:
+        m = out_len(r)
+        sample.append(np.unique(np.concatenate([g.integers(0, m, 4000), [0, 1, m // 2, m - 1]])))
+    return reqs, sample
+
+
+SERVE_SLOTS = {"simple": 256 << 10, "ll": 32 << 10, "ll128": 300 << 10}   # the server's defaults
+
+
+def sampled_want(r, plan, idx, q):
+    """Oracle values of rank q's output at `idx`, one element at a time."""
+    dt = r["dtype"]
+    if r["coll"] == "allgather":                 # block b of every output is rank b's input
+        n = r["n"]
+        return np.array([r["xs"][i // n][i % n] for i in idx], dtype=r["xs"][0].dtype)
+    if r["coll"] == "reducescatter":
+        return oracle.reduce_scatter_points(r["xs"], q, idx, dt, r["op"])
+    ch = chunk_for(plan["proto"], dt, SERVE_SLOTS, plan["chunkSteps"])
+    return oracle.all_reduce_points(r["xs"], idx, dt, r["op"], plan["nchannels"], ch, "ring")
+
+
+@pytest.mark.parametrize("proto", ["simple", "ll128", "auto"])
+@pytest.mark.parametrize("mode", MODES)
+def test_largest_requests_sampled(large_requests, mode, proto):
+    """Requests at the top of the served size range (up to 16 vranks x 128 MiB)
+    with the server's default FIFO slots, served together: sampled elements of
+    three ranks' outputs equal the oracle's one-element replay for the
+    reported plan, and every rank of an AllReduce / AllGather holds the same
+    sampled values."""
+    reqs, sample = large_requests
+    cfg = dict(CFG, mem_budget=16 << 30, big_threshold=4 << 20, slot_bytes=SERVE_SLOTS,
+               big_gang_channels=0, small_gangs=2)
+    outs, plans, stats = run_server(reqs, proto=proto, sample=sample, mode=mode, **cfg)
+    assert stats["completed"] == len(reqs) and stats["failed"] == 0
+    for r, o, p, idx in zip(reqs, outs, plans, sample):
+        assert wanted_proto(p["proto"], proto), p
+        same = r["coll"] != "reducescatter"
+        want = None
+        for q in sorted({0, r["k"] // 2, r["k"] - 1}):
+            if want is None or not same:
+                want = sampled_want(r, p, idx, q)
+            assert_same(o[q], want, f"{mode} {proto} {r['coll']} k={r['k']} rank {q}")
+        if same:
+            for q in range(1, r["k"]):
+                assert_same(o[q], o[0], f"{mode} {proto} {r['coll']} rank {q} vs 0")

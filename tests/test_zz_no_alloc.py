@@ -32,33 +32,55 @@ def _ptrs(ts):
     return a
 
 
-@pytest.mark.parametrize("dtype,op,dist", [("fp32", "sum", "normal"), ("bf16", "max", "normal")])
-def test_no_alloc_allreduce_matches_vallreduce(dtype, op, dist):
-    assert torch.cuda.is_available()
-    L = load_library()
-    k, C, n = 8, 4, 1_000_003
-    xs = inputs.workload(91, k, n, dtype, dist)
-    sends = [to_dev(x) for x in xs]
-    # the existing entry point with the same plan: ring, Simple, C channels,
-    # 64 KiB Simple slots, one slot per chunk
+def _reference(sends, k, C, dtype, op, inplace=()):
+    """vAllReduce with the same plan: ring, Simple, C channels, 64 KiB Simple
+    slots, one slot per chunk (in place for the ranks in `inplace`)."""
     comm = Comm(k, C, slot_bytes={"simple": 64 * 1024})
     comm.set_plan(nchannels=C, chunk_steps=1)
-    ref = [torch.empty_like(s) for s in sends]
-    comm.all_reduce(sends, ref, op=op, algo="ring", proto="simple")
+    srcs = [s.clone() for s in sends]
+    outs = [srcs[r] if r in inplace else torch.empty_like(s) for r, s in enumerate(sends)]
+    comm.all_reduce(srcs, outs, op=op, algo="ring", proto="simple")
     torch.cuda.synchronize()
     assert comm.async_error() == "vSuccess"
     comm.destroy()
-    want = [to_np(t, dtype) for t in ref]
+    return [to_np(t, dtype) for t in outs]
+
+
+# (vranks, channels, count, dtype, op, in-place ranks, pass a status buffer)
+CASES = [
+    (8, 4, 1_000_003, "fp32", "sum", (), True),
+    (8, 4, 1_000_003, "bf16", "max", (), True),
+    (1, 3, 70_001, "fp32", "sum", (), True),          # one vrank: a copy
+    (1, 1, 4_097, "bf16", "sum", (0,), True),         # one vrank in place
+    (5, 2, 333_337, "fp32", "sum", (0, 2, 4), True),  # in-place and out-of-place ranks mixed
+    (3, 5, 262_147, "fp16", "sum", (), True),         # odd channel split, ragged count
+    (4, 8, 500_001, "int32", "max", (1,), False),     # no status buffer
+    (6, 5, 123_457, "bf16", "sum", (), False),
+]
+
+
+@pytest.mark.parametrize("k,C,n,dtype,op,inplace,with_status", CASES)
+def test_no_alloc_allreduce_matches_vallreduce(k, C, n, dtype, op, inplace, with_status):
+    assert torch.cuda.is_available()
+    L = load_library()
+    dist = {"fp32": "normal", "bf16": "normal", "fp16": "uniform", "int32": "int"}[dtype]
+    kw = {"lo": -2 ** 20, "hi": 2 ** 20} if dtype == "int32" else {}
+    xs = inputs.workload(91 + k * 7 + C, k, n, dtype, dist, **kw)
+    sends = [to_dev(x) for x in xs]
+    want = _reference(sends, k, C, dtype, op, inplace)
 
     status = torch.full((4,), -1, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
-    for call in range(2):
-        outs = [torch.full_like(s, 7) for s in sends]
-        rc = L.vAllReduceNoAlloc(_ptrs(sends), _ptrs(outs), n, DTYPE_CODES[dtype], OP_CODES[op],
-                                 k, C, ctypes.c_void_p(status.data_ptr()), stream)
+    for call in range(2):       # two calls in a row share the scratch array
+        srcs = [s.clone() for s in sends]
+        outs = [srcs[r] if r in inplace else torch.full_like(s, 7) for r, s in enumerate(sends)]
+        st = ctypes.c_void_p(status.data_ptr()) if with_status else None
+        rc = L.vAllReduceNoAlloc(_ptrs(srcs), _ptrs(outs), n, DTYPE_CODES[dtype], OP_CODES[op],
+                                 k, C, st, stream)
         assert RESULTS[rc] == "vSuccess"
         torch.cuda.synchronize()
-        assert status.cpu().tolist() == [0, 0, 0, 0], f"call {call}"
+        if with_status:
+            assert status.cpu().tolist() == [0, 0, 0, 0], f"call {call}"
         for r in range(k):
             assert_same(to_np(outs[r], dtype), want[r], f"call {call} rank {r}")
 
