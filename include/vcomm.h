@@ -309,7 +309,11 @@ vResult_t vcommGetTuneTable(vcomm_t comm, int coll, vPlan_t* plans, size_t* byte
  * max(1, smallGangs) streams for the others -- whose grid is capped (the
  * large lane leaves 16 SMs; a small lane takes one CTA per 256 KiB of the
  * request's traffic, 4 to 32), so that requests on different lanes run side
- * by side; at most two launches per lane are in flight.  Plans as in mode 1, so results are bit-identical across modes.
+ * by side; at most two launches per lane are in flight.  With the paper's
+ * FIFO protocols, requests of the same vrank count share one communicator's
+ * FIFO arena, so each such launch waits on the device for the previous one
+ * (whatever its lane); direct-protocol requests have no FIFO and overlap
+ * freely.  Plans as in mode 1, so results are bit-identical across modes.
  * While a mode-0 server exists its kernel occupies the SMs: do not launch and
  * wait for other kernels meanwhile (copies are fine). */
 typedef enum { vCollAllReduce = 0, vCollReduceScatter = 1, vCollAllGather = 2 } vColl_t;

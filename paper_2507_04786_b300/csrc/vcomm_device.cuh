@@ -642,7 +642,104 @@ struct Prims {
       char* ss0 = doSend ? slotOf(sc0, sstep0) : nullptr;
       char* ss1 = (doSend && nsc > 1) ? slotOf(sc1, sstep1) : nullptr;
       const uint64_t rf0 = rstep0 + 1, rf1 = rstep1 + 1, sf0 = sstep0 + 1, sf1 = sstep1 + 1;
-      for (uint32_t q0 = warp; q0 < nquads; q0 += (uint32_t)U * nwarps) {
+      uint32_t q0 = warp;
+      // Fast path for rounds of UF full line quads when the user pointers
+      // are 16-byte aligned.  A half-warp covers a line pair: 240 user bytes,
+      // 15 aligned 16-byte chunks, and lane h < 15 of the half loads or
+      // stores chunk h in one access.  In the line layout, lanes 0..7 of
+      // the first line hold chunks 0..6 and the low half of chunk 7 as they
+      // are; lane 8 + j of the second line holds the high half of chunk
+      // 7 + j and the low half of chunk 8 + j, which one 64-bit shuffle moves
+      // between neighbouring lanes (up on the way in, down on the way out).
+      // Same lines, same words, same bits as the element-wise path below.
+      if (((((uintptr_t)local) | ((uintptr_t)out)) & 15) == 0) {
+        constexpr int UF = 4;
+        const uint32_t fullQuads = nbytes / 480;
+        const int h = lane & 15;
+        const uint32_t hoff = 240u * (uint32_t)(lane >> 4) + 16u * (uint32_t)h;
+        for (; q0 + (uint32_t)(UF - 1) * nwarps < fullQuads; q0 += (uint32_t)UF * nwarps) {
+          uint64_t v0[UF], v1[UF], w0[UF], w1[UF];
+#pragma unroll
+          for (int u = 0; u < UF; u++) {
+            const uint32_t q = q0 + (uint32_t)u * nwarps;
+            const uint32_t line = 4 * q + (lane >> 3);
+            v0[u] = 0;
+            v1[u] = 0;
+            if (doLocal && h < 15) {
+              const uint4 c = *(const uint4*)((const char*)local + 480ull * q + hoff);
+              v0[u] = ((uint64_t)c.y << 32) | c.x;
+              v1[u] = ((uint64_t)c.w << 32) | c.z;
+            }
+            if (doRecv) ldVolatile2(rs0 + 128ull * line + 16 * j, w0[u], w1[u]);
+          }
+          if (doLocal) {   // chunk layout -> line layout
+#pragma unroll
+            for (int u = 0; u < UF; u++) {
+              const uint64_t leftHi = __shfl_up_sync(0xffffffffu, v1[u], 1, 16);
+              const uint64_t lo = v0[u];
+              v0[u] = (h < 8) ? lo : leftHi;
+              v1[u] = (h < 7) ? v1[u] : lo;
+            }
+          }
+          bool fail = false;
+          for (int i = 0; i < (doRecv ? nrc : 0) && !fail; i++) {
+            const char* rs = i ? rs1 : rs0;
+            const uint64_t rf = i ? rf1 : rf0;
+            if (i > 0) {
+#pragma unroll
+              for (int u = 0; u < UF; u++) {
+                const uint32_t line = 4 * (q0 + (uint32_t)u * nwarps) + (lane >> 3);
+                ldVolatile2(rs + 128ull * line + 16 * j, w0[u], w1[u]);
+              }
+            }
+            bool ok = true;
+#pragma unroll
+            for (int u = 0; u < UF; u++) ok = ok && (j != 7 || w1[u] == rf);
+            if (!__all_sync(0xffffffffu, ok)) {
+#pragma unroll
+              for (int u = 0; u < UF; u++) {
+                const uint32_t line = 4 * (q0 + (uint32_t)u * nwarps) + (lane >> 3);
+                if (fail) continue;   // warp-uniform
+                if (!ll128Ready(a, rs, line, lane, true, rf, w0[u], w1[u], sAbort, rank, ch)) fail = true;
+              }
+            }
+            if (fail) break;
+#pragma unroll
+            for (int u = 0; u < UF; u++) {
+              if (doLocal || i > 0) {
+                v0[u] = applyWord<T, Op>(w0[u], v0[u]);
+                v1[u] = applyWord<T, Op>(w1[u], v1[u]);
+              } else {
+                v0[u] = w0[u];
+                v1[u] = w1[u];
+              }
+            }
+          }
+          if (fail) { q0 = nquads; break; }   // warp-uniform; sAbort records it
+#pragma unroll
+          for (int u = 0; u < UF; u++) {
+            const uint32_t q = q0 + (uint32_t)u * nwarps;
+            const uint32_t line = 4 * q + (lane >> 3);
+            if (div) {
+              v0[u] = divWord<T>(v0[u], div);
+              v1[u] = divWord<T>(v1[u], div);
+            }
+            if (doSend) {
+              ll128Store(ss0, line, j, v0[u], v1[u], sf0);
+              if (nsc > 1) ll128Store(ss1, line, j, v0[u], v1[u], sf1);
+            }
+            if (doOut) {   // line layout -> chunk layout
+              const uint64_t rightLo = __shfl_down_sync(0xffffffffu, v0[u], 1, 16);
+              const uint64_t lo = (h <= 7) ? v0[u] : v1[u];
+              const uint64_t hi = (h < 7) ? v1[u] : rightLo;
+              if (h < 15)
+                st16((char*)out + 480ull * q + hoff,
+                     make_uint4((uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, (uint32_t)(hi >> 32)));
+            }
+          }
+        }
+      }
+      for (; q0 < nquads; q0 += (uint32_t)U * nwarps) {
         uint64_t v0[U], v1[U], w0[U], w1[U];
         bool lv[U];
         int valid[U];

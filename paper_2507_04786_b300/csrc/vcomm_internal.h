@@ -40,11 +40,11 @@ constexpr int kNumOps = 5;
 constexpr int kCounterStride = 16;
 
 // Largest CTA each protocol's kernels are compiled for; the register budget
-// per thread is 65536 / that.  Simple streams 16-byte vectors with several
-// loads in flight per thread and wants 128 registers (no spills); LL and
-// LL128 poll flags line by line and want more warps instead.  A cluster-
-// protocol FIFO step is at most 512 line pairs: one per thread of 512.
-constexpr int maxThreadsFor(int proto) { return proto == kLL || proto == kLL128 ? 1024 : 512; }
+// per thread is 65536 / that.  Simple and LL128 stream 16-byte vectors with
+// several loads in flight per thread and want 128 registers (no spills); LL
+// polls flags pair by pair and wants more warps instead.  A cluster-protocol
+// FIFO step is at most 512 line pairs: one per thread of 512.
+constexpr int maxThreadsFor(int proto) { return proto == kLL ? 1024 : 512; }
 
 struct ConnDev {
   char* buf;                       // nsteps slots of slotBytes

@@ -141,6 +141,10 @@ struct vserve {
   std::vector<cudaStream_t> lanes;
   std::vector<int> laneCtas;
   std::vector<std::deque<uint64_t>> laneInflight;
+  // a FIFO-protocol launch on comms[k] waits for the previous one (the
+  // arena of a communicator serves one call at a time; lanes are streams)
+  cudaEvent_t commEv[kServeMaxRanks + 1] = {};
+  bool commEvUsed[kServeMaxRanks + 1] = {};
   // requests
   std::mutex mu;
   std::deque<uint64_t> incoming;      // submitted, not yet seen by the dispatcher
@@ -294,6 +298,11 @@ vResult_t launchLane(vserve* s, Request& q, int lane) {
   if (!q.ev0) cudaEventCreate(&q.ev0);
   cudaEventRecord(q.ev0, st);
   vcommSetPlan(c, &q.plan);
+  // FIFO protocols: requests of the same vrank count share comms[k] and its
+  // FIFO arena, so they run one after another whatever lane they are on;
+  // the direct protocol has no FIFO and needs no order
+  const bool fifo = q.plan.proto != vProtoDirect;
+  if (fifo && s->commEvUsed[q.nranks]) cudaStreamWaitEvent(st, s->commEv[q.nranks], 0);
   // a small lane's grid grows with the request (about 256 KiB of traffic per
   // CTA, 4..laneCtas CTAs): tiny requests stay on a few SMs, mid-size ones
   // are not starved
@@ -305,6 +314,10 @@ vResult_t launchLane(vserve* s, Request& q, int lane) {
   vResult_t r = serveCollective(q.coll, q.send, q.recv, q.count, q.dtype, q.redop, q.plan.proto, st, c,
                                 cap, &q.plan);
   if (r != vSuccess) return r;
+  if (fifo) {
+    cudaEventRecord(s->commEv[q.nranks], st);
+    s->commEvUsed[q.nranks] = true;
+  }
   if (!q.ev) cudaEventCreate(&q.ev);
   cudaEventRecord(q.ev, st);
   q.state = 1;
@@ -575,6 +588,8 @@ vResult_t vServeCreate(vserve_t* out, const vserveConfig_t* cfgIn) {
     s->laneInflight.assign(1 + nSmall, std::deque<uint64_t>());
     for (auto& st : s->lanes)
       if (r == vSuccess) r = fromCudaS(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    for (int k = 0; k <= kServeMaxRanks && r == vSuccess; k++)
+      r = fromCudaS(cudaEventCreateWithFlags(&s->commEv[k], cudaEventDisableTiming));
   }
   if (r == vSuccess && cfg.mode >= 1) {
     // one communicator per vrank count, arenas allocated now (not mid-stream)
@@ -689,6 +704,8 @@ vResult_t vServeDestroy(vserve_t s) {
     if (kv.second.ev) cudaEventDestroy(kv.second.ev);
     if (kv.second.ev0) cudaEventDestroy(kv.second.ev0);
   }
+  for (int k = 0; k <= kServeMaxRanks; k++)
+    if (s->commEv[k]) cudaEventDestroy(s->commEv[k]);
   for (int k = 0; k <= kServeMaxRanks; k++)
     if (s->comms[k]) vcommDestroy(s->comms[k]);
   for (int p = 0; p < 3; p++) {
