@@ -611,6 +611,103 @@ def fifo_proto(nbytes):
     return "ll" if nbytes < (64 << 10) else ("ll128" if nbytes < (2 << 20) else "simple")
 
 
+SERVE_NAMES = {"streams": "continuous_batching_streams", "batch": "continuous_batching",
+               "plain": "per_call", "tiles": "continuous_batching_tiles"}
+
+
+def served_requests(nreq, seed=None):
+    """The served workload's request stream: (collective, dtype, vranks,
+    count, per-rank bytes S) per request and the Poisson arrival times."""
+    w = workloads.SERVED
+    seed = w["seed"] if seed is None else seed
+    g = np.random.default_rng(seed)
+    gaps = g.exponential(1.0 / w["rate_per_s"], nreq)
+    arrivals = np.cumsum(gaps)
+    sizes = inputs.log_uniform_sizes(seed, nreq, w["lo_bytes"], w["hi_bytes"])
+    colls = g.integers(0, 3, nreq)
+    ks = g.integers(2, w["max_ranks"] + 1, nreq)
+    dts = g.integers(0, 2, nreq)
+    names = ("allreduce", "reducescatter", "allgather")
+    reqs = []
+    for i in range(nreq):
+        dt = ("fp32", "bf16")[dts[i]]
+        es = 4 if dt == "fp32" else 2
+        k = int(ks[i])
+        coll = names[colls[i]]
+        n = max(16 // es, int(sizes[i]) // es)            # S = the larger per-rank buffer
+        if coll != "allreduce":
+            n = max(1, n // k)
+        reqs.append((coll, dt, k, n, int(sizes[i])))
+    return reqs, arrivals
+
+
+def served_pool():
+    """Resident inputs: every request reads the same buffers (one per vrank
+    and dtype, the largest request's size)."""
+    import torch
+    w = workloads.SERVED
+    hi = w["hi_bytes"]
+    pool = {"fp32": [torch.ones(hi // 4, dtype=torch.float32, device="cuda") for _ in range(w["max_ranks"])],
+            "bf16": [torch.ones(hi // 2, dtype=torch.bfloat16, device="cuda") for _ in range(w["max_ranks"])]}
+    torch.cuda.synchronize()
+    return pool
+
+
+def user_bytes(coll, k, S):
+    """HBM bytes a request must move without a FIFO: AllReduce 2kS, ReduceScatter
+    and AllGather (k + 1) S."""
+    return 2 * k * S if coll == "allreduce" else (k + 1) * S
+
+
+def run_saturation(args, modes=("plain", "tiles"), nreq=None, outstanding=None):
+    """Closed loop: the served workload's requests with `outstanding` of them
+    in flight at all times (a new one is submitted as soon as one completes),
+    default protocol; the largest request rate and HBM rate each mode
+    sustains, with the latency it costs."""
+    from paper_2507_04786_b300 import Server
+    w = workloads.SERVED
+    nreq = nreq or w["saturation_requests"]
+    outstanding = outstanding or w["saturation_outstanding"]
+    reqs, _ = served_requests(nreq)
+    pool = served_pool()
+    res = {"workload": w["name"].replace("poisson-2000rps", "closed-loop"), "requests": nreq,
+           "outstanding": outstanding, "protocol": "auto (direct)"}
+    for mode in modes:
+        srv = Server(mode=mode, max_ranks=w["max_ranks"], mem_budget=w["budget_bytes"],
+                     small_gangs=w["small_lanes"] if mode == "streams" else 1)
+        live = {}
+        lats = []
+        nxt = 0
+        t0 = time.monotonic_ns()
+        while nxt < min(outstanding, nreq):
+            coll, dt, k, n, S = reqs[nxt]
+            live[srv.submit(coll, pool[dt][:k], n, dt, "sum", proto="auto", release=True)] = nxt
+            nxt += 1
+        deadline = time.time() + 120
+        while live and time.time() < deadline:
+            for t in list(live):
+                state, lat, _, _ = srv.query(t)
+                if state in ("done", "failed"):
+                    lats.append(lat / 1e6)
+                    srv.release(t)
+                    del live[t]
+                    if nxt < nreq:
+                        coll, dt, k, n, S = reqs[nxt]
+                        live[srv.submit(coll, pool[dt][:k], n, dt, "sum", proto="auto", release=True)] = nxt
+                        nxt += 1
+        span = (time.monotonic_ns() - t0) / 1e9
+        st = srv.stats()
+        srv.destroy()
+        lats = np.array(lats)
+        total = sum(user_bytes(c, k, S) for c, _, k, _, S in reqs[:len(lats)])
+        res[SERVE_NAMES[mode]] = {
+            "requests_per_s": round(len(lats) / span, 1), "hbm_GBps": round(total / span / 1e9, 1),
+            "p50_ms": round(float(np.percentile(lats, 50)), 4), "p99_ms": round(float(np.percentile(lats, 99)), 4),
+            "completed": int(st["completed"]), "failed": int(st["failed"])}
+    del pool
+    return res
+
+
 def run_served(args, rate=None, nreq=None, modes=("batch", "plain"), protocol="fifo"):
     """Poisson arrivals (mean 2000/s) of AllReduce / AllGather / ReduceScatter
     requests on 2..16 vranks, per-rank sizes log-uniform in 1 KiB..128 MiB,
@@ -625,29 +722,10 @@ def run_served(args, rate=None, nreq=None, modes=("batch", "plain"), protocol="f
     w = workloads.SERVED
     nreq = nreq or args.serve_requests
     rate = rate or w["rate_per_s"]
-    g = np.random.default_rng(w["seed"])
-    gaps = g.exponential(1.0 / rate, nreq)
-    arrivals = np.cumsum(gaps)
-    sizes = inputs.log_uniform_sizes(w["seed"], nreq, w["lo_bytes"], w["hi_bytes"])
-    colls = g.integers(0, 3, nreq)
-    ks = g.integers(2, w["max_ranks"] + 1, nreq)
-    dts = g.integers(0, 2, nreq)
-    # resident inputs: every request reads the same pool (one buffer per vrank and dtype)
-    hi = w["hi_bytes"]
-    pool = {"fp32": [torch.ones(hi // 4, dtype=torch.float32, device="cuda") for _ in range(w["max_ranks"])],
-            "bf16": [torch.ones(hi // 2, dtype=torch.bfloat16, device="cuda") for _ in range(w["max_ranks"])]}
-    torch.cuda.synchronize()
-    names = ("allreduce", "reducescatter", "allgather")
-    reqs = []
-    for i in range(nreq):
-        dt = ("fp32", "bf16")[dts[i]]
-        es = 4 if dt == "fp32" else 2
-        k = int(ks[i])
-        coll = names[colls[i]]
-        n = max(16 // es, int(sizes[i]) // es)            # S = the larger per-rank buffer
-        if coll != "allreduce":
-            n = max(1, n // k)
-        reqs.append((coll, dt, k, n, int(sizes[i])))
+    reqs, arrivals = served_requests(nreq)
+    if rate != w["rate_per_s"]:
+        arrivals = arrivals * (w["rate_per_s"] / rate)
+    pool = served_pool()
     out = {}
     for mode in modes:
         srv = Server(mode=mode, max_ranks=w["max_ranks"], mem_budget=w["budget_bytes"],
@@ -687,12 +765,13 @@ def run_served(args, rate=None, nreq=None, modes=("batch", "plain"), protocol="f
                      "max_inflight_GB": round(st["maxInflightBytes"] / 1e9, 2),
                      "mean_service_ms_large": round(float(np.mean(svc_big)), 4) if svc_big else None,
                      "mean_service_ms_small": round(float(np.mean(svc_small)), 4) if svc_small else None}
-    names = {"streams": "continuous_batching_streams", "batch": "continuous_batching",
-             "plain": "per_call"}
+    del pool
+    names = SERVE_NAMES
     res = {"workload": w["name"] if rate == w["rate_per_s"] else f"served-poisson-{int(rate)}rps",
            "requests": nreq, "rate_per_s": rate, "budget_GB": w["budget_bytes"] / 1e9,
            "protocol": ("the paper's FIFO protocols by size (LL < 64 KiB <= LL128 < 2 MiB <= Simple)"
-                        if protocol == "fifo" else "auto (direct)")}
+                        if protocol == "fifo" else "auto (direct)"),
+           "latency": "completion seen by the host minus the scheduled arrival (queueing included)"}
     for m in modes:
         res[names[m]] = out[m]
     return res
@@ -892,9 +971,11 @@ def main():
     ap.add_argument("--no-ll128", action="store_true",
                     help="skip the LL128 leg of the headline workload")
     ap.add_argument("--serve-requests", type=int, default=workloads.SERVED["bench_requests"],
-                    help="requests of the served leg (the full stream is 100000)")
+                    help="requests of the served legs of the other modes and the paper's protocols")
+    ap.add_argument("--serve-requests-direct", type=int, default=workloads.SERVED["requests"],
+                    help="requests of the default-protocol served comparison (the whole stream)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and served legs")
-    ap.add_argument("--extras", default="direct,alltoall,small,batched,served",
+    ap.add_argument("--extras", default="direct,alltoall,small,batched,served,saturation",
                     help="the extra legs to run, comma separated (profiling captures run one)")
     ap.add_argument("--sweep", default=None,
                     help="run the protocol x size x channel sweep, write JSON lines here, exit")
@@ -1003,8 +1084,15 @@ def main():
         if "batched" in legs:
             line["batched"] = run_batched(args)
         if "served" in legs:
+            # the default protocol over the whole stream: one launch per
+            # request against continuous batching of tiles; the other modes
+            # and the paper's protocols on the first 20,000 requests
+            line["served_direct"] = run_served(args, nreq=args.serve_requests_direct,
+                                               modes=("plain", "tiles"), protocol="auto")
+            line["served_direct_other_modes"] = run_served(args, modes=("streams", "batch"), protocol="auto")
             line["served"] = run_served(args)
-            line["served_direct"] = run_served(args, modes=("plain", "streams", "batch"), protocol="auto")
+        if "saturation" in legs:
+            line["saturation"] = run_saturation(args)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(k, args.proto, w["nchannels"], w["chunk_steps"],
                                             w["seed"])

@@ -314,13 +314,25 @@ vResult_t vcommGetTuneTable(vcomm_t comm, int coll, vPlan_t* plans, size_t* byte
  * FIFO arena, so each such launch waits on the device for the previous one
  * (whatever its lane); direct-protocol requests have no FIFO and overlap
  * freely.  Plans as in mode 1, so results are bit-identical across modes.
- * While a mode-0 server exists its kernel occupies the SMs: do not launch and
- * wait for other kernels meanwhile (copies are fine). */
+ * mode 3 ("tiles") is continuous batching for the direct protocol (Auto):
+ * one resident kernel; its CTA 0 takes requests in arrival order from a ring
+ * in host-mapped memory and queues them on the device, small requests
+ * (< bigThreshold per rank) ahead of large ones, and every other CTA takes
+ * the next tile (a range of 16-byte units, at most ~2 MiB of traffic) of the
+ * first queued request that has tiles left.  So a request starts as soon as
+ * a CTA is free, small requests overtake large ones at tile boundaries, and
+ * the CTA that finishes a request's last tile reports its completion to host
+ * memory.  Plans as in mode 1 (results bit-identical); other protocols are
+ * refused (vUnsupported).  The kernel returns after idleTimeoutSec without
+ * work and is started again by the next request.
+ * While a mode-0 or mode-3 server exists its kernel occupies the SMs: do not
+ * launch and wait for other kernels meanwhile (copies are fine). */
 typedef enum { vCollAllReduce = 0, vCollReduceScatter = 1, vCollAllGather = 2 } vColl_t;
 typedef struct vserve* vserve_t;
 typedef struct {
   int mode;              /* 0 continuous batching on resident gangs [default], 1 one launch
-                            per request, 2 continuous batching on lanes of streams */
+                            per request, 2 continuous batching on lanes of streams, 3
+                            continuous batching of direct-protocol tiles */
   int maxRanks;          /* vranks per request, <= 16 [16] */
   size_t memBudget;      /* bytes of request buffers in flight [40 GiB]; the pool is this size */
   int bigGangChannels;   /* channels of the wide gang [0: every co-resident CTA the

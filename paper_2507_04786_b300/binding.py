@@ -359,15 +359,16 @@ SERVE_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
 class Server:
     """Continuous-batching server of collective requests (vServe* in vcomm.h).
     mode: "streams" (concurrent launches on lanes of streams), "batch" (a
-    resident gang kernel fed through mailboxes) or "plain" (one launch per
-    request on one stream, for comparison)."""
+    resident gang kernel fed through mailboxes), "tiles" (a resident kernel
+    whose CTAs take tiles of direct-protocol requests, small ones first) or
+    "plain" (one launch per request on one stream, for comparison)."""
 
     def __init__(self, mode="batch", max_ranks=16, mem_budget=40 << 30, big_gang_channels=0,
                  small_gangs=1, big_threshold=4 << 20, slot_bytes=None, idle_timeout_sec=30.0,
                  threads=512):
         L = load_library()
         cfg = ServeConfig()
-        cfg.mode = {"batch": 0, "plain": 1, "streams": 2}[mode]
+        cfg.mode = {"batch": 0, "plain": 1, "streams": 2, "tiles": 3}[mode]
         cfg.maxRanks = max_ranks
         cfg.memBudget = mem_budget
         cfg.bigGangChannels = big_gang_channels

@@ -166,6 +166,73 @@ struct ServeArgs {
   int gangConn[kMaxServeGangs];
 };
 
+// ---- serving mode 3 ("tiles"): one resident kernel for direct-protocol
+// requests.  CTA 0 ingests requests from a host-mapped ring (in order) into
+// device state and publishes them on one of two device queues (small
+// requests, then large ones); every other CTA takes the next tile (a range of
+// 16-byte units) of the first request in the small queue that has tiles left,
+// else of the large queue; the CTA that finishes a request's last tile writes
+// its completion into host-mapped memory.  Requests never wait on each other.
+constexpr int kTileRing = 4096;        // request ring entries
+
+struct TileReq {                       // host-mapped ring entry, written by the host
+  ServeReq req;                        // a direct-protocol request (proto == kDirect)
+  unsigned long long units;            // 16-byte units (elements or bytes if !req.vec), all blocks
+  unsigned long long tileUnits;        // units per tile
+  unsigned long long ntiles;           // >= 1 (the last tile also does the element tails)
+  unsigned long long klass;            // 0: small (served first), 1: large
+  unsigned long long seq;              // written last: the request's sequence number + 1
+  unsigned long long pad[3];
+};
+
+struct TileDone {                      // host-mapped, one per ring entry, written by the device
+  unsigned long long seq;              // sequence number + 1 of the completed request
+  unsigned long long tStart, tEnd;     // %globaltimer at ingest and at completion
+  unsigned long long pad;
+};
+
+struct TileCtl {                       // host-mapped control words
+  unsigned long long ingested;         // device: requests ingested so far (a sequence number)
+  unsigned long long completed;        // device: requests completed so far
+  int shutdown;                        // host: stop after the ingested requests
+  int abort;                           // host: stop after the tiles in progress (unused by the server)
+  int stopped;                         // device: the kernel has stopped taking work
+  int pad;
+};
+
+struct TileState {                     // device memory, one per ring entry
+  ServeReq req;                        // copied from the ring entry with units .. klass
+  unsigned long long units, tileUnits, ntiles, klass;
+  unsigned long long next;             // tiles claimed (atomic; may run past ntiles)
+  unsigned long long pad0[7];
+  unsigned long long done;             // tiles finished (atomic)
+  unsigned long long pad1[7];
+  unsigned long long seq, tStart;
+};
+
+struct TileQueues {                    // device memory, zeroed before the first launch
+  unsigned long long tail[2];          // requests published per class (the ingester only)
+  unsigned long long pad0[14];
+  unsigned long long head[2];          // first entry per class that may still have tiles
+  unsigned long long pad1[14];
+  unsigned long long completed;        // requests completed (atomic)
+  unsigned long long pad2[15];
+  int stop;                            // ingester -> workers
+  int pad3[31];
+  unsigned long long entry[2][kTileRing];   // (position << 32) | (ring entry + 1)
+};
+
+struct TileArgs {
+  TileReq* ring;                       // host-mapped
+  TileDone* done;                      // host-mapped
+  TileCtl* ctl;                        // host-mapped
+  TileState* state;
+  TileQueues* q;
+  unsigned long long firstSeq;         // the first request this launch ingests
+  unsigned long long idleTimeoutNs;    // stop after this long with nothing to do
+  unsigned long long drainTimeoutNs;   // shutdown: wait at most this long for work in progress
+};
+
 // ---- the direct protocol (no FIFO): one thread computes a unit's whole
 // ring chain from the k user buffers.  count is in elements (AllReduce,
 // ReduceScatter's recvcount, Reduce) or bytes (AllGather, Broadcast); chunk

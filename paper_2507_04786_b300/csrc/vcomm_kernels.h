@@ -50,4 +50,10 @@ namespace vc {
 const void* batchKernel();
 // the persistent serving kernel (vcomm_batch.cu); its parameter is a ServeArgs
 const void* serveKernel();
+// serving mode 3 (vcomm_serve_tiles.cu): the resident tile kernel, a TileArgs;
+// serveTilesThreads() threads per CTA; a tile is a multiple of
+// serveTilesUnitsPerIter() units
+const void* serveTilesKernel();
+int serveTilesThreads();
+int serveTilesUnitsPerIter();
 }  // namespace vc

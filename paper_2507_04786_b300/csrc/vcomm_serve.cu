@@ -18,6 +18,7 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <cstddef>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -103,6 +104,7 @@ struct Request {
   cudaEvent_t ev = nullptr;           // modes 1, 2: end of the request's launch
   cudaEvent_t ev0 = nullptr;          // modes 1, 2: start of the request's launch
   int lane = -1;                      // mode 2: the stream it runs on
+  uint64_t tseq = 0;                  // mode 3: its sequence number in the request ring
 };
 
 }  // namespace
@@ -145,6 +147,22 @@ struct vserve {
   // arena of a communicator serves one call at a time; lanes are streams)
   cudaEvent_t commEv[kServeMaxRanks + 1] = {};
   bool commEvUsed[kServeMaxRanks + 1] = {};
+  // tiles mode (3): the request ring, completions and control words
+  // (host-mapped), the kernel's device state, and the host's view of them
+  TileReq* hRing = nullptr;
+  TileReq* dRing = nullptr;
+  TileDone* hDone = nullptr;
+  TileDone* dDone = nullptr;
+  TileCtl* hCtl = nullptr;
+  TileCtl* dCtl = nullptr;
+  TileState* dState = nullptr;
+  TileQueues* dQueues = nullptr;
+  cudaEvent_t tilesEnd = nullptr;     // recorded after every launch of the tile kernel
+  bool tilesUp = false;
+  int tileWorkers = 0;
+  uint64_t tilePosted = 0;            // requests written to the ring (sequence numbers 0, 1, ...)
+  std::vector<uint64_t> tileTicket;   // ring entry -> ticket of its request (0: free)
+  std::deque<uint64_t> tileInflight;  // tickets posted, not completed
   // requests
   std::mutex mu;
   std::deque<uint64_t> incoming;      // submitted, not yet seen by the dispatcher
@@ -171,6 +189,7 @@ void planFor(const vserve* s, Request& q) {
   // (mode 1: over up to 2 CTAs per SM), at most ~1 MiB of message per channel
   const int ctas = (s->cfg.mode == 0) ? (q.big ? s->gangCpg[0] : 1) * s->cfg.maxRanks
                                       : std::min(2 * s->nsm, q.nranks * VCOMM_MAX_CHANNELS);
+  // (modes 1, 2 and 3 share this rule, so their plans and results agree)
   size_t per = (size_t)1 << 20;
   int ch = (int)std::max<size_t>(1, std::min<size_t>((S + per - 1) / per,
                                                       (size_t)std::max(1, ctas / q.nranks)));
@@ -265,6 +284,112 @@ void postToGang(vserve* s, Request& q, int g) {
   q.state = 1;
 }
 
+// mode 3: (re)start the tile kernel; it ingests from ring sequence firstSeq on
+vResult_t launchTiles(vserve* s, uint64_t firstSeq) {
+  volatile TileCtl* ctl = s->hCtl;
+  ctl->stopped = 0;
+  ctl->shutdown = 0;
+  ctl->abort = 0;
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  vResult_t r = fromCudaS(cudaMemsetAsync(&s->dQueues->stop, 0, sizeof(int), s->stream));
+  if (r != vSuccess) return r;
+  TileArgs a;
+  memset(&a, 0, sizeof(a));
+  a.ring = s->dRing;
+  a.done = s->dDone;
+  a.ctl = s->dCtl;
+  a.state = s->dState;
+  a.q = s->dQueues;
+  a.firstSeq = firstSeq;
+  a.idleTimeoutNs = (unsigned long long)(s->cfg.idleTimeoutSec * 1e9);
+  a.drainTimeoutNs = 5000000000ull;
+  void* args[] = {(void*)&a};
+  r = fromCudaS(cudaLaunchCooperativeKernel(serveTilesKernel(), dim3(1 + s->tileWorkers),
+                                            dim3(serveTilesThreads()), args, 0, s->stream));
+  if (r != vSuccess) return r;
+  r = fromCudaS(cudaEventRecord(s->tilesEnd, s->stream));
+  if (r == vSuccess) s->tilesUp = true;
+  return r;
+}
+
+// mode 3: the tile kernel has returned (idle, or stopped): requests it took
+// and finished are reported by the completion scan; the ones it never took
+// are taken by the next launch
+void noteTilesExit(vserve* s) {
+  if (!s->tilesUp) return;
+  cudaError_t e = cudaEventQuery(s->tilesEnd);
+  if (e == cudaErrorNotReady) return;
+  (void)cudaGetLastError();
+  s->tilesUp = false;
+}
+
+// mode 3: write request q into the ring (false: its ring entry is still busy)
+bool postTile(vserve* s, Request& q) {
+  const uint64_t seq = s->tilePosted;
+  const int slot = (int)(seq % kTileRing);
+  if (s->tileTicket[slot]) return false;
+  noteTilesExit(s);
+  if (!s->tilesUp) {
+    // the kernel went idle: start it again at the first request it has not taken
+    const uint64_t from = *(volatile unsigned long long*)&s->hCtl->ingested;
+    if (launchTiles(s, from) != vSuccess) return false;
+  }
+  TileReq tr;
+  memset(&tr, 0, sizeof(tr));
+  ServeReq& sr = tr.req;
+  const size_t esz = (q.dtype == vFloat16 || q.dtype == vBfloat16) ? 2 : 4;
+  const bool copy = (q.coll == kAllGather);
+  sr.coll = q.coll;
+  sr.proto = kDirect;
+  sr.dtype = q.dtype;
+  sr.redop = q.redop;
+  sr.nranks = q.nranks;
+  sr.nsub = q.plan.nchannels;
+  sr.count = copy ? q.count * esz : q.count;
+  // the segments (fold order) come from the Simple slot's chunk, as in a plain call
+  const unsigned long long unitBytes = copy ? 1 : esz;
+  const unsigned long long epp = 16 / unitBytes;
+  unsigned long long ch = s->cfg.slotBytes[kSimple] * (unsigned long long)q.plan.chunkSteps / unitBytes;
+  ch = ch / epp * epp;
+  sr.chunk = ch < epp ? epp : ch;
+  bool aligned = true;
+  for (int r = 0; r < q.nranks; r++) {
+    sr.send[r] = q.send[r];
+    sr.recv[r] = q.recv[r];
+    if (((uintptr_t)q.send[r] | (uintptr_t)q.recv[r]) & 15) aligned = false;
+  }
+  if ((q.coll == kReduceScatter || q.coll == kAllGather) && (q.count * esz) % 16) aligned = false;
+  sr.vec = aligned ? 1 : 0;
+  // units and tiles: about two tiles per worker CTA, whole iterations of the
+  // CTA, and at most ~2 MiB of traffic per tile so that a small request never
+  // waits long for a free CTA
+  const unsigned long long E = sr.vec ? (copy ? 16 : 16 / esz) : 1;
+  const unsigned long long blocks = (q.coll == kAllReduce) ? 1 : (unsigned long long)q.nranks;
+  tr.units = (sr.count / E) * blocks;
+  const unsigned long long g = (unsigned long long)serveTilesUnitsPerIter();
+  const unsigned long long unitTraffic = E * unitBytes *
+      (q.coll == kAllReduce ? 2ull * q.nranks : (unsigned long long)q.nranks + 1);
+  const unsigned long long maxTile = std::max<unsigned long long>(g, (2ull << 20) / unitTraffic / g * g);
+  unsigned long long tu = (tr.units + 2ull * s->tileWorkers - 1) / (2ull * s->tileWorkers);
+  tu = std::min(std::max(tu, g), maxTile);
+  tu = (tu + g - 1) / g * g;
+  tr.tileUnits = tu;
+  tr.ntiles = std::max<unsigned long long>(1, (tr.units + tu - 1) / tu);
+  tr.klass = q.big ? 1 : 0;
+  volatile TileReq* dst = &s->hRing[slot];
+  memcpy((void*)dst, &tr, offsetof(TileReq, seq));
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  dst->seq = seq + 1;
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  s->tileTicket[slot] = q.ticket;
+  s->tilePosted = seq + 1;
+  s->tileInflight.push_back(q.ticket);
+  q.tseq = seq;
+  q.gang = slot;
+  q.state = 1;
+  return true;
+}
+
 vResult_t launchPlain(vserve* s, Request& q) {
   vcomm_t c = s->comms[q.nranks];
   if (!q.ev0) cudaEventCreate(&q.ev0);
@@ -332,10 +457,16 @@ bool tryStart(vserve* s, std::deque<uint64_t>& q, int g) {
   Request& r = s->reqs[q.front()];
   const size_t bytes = (r.sb + r.rb) * r.nranks;
   if (s->inflight + bytes > s->cfg.memBudget) return false;
+  if (s->cfg.mode == 3 && s->tileTicket[s->tilePosted % kTileRing]) return false;   // ring full
   if (!allocOutputs(s, r)) return false;
   s->inflight += bytes;
   s->maxInflight = std::max(s->maxInflight, s->inflight);
-  if (s->cfg.mode == 2) {
+  if (s->cfg.mode == 3) {
+    if (!postTile(s, r)) {   // the kernel could not be started
+      s->threadErr = vCudaError;
+      completeReq(s, r, false);
+    }
+  } else if (s->cfg.mode == 2) {
     vResult_t e = launchLane(s, r, g);
     if (e != vSuccess) {
       s->threadErr = e;
@@ -377,6 +508,29 @@ void dispatcher(vserve* s) {
           s->running[g] = 0;
           progress = true;
         }
+      }
+    } else if (s->cfg.mode == 3) {
+      for (auto it = s->tileInflight.begin(); it != s->tileInflight.end();) {
+        Request& q = s->reqs[*it];
+        volatile TileDone* d = &s->hDone[q.gang];
+        if (d->seq == q.tseq + 1) {
+          q.serviceNs = (int64_t)(d->tEnd - d->tStart);
+          s->tileTicket[q.gang] = 0;
+          completeReq(s, q, true);
+          it = s->tileInflight.erase(it);
+          progress = true;
+        } else {
+          ++it;
+        }
+      }
+      noteTilesExit(s);
+      if (!s->tilesUp && !s->tileInflight.empty()) {
+        // the kernel went idle just as requests were posted: the ones it did
+        // not take (every one it took has completed) go to a new launch
+        const uint64_t from = *(volatile unsigned long long*)&s->hCtl->ingested;
+        bool pending = false;
+        for (uint64_t t : s->tileInflight) pending = pending || s->reqs[t].tseq >= from;
+        if (pending && launchTiles(s, from) != vSuccess) s->threadErr = vCudaError;
       }
     } else if (s->cfg.mode == 2) {
       for (size_t l = 0; l < s->lanes.size(); l++) {
@@ -440,7 +594,8 @@ void dispatcher(vserve* s) {
         progress = true;
       }
     } else {
-      // one stream: requests are launched in arrival order
+      // one stream (mode 1) or the request ring (mode 3): requests start in
+      // arrival order
       while (true) {
         std::deque<uint64_t>* q = nullptr;
         if (!s->bigQ.empty() && !s->smallQ.empty())
@@ -475,7 +630,7 @@ vResult_t vServeCreate(vserve_t* out, const vserveConfig_t* cfgIn) {
   for (int p = 0; p < 3; p++)
     if (cfg.slotBytes[p] == 0) cfg.slotBytes[p] = defSlot[p];
   if (cfg.idleTimeoutSec <= 0) cfg.idleTimeoutSec = 30.0;
-  if (cfg.mode < 0 || cfg.mode > 2 || cfg.maxRanks > kServeMaxRanks ||
+  if (cfg.mode < 0 || cfg.mode > 3 || cfg.maxRanks > kServeMaxRanks ||
       1 + cfg.smallGangs > kMaxServeGangs || cfg.threads % 64 || cfg.threads > 512)
     return vInvalidArgument;
   for (int p = 0; p < 3; p++)
@@ -591,7 +746,34 @@ vResult_t vServeCreate(vserve_t* out, const vserveConfig_t* cfgIn) {
     for (int k = 0; k <= kServeMaxRanks && r == vSuccess; k++)
       r = fromCudaS(cudaEventCreateWithFlags(&s->commEv[k], cudaEventDisableTiming));
   }
-  if (r == vSuccess && cfg.mode >= 1) {
+  if (r == vSuccess && cfg.mode == 3) {
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, serveTilesKernel(), serveTilesThreads(), 0) !=
+        cudaSuccess) {
+      (void)cudaGetLastError();
+      per = 0;
+    }
+    s->tileWorkers = per * s->nsm - 1;   // CTA 0 ingests
+    if (s->tileWorkers < 1) r = vUnsupported;
+    if (r == vSuccess) r = fromCudaS(cudaHostAlloc((void**)&s->hRing, sizeof(TileReq) * kTileRing, cudaHostAllocMapped));
+    if (r == vSuccess) r = fromCudaS(cudaHostGetDevicePointer((void**)&s->dRing, s->hRing, 0));
+    if (r == vSuccess) memset(s->hRing, 0, sizeof(TileReq) * kTileRing);
+    if (r == vSuccess) r = fromCudaS(cudaHostAlloc((void**)&s->hDone, sizeof(TileDone) * kTileRing, cudaHostAllocMapped));
+    if (r == vSuccess) r = fromCudaS(cudaHostGetDevicePointer((void**)&s->dDone, s->hDone, 0));
+    if (r == vSuccess) memset(s->hDone, 0, sizeof(TileDone) * kTileRing);
+    if (r == vSuccess) r = fromCudaS(cudaHostAlloc((void**)&s->hCtl, sizeof(TileCtl), cudaHostAllocMapped));
+    if (r == vSuccess) r = fromCudaS(cudaHostGetDevicePointer((void**)&s->dCtl, s->hCtl, 0));
+    if (r == vSuccess) memset(s->hCtl, 0, sizeof(TileCtl));
+    if (r == vSuccess) r = fromCudaS(cudaMalloc(&s->dState, sizeof(TileState) * kTileRing));
+    if (r == vSuccess) r = fromCudaS(cudaMemset(s->dState, 0, sizeof(TileState) * kTileRing));
+    if (r == vSuccess) r = fromCudaS(cudaMalloc(&s->dQueues, sizeof(TileQueues)));
+    if (r == vSuccess) r = fromCudaS(cudaMemset(s->dQueues, 0, sizeof(TileQueues)));
+    if (r == vSuccess) r = fromCudaS(cudaEventCreateWithFlags(&s->tilesEnd, cudaEventDisableTiming));
+    if (r == vSuccess) r = fromCudaS(cudaDeviceSynchronize());
+    s->tileTicket.assign(kTileRing, 0);
+    if (r == vSuccess) r = launchTiles(s, 0);
+  }
+  if (r == vSuccess && (cfg.mode == 1 || cfg.mode == 2)) {
     // one communicator per vrank count, arenas allocated now (not mid-stream)
     vcommConfig_t cc{};
     for (int p = 0; p < 3; p++) cc.slotBytes[p] = cfg.slotBytes[p];
@@ -623,8 +805,9 @@ vResult_t vServeSubmit(vserve_t s, int coll, const void* const* sendbufs, size_t
   q.redop = op;
   q.nranks = nranks;
   q.flags = flags;
-  // gangs have no cluster protocol
+  // gangs have no cluster protocol; the tile kernel runs the direct protocol only
   q.proto = (proto == vProtoCluster) ? vProtoLL : proto;
+  if (s->cfg.mode == 3 && proto != vProtoAuto && proto != vProtoDirect) return vUnsupported;
   q.count = count;
   const size_t esz = (dtype == vFloat16 || dtype == vBfloat16) ? 2 : 4;
   q.sb = count * esz;
@@ -697,6 +880,7 @@ vResult_t vServeDestroy(vserve_t s) {
   s->stop.store(true);
   if (s->th.joinable()) s->th.join();
   if (s->hShutdown) *(volatile int*)s->hShutdown = 1;
+  if (s->hCtl) *(volatile int*)&s->hCtl->shutdown = 1;   // the tile kernel drains, then returns
   if (s->stream) cudaStreamSynchronize(s->stream);
   for (auto st : s->lanes)
     if (st) cudaStreamSynchronize(st);
@@ -713,6 +897,12 @@ vResult_t vServeDestroy(vserve_t s) {
     if (s->arenaCtr[p]) cudaFree(s->arenaCtr[p]);
     if (s->arenaConns[p]) cudaFree(s->arenaConns[p]);
   }
+  if (s->hRing) cudaFreeHost(s->hRing);
+  if (s->hDone) cudaFreeHost(s->hDone);
+  if (s->hCtl) cudaFreeHost(s->hCtl);
+  if (s->dState) cudaFree(s->dState);
+  if (s->dQueues) cudaFree(s->dQueues);
+  if (s->tilesEnd) cudaEventDestroy(s->tilesEnd);
   if (s->dGangs) cudaFree(s->dGangs);
   if (s->dClaim) cudaFree(s->dClaim);
   if (s->hSlots) cudaFreeHost(s->hSlots);

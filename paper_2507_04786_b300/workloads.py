@@ -52,9 +52,11 @@ SERVED = {
     "max_ranks": 16,
     "lo_bytes": 1 * KiB,
     "hi_bytes": 128 * MiB,
-    "budget_bytes": 40 * (1 << 30),
-    "requests": 100_000,
-    "bench_requests": 20_000,     # default bench run: 10 s of arrivals per mode
+    "budget_bytes": 40 * 10 ** 9,
+    "requests": 100_000,          # the default-protocol comparison runs all of them
+    "bench_requests": 20_000,     # the other served legs: 10 s of arrivals per mode
+    "saturation_requests": 8_000,        # closed loop: requests per mode
+    "saturation_outstanding": 32,        # closed loop: requests kept in flight
     "small_lanes": 4,             # continuous batching on streams: lanes for small requests
     "seed": 4,
 }

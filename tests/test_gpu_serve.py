@@ -28,6 +28,9 @@ TYPESTR = {"fp32": "<f4", "bf16": "<i2", "fp16": "<f2", "int32": "<i4"}
 NPDT = {"fp32": np.float32, "bf16": np.uint16, "fp16": np.float16, "int32": np.int32}
 PROTOS = ["simple", "ll", "ll128", "auto"]
 MODES = ["batch", "streams", "plain"]
+# continuous-batching modes and protocols: resident gangs and lanes of streams
+# run every protocol; the tile kernel runs the direct protocol (Auto) only
+BATCHING = [(m, p) for m in ("batch", "streams") for p in PROTOS] + [("tiles", "auto")]
 
 
 class _Dev:
@@ -145,8 +148,7 @@ def wanted_proto(plan_proto, asked):
     return ("direct" if asked == "auto" else asked) == plan_proto
 
 
-@pytest.mark.parametrize("proto", PROTOS)
-@pytest.mark.parametrize("mode", ["batch", "streams"])
+@pytest.mark.parametrize("mode,proto", BATCHING)
 def test_serving_results_exact_and_same_alone(mode, proto):
     reqs = requests("mix")
     outs, plans, stats = run_server(reqs, proto=proto, mode=mode, **CFG)
@@ -166,8 +168,7 @@ def test_serving_results_exact_and_same_alone(mode, proto):
             assert_same(o1[0][q], outs[i][q], f"{proto} request {i} alone vs in the mix, rank {q}")
 
 
-@pytest.mark.parametrize("proto", PROTOS)
-@pytest.mark.parametrize("mode", ["batch", "streams"])
+@pytest.mark.parametrize("mode,proto", BATCHING)
 def test_serving_respects_memory_budget(mode, proto):
     reqs = requests("budget")
     budget = 40 << 20
@@ -204,6 +205,68 @@ def test_streams_and_plain_give_the_same_bits(proto):
     for i in range(len(reqs)):
         for q in range(reqs[i]["k"]):
             assert_same(o1[i][q], o2[i][q], f"{proto} request {i} rank {q}")
+
+
+def test_tiles_and_plain_give_the_same_bits():
+    """The tile kernel plans like one launch per request, so the two give
+    identical results."""
+    reqs = requests("plain")
+    o1, p1, _ = run_server(reqs, proto="auto", mode="tiles", **CFG)
+    o2, p2, _ = run_server(reqs, proto="auto", mode="plain", **CFG)
+    assert p1 == p2
+    for i in range(len(reqs)):
+        for q in range(reqs[i]["k"]):
+            assert_same(o1[i][q], o2[i][q], f"tiles request {i} rank {q}")
+
+
+def test_tiles_refuses_fifo_protocols():
+    from paper_2507_04786_b300 import VcommError
+    r = requests("plain")[0]
+    s = [to_dev(x) for x in r["xs"]]
+    srv = Server(mode="tiles", **{k: v for k, v in CFG.items() if k != "slot_bytes"})
+    try:
+        for proto in ("simple", "ll", "ll128"):
+            with pytest.raises(VcommError):
+                srv.submit(r["coll"], s, r["n"], r["dtype"], r["op"], proto=proto)
+    finally:
+        srv.destroy()
+
+
+def test_tiles_kernel_restarts_after_idle():
+    """The tile kernel returns after its idle timeout; later requests start it
+    again and give the same bits as before."""
+    reqs = requests("mix")[:6]
+    sends = [[to_dev(x) for x in r["xs"]] for r in reqs]
+    torch.cuda.synchronize()
+    cfg = dict(CFG, idle_timeout_sec=0.2)
+    srv = Server(mode="tiles", **cfg)
+    try:
+        got = []
+        for rnd in range(3):
+            tickets = [srv.submit(r["coll"], s, r["n"], r["dtype"], r["op"]) for r, s in zip(reqs, sends)]
+            outs = []
+            for r, t in zip(reqs, tickets):
+                t0 = time.time()
+                while srv.query(t)[0] not in ("done", "failed"):
+                    assert time.time() - t0 < 30
+                    time.sleep(0.001)
+                st, lat, plan, bufs = srv.query(t)
+                assert st == "done"
+                outs.append(([read_back(bufs[q], out_len(r), r["dtype"]) for q in range(r["k"])], plan))
+                srv.release(t)
+            got.append(outs)
+            time.sleep(0.6)        # longer than the idle timeout: the kernel returns
+        for rnd in (1, 2):
+            for i, r in enumerate(reqs):
+                assert got[rnd][i][1] == got[0][i][1]
+                for q in range(r["k"]):
+                    assert_same(got[rnd][i][0][q], got[0][i][0][q], f"round {rnd} request {i} rank {q}")
+        for i, r in enumerate(reqs):
+            want = oracle_for(r, got[0][i][1])
+            for q in range(r["k"]):
+                assert_same(got[0][i][0][q], want[q], f"request {i} rank {q}")
+    finally:
+        srv.destroy()
 
 
 # ------------------------------------------------------------ the largest requests
@@ -248,8 +311,8 @@ def sampled_want(r, plan, idx, q):
     return oracle.all_reduce_points(r["xs"], idx, dt, r["op"], plan["nchannels"], ch, "ring")
 
 
-@pytest.mark.parametrize("proto", ["simple", "ll128", "auto"])
-@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("mode,proto", [(m, p) for m in MODES for p in ("simple", "ll128", "auto")] +
+                         [("tiles", "auto")])
 def test_largest_requests_sampled(large_requests, mode, proto):
     """Requests at the top of the served size range (up to 16 vranks x 128 MiB)
     with the server's default FIFO slots, served together: sampled elements of
