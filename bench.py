@@ -842,6 +842,48 @@ def run_sweep(path, protos=("simple", "ll", "ll128", "cluster"), algo="ring"):
     return [best[k_] for k_ in sorted(best)]
 
 
+def run_hop(args):
+    """Per-hop latency of the FIFO protocols (vDebugHopLatency): rings of 8
+    and 16 CTAs on consecutive SM ids, on SM ids alternating between the two
+    halves of the id range, and as one thread-block cluster; and an LL
+    ping-pong between SM 0 and every other SM (the spread shows whether some
+    pairs pay more, e.g. across the two dies)."""
+    import torch
+
+    from paper_2507_04786_b300 import VcommError
+    from paper_2507_04786_b300.binding import debug_hop_latency
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    half = nsm // 2
+    rows = []
+    for proto in ("ll", "ll128", "simple"):
+        for k in (8, 16):
+            rings = {"consecutive": list(range(k)),
+                     "alternating_halves": [i // 2 + (i % 2) * half for i in range(k)],
+                     "cluster": None}
+            for name, sms in rings.items():
+                try:
+                    ns, got = debug_hop_latency(proto, sms, n=k, laps=2000)
+                    rows.append({"proto": proto, "ring": name, "ctas": k, "us_per_hop": round(ns / 1e3, 3),
+                                 "sms": got})
+                except VcommError as e:
+                    rows.append({"proto": proto, "ring": name, "ctas": k, "error": e.name})
+    pp = {}
+    for j in range(1, nsm):
+        try:
+            ns, _ = debug_hop_latency("ll", [0, j], laps=500)
+            pp[j] = round(ns / 1e3, 3)
+        except VcommError as e:
+            pp[j] = e.name
+    vals = np.array([v for v in pp.values() if isinstance(v, float)])
+    summary = {}
+    if vals.size:
+        lo = float(vals.min())
+        summary = {"min_us": lo, "median_us": float(np.median(vals)), "max_us": float(vals.max()),
+                   "sms_above_1.5x_min": int((vals > 1.5 * lo).sum()), "sms": int(vals.size)}
+    return {"paper_us_per_hop": {"simple": 6, "ll": 1, "ll128": 2}, "rings": rows,
+            "pingpong_ll_from_sm0": summary, "pingpong_ll_us_by_sm": pp}
+
+
 COLL_SWEEP_BYTES = [workloads.KiB * 4 ** i for i in range(1, 9)] + [128 << 20]
 
 
@@ -975,7 +1017,7 @@ def main():
     ap.add_argument("--serve-requests-direct", type=int, default=workloads.SERVED["requests"],
                     help="requests of the default-protocol served comparison (the whole stream)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and served legs")
-    ap.add_argument("--extras", default="direct,alltoall,small,batched,served,saturation",
+    ap.add_argument("--extras", default="direct,alltoall,small,batched,served,saturation,hop",
                     help="the extra legs to run, comma separated (profiling captures run one)")
     ap.add_argument("--sweep", default=None,
                     help="run the protocol x size x channel sweep, write JSON lines here, exit")
@@ -1093,6 +1135,8 @@ def main():
             line["served"] = run_served(args)
         if "saturation" in legs:
             line["saturation"] = run_saturation(args)
+        if "hop" in legs:
+            line["hop_latency"] = run_hop(args)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(k, args.proto, w["nchannels"], w["chunk_steps"],
                                             w["seed"])

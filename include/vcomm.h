@@ -418,6 +418,21 @@ vResult_t vDebugEncode(vProto_t proto, const void* src, size_t nbytes, uint64_t 
 vResult_t vDebugDecode(vProto_t proto, const void* lines, size_t nbytes, uint64_t flag,
                        void* dst, double timeoutSec, vStream_t stream);
 
+/* Per-hop latency of the FIFO protocols (Sec. III quotes ~6 / ~1 / ~2 us per
+ * hop for Simple / LL / LL128): a ring of n CTAs (one warp each) passes one
+ * FIFO line around `laps` times -- LL: one 8-byte {data, flag} line; LL128:
+ * one 128-byte line written by 8 lanes, the flag in its last 8 bytes;
+ * Simple: a 128-byte payload, a fence and a release store of a counter that
+ * the receiver acquires -- and *nsPerHop = elapsed %globaltimer / (laps x n).
+ * ringSms: n SM ids (%smid, distinct, < 1024), position i of the ring on SM
+ * ringSms[i] (the kernel runs one CTA on every SM; n <= SM count); NULL: the
+ * ring is one thread-block cluster of n <= 16 CTAs (one GPC).  smOut (may be
+ * NULL): n ints, the SM id of each position.  Every wait is bounded by
+ * timeoutSec (vTimeout, e.g. for an SM id no SM has).  Allocates a few KB,
+ * synchronous; vInvalidArgument for n < 2, laps < 1, bad ids or protocols. */
+vResult_t vDebugHopLatency(vProto_t proto, const int* ringSms, int n, int laps, double timeoutSec,
+                           double* nsPerHop, int* smOut);
+
 /* Fault injection for tests of failure detection: from the next call on,
  * vrank `rank`'s CTAs return without taking part (-1 turns it off), so the
  * other vranks' flag waits run into their deadline (vTimeout) or the abort

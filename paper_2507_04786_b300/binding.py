@@ -30,7 +30,8 @@ EXPORTS = ("vcommInit", "vcommInitConfig", "vcommPrepare", "vcommDestroy", "vcom
            "vDebugEncode", "vDebugDecode", "vAllReduceNoAlloc", "vGroupStart", "vGroupEnd",
            "vcommGetGroupPlans", "vcommTune", "vcommGetTuneTable", "vcommDebugSetSkipRank",
            "vServeCreate", "vServeSubmit", "vServeQuery", "vServeRelease", "vServeGetStats",
-           "vServeDestroy", "vSend", "vRecv", "vAllToAll", "vcommAbortPending", "vcommReset")
+           "vServeDestroy", "vSend", "vRecv", "vAllToAll", "vcommAbortPending", "vcommReset",
+           "vDebugHopLatency")
 
 
 class VcommError(RuntimeError):
@@ -103,6 +104,8 @@ def load_library():
     L.vDebugDecode.argtypes = [i32, vp, sz, ctypes.c_uint64, vp, ctypes.c_double, vp]
     L.vAllReduceNoAlloc.argtypes = [pp, pp, sz, i32, i32, i32, i32, vp, vp]
     L.vcommDebugSetSkipRank.argtypes = [vp, i32]
+    L.vDebugHopLatency.argtypes = [i32, ctypes.POINTER(i32), i32, i32, ctypes.c_double,
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
     L.vServeCreate.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ServeConfig)]
     L.vServeSubmit.argtypes = [vp, i32, pp, sz, i32, i32, i32, i32, i32, ctypes.c_int64,
                                ctypes.POINTER(ctypes.c_uint64)]
@@ -420,6 +423,22 @@ class Server:
             self.destroy()
         except Exception:
             pass
+
+
+def debug_hop_latency(proto: str, sms=None, n: int = 0, laps: int = 1000, timeout_sec: float = 2.0):
+    """(ns per hop, SM id of each ring position) of a ring of CTAs passing one
+    FIFO line (vDebugHopLatency): `sms` lists the ring's SM ids, or None for
+    one cluster of n CTAs."""
+    if sms is not None:
+        n = len(sms)
+        arr = (ctypes.c_int * n)(*sms)
+    else:
+        arr = None
+    ns = ctypes.c_double()
+    out = (ctypes.c_int * n)()
+    _check(load_library().vDebugHopLatency(PROTO_CODES[proto], arr, n, laps, ctypes.c_double(timeout_sec),
+                                           ctypes.byref(ns), out), "vDebugHopLatency")
+    return ns.value, list(out)
 
 
 def debug_encode(proto: str, src, nbytes: int, flag: int, lines, stream=None):
