@@ -27,9 +27,12 @@ __global__ void __launch_bounds__(256) kDirectCopy(const __grid_constant__ Direc
   const DirectView v = viewOf(a);
   const bool last = blockIdx.x == gridDim.x - 1;
   unsigned long long lo, hi;
-  if (a.vec) {
+  if (a.vec == 1) {
     ctaRange(copyUnits(v, 16), &lo, &hi);
     directCopy<Unit16<uint8_t>>(v, lo, hi, last);
+  } else if (a.vec == 2) {
+    ctaRange(shiftedUnits(v, 1), &lo, &hi);
+    directCopyShifted<PlainMem>(v, lo, hi, last);
   } else {
     ctaRange(copyUnits(v, 1), &lo, &hi);
     directCopy<Unit1<uint8_t>>(v, lo, hi, last);
@@ -46,7 +49,8 @@ __global__ void __launch_bounds__(256) kDirectBatchCopy(const __grid_constant__ 
     bool tail;
     opShare(pb, i, glo, ghi, &lo, &hi, &tail);
     const DirectView v = viewOfOp(pb, i);
-    if (pb->ops[i].vec) directCopy<Unit16<uint8_t>>(v, lo, hi, tail);
+    if (pb->ops[i].vec == 1) directCopy<Unit16<uint8_t>>(v, lo, hi, tail);
+    else if (pb->ops[i].vec == 2) directCopyShifted<PlainMem>(v, lo, hi, tail);
     else directCopy<Unit1<uint8_t>>(v, lo, hi, tail);
   }
 }

@@ -47,9 +47,11 @@ VDEV int arSegment(const DirectView& a, unsigned long long i, int esz, unsigned 
   return (int)s;
 }
 
+template <class T> struct Unit1;
 template <class T>
 struct Unit16 {   // 16-byte unit
   using W = uint4;
+  using Tail = Unit1<T>;   // the element accesses of the same kernel
   static constexpr int kElems = 16 / sizeof(T);
   static VDEV W load(const char* p) { return __ldcs((const uint4*)p); }
   static VDEV void store(char* p, W v) { __stcs((uint4*)p, v); }
@@ -57,9 +59,53 @@ struct Unit16 {   // 16-byte unit
 template <class T>
 struct Unit1 {    // one element (unaligned buffers)
   using W = T;
+  using Tail = Unit1<T>;
   static constexpr int kElems = 1;
   static VDEV W load(const char* p) { return *(const T*)p; }
   static VDEV void store(char* p, W v) { *(T*)p = v; }
+};
+
+// The same units read through L2 only, for a kernel that outlives the
+// requests it serves: a buffer rewritten between two requests must not be
+// read from a line that an SM's L1 kept from the earlier one.
+template <class T>
+struct Unit1L2 {
+  using W = T;
+  using Tail = Unit1L2<T>;
+  static constexpr int kElems = 1;
+  static VDEV W load(const char* p) {
+    if constexpr (sizeof(T) == 1) {
+      unsigned short v;
+      asm volatile("ld.global.cg.u8 %0, [%1];" : "=h"(v) : "l"(p));
+      const uint8_t b = (uint8_t)v;
+      return *(const T*)&b;
+    } else if constexpr (sizeof(T) == 2) {
+      unsigned short v;
+      asm volatile("ld.global.cg.u16 %0, [%1];" : "=h"(v) : "l"(p));
+      if constexpr (std::is_same<T, __half>::value) return __ushort_as_half(v);
+      else if constexpr (std::is_same<T, __nv_bfloat16>::value) return __ushort_as_bfloat16(v);
+      else return (T)v;
+    } else if constexpr (sizeof(T) == 4) {
+      unsigned v;
+      asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(v) : "l"(p));
+      if constexpr (std::is_same<T, float>::value) return __uint_as_float(v);
+      else return (T)v;
+    } else {
+      unsigned long long v;
+      asm volatile("ld.global.cg.u64 %0, [%1];" : "=l"(v) : "l"(p));
+      if constexpr (std::is_same<T, double>::value) return __longlong_as_double((long long)v);
+      else return (T)v;
+    }
+  }
+  static VDEV void store(char* p, W v) { *(T*)p = v; }
+};
+template <class T>
+struct Unit16L2 {
+  using W = uint4;
+  using Tail = Unit1L2<T>;
+  static constexpr int kElems = 16 / sizeof(T);
+  static VDEV W load(const char* p) { return ldCG(p); }
+  static VDEV void store(char* p, W v) { __stcs((uint4*)p, v); }
 };
 
 template <class T, class Op, class W>
@@ -188,20 +234,21 @@ VDEV void directReduce(const DirectView& a, unsigned long long lo, unsigned long
     const unsigned long long nblk = (a.coll == kReduceScatter) ? (unsigned long long)k : 1ull;
     for (unsigned long long t = threadIdx.x; t < nt * nblk; t += blockDim.x) {
       const unsigned long long b = t / nt, i = nunit * E + t % nt;
+      using U1 = typename U::Tail;
       if (a.coll == kAllReduce) {
         unsigned long long re;
         const int s = arSegment(a, i, (int)esz, &re);
-        T v = foldChain<T, Op, Unit1<T>>(a, s, i * esz);
+        T v = foldChain<T, Op, U1>(a, s, i * esz);
         if (a.postDiv) v = divElem<T>(v, a.postDiv);
-        for (int r = 0; r < k; r++) Unit1<T>::store((char*)a.recv[r] + i * esz, v);
+        for (int r = 0; r < k; r++) U1::store((char*)a.recv[r] + i * esz, v);
       } else if (a.coll == kReduceScatter) {
-        T v = foldChain<T, Op, Unit1<T>>(a, (int)b, (b * a.count + i) * esz);
+        T v = foldChain<T, Op, U1>(a, (int)b, (b * a.count + i) * esz);
         if (a.postDiv) v = divElem<T>(v, a.postDiv);
-        Unit1<T>::store((char*)a.recv[b] + i * esz, v);
+        U1::store((char*)a.recv[b] + i * esz, v);
       } else {
-        T v = foldChain<T, Op, Unit1<T>>(a, a.root, i * esz);
+        T v = foldChain<T, Op, U1>(a, a.root, i * esz);
         if (a.postDiv) v = divElem<T>(v, a.postDiv);
-        Unit1<T>::store((char*)a.recv[a.root] + i * esz, v);
+        U1::store((char*)a.recv[a.root] + i * esz, v);
       }
     }
   }
@@ -231,7 +278,7 @@ VDEV void directCopy(const DirectView& a, unsigned long long lo, unsigned long l
     for (unsigned long long t = threadIdx.x; t < nt * nblk; t += blockDim.x) {
       const unsigned long long b = (a.coll == kAllGather) ? t / nt : (unsigned long long)a.root;
       const unsigned long long off = nunit * E + t % nt;
-      const uint8_t v = ((const uint8_t*)a.send[b])[off];
+      const uint8_t v = U::Tail::load((const char*)a.send[b] + off);
       const unsigned long long dst = (a.coll == kAllGather) ? b * a.count + off : off;
       for (int r = 0; r < k; r++) {
         if ((unsigned long long)r == b && ((a.inplaceMask >> r) & 1ull)) continue;
@@ -239,6 +286,139 @@ VDEV void directCopy(const DirectView& a, unsigned long long lo, unsigned long l
       }
     }
   }
+}
+
+// ---- ReduceScatter / AllGather of 16-byte aligned buffers whose blocks are
+// not whole 16-byte units (n elements of a block take n x size bytes, not a
+// multiple of 16).  Block b then starts (b n size) mod 16 bytes into an
+// aligned unit of a send buffer (ReduceScatter) or of the receive buffers
+// (AllGather), so the element-wise path would serve them one element per
+// access.  Instead every access stays a 16-byte vector: a misaligned
+// 16-byte piece is cut out of the two aligned units around it (shiftBytes),
+// and the receive buffers are written in aligned units.  Same values, same
+// fold order, so the bits are the element-wise path's.
+
+// the 16 bytes that start d bytes (0..15) into the 32 bytes lo:hi
+VDEV uint4 shiftBytes(uint4 lo, uint4 hi, unsigned d) {
+  const unsigned s = d >> 2, r = (d & 3u) * 8u;
+  uint32_t w0, w1, w2, w3, w4;
+  if (s == 0) { w0 = lo.x; w1 = lo.y; w2 = lo.z; w3 = lo.w; w4 = hi.x; }
+  else if (s == 1) { w0 = lo.y; w1 = lo.z; w2 = lo.w; w3 = hi.x; w4 = hi.y; }
+  else if (s == 2) { w0 = lo.z; w1 = lo.w; w2 = hi.x; w3 = hi.y; w4 = hi.z; }
+  else { w0 = lo.w; w1 = hi.x; w2 = hi.y; w3 = hi.z; w4 = hi.w; }
+  return make_uint4(__funnelshift_r(w0, w1, r), __funnelshift_r(w1, w2, r), __funnelshift_r(w2, w3, r),
+                    __funnelshift_r(w3, w4, r));
+}
+
+// Memory access policies of the shifted paths: the per-call kernels read
+// with plain loads (a thread's two aligned units overlap its neighbours',
+// which then come from L1); the resident serving kernel reads through L2 only.
+struct PlainMem {
+  template <class T> using Elem = Unit1<T>;
+  static VDEV uint4 load16(const char* p) { return *(const uint4*)p; }
+};
+struct L2Mem {
+  template <class T> using Elem = Unit1L2<T>;
+  static VDEV uint4 load16(const char* p) { return ldCG(p); }
+};
+
+// 16 bytes at byte offset x of buffer p of `size` bytes (x + 16 <= size),
+// p 16-byte aligned: one or two aligned loads, or byte loads when the second
+// aligned unit would reach past the end
+template <class M>
+VDEV uint4 loadShifted(const char* p, unsigned long long x, unsigned long long size) {
+  const unsigned d = (unsigned)(x & 15ull);
+  const unsigned long long a0 = x - d;
+  if (d == 0) return M::load16(p + a0);
+  if (a0 + 32 <= size) return shiftBytes(M::load16(p + a0), M::load16(p + a0 + 16), d);
+  union { uint4 v; uint8_t c[16]; } u;
+#pragma unroll 1
+  for (int i = 0; i < 16; i++) u.c[i] = M::template Elem<uint8_t>::load(p + x + i);
+  return u.v;
+}
+
+// ReduceScatter units [lo, hi) (16-byte output units of the k blocks, block
+// b's full units first); `tail`: this CTA also does each block's element tail
+template <class T, class Op, class M>
+VDEV void directReduceShifted(const DirectView& a, unsigned long long lo, unsigned long long hi, bool tail) {
+  const int k = a.nranks;
+  constexpr int E = 16 / sizeof(T);
+  const unsigned long long esz = sizeof(T);
+  const unsigned long long nunit = a.count / E;   // full output units per block
+  const unsigned long long blockB = a.count * esz, size = blockB * (unsigned long long)k;
+  for (unsigned long long g = lo + threadIdx.x; g < hi; g += blockDim.x) {
+    const unsigned long long b = g / nunit, e = g % nunit;
+    const unsigned long long x = b * blockB + e * 16ull;
+    int r = (int)b + 1 < k ? (int)b + 1 : 0;
+    uint4 acc = loadShifted<M>((const char*)a.send[r], x, size);
+    constexpr int B = 4;
+    for (int j = 1; j < k; j += B) {
+      uint4 v[B];
+#pragma unroll
+      for (int i = 0; i < B; i++) {
+        int rr = r + 1 + i;
+        if (rr >= k) rr -= k;
+        if (j + i < k) v[i] = loadShifted<M>((const char*)a.send[rr], x, size);
+      }
+#pragma unroll
+      for (int i = 0; i < B; i++)
+        if (j + i < k) acc = combine<T, Op, uint4>(acc, v[i]);
+      r += B;
+      if (r >= k) r -= k;
+    }
+    if (a.postDiv) acc = divide<T, Unit16<T>>(acc, a.postDiv);
+    *(uint4*)((char*)a.recv[b] + e * 16ull) = acc;
+  }
+  const unsigned long long nt = a.count - nunit * E;   // element tail of each block
+  if (nt && tail) {
+    using U1 = typename M::template Elem<T>;
+    for (unsigned long long t = threadIdx.x; t < nt * (unsigned long long)k; t += blockDim.x) {
+      const unsigned long long b = t / nt, i = nunit * E + t % nt;
+      T v = foldChain<T, Op, U1>(a, (int)b, (b * a.count + i) * esz);
+      if (a.postDiv) v = divElem<T>(v, a.postDiv);
+      U1::store((char*)a.recv[b] + i * esz, v);
+    }
+  }
+}
+
+// AllGather units [lo, hi): the 16-byte units of the k blocks laid end to end
+// (count bytes each, not a multiple of 16), each written to every receive
+// buffer; `tail`: this CTA also writes the last, partial unit
+template <class M>
+VDEV void directCopyShifted(const DirectView& a, unsigned long long lo, unsigned long long hi, bool tail) {
+  using UB = typename M::template Elem<uint8_t>;
+  const int k = a.nranks;
+  const unsigned long long B = a.count, total = B * (unsigned long long)k;
+  for (unsigned long long u = lo + threadIdx.x; u < hi; u += blockDim.x) {
+    const unsigned long long x = u * 16ull, b = x / B, o = x - b * B;
+    uint4 v;
+    if (o + 16 <= B) {
+      v = loadShifted<M>((const char*)a.send[b], o, B);
+    } else {   // the unit straddles two blocks: byte by byte
+      union { uint4 w; uint8_t c[16]; } t;
+#pragma unroll 1
+      for (int i = 0; i < 16; i++) {
+        const unsigned long long y = x + i, bb = y / B;
+        t.c[i] = UB::load((const char*)a.send[bb] + (y - bb * B));
+      }
+      v = t.w;
+    }
+    for (int r = 0; r < k; r++) *(uint4*)((char*)a.recv[r] + x) = v;
+  }
+  const unsigned long long full = total / 16ull;
+  if (tail && full * 16ull < total) {
+    for (unsigned long long y = full * 16ull + threadIdx.x; y < total; y += blockDim.x) {
+      const unsigned long long bb = y / B;
+      const uint8_t c = UB::load((const char*)a.send[bb] + (y - bb * B));
+      for (int r = 0; r < k; r++) ((uint8_t*)a.recv[r])[y] = c;
+    }
+  }
+}
+
+// units of the shifted paths
+VDEV unsigned long long shiftedUnits(const DirectView& a, int esz) {
+  if (a.coll == kAllGather) return a.count * (unsigned long long)a.nranks / 16ull;
+  return (a.count / (16ull / (unsigned long long)esz)) * (unsigned long long)a.nranks;
 }
 
 // this CTA's contiguous share [*lo, *hi) of `total` units, in whole blocks

@@ -18,9 +18,12 @@ __global__ void __launch_bounds__(DirectShape<T>::kThreads, 1)
   const DirectView v = viewOf(a);
   const bool last = blockIdx.x == gridDim.x - 1;
   unsigned long long lo, hi;
-  if (a.vec) {
+  if (a.vec == 1) {
     ctaRange(reduceUnits(v, Unit16<T>::kElems), &lo, &hi);
     directReduce<T, Op, Unit16<T>, DirectShape<T>::kUnits>(v, lo, hi, last);
+  } else if (a.vec == 2) {
+    ctaRange(shiftedUnits(v, (int)sizeof(T)), &lo, &hi);
+    directReduceShifted<T, Op, PlainMem>(v, lo, hi, last);
   } else {
     ctaRange(reduceUnits(v, 1), &lo, &hi);
     directReduce<T, Op, Unit1<T>, 1>(v, lo, hi, last);
@@ -42,7 +45,8 @@ __global__ void __launch_bounds__(DirectShape<T>::kThreads, 1)
     // (2-byte types: one unit per thread, which the loop over ops leaves
     // registers for)
     constexpr int NU = sizeof(T) == 2 ? 1 : DirectShape<T>::kUnits;
-    if (pb->ops[i].vec) directReduce<T, Op, Unit16<T>, NU>(v, lo, hi, tail);
+    if (pb->ops[i].vec == 1) directReduce<T, Op, Unit16<T>, NU>(v, lo, hi, tail);
+    else if (pb->ops[i].vec == 2) directReduceShifted<T, Op, PlainMem>(v, lo, hi, tail);
     else directReduce<T, Op, Unit1<T>, 1>(v, lo, hi, tail);
   }
 }

@@ -128,7 +128,7 @@ constexpr int kMaxServeGangs = 16;
 
 struct ServeReq {
   int coll, proto, dtype, redop, nranks, nsub, root;
-  int vec;                           // direct protocol: every access a 16-byte vector
+  int vec;                           // direct protocol: as DirectArgs::vec
   unsigned long long count, chunk, slotUnits, slotBytes, inplaceMask;
   const void* send[kServeMaxRanks];
   void* recv[kServeMaxRanks];
@@ -177,12 +177,20 @@ constexpr int kTileRing = 4096;        // request ring entries
 
 struct TileReq {                       // host-mapped ring entry, written by the host
   ServeReq req;                        // a direct-protocol request (proto == kDirect)
-  unsigned long long units;            // 16-byte units (elements or bytes if !req.vec), all blocks
-  unsigned long long tileUnits;        // units per tile
+  // staged requests (16-byte aligned): tiles are byte ranges of one block
+  // (AllReduce: the buffer; ReduceScatter / AllGather: block b of k) that
+  // move by bulk copies; otherwise tiles are ranges of the register kernels'
+  // units (elements, or bytes for AllGather)
+  unsigned long long staged;           // 1: bulk-copy tiles
+  unsigned long long units;            // register path: units of all blocks
+  unsigned long long tileUnits;        // register path: units per tile
+  unsigned long long blockBytes;       // staged: 16-byte units of one block, in bytes
+  unsigned long long tileBytes;        // staged: bytes of a block per tile (a multiple of 16)
+  unsigned long long perBlock;         // staged: tiles per block
   unsigned long long ntiles;           // >= 1 (the last tile also does the element tails)
   unsigned long long klass;            // 0: small (served first), 1: large
   unsigned long long seq;              // written last: the request's sequence number + 1
-  unsigned long long pad[3];
+  unsigned long long pad[7];
 };
 
 struct TileDone {                      // host-mapped, one per ring entry, written by the device
@@ -195,14 +203,14 @@ struct TileCtl {                       // host-mapped control words
   unsigned long long ingested;         // device: requests ingested so far (a sequence number)
   unsigned long long completed;        // device: requests completed so far
   int shutdown;                        // host: stop after the ingested requests
-  int abort;                           // host: stop after the tiles in progress (unused by the server)
+  int error;                           // device: a bulk copy did not complete in time (vTimeout)
   int stopped;                         // device: the kernel has stopped taking work
   int pad;
 };
 
 struct TileState {                     // device memory, one per ring entry
-  ServeReq req;                        // copied from the ring entry with units .. klass
-  unsigned long long units, tileUnits, ntiles, klass;
+  ServeReq req;                        // copied from the ring entry with staged .. klass
+  unsigned long long staged, units, tileUnits, blockBytes, tileBytes, perBlock, ntiles, klass;
   unsigned long long next;             // tiles claimed (atomic; may run past ntiles)
   unsigned long long pad0[7];
   unsigned long long done;             // tiles finished (atomic)
@@ -231,6 +239,9 @@ struct TileArgs {
   unsigned long long firstSeq;         // the first request this launch ingests
   unsigned long long idleTimeoutNs;    // stop after this long with nothing to do
   unsigned long long drainTimeoutNs;   // shutdown: wait at most this long for work in progress
+  unsigned long long copyTimeoutNs;    // a bulk copy that takes longer fails the kernel
+  unsigned stageBytes;                 // shared memory per pipeline stage (a multiple of 128)
+  int pad;
 };
 
 // ---- the direct protocol (no FIFO): one thread computes a unit's whole
@@ -245,7 +256,9 @@ struct DirectArgs {
   unsigned long long chunk;
   unsigned long long inplaceMask;
   int coll, nranks, nsub, root;
-  int vec;                         // 1: every access is a 16-byte vector
+  int vec;                         // 1: every access is a 16-byte vector; 2: 16-byte aligned
+                                   // buffers, ReduceScatter / AllGather blocks that are not whole
+                                   // 16-byte units (shifted vectors); 0: element accesses
   int postDiv;                     // avg: divide the folded value by this (0: none)
   // the staged reducing kernel (kDirectReduceStaged) only:
   int stages;                      // tiles of loads in flight (2 or 3)

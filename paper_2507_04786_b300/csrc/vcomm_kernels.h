@@ -51,9 +51,14 @@ const void* batchKernel();
 // the persistent serving kernel (vcomm_batch.cu); its parameter is a ServeArgs
 const void* serveKernel();
 // serving mode 3 (vcomm_serve_tiles.cu): the resident tile kernel, a TileArgs;
-// serveTilesThreads() threads per CTA; a tile is a multiple of
-// serveTilesUnitsPerIter() units
+// serveTilesThreads() threads per CTA and serveTilesSmem(stageBytes) bytes of
+// dynamic shared memory (serveTilesStages() stages of stageBytes plus two
+// output buffers of serveTilesOutBytes()); a register-path tile is a
+// multiple of serveTilesUnitsPerIter() units
 const void* serveTilesKernel();
 int serveTilesThreads();
 int serveTilesUnitsPerIter();
+int serveTilesStages();
+unsigned serveTilesOutBytes();
+size_t serveTilesSmem(unsigned stageBytes);
 }  // namespace vc

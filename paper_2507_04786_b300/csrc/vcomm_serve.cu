@@ -160,6 +160,7 @@ struct vserve {
   cudaEvent_t tilesEnd = nullptr;     // recorded after every launch of the tile kernel
   bool tilesUp = false;
   int tileWorkers = 0;
+  unsigned tileStageBytes = 0;
   uint64_t tilePosted = 0;            // requests written to the ring (sequence numbers 0, 1, ...)
   std::vector<uint64_t> tileTicket;   // ring entry -> ticket of its request (0: free)
   std::deque<uint64_t> tileInflight;  // tickets posted, not completed
@@ -287,9 +288,9 @@ void postToGang(vserve* s, Request& q, int g) {
 // mode 3: (re)start the tile kernel; it ingests from ring sequence firstSeq on
 vResult_t launchTiles(vserve* s, uint64_t firstSeq) {
   volatile TileCtl* ctl = s->hCtl;
+  if (ctl->error) return (vResult_t)ctl->error;   // a failed kernel is not restarted
   ctl->stopped = 0;
   ctl->shutdown = 0;
-  ctl->abort = 0;
   std::atomic_thread_fence(std::memory_order_seq_cst);
   vResult_t r = fromCudaS(cudaMemsetAsync(&s->dQueues->stop, 0, sizeof(int), s->stream));
   if (r != vSuccess) return r;
@@ -303,9 +304,12 @@ vResult_t launchTiles(vserve* s, uint64_t firstSeq) {
   a.firstSeq = firstSeq;
   a.idleTimeoutNs = (unsigned long long)(s->cfg.idleTimeoutSec * 1e9);
   a.drainTimeoutNs = 5000000000ull;
+  a.copyTimeoutNs = 5000000000ull;
+  a.stageBytes = s->tileStageBytes;
   void* args[] = {(void*)&a};
   r = fromCudaS(cudaLaunchCooperativeKernel(serveTilesKernel(), dim3(1 + s->tileWorkers),
-                                            dim3(serveTilesThreads()), args, 0, s->stream));
+                                            dim3(serveTilesThreads()), args,
+                                            serveTilesSmem(s->tileStageBytes), s->stream));
   if (r != vSuccess) return r;
   r = fromCudaS(cudaEventRecord(s->tilesEnd, s->stream));
   if (r == vSuccess) s->tilesUp = true;
@@ -352,29 +356,50 @@ bool postTile(vserve* s, Request& q) {
   unsigned long long ch = s->cfg.slotBytes[kSimple] * (unsigned long long)q.plan.chunkSteps / unitBytes;
   ch = ch / epp * epp;
   sr.chunk = ch < epp ? epp : ch;
-  bool aligned = true;
+  bool ptrs = true;
   for (int r = 0; r < q.nranks; r++) {
     sr.send[r] = q.send[r];
     sr.recv[r] = q.recv[r];
-    if (((uintptr_t)q.send[r] | (uintptr_t)q.recv[r]) & 15) aligned = false;
+    if (((uintptr_t)q.send[r] | (uintptr_t)q.recv[r]) & 15) ptrs = false;
   }
-  if ((q.coll == kReduceScatter || q.coll == kAllGather) && (q.count * esz) % 16) aligned = false;
-  sr.vec = aligned ? 1 : 0;
-  // units and tiles: about two tiles per worker CTA, whole iterations of the
-  // CTA, and at most ~2 MiB of traffic per tile so that a small request never
-  // waits long for a free CTA
-  const unsigned long long E = sr.vec ? (copy ? 16 : 16 / esz) : 1;
+  const bool whole = !((q.coll == kReduceScatter || q.coll == kAllGather) && (q.count * esz) % 16);
+  // 1: 16-byte units; 2: aligned buffers, blocks not whole units (shifted
+  // 16-byte accesses, register path); 0: element accesses
+  sr.vec = ptrs ? (whole ? 1 : 2) : 0;
+  // Tiles: about two per worker CTA, and at most ~4 MiB of traffic each so
+  // that a small request never waits long for a free CTA.  Traffic per byte
+  // of a block: AllReduce 2k (k inputs, k outputs), ReduceScatter and
+  // AllGather k + 1.
   const unsigned long long blocks = (q.coll == kAllReduce) ? 1 : (unsigned long long)q.nranks;
-  tr.units = (sr.count / E) * blocks;
-  const unsigned long long g = (unsigned long long)serveTilesUnitsPerIter();
-  const unsigned long long unitTraffic = E * unitBytes *
-      (q.coll == kAllReduce ? 2ull * q.nranks : (unsigned long long)q.nranks + 1);
-  const unsigned long long maxTile = std::max<unsigned long long>(g, (2ull << 20) / unitTraffic / g * g);
-  unsigned long long tu = (tr.units + 2ull * s->tileWorkers - 1) / (2ull * s->tileWorkers);
-  tu = std::min(std::max(tu, g), maxTile);
-  tu = (tu + g - 1) / g * g;
-  tr.tileUnits = tu;
-  tr.ntiles = std::max<unsigned long long>(1, (tr.units + tu - 1) / tu);
+  const unsigned long long factor = q.coll == kAllReduce ? 2ull * q.nranks : (unsigned long long)q.nranks + 1;
+  const unsigned long long twoW = 2ull * (unsigned long long)s->tileWorkers;
+  const unsigned long long Ev = copy ? 16 : 16 / esz;   // elements (bytes) per 16-byte unit
+  tr.blockBytes = sr.vec == 1 ? (sr.count / Ev) * 16 : 0;
+  tr.staged = (sr.vec == 1 && tr.blockBytes >= 16) ? 1 : 0;
+  if (tr.staged) {
+    // byte ranges of a block, whole 4 KiB pieces (bulk copies of 16-byte units)
+    const unsigned long long piece = 4096;
+    const unsigned long long maxTile = std::max<unsigned long long>(piece, (4ull << 20) / factor / piece * piece);
+    unsigned long long tb = (blocks * tr.blockBytes + twoW - 1) / twoW;
+    tb = std::min(std::max(tb, piece), maxTile);
+    tb = (tb + piece - 1) / piece * piece;
+    tr.tileBytes = tb;
+    tr.perBlock = (tr.blockBytes + tb - 1) / tb;
+    tr.ntiles = blocks * tr.perBlock;
+  } else {
+    // the register kernels' units (16-byte units, shifted 16-byte units of
+    // the k blocks, or elements / bytes), whole iterations of the CTA
+    const unsigned long long E = sr.vec ? Ev : 1;
+    tr.units = (sr.vec == 2 && copy) ? sr.count * blocks / 16 : (sr.count / E) * blocks;
+    const unsigned long long g = (unsigned long long)serveTilesUnitsPerIter();
+    const unsigned long long unitTraffic = E * unitBytes * factor;
+    const unsigned long long maxTile = std::max<unsigned long long>(g, (4ull << 20) / unitTraffic / g * g);
+    unsigned long long tu = (tr.units + twoW - 1) / twoW;
+    tu = std::min(std::max(tu, g), maxTile);
+    tu = (tu + g - 1) / g * g;
+    tr.tileUnits = tu;
+    tr.ntiles = std::max<unsigned long long>(1, (tr.units + tu - 1) / tu);
+  }
   tr.klass = q.big ? 1 : 0;
   volatile TileReq* dst = &s->hRing[slot];
   memcpy((void*)dst, &tr, offsetof(TileReq, seq));
@@ -524,7 +549,16 @@ void dispatcher(vserve* s) {
         }
       }
       noteTilesExit(s);
-      if (!s->tilesUp && !s->tileInflight.empty()) {
+      if (!s->tilesUp && s->hCtl->error) {
+        // a bulk copy of the kernel timed out: what it did not finish has failed
+        for (uint64_t t : s->tileInflight) {
+          Request& q = s->reqs[t];
+          s->tileTicket[q.gang] = 0;
+          completeReq(s, q, false);
+        }
+        s->tileInflight.clear();
+        s->threadErr = (vResult_t)s->hCtl->error;
+      } else if (!s->tilesUp && !s->tileInflight.empty()) {
         // the kernel went idle just as requests were posted: the ones it did
         // not take (every one it took has completed) go to a new launch
         const uint64_t from = *(volatile unsigned long long*)&s->hCtl->ingested;
@@ -747,14 +781,28 @@ vResult_t vServeCreate(vserve_t* out, const vserveConfig_t* cfgIn) {
       r = fromCudaS(cudaEventCreateWithFlags(&s->commEv[k], cudaEventDisableTiming));
   }
   if (r == vSuccess && cfg.mode == 3) {
+    // the pipeline stages take the shared memory the kernel's own leaves
+    int maxSmem = 0;
+    cudaFuncAttributes fa{};
+    r = fromCudaS(cudaDeviceGetAttribute(&maxSmem, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->dev));
+    if (r == vSuccess) r = fromCudaS(cudaFuncGetAttributes(&fa, serveTilesKernel()));
+    if (r == vSuccess) {
+      const long long room = (long long)maxSmem - (long long)fa.sharedSizeBytes - (long long)serveTilesSmem(0);
+      s->tileStageBytes = room > 0 ? (unsigned)(room / serveTilesStages() / 128 * 128) : 0;
+      if (s->tileStageBytes < 16 * 128) r = vUnsupported;   // a 128-byte sub-tile for each of 16 inputs
+    }
+    if (r == vSuccess)
+      r = fromCudaS(cudaFuncSetAttribute(serveTilesKernel(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)serveTilesSmem(s->tileStageBytes)));
     int per = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, serveTilesKernel(), serveTilesThreads(), 0) !=
-        cudaSuccess) {
+    if (r == vSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, serveTilesKernel(), serveTilesThreads(),
+                                                      serveTilesSmem(s->tileStageBytes)) != cudaSuccess) {
       (void)cudaGetLastError();
       per = 0;
     }
     s->tileWorkers = per * s->nsm - 1;   // CTA 0 ingests
-    if (s->tileWorkers < 1) r = vUnsupported;
+    if (r == vSuccess && s->tileWorkers < 1) r = vUnsupported;
     if (r == vSuccess) r = fromCudaS(cudaHostAlloc((void**)&s->hRing, sizeof(TileReq) * kTileRing, cudaHostAllocMapped));
     if (r == vSuccess) r = fromCudaS(cudaHostGetDevicePointer((void**)&s->dRing, s->hRing, 0));
     if (r == vSuccess) memset(s->hRing, 0, sizeof(TileReq) * kTileRing);

@@ -4,18 +4,29 @@
 // The host appends requests to a ring in host-mapped memory.  CTA 0 of the
 // kernel (one warp) ingests them in order: it copies each entry into device
 // state and publishes it on one of two device queues, small requests and
-// large ones.  Every other CTA loops: it claims the next tile (a range of
-// 16-byte units) of the first request of the small queue that still has
-// tiles, else of the large queue, folds those units exactly as the direct
-// protocol's kernels do (each unit's ring chain in the ring schedule's order,
-// so the bits are those of a per-call launch with the same plan), and the
-// CTA that finishes a request's last tile writes its completion into
-// host-mapped memory.  A small request that arrives while a large one runs
-// takes the next free CTAs, so it waits for one tile at most, never for the
-// large request; large requests share the GPU tile by tile in arrival order.
+// large ones.  Every other CTA takes the next tile of the first request of
+// the small queue that still has tiles, else of the large queue, and folds
+// its 16-byte units exactly as the direct protocol's kernels do (each unit's
+// ring chain in the ring schedule's order, so the bits are those of a
+// per-call launch with the same plan).  The CTA that finishes a request's
+// last tile writes its completion into host-mapped memory.  A small request
+// that arrives while a large one runs takes the next free CTAs, so it waits
+// for a tile at most, never for the large request; large requests share the
+// GPU tile by tile in arrival order.
+//
+// Data movement.  A tile of a 16-byte aligned request is a byte range of one
+// block (AllReduce: the buffer; ReduceScatter / AllGather: block b) that moves
+// through shared memory in sub-tiles: thread 0 issues bulk asynchronous copies
+// of the sub-tile's inputs (k for a reduction, one for AllGather) into one of
+// three stages, all threads fold the stage into an output buffer, and thread 0
+// bulk-stores it to every output.  The stages run ahead across tile
+// boundaries (thread 0 claims the next tile while the current one is still
+// folding), so the loads in flight never drain between tiles.  Unaligned
+// requests take the register kernels' element-wise path, one tile at a time.
 //
 // No CTA waits on another: claims and completions are atomics, and the only
-// waits are the idle polls, bounded by the idle timeout and by the stop word.
+// waits are the idle polls (bounded by the idle timeout and the stop word)
+// and the waits for this CTA's own bulk copies (bounded by copyTimeoutNs).
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -28,10 +39,10 @@ namespace {
 
 using namespace direct;
 
-// units per thread per iteration (one body per (dtype, op), out of line, so
-// that each keeps its own registers)
-template <class T> struct TileNU { static constexpr int value = 2; };
 constexpr int kTileThreads = 256;
+constexpr int kTileStages = 3;
+constexpr unsigned kTileOutBytes = 16384;   // one folded sub-tile, double buffered
+constexpr int kTileNU = 2;                  // register path: units per thread per iteration
 
 VDEV uint64_t ldAcquireSys(const unsigned long long* p) {
   uint64_t v;
@@ -40,63 +51,31 @@ VDEV uint64_t ldAcquireSys(const unsigned long long* p) {
 }
 VDEV uint64_t ldVol(const unsigned long long* p) { return *(const volatile unsigned long long*)p; }
 VDEV void stVol(unsigned long long* p, uint64_t v) { *(volatile unsigned long long*)p = v; }
-
-// 16-byte units read through L2 only: the kernel outlives the requests, and
-// a buffer the host rewrote between two requests must not be served from a
-// line an SM's L1 kept from the earlier one
-template <class T>
-struct Unit16L2 {
-  using W = uint4;
-  static constexpr int kElems = 16 / sizeof(T);
-  static VDEV W load(const char* p) { return ldCG(p); }
-  static VDEV void store(char* p, W v) { __stcs((uint4*)p, v); }
-};
-template <class T>
-struct Unit1L2 {
-  using W = T;
-  static constexpr int kElems = 1;
-  static VDEV W load(const char* p) {
-    if constexpr (sizeof(T) == 1) {
-      unsigned short v;
-      asm volatile("ld.global.cg.u8 %0, [%1];" : "=h"(v) : "l"(p));
-      return (T)v;
-    } else if constexpr (std::is_same<T, __half>::value) {
-      unsigned short v;
-      asm volatile("ld.global.cg.u16 %0, [%1];" : "=h"(v) : "l"(p));
-      return __ushort_as_half(v);
-    } else if constexpr (std::is_same<T, __nv_bfloat16>::value) {
-      unsigned short v;
-      asm volatile("ld.global.cg.u16 %0, [%1];" : "=h"(v) : "l"(p));
-      return __ushort_as_bfloat16(v);
-    } else if constexpr (std::is_same<T, float>::value) {
-      unsigned v;
-      asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(v) : "l"(p));
-      return __uint_as_float(v);
-    } else {
-      unsigned v;
-      asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(v) : "l"(p));
-      return (T)v;
-    }
-  }
-  static VDEV void store(char* p, W v) { *(T*)p = v; }
-};
+VDEV void bulkWaitDone1() { asm volatile("cp.async.bulk.wait_group 1;" ::: "memory"); }
+// the completed bulk stores' global writes, ordered before what follows
+VDEV void fenceProxyGlobal() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
 VDEV DirectView viewOfReq(const ServeReq* q) {
   return DirectView{(const void* const*)q->send, (void* const*)q->recv, q->count, q->chunk, q->inplaceMask,
                     q->coll, q->nranks, q->nsub, q->root, 0};
 }
 
+// ---- register path (requests that are not 16-byte aligned; vec 2: aligned
+// buffers whose blocks are not whole 16-byte units), one body per (dtype,
+// op), out of line
 template <class T, class Op>
 __device__ __noinline__ void tileReduce(const ServeReq* q, unsigned long long lo, unsigned long long hi,
                                         bool tail) {
   const DirectView v = viewOfReq(q);
-  if (q->vec) directReduce<T, Op, Unit16L2<T>, TileNU<T>::value>(v, lo, hi, tail);
+  if (q->vec == 1) directReduce<T, Op, Unit16L2<T>, kTileNU>(v, lo, hi, tail);
+  else if (q->vec == 2) directReduceShifted<T, Op, L2Mem>(v, lo, hi, tail);
   else directReduce<T, Op, Unit1L2<T>, 1>(v, lo, hi, tail);
 }
 
 __device__ __noinline__ void tileCopy(const ServeReq* q, unsigned long long lo, unsigned long long hi, bool tail) {
   const DirectView v = viewOfReq(q);
-  if (q->vec) directCopy<Unit16L2<uint8_t>>(v, lo, hi, tail);
+  if (q->vec == 1) directCopy<Unit16L2<uint8_t>>(v, lo, hi, tail);
+  else if (q->vec == 2) directCopyShifted<L2Mem>(v, lo, hi, tail);
   else directCopy<Unit1L2<uint8_t>>(v, lo, hi, tail);
 }
 
@@ -112,7 +91,78 @@ __device__ void runTile(const ServeReq* q, unsigned long long lo, unsigned long 
   else mx ? tileReduce<__nv_bfloat16, OpMax>(q, lo, hi, tail) : tileReduce<__nv_bfloat16, OpSum>(q, lo, hi, tail);
 }
 
-// CTA 0, warp 0: ingest ring entries firstSeq, firstSeq + 1, ... in order
+// ---- staged path: fold one sub-tile of `len` bytes (block b, byte offset
+// off in the block) from the stage's inputs (`sub` bytes apart) into o
+template <class T, class Op>
+__device__ __noinline__ void foldStage(const ServeReq* q, const unsigned char* in, unsigned sub,
+                                       unsigned char* o, int b, unsigned long long off, unsigned len) {
+  const DirectView v = viewOfReq(q);
+  const int k = q->nranks;
+  constexpr unsigned long long esz = sizeof(T);
+  unsigned long long runEnd = 0;
+  int seg = 0;
+  for (unsigned u = threadIdx.x * 16u; u < len; u += blockDim.x * 16u) {
+    if (q->coll == kAllReduce) {
+      const unsigned long long e0 = (off + u) / esz;
+      if (e0 >= runEnd) seg = arSegment(v, e0, (int)esz, &runEnd);
+    } else {
+      seg = b;   // ReduceScatter block b: the chain starts at rank b + 1
+    }
+    int r = seg + 1 < k ? seg + 1 : 0;
+    uint4 acc = *(const uint4*)(in + (size_t)r * sub + u);
+    for (int j = 1; j < k; j++) {
+      if (++r == k) r = 0;
+      acc = combine<T, Op, uint4>(acc, *(const uint4*)(in + (size_t)r * sub + u));
+    }
+    *(uint4*)(o + u) = acc;
+  }
+}
+
+VDEV void foldStageAny(const ServeReq* q, const unsigned char* in, unsigned sub, unsigned char* o, int b,
+                       unsigned long long off, unsigned len) {
+  if (q->coll == kAllGather) {   // a copy: the one input as it is
+    for (unsigned u = threadIdx.x * 16u; u < len; u += blockDim.x * 16u)
+      *(uint4*)(o + u) = *(const uint4*)(in + u);
+    return;
+  }
+  const bool mx = q->redop == kMax;
+  if (q->dtype == kI32) mx ? foldStage<int32_t, OpMax>(q, in, sub, o, b, off, len) : foldStage<int32_t, OpSum>(q, in, sub, o, b, off, len);
+  else if (q->dtype == kF32) mx ? foldStage<float, OpMax>(q, in, sub, o, b, off, len) : foldStage<float, OpSum>(q, in, sub, o, b, off, len);
+  else if (q->dtype == kF16) mx ? foldStage<__half, OpMax>(q, in, sub, o, b, off, len) : foldStage<__half, OpSum>(q, in, sub, o, b, off, len);
+  else mx ? foldStage<__nv_bfloat16, OpMax>(q, in, sub, o, b, off, len) : foldStage<__nv_bfloat16, OpSum>(q, in, sub, o, b, off, len);
+}
+
+// the element tail of a staged AllReduce (count not a multiple of the units)
+template <class T, class Op>
+__device__ __noinline__ void tailReduce(const ServeReq* q) {
+  const DirectView v = viewOfReq(q);
+  constexpr unsigned long long E = 16 / sizeof(T);
+  const unsigned long long nunit = q->count / E;
+  const unsigned long long nt = q->count - nunit * E;
+  for (unsigned long long t = threadIdx.x; t < nt; t += blockDim.x) {
+    const unsigned long long i = nunit * E + t;
+    unsigned long long re;
+    const int s = arSegment(v, i, (int)sizeof(T), &re);
+    const T x = foldChain<T, Op, Unit1L2<T>>(v, s, i * sizeof(T));
+    for (int r = 0; r < q->nranks; r++) *(T*)((char*)v.recv[r] + i * sizeof(T)) = x;
+  }
+}
+
+VDEV void tailAny(const ServeReq* q) {
+  const bool mx = q->redop == kMax;
+  if (q->dtype == kI32) mx ? tailReduce<int32_t, OpMax>(q) : tailReduce<int32_t, OpSum>(q);
+  else if (q->dtype == kF32) mx ? tailReduce<float, OpMax>(q) : tailReduce<float, OpSum>(q);
+  else if (q->dtype == kF16) mx ? tailReduce<__half, OpMax>(q) : tailReduce<__half, OpSum>(q);
+  else mx ? tailReduce<__nv_bfloat16, OpMax>(q) : tailReduce<__nv_bfloat16, OpSum>(q);
+}
+
+VDEV bool hasTail(const ServeReq* q) {
+  if (q->coll != kAllReduce) return false;
+  const unsigned long long E = (q->dtype == kF16 || q->dtype == kBF16) ? 8 : 4;
+  return q->count % E != 0;
+}
+
+// ---- CTA 0, warp 0: ingest ring entries firstSeq, firstSeq + 1, ... in order
 __device__ void ingest(const TileArgs& a) {
   const int lane = threadIdx.x & 31;
   TileQueues* q = a.q;
@@ -124,8 +174,8 @@ __device__ void ingest(const TileArgs& a) {
   while (true) {
     int stop = 0, got = 0;
     if (lane == 0) {
-      if (ctl->abort) {
-        stop = 1;
+      if (*(volatile int*)&q->stop) {
+        stop = 1;   // a worker failed
       } else if (ctl->shutdown) {
         // stop taking requests; stop once every ingested one has completed
         const uint64_t now = globaltimer();
@@ -178,80 +228,262 @@ __device__ void ingest(const TileArgs& a) {
   }
 }
 
-// CTAs 1..: take tiles until the stop word is raised and no tile is left
-__device__ void work(const TileArgs& a) {
-  __shared__ ServeReq sReq;
-  __shared__ long long sSlot;
-  __shared__ unsigned long long sTile, sUnits, sTileUnits, sTiles;
-  __shared__ int sStop;
+// thread 0 of a worker: the next tile, small queue first; -1 if none
+VDEV long long claimTile(const TileArgs& a, unsigned long long* tile) {
   TileQueues* q = a.q;
+  for (int c = 0; c < 2; c++) {
+    unsigned long long h = ldVol(&q->head[c]);
+    const unsigned long long t = ldAcquire(&q->tail[c]);
+    while (h < t) {
+      const unsigned long long e = ldVol(&q->entry[c][h % kTileRing]);
+      if ((e >> 32) != (h & 0xffffffffull)) break;   // not this position (cannot happen after tail)
+      const int s = (int)(e & 0xffffffffull) - 1;
+      TileState* st = &a.state[s];
+      const unsigned long long tl = atomicAdd(&st->next, 1ull);
+      if (tl < ldVol(&st->ntiles)) {
+        *tile = tl;
+        return s;
+      }
+      atomicCAS(&q->head[c], h, h + 1);               // every tile of entry h is claimed
+      h++;
+    }
+  }
+  return -1;
+}
+
+// thread 0: one finished tile of request `slot`; the CTA that finishes the
+// last one reports the request
+VDEV void tileDone(const TileArgs& a, int slot) {
+  TileState* st = &a.state[slot];
+  fenceProxyGlobal();
+  __threadfence();                                       // the tile's stores before the count
+  const unsigned long long d = atomicAdd(&st->done, 1ull);
+  if (d + 1 == ldVol(&st->ntiles)) {
+    __threadfence();
+    TileDone* dn = &a.done[slot];
+    stVol(&dn->tStart, ldVol(&st->tStart));
+    stVol(&dn->tEnd, globaltimer());
+    __threadfence_system();
+    stVol(&dn->seq, ldVol(&st->seq));
+    __threadfence_system();
+    atomicAdd(&a.q->completed, 1ull);
+  }
+}
+
+struct StageInfo {
+  unsigned long long off;   // byte offset in the block
+  unsigned len;             // bytes (a multiple of 16)
+  unsigned sub;             // bytes per input in the stage
+  int slot, b;
+  int endOfTile;            // the tile's last sub-tile
+  int tail;                 // the request's last tile, with an element tail
+};
+
+constexpr int kMaxPendingDone = kTileStages + 2;
+
+// ---- CTAs 1..: take tiles until the stop word is raised and none is left
+__device__ void work(const TileArgs& a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ ServeReq sReq[kTileStages];   // the request of each stage
+  __shared__ ServeReq sCur;                // the request being issued (thread 0), or a register tile's
+  __shared__ StageInfo sInfo[kTileStages];
+  __shared__ int sAct;
+  __shared__ long long sRegSlot;
+  __shared__ unsigned long long sRegTile;
+  const unsigned stageBytes = a.stageBytes;
+  unsigned char* in = smem;
+  unsigned char* out = smem + (size_t)kTileStages * stageBytes;
+  uint64_t* bar = (uint64_t*)(out + 2 * (size_t)kTileOutBytes);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kTileStages; s++) mbarInit(&bar[s], 1);
+    fenceBarrierInit();
+  }
+  __syncthreads();
+
+  // thread 0's state: the tile being issued, and the finished tiles whose
+  // completion is not yet confirmed (a tile is done once the bulk-store
+  // group of its last sub-tile has completed)
+  unsigned long long issued = 0, consumed = 0;
+  long long curSlot = -1;
+  unsigned long long curOff = 0, curEnd = 0;
+  unsigned curSub = 0;
+  int curB = 0, curTail = 0;
+  long long regSlot = -1;
+  unsigned long long regTile = 0;
+  int doneSlot[kMaxPendingDone];
+  unsigned long long doneGroup[kMaxPendingDone];
+  int ndone = 0;
   unsigned backoff = 64;
+
   while (true) {
     if (threadIdx.x == 0) {
-      long long slot = -1;
-      unsigned long long tile = 0;
-      for (int c = 0; c < 2 && slot < 0; c++) {
-        unsigned long long h = ldVol(&q->head[c]);
-        const unsigned long long t = ldAcquire(&q->tail[c]);
-        while (h < t) {
-          const unsigned long long e = ldVol(&q->entry[c][h % kTileRing]);
-          if ((e >> 32) != (h & 0xffffffffull)) break;   // not this position (cannot happen after tail)
-          const int s = (int)(e & 0xffffffffull) - 1;
+      // top up the stages: issue sub-tiles of the current tile, claiming the
+      // next tile when it runs out; a register (unaligned) tile waits until
+      // the stages have drained
+      while (issued - consumed < (unsigned long long)kTileStages && regSlot < 0) {
+        if (curSlot < 0) {
+          unsigned long long tl = 0;
+          const long long s = claimTile(a, &tl);
+          if (s < 0) break;
           TileState* st = &a.state[s];
-          const unsigned long long tl = atomicAdd(&st->next, 1ull);
-          if (tl < ldVol(&st->ntiles)) {
-            slot = s;
-            tile = tl;
+          if (!ldVol(&st->staged)) {
+            regSlot = s;
+            regTile = tl;
             break;
           }
-          atomicCAS(&q->head[c], h, h + 1);               // every tile of entry h is claimed
-          h++;
+          for (int i = 0; i < (int)(sizeof(ServeReq) / 8); i++)
+            ((unsigned long long*)&sCur)[i] = ldVol(&((const unsigned long long*)&st->req)[i]);
+          const unsigned long long perBlock = ldVol(&st->perBlock), tb = ldVol(&st->tileBytes);
+          const unsigned long long bb = ldVol(&st->blockBytes);
+          curSlot = s;
+          curB = (int)(tl / perBlock);
+          curOff = (tl % perBlock) * tb;
+          curEnd = curOff + tb < bb ? curOff + tb : bb;
+          curTail = (tl + 1 == ldVol(&st->ntiles)) && hasTail(&sCur);
+          const unsigned nIn = sCur.coll == kAllGather ? 1u : (unsigned)sCur.nranks;
+          unsigned sub = stageBytes / nIn;
+          sub = sub < kTileOutBytes ? sub : kTileOutBytes;
+          curSub = sub & ~127u;
+        }
+        const int stg = (int)(issued % kTileStages);
+        const unsigned len = (unsigned)(curEnd - curOff < curSub ? curEnd - curOff : curSub);
+        StageInfo& si = sInfo[stg];
+        si.off = curOff;
+        si.len = len;
+        si.sub = curSub;
+        si.slot = (int)curSlot;
+        si.b = curB;
+        si.endOfTile = (curOff + len >= curEnd) ? 1 : 0;
+        si.tail = si.endOfTile && curTail;
+        sReq[stg] = sCur;
+        const ServeReq& r = sCur;
+        unsigned char* dst = in + (size_t)stg * stageBytes;
+        if (r.coll == kAllGather) {
+          mbarExpect(&bar[stg], len);
+          bulkLoad(dst, (const char*)r.send[curB] + curOff, len, &bar[stg]);
+        } else {
+          const unsigned long long esz = (r.dtype == kF16 || r.dtype == kBF16) ? 2 : 4;
+          const unsigned long long src =
+              (r.coll == kReduceScatter ? (unsigned long long)curB * r.count * esz : 0ull) + curOff;
+          mbarExpect(&bar[stg], len * (unsigned)r.nranks);
+          for (int q = 0; q < r.nranks; q++)
+            bulkLoad(dst + (size_t)q * curSub, (const char*)r.send[q] + src, len, &bar[stg]);
+        }
+        issued++;
+        curOff += len;
+        if (curOff >= curEnd) curSlot = -1;
+      }
+      int act;
+      if (issued > consumed) {
+        act = 1;                                   // fold the oldest stage
+      } else {
+        // nothing in flight: every store group may complete now
+        bulkWaitAll();
+        for (int i = 0; i < ndone; i++) tileDone(a, doneSlot[i]);
+        ndone = 0;
+        if (regSlot >= 0) {
+          act = 2;                                 // a register tile
+          sRegSlot = regSlot;
+          sRegTile = regTile;
+          TileState* st = &a.state[regSlot];
+          for (int i = 0; i < (int)(sizeof(ServeReq) / 8); i++)
+            ((unsigned long long*)&sCur)[i] = ldVol(&((const unsigned long long*)&st->req)[i]);
+          regSlot = -1;
+        } else if (*(volatile int*)&a.q->stop) {
+          act = 3;                                 // stop
+        } else {
+          act = 0;                                 // idle
+          __nanosleep(backoff);
         }
       }
-      sStop = (slot < 0 && *(volatile int*)&q->stop) ? 1 : 0;
-      sSlot = slot;
-      sTile = tile;
-      if (slot >= 0) {
-        TileState* st = &a.state[slot];
-        sUnits = ldVol(&st->units);
-        sTileUnits = ldVol(&st->tileUnits);
-        sTiles = ldVol(&st->ntiles);
-      } else if (!sStop) {
-        __nanosleep(backoff);
-      }
+      sAct = act;
     }
     __syncthreads();
-    if (sStop) return;
-    const long long slot = sSlot;
-    if (slot < 0) {
+    const int act = sAct;
+    if (act == 3) return;
+    if (act == 0) {
       backoff = backoff < 2048 ? 2 * backoff : 2048;
-      __syncthreads();   // everyone has read sSlot before thread 0 writes it again
+      __syncthreads();   // everyone has read sAct before thread 0 writes it again
       continue;
     }
     backoff = 64;
-    TileState* st = &a.state[slot];
-    for (int i = threadIdx.x; i < (int)(sizeof(ServeReq) / 8); i += blockDim.x)
-      ((unsigned long long*)&sReq)[i] = ldVol(&((const unsigned long long*)&st->req)[i]);
-    __syncthreads();
-    const unsigned long long lo = sTile * sTileUnits;
-    const unsigned long long hi = lo + sTileUnits < sUnits ? lo + sTileUnits : sUnits;
-    runTile(&sReq, lo < hi ? lo : hi, hi, sTile + 1 == sTiles);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();                                   // this tile's stores before the count
-      const unsigned long long d = atomicAdd(&st->done, 1ull);
-      if (d + 1 == sTiles) {                             // the request's last tile: report it
-        __threadfence();
-        TileDone* dn = &a.done[slot];
-        stVol(&dn->tStart, ldVol(&st->tStart));
-        stVol(&dn->tEnd, globaltimer());
-        __threadfence_system();
-        stVol(&dn->seq, ldVol(&st->seq));
-        __threadfence_system();
-        atomicAdd(&q->completed, 1ull);
-      }
+    if (act == 2) {
+      // a tile of an unaligned request: the register kernels' element path
+      TileState* st = &a.state[sRegSlot];
+      const unsigned long long tu = ldVol(&st->tileUnits), units = ldVol(&st->units);
+      const unsigned long long nt = ldVol(&st->ntiles);
+      const unsigned long long lo = sRegTile * tu;
+      const unsigned long long hi = lo + tu < units ? lo + tu : units;
+      runTile(&sCur, lo < hi ? lo : hi, hi, sRegTile + 1 == nt);
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) tileDone(a, (int)sRegSlot);
+      __syncthreads();
+      continue;
     }
-    __syncthreads();   // sReq and the shared words are free again
+    // act == 1: the oldest issued sub-tile
+    const int stg = (int)(consumed % kTileStages);
+    const bool ok = stageWait(&bar[stg], (unsigned)((consumed / kTileStages) & 1ull), a.copyTimeoutNs);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        // loads still in flight must land before the CTA's shared memory is released
+        for (unsigned long long j = consumed; j < issued; j++)
+          (void)stageWait(&bar[j % kTileStages], (unsigned)((j / kTileStages) & 1ull), a.copyTimeoutNs);
+        bulkWaitAll();
+        atomicCAS((int*)&a.ctl->error, 0, (int)vTimeout);
+        atomicExch(&a.q->stop, 1);
+        __threadfence_system();
+      }
+      return;
+    }
+    const int ob = (int)(consumed & 1ull);
+    if (threadIdx.x == 0) {
+      // out[ob] was last read by the store group of sub-tile consumed - 2,
+      // complete once at most one group (that of consumed - 1) is pending;
+      // the tiles whose last group is complete are done
+      bulkWaitDone1();
+      int keep = 0;
+      for (int i = 0; i < ndone; i++) {
+        if (doneGroup[i] + 2 <= consumed) {
+          tileDone(a, doneSlot[i]);
+        } else {
+          doneSlot[keep] = doneSlot[i];
+          doneGroup[keep] = doneGroup[i];
+          keep++;
+        }
+      }
+      ndone = keep;
+    }
+    __syncthreads();
+    const StageInfo si = sInfo[stg];
+    const ServeReq* r = &sReq[stg];
+    unsigned char* o = out + (size_t)ob * kTileOutBytes;
+    foldStageAny(r, in + (size_t)stg * stageBytes, si.sub, o, si.b, si.off, si.len);
+    fenceProxyAsync();
+    __syncthreads();   // o written; the stage read by every thread
+    if (threadIdx.x == 0) {
+      if (r->coll == kReduceScatter) {
+        bulkStore((char*)r->recv[si.b] + si.off, o, si.len);
+      } else {
+        const unsigned long long dst = (r->coll == kAllGather ? (unsigned long long)si.b * r->count : 0ull) + si.off;
+        for (int q = 0; q < r->nranks; q++) bulkStore((char*)r->recv[q] + dst, o, si.len);
+      }
+      bulkCommit();
+    }
+    if (si.tail) {   // the element tail, with ordinary loads and stores
+      tailAny(r);
+      __threadfence();
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      if (si.endOfTile) {
+        doneSlot[ndone] = si.slot;
+        doneGroup[ndone] = consumed;
+        ndone++;
+      }
+      consumed++;
+    }
+    __syncthreads();   // the stage info and request copies are free again
   }
 }
 
@@ -267,6 +499,11 @@ __global__ void __launch_bounds__(kTileThreads, 1) kServeTiles(const __grid_cons
 
 const void* serveTilesKernel() { return (const void*)kServeTiles; }
 int serveTilesThreads() { return kTileThreads; }
-int serveTilesUnitsPerIter() { return kTileThreads * 2; }
+int serveTilesUnitsPerIter() { return kTileThreads * kTileNU; }
+int serveTilesStages() { return kTileStages; }
+unsigned serveTilesOutBytes() { return kTileOutBytes; }
+size_t serveTilesSmem(unsigned stageBytes) {
+  return (size_t)kTileStages * stageBytes + 2 * (size_t)kTileOutBytes + 8 * (size_t)kTileStages;
+}
 
 }  // namespace vc
