@@ -978,6 +978,54 @@ def headline_leg(args, rank, world, proto, wname):
             "clocks": r["clocks"]}
 
 
+def run_chain_sweep(path):
+    """Ring Broadcast (root 0), Reduce (root 0) and AllReduce with the Simple
+    protocol, fp16, 128 MiB per vrank, on 8, 12 and 16 vranks at pinned
+    channel counts on both sides of SMs / vranks (the chains' channels are
+    capped there; the plan read back shows the channels that ran); median of
+    5 launches timed alone.  One JSON line per point."""
+    import torch
+
+    from paper_2507_04786_b300 import Comm
+    S = 128 << 20
+    rows = []
+    with open(path, "w") as f:
+        for k, chans in ((8, (8, 16, 18)), (12, (8, 12, 16)), (16, (4, 8, 9, 10, 12, 16))):
+            n = S // 2
+            xs = [torch.ones(n, dtype=torch.float16, device="cuda") for _ in range(k)]
+            ys = [torch.empty_like(x) for x in xs]
+            c = Comm(k, max(chans))
+            for C in chans:
+                c.set_plan(nchannels=C, chunk_steps=1)
+                for coll in ("broadcast", "reduce", "allreduce"):
+                    if coll == "broadcast":
+                        call = lambda: c.broadcast(xs, ys, root=0, algo="ring", proto="simple")
+                    elif coll == "reduce":
+                        call = lambda: c.reduce(xs, [ys[0]] + [None] * (k - 1), root=0, algo="ring",
+                                                proto="simple")
+                    else:
+                        call = lambda: c.all_reduce(xs, ys, algo="ring", proto="simple")
+                    for _ in range(2):
+                        call()
+                    torch.cuda.synchronize()
+                    ts = []
+                    for _ in range(5):
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record()
+                        call()
+                        e1.record()
+                        e1.synchronize()
+                        ts.append(e0.elapsed_time(e1))
+                    row = {"coll": coll, "nranks": k, "pinned_channels": C,
+                           "channels": c.last_plan()["nchannels"], "ms": round(float(np.median(ts)), 3)}
+                    rows.append(row)
+                    f.write(json.dumps(row) + "\n")
+            assert c.async_error() == "vSuccess"
+            c.destroy()
+            del xs, ys
+    return rows
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -1028,6 +1076,9 @@ def main():
     ap.add_argument("--sweep-colls", default=None,
                     help="sweep ReduceScatter / AllGather / Broadcast / Reduce (direct and Simple), "
                          "write JSON lines here, exit")
+    ap.add_argument("--sweep-chains", default=None,
+                    help="time ring Broadcast / Reduce / AllReduce (Simple, fp16, 128 MiB) over vranks and "
+                         "channels, write JSON lines here, exit")
     ap.add_argument("--bytes", type=int, default=workloads.HEADLINE["bytes_per_rank"],
                     help="bytes per vrank (default: the headline's 256 MiB; smaller sizes are "
                          "for profiling captures only)")
@@ -1040,6 +1091,10 @@ def main():
         return
     if args.sweep_colls:
         run_coll_sweep(args.sweep_colls)
+        return
+    if args.sweep_chains:
+        for r in run_chain_sweep(args.sweep_chains):
+            print(json.dumps(r))
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -221,6 +221,9 @@ VDEV void reportFailure(const KernArgs& a, int code, int rank, int ch, int where
 }
 
 // Spin until *p >= v.  Returns false (after recording why) on deadline or abort.
+// After ~1024 polls (a few microseconds: a chain's pipeline filling, not a
+// step's hand-over) the poller sleeps between polls, so that it stops taking
+// issue slots and L2 requests from a CTA moving data on the same SM.
 VDEV bool waitGeq(const KernArgs& a, const unsigned long long* p, uint64_t v, int rank, int ch,
                   int where) {
   if (ldAcquire(p) >= v) return true;
@@ -228,6 +231,7 @@ VDEV bool waitGeq(const KernArgs& a, const unsigned long long* p, uint64_t v, in
   unsigned it = 0;
   while (true) {
     if (ldAcquire(p) >= v) return true;
+    if (it >= 1024) __nanosleep(128);
     if (((++it) & 127u) == 0) {
       if (*a.abortFlag) { reportFailure(a, vAborted, rank, ch, where); return false; }
       if (globaltimer() - t0 > a.timeoutNs) { reportFailure(a, vTimeout, rank, ch, where); return false; }

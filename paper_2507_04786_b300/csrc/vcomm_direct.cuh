@@ -338,45 +338,74 @@ VDEV uint4 loadShifted(const char* p, unsigned long long x, unsigned long long s
 }
 
 // ReduceScatter units [lo, hi) (16-byte output units of the k blocks, block
-// b's full units first); `tail`: this CTA also does each block's element tail
-template <class T, class Op, class M>
+// b's full units first), NU units per thread per iteration whose loads are
+// issued together, 4 ranks at a time; `tail`: this CTA also does each
+// block's element tail
+template <class T, class Op, class M, int NU>
 VDEV void directReduceShifted(const DirectView& a, unsigned long long lo, unsigned long long hi, bool tail) {
   const int k = a.nranks;
   constexpr int E = 16 / sizeof(T);
   const unsigned long long esz = sizeof(T);
   const unsigned long long nunit = a.count / E;   // full output units per block
   const unsigned long long blockB = a.count * esz, size = blockB * (unsigned long long)k;
-  for (unsigned long long g = lo + threadIdx.x; g < hi; g += blockDim.x) {
-    const unsigned long long b = g / nunit, e = g % nunit;
-    const unsigned long long x = b * blockB + e * 16ull;
-    int r = (int)b + 1 < k ? (int)b + 1 : 0;
-    uint4 acc = loadShifted<M>((const char*)a.send[r], x, size);
+  for (unsigned long long g0 = lo + threadIdx.x; g0 < hi; g0 += (unsigned long long)NU * blockDim.x) {
+    unsigned long long x[NU], b[NU], e[NU];
+    int r[NU];
+    int nu = 0;
+#pragma unroll
+    for (int u = 0; u < NU; u++) {
+      const unsigned long long g = g0 + (unsigned long long)u * blockDim.x;
+      b[u] = 0;
+      e[u] = 0;
+      x[u] = 0;
+      r[u] = 0;
+      if (g >= hi) continue;
+      nu = u + 1;
+      b[u] = g / nunit;
+      e[u] = g % nunit;
+      x[u] = b[u] * blockB + e[u] * 16ull;
+      r[u] = (int)b[u] + 1 < k ? (int)b[u] + 1 : 0;
+    }
+    uint4 acc[NU];
+#pragma unroll
+    for (int u = 0; u < NU; u++)
+      if (u < nu) acc[u] = loadShifted<M>((const char*)a.send[r[u]], x[u], size);
     constexpr int B = 4;
     for (int j = 1; j < k; j += B) {
-      uint4 v[B];
+      uint4 v[NU][B];
 #pragma unroll
-      for (int i = 0; i < B; i++) {
-        int rr = r + 1 + i;
-        if (rr >= k) rr -= k;
-        if (j + i < k) v[i] = loadShifted<M>((const char*)a.send[rr], x, size);
+      for (int u = 0; u < NU; u++) {
+#pragma unroll
+        for (int i = 0; i < B; i++) {
+          int rr = r[u] + 1 + i;
+          if (rr >= k) rr -= k;
+          if (u < nu && j + i < k) v[u][i] = loadShifted<M>((const char*)a.send[rr], x[u], size);
+        }
       }
 #pragma unroll
-      for (int i = 0; i < B; i++)
-        if (j + i < k) acc = combine<T, Op, uint4>(acc, v[i]);
-      r += B;
-      if (r >= k) r -= k;
+      for (int u = 0; u < NU; u++) {
+#pragma unroll
+        for (int i = 0; i < B; i++)
+          if (u < nu && j + i < k) acc[u] = combine<T, Op, uint4>(acc[u], v[u][i]);
+        r[u] += B;
+        if (r[u] >= k) r[u] -= k;
+      }
     }
-    if (a.postDiv) acc = divide<T, Unit16<T>>(acc, a.postDiv);
-    *(uint4*)((char*)a.recv[b] + e * 16ull) = acc;
+#pragma unroll
+    for (int u = 0; u < NU; u++) {
+      if (u >= nu) continue;
+      if (a.postDiv) acc[u] = divide<T, Unit16<T>>(acc[u], a.postDiv);
+      *(uint4*)((char*)a.recv[b[u]] + e[u] * 16ull) = acc[u];
+    }
   }
   const unsigned long long nt = a.count - nunit * E;   // element tail of each block
   if (nt && tail) {
     using U1 = typename M::template Elem<T>;
     for (unsigned long long t = threadIdx.x; t < nt * (unsigned long long)k; t += blockDim.x) {
-      const unsigned long long b = t / nt, i = nunit * E + t % nt;
-      T v = foldChain<T, Op, U1>(a, (int)b, (b * a.count + i) * esz);
+      const unsigned long long bl = t / nt, i = nunit * E + t % nt;
+      T v = foldChain<T, Op, U1>(a, (int)bl, (bl * a.count + i) * esz);
       if (a.postDiv) v = divElem<T>(v, a.postDiv);
-      U1::store((char*)a.recv[b] + i * esz, v);
+      U1::store((char*)a.recv[bl] + i * esz, v);
     }
   }
 }

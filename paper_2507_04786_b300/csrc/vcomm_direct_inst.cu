@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(DirectShape<T>::kThreads, 1)
     directReduce<T, Op, Unit16<T>, DirectShape<T>::kUnits>(v, lo, hi, last);
   } else if (a.vec == 2) {
     ctaRange(shiftedUnits(v, (int)sizeof(T)), &lo, &hi);
-    directReduceShifted<T, Op, PlainMem>(v, lo, hi, last);
+    directReduceShifted<T, Op, PlainMem, DirectShape<T>::kUnits>(v, lo, hi, last);
   } else {
     ctaRange(reduceUnits(v, 1), &lo, &hi);
     directReduce<T, Op, Unit1<T>, 1>(v, lo, hi, last);
@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(DirectShape<T>::kThreads, 1)
     // registers for)
     constexpr int NU = sizeof(T) == 2 ? 1 : DirectShape<T>::kUnits;
     if (pb->ops[i].vec == 1) directReduce<T, Op, Unit16<T>, NU>(v, lo, hi, tail);
-    else if (pb->ops[i].vec == 2) directReduceShifted<T, Op, PlainMem>(v, lo, hi, tail);
+    else if (pb->ops[i].vec == 2) directReduceShifted<T, Op, PlainMem, 1>(v, lo, hi, tail);
     else directReduce<T, Op, Unit1<T>, 1>(v, lo, hi, tail);
   }
 }

@@ -197,6 +197,28 @@ void planFor(const vserve* s, Request& q) {
   q.plan = vPlan_t{vAlgoRing, p, ch, 1};
 }
 
+// Kernels are loaded on their first launch; a server that launches per
+// request would otherwise pay that (milliseconds) inside the latency of its
+// first requests of every kind.  Looking up a kernel's attributes loads it.
+void preloadKernels(int mode) {
+  std::vector<const void*> fns;
+  for (int dt = vInt32; dt <= vBfloat16; dt++) {
+    for (int op = vSum; op <= vMax; op++) {
+      for (int coll : {kAllReduce, kReduceScatter, kAllGather}) fns.push_back(directKernel(coll, dt, op));
+      fns.push_back(directStagedKernel(dt, op));
+      if (mode == 1 || mode == 2)
+        for (int p = 0; p < 3; p++) fns.push_back(reduceKernel(p, dt, op));
+    }
+  }
+  fns.push_back(copyStagedKernel());
+  if (mode == 1 || mode == 2)
+    for (int p = 0; p < 3; p++) fns.push_back(copyKernel(p));
+  for (const void* f : fns) {
+    cudaFuncAttributes fa;
+    if (f && cudaFuncGetAttributes(&fa, f) != cudaSuccess) (void)cudaGetLastError();
+  }
+}
+
 void completeReq(vserve* s, Request& q, bool ok) {
   q.doneNs = nowNs();
   q.state = ok ? 2 : 3;
@@ -830,6 +852,7 @@ vResult_t vServeCreate(vserve_t* out, const vserveConfig_t* cfgIn) {
       if (r == vSuccess && k > 1) r = vcommPrepare(s->comms[k], 1u << vAlgoRing, 0xEu);
     }
   }
+  if (r == vSuccess && cfg.mode >= 1) preloadKernels(cfg.mode);
   if (r != vSuccess) {
     vServeDestroy(s);
     return r;

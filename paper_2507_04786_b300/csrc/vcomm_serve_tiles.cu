@@ -68,7 +68,7 @@ __device__ __noinline__ void tileReduce(const ServeReq* q, unsigned long long lo
                                         bool tail) {
   const DirectView v = viewOfReq(q);
   if (q->vec == 1) directReduce<T, Op, Unit16L2<T>, kTileNU>(v, lo, hi, tail);
-  else if (q->vec == 2) directReduceShifted<T, Op, L2Mem>(v, lo, hi, tail);
+  else if (q->vec == 2) directReduceShifted<T, Op, L2Mem, kTileNU>(v, lo, hi, tail);
   else directReduce<T, Op, Unit1L2<T>, 1>(v, lo, hi, tail);
 }
 
@@ -300,9 +300,10 @@ __device__ void work(const TileArgs& a) {
   }
   __syncthreads();
 
-  // thread 0's state: the tile being issued, and the finished tiles whose
-  // completion is not yet confirmed (a tile is done once the bulk-store
-  // group of its last sub-tile has completed)
+  // `consumed`: sub-tiles folded, counted by every thread alike.  The rest
+  // is thread 0's: sub-tiles issued, the tile being issued, and the finished
+  // tiles whose completion is not yet confirmed (a tile is done once the
+  // bulk-store group of its last sub-tile has completed)
   unsigned long long issued = 0, consumed = 0;
   long long curSlot = -1;
   unsigned long long curOff = 0, curEnd = 0;
@@ -475,14 +476,12 @@ __device__ void work(const TileArgs& a) {
       __threadfence();
       __syncthreads();
     }
-    if (threadIdx.x == 0) {
-      if (si.endOfTile) {
-        doneSlot[ndone] = si.slot;
-        doneGroup[ndone] = consumed;
-        ndone++;
-      }
-      consumed++;
+    if (threadIdx.x == 0 && si.endOfTile) {
+      doneSlot[ndone] = si.slot;
+      doneGroup[ndone] = consumed;
+      ndone++;
     }
+    consumed++;        // every thread counts the stages it has folded
     __syncthreads();   // the stage info and request copies are free again
   }
 }
