@@ -337,6 +337,34 @@ VDEV uint4 loadShifted(const char* p, unsigned long long x, unsigned long long s
   return u.v;
 }
 
+// The same 16 bytes when the warp's 32 lanes take 32 consecutive pieces of
+// one block (warp-uniform `together`, every lane active): lane l's piece
+// starts d bytes into aligned unit a0 and ends in unit a0 + 16, which is
+// lane l + 1's a0, so each lane loads its own unit, takes its neighbour's by
+// shuffle, and lane 31 loads the one after.  One load per piece instead of two.
+template <class M>
+VDEV uint4 loadShiftedWarp(const char* p, unsigned long long x, unsigned long long size, bool together) {
+  if (!together) return loadShifted<M>(p, x, size);
+  const unsigned d = (unsigned)(x & 15ull);   // the same in every lane (one block)
+  const unsigned long long a0 = x - d;
+  const uint4 lo = M::load16(p + a0);
+  if (d == 0) return lo;
+  const int lane = threadIdx.x & 31;
+  const bool extraOk = a0 + 32 <= size;
+  uint4 extra = lo;
+  if (lane == 31 && extraOk) extra = M::load16(p + a0 + 16);
+  uint4 hi;
+  hi.x = __shfl_down_sync(0xffffffffu, lo.x, 1);
+  hi.y = __shfl_down_sync(0xffffffffu, lo.y, 1);
+  hi.z = __shfl_down_sync(0xffffffffu, lo.z, 1);
+  hi.w = __shfl_down_sync(0xffffffffu, lo.w, 1);
+  if (lane == 31) {
+    if (!extraOk) return loadShifted<M>(p, x, size);
+    hi = extra;
+  }
+  return shiftBytes(lo, hi, d);
+}
+
 // ReduceScatter units [lo, hi) (16-byte output units of the k blocks, block
 // b's full units first), NU units per thread per iteration whose loads are
 // issued together, 4 ranks at a time; `tail`: this CTA also does each
@@ -366,10 +394,22 @@ VDEV void directReduceShifted(const DirectView& a, unsigned long long lo, unsign
       x[u] = b[u] * blockB + e[u] * 16ull;
       r[u] = (int)b[u] + 1 < k ? (int)b[u] + 1 : 0;
     }
+    // the pieces of a unit group are loaded warp-cooperatively when all 32
+    // lanes are active and in one block
+    bool together[NU];
+    const unsigned am = __activemask();
+#pragma unroll
+    for (int u = 0; u < NU; u++) {
+      together[u] = false;
+      if (am == 0xffffffffu) {
+        const unsigned long long b0 = __shfl_sync(0xffffffffu, b[u], 0);
+        together[u] = __all_sync(0xffffffffu, u < nu && b[u] == b0);
+      }
+    }
     uint4 acc[NU];
 #pragma unroll
     for (int u = 0; u < NU; u++)
-      if (u < nu) acc[u] = loadShifted<M>((const char*)a.send[r[u]], x[u], size);
+      if (u < nu || together[u]) acc[u] = loadShiftedWarp<M>((const char*)a.send[r[u]], x[u], size, together[u]);
     constexpr int B = 4;
     for (int j = 1; j < k; j += B) {
       uint4 v[NU][B];
@@ -379,7 +419,7 @@ VDEV void directReduceShifted(const DirectView& a, unsigned long long lo, unsign
         for (int i = 0; i < B; i++) {
           int rr = r[u] + 1 + i;
           if (rr >= k) rr -= k;
-          if (u < nu && j + i < k) v[u][i] = loadShifted<M>((const char*)a.send[rr], x[u], size);
+          if (u < nu && j + i < k) v[u][i] = loadShiftedWarp<M>((const char*)a.send[rr], x[u], size, together[u]);
         }
       }
 #pragma unroll

@@ -51,7 +51,9 @@ VDEV uint64_t ldAcquireSys(const unsigned long long* p) {
 }
 VDEV uint64_t ldVol(const unsigned long long* p) { return *(const volatile unsigned long long*)p; }
 VDEV void stVol(unsigned long long* p, uint64_t v) { *(volatile unsigned long long*)p = v; }
-VDEV void bulkWaitDone1() { asm volatile("cp.async.bulk.wait_group 1;" ::: "memory"); }
+// every store group but the newest kDoneLag has completed (its global writes)
+constexpr int kDoneLag = 4;
+VDEV void bulkWaitDoneLag() { asm volatile("cp.async.bulk.wait_group 4;" ::: "memory"); }
 // the completed bulk stores' global writes, ordered before what follows
 VDEV void fenceProxyGlobal() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
@@ -279,7 +281,7 @@ struct StageInfo {
   int tail;                 // the request's last tile, with an element tail
 };
 
-constexpr int kMaxPendingDone = kTileStages + 2;
+constexpr int kMaxPendingDone = kDoneLag + 4;
 
 // ---- CTAs 1..: take tiles until the stop word is raised and none is left
 __device__ void work(const TileArgs& a) {
@@ -311,6 +313,8 @@ __device__ void work(const TileArgs& a) {
   int curB = 0, curTail = 0;
   long long regSlot = -1;
   unsigned long long regTile = 0;
+  unsigned curGen = 0, stageGen[kTileStages];   // which claim each stage's request copy is of
+  for (int i = 0; i < kTileStages; i++) stageGen[i] = ~0u;
   int doneSlot[kMaxPendingDone];
   unsigned long long doneGroup[kMaxPendingDone];
   int ndone = 0;
@@ -337,6 +341,7 @@ __device__ void work(const TileArgs& a) {
           const unsigned long long perBlock = ldVol(&st->perBlock), tb = ldVol(&st->tileBytes);
           const unsigned long long bb = ldVol(&st->blockBytes);
           curSlot = s;
+          curGen++;
           curB = (int)(tl / perBlock);
           curOff = (tl % perBlock) * tb;
           curEnd = curOff + tb < bb ? curOff + tb : bb;
@@ -356,7 +361,10 @@ __device__ void work(const TileArgs& a) {
         si.b = curB;
         si.endOfTile = (curOff + len >= curEnd) ? 1 : 0;
         si.tail = si.endOfTile && curTail;
-        sReq[stg] = sCur;
+        if (stageGen[stg] != curGen) {   // the stage holds another claim's request
+          sReq[stg] = sCur;
+          stageGen[stg] = curGen;
+        }
         const ServeReq& r = sCur;
         unsigned char* dst = in + (size_t)stg * stageBytes;
         if (r.coll == kAllGather) {
@@ -440,12 +448,13 @@ __device__ void work(const TileArgs& a) {
     const int ob = (int)(consumed & 1ull);
     if (threadIdx.x == 0) {
       // out[ob] was last read by the store group of sub-tile consumed - 2,
-      // complete once at most one group (that of consumed - 1) is pending;
-      // the tiles whose last group is complete are done
-      bulkWaitDone1();
+      // which has read it once at most one group is pending; the tiles whose
+      // last group is older than the newest kDoneLag are done
+      bulkWaitRead1();
+      bulkWaitDoneLag();
       int keep = 0;
       for (int i = 0; i < ndone; i++) {
-        if (doneGroup[i] + 2 <= consumed) {
+        if (doneGroup[i] + kDoneLag + 1 <= consumed) {
           tileDone(a, doneSlot[i]);
         } else {
           doneSlot[keep] = doneSlot[i];
