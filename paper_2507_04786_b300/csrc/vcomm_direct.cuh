@@ -337,38 +337,15 @@ VDEV uint4 loadShifted(const char* p, unsigned long long x, unsigned long long s
   return u.v;
 }
 
-// The same 16 bytes when the warp's 32 lanes take 32 consecutive pieces of
-// one block (warp-uniform `together`, every lane active): lane l's piece
-// starts d bytes into aligned unit a0 and ends in unit a0 + 16, which is
-// lane l + 1's a0, so each lane loads its own unit, takes its neighbour's by
-// shuffle, and lane 31 loads the one after.  One load per piece instead of two.
-template <class M>
-VDEV uint4 loadShiftedWarp(const char* p, unsigned long long x, unsigned long long size, bool together) {
-  if (!together) return loadShifted<M>(p, x, size);
-  const unsigned d = (unsigned)(x & 15ull);   // the same in every lane (one block)
-  const unsigned long long a0 = x - d;
-  const uint4 lo = M::load16(p + a0);
-  if (d == 0) return lo;
-  const int lane = threadIdx.x & 31;
-  const bool extraOk = a0 + 32 <= size;
-  uint4 extra = lo;
-  if (lane == 31 && extraOk) extra = M::load16(p + a0 + 16);
-  uint4 hi;
-  hi.x = __shfl_down_sync(0xffffffffu, lo.x, 1);
-  hi.y = __shfl_down_sync(0xffffffffu, lo.y, 1);
-  hi.z = __shfl_down_sync(0xffffffffu, lo.z, 1);
-  hi.w = __shfl_down_sync(0xffffffffu, lo.w, 1);
-  if (lane == 31) {
-    if (!extraOk) return loadShifted<M>(p, x, size);
-    hi = extra;
-  }
-  return shiftBytes(lo, hi, d);
-}
-
 // ReduceScatter units [lo, hi) (16-byte output units of the k blocks, block
-// b's full units first), NU units per thread per iteration whose loads are
-// issued together, 4 ranks at a time; `tail`: this CTA also does each
-// block's element tail
+// b's full units first), NU units per thread per iteration, 4 ranks at a
+// time.  A unit's piece starts d = (b n size) mod 16 bytes into aligned unit
+// a0 of every rank's buffer; whether the unit after a0 lies inside the
+// buffer is decided once per unit, so the loads of all ranks are issued
+// together, without branches, before the first shift (for d = 0 the second
+// load repeats the first).  Units whose second aligned unit would pass the
+// end of the buffer take loadShifted.  `tail`: this CTA also does each
+// block's element tail.
 template <class T, class Op, class M, int NU>
 VDEV void directReduceShifted(const DirectView& a, unsigned long long lo, unsigned long long hi, bool tail) {
   const int k = a.nranks;
@@ -377,9 +354,11 @@ VDEV void directReduceShifted(const DirectView& a, unsigned long long lo, unsign
   const unsigned long long nunit = a.count / E;   // full output units per block
   const unsigned long long blockB = a.count * esz, size = blockB * (unsigned long long)k;
   for (unsigned long long g0 = lo + threadIdx.x; g0 < hi; g0 += (unsigned long long)NU * blockDim.x) {
-    unsigned long long x[NU], b[NU], e[NU];
+    unsigned long long x[NU], a0[NU], a1[NU], b[NU], e[NU];
+    unsigned d[NU];
     int r[NU];
     int nu = 0;
+    bool fast = true;
 #pragma unroll
     for (int u = 0; u < NU; u++) {
       const unsigned long long g = g0 + (unsigned long long)u * blockDim.x;
@@ -387,46 +366,73 @@ VDEV void directReduceShifted(const DirectView& a, unsigned long long lo, unsign
       e[u] = 0;
       x[u] = 0;
       r[u] = 0;
-      if (g >= hi) continue;
-      nu = u + 1;
-      b[u] = g / nunit;
-      e[u] = g % nunit;
-      x[u] = b[u] * blockB + e[u] * 16ull;
-      r[u] = (int)b[u] + 1 < k ? (int)b[u] + 1 : 0;
-    }
-    // the pieces of a unit group are loaded warp-cooperatively when all 32
-    // lanes are active and in one block
-    bool together[NU];
-    const unsigned am = __activemask();
-#pragma unroll
-    for (int u = 0; u < NU; u++) {
-      together[u] = false;
-      if (am == 0xffffffffu) {
-        const unsigned long long b0 = __shfl_sync(0xffffffffu, b[u], 0);
-        together[u] = __all_sync(0xffffffffu, u < nu && b[u] == b0);
+      if (g < hi) {
+        nu = u + 1;
+        b[u] = g / nunit;
+        e[u] = g % nunit;
+        x[u] = b[u] * blockB + e[u] * 16ull;
+        r[u] = (int)b[u] + 1 < k ? (int)b[u] + 1 : 0;
       }
+      d[u] = (unsigned)(x[u] & 15ull);
+      a0[u] = x[u] - d[u];
+      a1[u] = d[u] ? a0[u] + 16 : a0[u];
+      if (g < hi && a0[u] + 32 > size && d[u]) fast = false;
     }
     uint4 acc[NU];
-#pragma unroll
-    for (int u = 0; u < NU; u++)
-      if (u < nu || together[u]) acc[u] = loadShiftedWarp<M>((const char*)a.send[r[u]], x[u], size, together[u]);
-    constexpr int B = 4;
-    for (int j = 1; j < k; j += B) {
-      uint4 v[NU][B];
+    if (fast) {
+      uint4 l0[NU], h0[NU];
 #pragma unroll
       for (int u = 0; u < NU; u++) {
+        if (u < nu) {
+          l0[u] = M::load16((const char*)a.send[r[u]] + a0[u]);
+          h0[u] = M::load16((const char*)a.send[r[u]] + a1[u]);
+        }
+      }
 #pragma unroll
-        for (int i = 0; i < B; i++) {
-          int rr = r[u] + 1 + i;
-          if (rr >= k) rr -= k;
-          if (u < nu && j + i < k) v[u][i] = loadShiftedWarp<M>((const char*)a.send[rr], x[u], size, together[u]);
+      for (int u = 0; u < NU; u++)
+        if (u < nu) acc[u] = shiftBytes(l0[u], h0[u], d[u]);
+    } else {
+#pragma unroll
+      for (int u = 0; u < NU; u++)
+        if (u < nu) acc[u] = loadShifted<M>((const char*)a.send[r[u]], x[u], size);
+    }
+    constexpr int B = 4;
+    for (int j = 1; j < k; j += B) {
+      uint4 vl[NU][B], vh[NU][B];
+      if (fast) {
+#pragma unroll
+        for (int u = 0; u < NU; u++) {
+#pragma unroll
+          for (int i = 0; i < B; i++) {
+            int rr = r[u] + 1 + i;
+            if (rr >= k) rr -= k;
+            if (u < nu && j + i < k) {
+              vl[u][i] = M::load16((const char*)a.send[rr] + a0[u]);
+              vh[u][i] = M::load16((const char*)a.send[rr] + a1[u]);
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < NU; u++)
+#pragma unroll
+          for (int i = 0; i < B; i++)
+            if (u < nu && j + i < k) vl[u][i] = shiftBytes(vl[u][i], vh[u][i], d[u]);
+      } else {
+#pragma unroll
+        for (int u = 0; u < NU; u++) {
+#pragma unroll
+          for (int i = 0; i < B; i++) {
+            int rr = r[u] + 1 + i;
+            if (rr >= k) rr -= k;
+            if (u < nu && j + i < k) vl[u][i] = loadShifted<M>((const char*)a.send[rr], x[u], size);
+          }
         }
       }
 #pragma unroll
       for (int u = 0; u < NU; u++) {
 #pragma unroll
         for (int i = 0; i < B; i++)
-          if (u < nu && j + i < k) acc[u] = combine<T, Op, uint4>(acc[u], v[u][i]);
+          if (u < nu && j + i < k) acc[u] = combine<T, Op, uint4>(acc[u], vl[u][i]);
         r[u] += B;
         if (r[u] >= k) r[u] -= k;
       }

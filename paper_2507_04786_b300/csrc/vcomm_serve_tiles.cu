@@ -94,10 +94,23 @@ __device__ void runTile(const ServeReq* q, unsigned long long lo, unsigned long 
 }
 
 // ---- staged path: fold one sub-tile of `len` bytes (block b, byte offset
-// off in the block) from the stage's inputs (`sub` bytes apart) into o
+// off in the block) from the stage's inputs (`sub` bytes apart, shared
+// memory address in) into shared memory address o.  Explicit shared-memory
+// accesses: the fold is out of line and its pointers would otherwise be
+// generic.
+VDEV uint4 lds16(unsigned a) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+  return v;
+}
+VDEV void sts16(unsigned a, uint4 v) {
+  asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+               : "memory");
+}
+
 template <class T, class Op>
-__device__ __noinline__ void foldStage(const ServeReq* q, const unsigned char* in, unsigned sub,
-                                       unsigned char* o, int b, unsigned long long off, unsigned len) {
+__device__ __noinline__ void foldStage(const ServeReq* q, unsigned in, unsigned sub, unsigned o, int b,
+                                       unsigned long long off, unsigned len) {
   const DirectView v = viewOfReq(q);
   const int k = q->nranks;
   constexpr unsigned long long esz = sizeof(T);
@@ -111,20 +124,19 @@ __device__ __noinline__ void foldStage(const ServeReq* q, const unsigned char* i
       seg = b;   // ReduceScatter block b: the chain starts at rank b + 1
     }
     int r = seg + 1 < k ? seg + 1 : 0;
-    uint4 acc = *(const uint4*)(in + (size_t)r * sub + u);
+    uint4 acc = lds16(in + (unsigned)r * sub + u);
     for (int j = 1; j < k; j++) {
       if (++r == k) r = 0;
-      acc = combine<T, Op, uint4>(acc, *(const uint4*)(in + (size_t)r * sub + u));
+      acc = combine<T, Op, uint4>(acc, lds16(in + (unsigned)r * sub + u));
     }
-    *(uint4*)(o + u) = acc;
+    sts16(o + u, acc);
   }
 }
 
-VDEV void foldStageAny(const ServeReq* q, const unsigned char* in, unsigned sub, unsigned char* o, int b,
+VDEV void foldStageAny(const ServeReq* q, unsigned in, unsigned sub, unsigned o, int b,
                        unsigned long long off, unsigned len) {
   if (q->coll == kAllGather) {   // a copy: the one input as it is
-    for (unsigned u = threadIdx.x * 16u; u < len; u += blockDim.x * 16u)
-      *(uint4*)(o + u) = *(const uint4*)(in + u);
+    for (unsigned u = threadIdx.x * 16u; u < len; u += blockDim.x * 16u) sts16(o + u, lds16(in + u));
     return;
   }
   const bool mx = q->redop == kMax;
@@ -468,7 +480,7 @@ __device__ void work(const TileArgs& a) {
     const StageInfo si = sInfo[stg];
     const ServeReq* r = &sReq[stg];
     unsigned char* o = out + (size_t)ob * kTileOutBytes;
-    foldStageAny(r, in + (size_t)stg * stageBytes, si.sub, o, si.b, si.off, si.len);
+    foldStageAny(r, smemU32(in + (size_t)stg * stageBytes), si.sub, smemU32(o), si.b, si.off, si.len);
     fenceProxyAsync();
     __syncthreads();   // o written; the stage read by every thread
     if (threadIdx.x == 0) {
