@@ -110,6 +110,7 @@ struct vcomm {
   int treeNode = 1;                  // vranks per node of the hierarchical tree
   // direct AllReduce: bytes per rank from which the staged kernel runs
   unsigned long long stagedMinBytes = 8ull << 20;
+  bool tileGroups = true;                     // groups of direct calls: one tile-engine launch
   Arena arena[2][3];
   ErrWord* hErr = nullptr;
   ErrWord* dErr = nullptr;
@@ -204,6 +205,7 @@ vResult_t vcommInitConfig(vcomm_t* comm, int nranks, int nchannels, const vcommC
     const char* env = getenv("VCOMM_TIMEOUT_MS");
     if (env && atof(env) > 0) c->timeoutSec = atof(env) / 1000.0;
   }
+  if (const char* env = getenv("VCOMM_TILE_GROUPS")) c->tileGroups = !(env[0] == '0' && env[1] == 0);
   if (const char* env = getenv("VCOMM_STAGED_MIN_BYTES")) {
     char* end = nullptr;
     const unsigned long long v = strtoull(env, &end, 10);
@@ -1006,9 +1008,113 @@ static vResult_t matchP2P(vcomm* c, const std::vector<P2PSpec>& ops, std::vector
 
 // the direct calls of a group: one launch per (dtype, op) class present (one
 // for the copies), each over up to kMaxBatchOps calls
+// Shared memory per pipeline stage of the tile engine on this device: what
+// the kernel's own shared memory and the output buffers leave of the
+// largest opt-in, in three stages; 0 if the tile kernels cannot run.
+static unsigned tileStageBytes(int dev) {
+  static std::mutex mu;
+  static std::map<int, unsigned> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  int maxSmem = 0;
+  cudaFuncAttributes fa{};
+  unsigned sb = 0;
+  if (cudaDeviceGetAttribute(&maxSmem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+      cudaFuncGetAttributes(&fa, batchTilesKernel()) == cudaSuccess) {
+    const long long room = (long long)maxSmem - (long long)fa.sharedSizeBytes - (long long)serveTilesSmem(0);
+    sb = room > 0 ? (unsigned)(room / serveTilesStages() / 128 * 128) : 0;
+    if (sb < 16 * 128 ||
+        cudaFuncSetAttribute(batchTilesKernel(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)serveTilesSmem(sb)) != cudaSuccess)
+      sb = 0;
+  }
+  (void)cudaGetLastError();
+  cache[dev] = sb;
+  return sb;
+}
+
+// A group of direct calls as ONE launch of the tile engine (kBatchTiles):
+// every call's tiles laid end to end, CTA j (one per SM) taking tiles j,
+// j + grid, ...; 16-byte aligned AllReduce / ReduceScatter / AllGather tiles
+// move by bulk copies through shared memory, the others take the register
+// kernels' paths.  For calls of up to 16 vranks whose type and op the tile
+// engine folds (int32, fp32, fp16, bf16; sum, max; copies); else false.
+static bool tileBatchable(const vcomm* c, const std::vector<CallSpec>& ops) {
+  if (c->k > kServeMaxRanks || ops.empty()) return false;
+  for (const auto& o : ops) {
+    if (o.kcoll != kAllReduce && o.kcoll != kReduceScatter && o.kcoll != kAllGather &&
+        o.kcoll != kBroadcast && o.kcoll != kReduce)
+      return false;
+    if (o.postDiv) return false;
+    const bool copy = (o.kcoll == kAllGather || o.kcoll == kBroadcast);
+    if (!copy && !(o.dtype == kI32 || o.dtype == kF32 || o.dtype == kF16 || o.dtype == kBF16)) return false;
+    if (!copy && !(o.redop == kSum || o.redop == kMax)) return false;
+  }
+  return true;
+}
+
+static vResult_t launchTileGroup(vcomm* c, std::vector<CallSpec>& ops, unsigned stageBytes) {
+  const int k = c->k;
+  const cudaStream_t stream = ops[0].stream;
+  for (size_t base = 0; base < ops.size(); base += kMaxBatchOps) {
+    const int n = (int)std::min<size_t>(kMaxBatchOps, ops.size() - base);
+    std::unique_ptr<TileBatchArgs> b(new TileBatchArgs());
+    memset(b.get(), 0, sizeof(TileBatchArgs));
+    b->nops = n;
+    b->stageBytes = stageBytes;
+    b->copyTimeoutNs = (unsigned long long)(c->timeoutSec * 1e9);
+    b->errClaim = c->dClaim;
+    b->err = c->dErr;
+    unsigned long long start = 0;
+    for (int i = 0; i < n; i++) {
+      const CallSpec& o = ops[base + i];
+      const DirectGeom g = directGeom(o);
+      const int esz = dtypeSize(o.dtype);
+      const TileGeometry tg = tileGeometry(o.kcoll, k, o.units, esz, g.vec, (unsigned long long)c->nsm,
+                                           (unsigned long long)serveTilesUnitsPerIter());
+      TileOpDesc& d = b->ops[i];
+      d.count = o.units;
+      d.chunk = g.chunk;
+      d.inplaceMask = o.inplace;
+      d.staged = tg.staged;
+      d.units = tg.units;
+      d.tileUnits = tg.tileUnits;
+      d.blockBytes = tg.blockBytes;
+      d.tileBytes = tg.tileBytes;
+      d.perBlock = tg.perBlock;
+      d.ntiles = tg.ntiles;
+      d.tileStart = start;
+      d.coll = o.kcoll;
+      d.dtype = o.dtype;
+      d.redop = o.redop;
+      d.nranks = k;
+      d.nsub = o.plan.nchannels;
+      d.root = o.root;
+      d.vec = g.vec;
+      d.ptrBase = 2 * k * i;
+      for (int r = 0; r < k; r++) {
+        b->ptrs[d.ptrBase + r] = o.send[r];
+        b->ptrs[d.ptrBase + k + r] = o.recv[r];
+      }
+      start += tg.ntiles;
+    }
+    b->totalTiles = start;
+    const unsigned grid = (unsigned)std::max<unsigned long long>(1, std::min<unsigned long long>(start, c->nsm));
+    void* args[] = {(void*)b.get()};
+    VC_TRY(cudaLaunchKernel(batchTilesKernel(), dim3(grid), dim3(serveTilesThreads()), args,
+                            serveTilesSmem(stageBytes), stream));
+  }
+  return vSuccess;
+}
+
 static vResult_t launchDirectGroup(vcomm* c, std::vector<CallSpec>& ops) {
   const int k = c->k;
   const cudaStream_t stream = ops[0].stream;
+  if (c->tileGroups && tileBatchable(c, ops)) {
+    const unsigned sb = tileStageBytes(c->dev);
+    if (sb) return launchTileGroup(c, ops, sb);
+  }
   const int perLaunch = std::min<int>(kMaxBatchOps, kMaxBatchPtrs / (2 * k));
   const int kCopyClass = kNumDtypes * kNumOps;
   auto classOf = [&](const CallSpec& o) {

@@ -11,6 +11,7 @@
 //     up edge r -> parent(r); index downOffset + j * k + r the down edge
 //     parent(r) -> r, with downOffset = (2 x the communicator's channels) x k.
 #pragma once
+#include <algorithm>
 #include <stddef.h>
 #include <stdint.h>
 
@@ -242,6 +243,72 @@ struct TileArgs {
   unsigned long long copyTimeoutNs;    // a bulk copy that takes longer fails the kernel
   unsigned stageBytes;                 // shared memory per pipeline stage (a multiple of 128)
   int pad;
+};
+
+// ---- a group's direct calls as tiles of one launch (the tile engine of the
+// serving kernel over a fixed list: CTA j takes tiles j, j + grid, ...).
+// Op i owns tiles [tileStart[i], tileStart[i + 1]); its send / recv pointers
+// are ptrs[ptrBase .. + nranks) and ptrs[ptrBase + nranks .. + nranks).
+struct TileOpDesc {
+  unsigned long long count, chunk, inplaceMask;
+  unsigned long long staged, units, tileUnits, blockBytes, tileBytes, perBlock, ntiles, tileStart;
+  int coll, dtype, redop, nranks, nsub, root, vec, ptrBase;
+};
+// The tiles of one direct-protocol op (host side, serving and groups).
+// Staged (16-byte aligned AllReduce / ReduceScatter / AllGather with whole
+// 16-byte units): byte ranges of a block, whole 4 KiB pieces.  Otherwise
+// ranges of the register kernels' units, whole iterations (`iter` units) of
+// a CTA.  About two tiles per worker CTA (`workers`), and at most ~4 MiB of
+// traffic per tile so that small work never waits long for a free CTA.
+// count: elements, or bytes for AllGather / Broadcast; vec as DirectArgs::vec.
+struct TileGeometry {
+  unsigned long long staged, units, tileUnits, blockBytes, tileBytes, perBlock, ntiles;
+};
+inline TileGeometry tileGeometry(int coll, int k, unsigned long long count, int esz, int vec,
+                                 unsigned long long workers, unsigned long long iter) {
+  TileGeometry g{};
+  const bool copy = (coll == kAllGather || coll == kBroadcast);
+  const unsigned long long unitBytes = copy ? 1ull : (unsigned long long)esz;
+  const unsigned long long blocks = (coll == kReduceScatter || coll == kAllGather) ? (unsigned long long)k : 1ull;
+  // traffic per byte of a block: k inputs and k outputs (AllReduce), else k + 1
+  const unsigned long long factor = coll == kAllReduce ? 2ull * k : (unsigned long long)k + 1;
+  const unsigned long long twoW = 2ull * (workers > 0 ? workers : 1);
+  const unsigned long long Ev = 16 / unitBytes;   // elements (bytes) per 16-byte unit
+  const bool stageable = (coll == kAllReduce || coll == kReduceScatter || coll == kAllGather) && vec == 1;
+  g.blockBytes = stageable ? (count / Ev) * 16 : 0;
+  g.staged = (stageable && g.blockBytes >= 16) ? 1 : 0;
+  if (g.staged) {
+    const unsigned long long piece = 4096;
+    const unsigned long long maxTile = std::max<unsigned long long>(piece, (4ull << 20) / factor / piece * piece);
+    unsigned long long tb = (blocks * g.blockBytes + twoW - 1) / twoW;
+    tb = std::min(std::max(tb, piece), maxTile);
+    tb = (tb + piece - 1) / piece * piece;
+    g.tileBytes = tb;
+    g.perBlock = (g.blockBytes + tb - 1) / tb;
+    g.ntiles = blocks * g.perBlock;
+  } else {
+    const unsigned long long E = vec ? Ev : 1;
+    g.units = (vec == 2 && copy) ? count * blocks / 16 : (count / E) * blocks;
+    const unsigned long long unitTraffic = E * unitBytes * factor;
+    const unsigned long long maxTile = std::max<unsigned long long>(iter, (4ull << 20) / unitTraffic / iter * iter);
+    unsigned long long tu = (g.units + twoW - 1) / twoW;
+    tu = std::min(std::max(tu, iter), maxTile);
+    tu = (tu + iter - 1) / iter * iter;
+    g.tileUnits = tu;
+    g.ntiles = std::max<unsigned long long>(1, (g.units + tu - 1) / tu);
+  }
+  return g;
+}
+
+struct TileBatchArgs {
+  int nops;
+  unsigned stageBytes;
+  unsigned long long totalTiles;
+  unsigned long long copyTimeoutNs;
+  int* errClaim;
+  ErrWord* err;
+  TileOpDesc ops[kMaxBatchOps];
+  const void* ptrs[kMaxBatchOps * 2 * kServeMaxRanks];
 };
 
 // ---- the direct protocol (no FIFO): one thread computes a unit's whole

@@ -56,6 +56,9 @@ const void* serveKernel();
 // output buffers of serveTilesOutBytes()); a register-path tile is a
 // multiple of serveTilesUnitsPerIter() units
 const void* serveTilesKernel();
+// a group's direct calls as tiles of one launch (TileBatchArgs); same threads
+// and shared memory as the serving tile kernel, one CTA per SM
+const void* batchTilesKernel();
 int serveTilesThreads();
 int serveTilesUnitsPerIter();
 int serveTilesStages();

@@ -388,40 +388,16 @@ bool postTile(vserve* s, Request& q) {
   // 1: 16-byte units; 2: aligned buffers, blocks not whole units (shifted
   // 16-byte accesses, register path); 0: element accesses
   sr.vec = ptrs ? (whole ? 1 : 2) : 0;
-  // Tiles: about two per worker CTA, and at most ~4 MiB of traffic each so
-  // that a small request never waits long for a free CTA.  Traffic per byte
-  // of a block: AllReduce 2k (k inputs, k outputs), ReduceScatter and
-  // AllGather k + 1.
-  const unsigned long long blocks = (q.coll == kAllReduce) ? 1 : (unsigned long long)q.nranks;
-  const unsigned long long factor = q.coll == kAllReduce ? 2ull * q.nranks : (unsigned long long)q.nranks + 1;
-  const unsigned long long twoW = 2ull * (unsigned long long)s->tileWorkers;
-  const unsigned long long Ev = copy ? 16 : 16 / esz;   // elements (bytes) per 16-byte unit
-  tr.blockBytes = sr.vec == 1 ? (sr.count / Ev) * 16 : 0;
-  tr.staged = (sr.vec == 1 && tr.blockBytes >= 16) ? 1 : 0;
-  if (tr.staged) {
-    // byte ranges of a block, whole 4 KiB pieces (bulk copies of 16-byte units)
-    const unsigned long long piece = 4096;
-    const unsigned long long maxTile = std::max<unsigned long long>(piece, (4ull << 20) / factor / piece * piece);
-    unsigned long long tb = (blocks * tr.blockBytes + twoW - 1) / twoW;
-    tb = std::min(std::max(tb, piece), maxTile);
-    tb = (tb + piece - 1) / piece * piece;
-    tr.tileBytes = tb;
-    tr.perBlock = (tr.blockBytes + tb - 1) / tb;
-    tr.ntiles = blocks * tr.perBlock;
-  } else {
-    // the register kernels' units (16-byte units, shifted 16-byte units of
-    // the k blocks, or elements / bytes), whole iterations of the CTA
-    const unsigned long long E = sr.vec ? Ev : 1;
-    tr.units = (sr.vec == 2 && copy) ? sr.count * blocks / 16 : (sr.count / E) * blocks;
-    const unsigned long long g = (unsigned long long)serveTilesUnitsPerIter();
-    const unsigned long long unitTraffic = E * unitBytes * factor;
-    const unsigned long long maxTile = std::max<unsigned long long>(g, (4ull << 20) / unitTraffic / g * g);
-    unsigned long long tu = (tr.units + twoW - 1) / twoW;
-    tu = std::min(std::max(tu, g), maxTile);
-    tu = (tu + g - 1) / g * g;
-    tr.tileUnits = tu;
-    tr.ntiles = std::max<unsigned long long>(1, (tr.units + tu - 1) / tu);
-  }
+  const TileGeometry tg = tileGeometry(q.coll, q.nranks, sr.count, (int)esz, sr.vec,
+                                      (unsigned long long)s->tileWorkers,
+                                      (unsigned long long)serveTilesUnitsPerIter());
+  tr.staged = tg.staged;
+  tr.units = tg.units;
+  tr.tileUnits = tg.tileUnits;
+  tr.blockBytes = tg.blockBytes;
+  tr.tileBytes = tg.tileBytes;
+  tr.perBlock = tg.perBlock;
+  tr.ntiles = tg.ntiles;
   tr.klass = q.big ? 1 : 0;
   volatile TileReq* dst = &s->hRing[slot];
   memcpy((void*)dst, &tr, offsetof(TileReq, seq));

@@ -242,69 +242,175 @@ __device__ void ingest(const TileArgs& a) {
   }
 }
 
-// thread 0 of a worker: the next tile, small queue first; -1 if none
-VDEV long long claimTile(const TileArgs& a, unsigned long long* tile) {
-  TileQueues* q = a.q;
-  for (int c = 0; c < 2; c++) {
-    unsigned long long h = ldVol(&q->head[c]);
-    const unsigned long long t = ldAcquire(&q->tail[c]);
-    while (h < t) {
-      const unsigned long long e = ldVol(&q->entry[c][h % kTileRing]);
-      if ((e >> 32) != (h & 0xffffffffull)) break;   // not this position (cannot happen after tail)
-      const int s = (int)(e & 0xffffffffull) - 1;
-      TileState* st = &a.state[s];
-      const unsigned long long tl = atomicAdd(&st->next, 1ull);
-      if (tl < ldVol(&st->ntiles)) {
-        *tile = tl;
-        return s;
-      }
-      atomicCAS(&q->head[c], h, h + 1);               // every tile of entry h is claimed
-      h++;
-    }
-  }
-  return -1;
+// ---- where tiles come from.  The engine below calls a source from thread 0:
+//   claim(&tile)        the next tile: an op id (>= 0) and its tile index; -1: none now
+//   loadReq(id, dst)    the op's description, into shared memory
+//   geom(id, tile, &w)  the tile's work: a byte range of one block (staged),
+//                       or a range of the register kernels' units
+//   done(id)            a tile of op `id` has completed (its stores are visible)
+//   finished()          no tile will come any more
+//   fail()              a bulk copy did not complete in time
+struct TileWork {
+  int staged, b, tail;                  // staged: block b; tail: also the element tail
+  unsigned long long off, end;          // staged: bytes [off, end) of block b
+  unsigned long long lo, hi;            // register path: units [lo, hi)
+};
+
+VDEV void stagedGeom(unsigned long long tile, unsigned long long perBlock, unsigned long long tileBytes,
+                     unsigned long long blockBytes, unsigned long long ntiles, TileWork* w) {
+  w->staged = 1;
+  w->b = (int)(tile / perBlock);
+  w->off = (tile % perBlock) * tileBytes;
+  w->end = w->off + tileBytes < blockBytes ? w->off + tileBytes : blockBytes;
+  w->tail = (tile + 1 == ntiles) ? 1 : 0;   // the request's element tail, if it has one
+}
+VDEV void registerGeom(unsigned long long tile, unsigned long long tileUnits, unsigned long long units,
+                       unsigned long long ntiles, TileWork* w) {
+  w->staged = 0;
+  w->lo = tile * tileUnits;
+  w->hi = w->lo + tileUnits < units ? w->lo + tileUnits : units;
+  if (w->lo > w->hi) w->lo = w->hi;
+  w->tail = (tile + 1 == ntiles) ? 1 : 0;
 }
 
-// thread 0: one finished tile of request `slot`; the CTA that finishes the
-// last one reports the request
-VDEV void tileDone(const TileArgs& a, int slot) {
-  TileState* st = &a.state[slot];
-  fenceProxyGlobal();
-  __threadfence();                                       // the tile's stores before the count
-  const unsigned long long d = atomicAdd(&st->done, 1ull);
-  if (d + 1 == ldVol(&st->ntiles)) {
-    __threadfence();
-    TileDone* dn = &a.done[slot];
-    stVol(&dn->tStart, ldVol(&st->tStart));
-    stVol(&dn->tEnd, globaltimer());
-    __threadfence_system();
-    stVol(&dn->seq, ldVol(&st->seq));
-    __threadfence_system();
-    atomicAdd(&a.q->completed, 1ull);
+// the serving queues (small requests first), claimed with atomics
+struct ServeSource {
+  const TileArgs& a;
+  VDEV long long claim(unsigned long long* tile) {
+    TileQueues* q = a.q;
+    for (int c = 0; c < 2; c++) {
+      unsigned long long h = ldVol(&q->head[c]);
+      const unsigned long long t = ldAcquire(&q->tail[c]);
+      while (h < t) {
+        const unsigned long long e = ldVol(&q->entry[c][h % kTileRing]);
+        if ((e >> 32) != (h & 0xffffffffull)) break;   // not this position (cannot happen after tail)
+        const int s = (int)(e & 0xffffffffull) - 1;
+        TileState* st = &a.state[s];
+        const unsigned long long tl = atomicAdd(&st->next, 1ull);
+        if (tl < ldVol(&st->ntiles)) {
+          *tile = tl;
+          return s;
+        }
+        atomicCAS(&q->head[c], h, h + 1);               // every tile of entry h is claimed
+        h++;
+      }
+    }
+    return -1;
   }
-}
+  VDEV void loadReq(long long id, ServeReq* dst) {
+    const unsigned long long* src = (const unsigned long long*)&a.state[id].req;
+    for (int i = 0; i < (int)(sizeof(ServeReq) / 8); i++) ((unsigned long long*)dst)[i] = ldVol(&src[i]);
+  }
+  VDEV void geom(long long id, unsigned long long tile, TileWork* w) {
+    TileState* st = &a.state[id];
+    if (ldVol(&st->staged))
+      stagedGeom(tile, ldVol(&st->perBlock), ldVol(&st->tileBytes), ldVol(&st->blockBytes), ldVol(&st->ntiles), w);
+    else
+      registerGeom(tile, ldVol(&st->tileUnits), ldVol(&st->units), ldVol(&st->ntiles), w);
+  }
+  // the CTA that finishes a request's last tile reports the request
+  VDEV void done(long long id) {
+    TileState* st = &a.state[id];
+    fenceProxyGlobal();
+    __threadfence();                                     // the tile's stores before the count
+    const unsigned long long d = atomicAdd(&st->done, 1ull);
+    if (d + 1 == ldVol(&st->ntiles)) {
+      __threadfence();
+      TileDone* dn = &a.done[id];
+      stVol(&dn->tStart, ldVol(&st->tStart));
+      stVol(&dn->tEnd, globaltimer());
+      __threadfence_system();
+      stVol(&dn->seq, ldVol(&st->seq));
+      __threadfence_system();
+      atomicAdd(&a.q->completed, 1ull);
+    }
+  }
+  VDEV bool finished() { return *(volatile int*)&a.q->stop != 0; }
+  VDEV void fail() {
+    atomicCAS((int*)&a.ctl->error, 0, (int)vTimeout);
+    atomicExch(&a.q->stop, 1);
+    __threadfence_system();
+  }
+};
+
+// a group's ops, tiles assigned statically: CTA j takes j, j + grid, ...
+struct BatchSource {
+  const TileBatchArgs& b;
+  unsigned long long next;
+  VDEV long long claim(unsigned long long* tile) {
+    if (next >= b.totalTiles) return -1;
+    int lo = 0, hi = b.nops - 1;   // the op whose tiles hold `next`
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (b.ops[mid].tileStart <= next) lo = mid;
+      else hi = mid - 1;
+    }
+    *tile = next - b.ops[lo].tileStart;
+    next += gridDim.x;
+    return lo;
+  }
+  VDEV void loadReq(long long id, ServeReq* dst) {
+    const TileOpDesc& o = b.ops[id];
+    dst->coll = o.coll;
+    dst->proto = kDirect;
+    dst->dtype = o.dtype;
+    dst->redop = o.redop;
+    dst->nranks = o.nranks;
+    dst->nsub = o.nsub;
+    dst->root = o.root;
+    dst->vec = o.vec;
+    dst->count = o.count;
+    dst->chunk = o.chunk;
+    dst->slotUnits = 0;
+    dst->slotBytes = 0;
+    dst->inplaceMask = o.inplaceMask;
+    for (int r = 0; r < o.nranks; r++) {
+      dst->send[r] = b.ptrs[o.ptrBase + r];
+      dst->recv[r] = const_cast<void*>(b.ptrs[o.ptrBase + o.nranks + r]);
+    }
+  }
+  VDEV void geom(long long id, unsigned long long tile, TileWork* w) {
+    const TileOpDesc& o = b.ops[id];
+    if (o.staged) stagedGeom(tile, o.perBlock, o.tileBytes, o.blockBytes, o.ntiles, w);
+    else registerGeom(tile, o.tileUnits, o.units, o.ntiles, w);
+  }
+  VDEV void done(long long) {}
+  VDEV bool finished() { return next >= b.totalTiles; }
+  VDEV void fail() {
+    if (atomicCAS(b.errClaim, 0, (int)vTimeout) == 0) {
+      volatile ErrWord* e = b.err;
+      e->rank = -1;
+      e->channel = (int)blockIdx.x;
+      e->where = 4;
+      __threadfence_system();
+      e->code = (int)vTimeout;
+      __threadfence_system();
+    }
+  }
+};
 
 struct StageInfo {
   unsigned long long off;   // byte offset in the block
   unsigned len;             // bytes (a multiple of 16)
   unsigned sub;             // bytes per input in the stage
-  int slot, b;
+  int id, b;
   int endOfTile;            // the tile's last sub-tile
-  int tail;                 // the request's last tile, with an element tail
+  int tail;                 // the op's last tile, with an element tail
 };
 
 constexpr int kMaxPendingDone = kDoneLag + 4;
 
-// ---- CTAs 1..: take tiles until the stop word is raised and none is left
-__device__ void work(const TileArgs& a) {
+// ---- the tile engine: take tiles from `src` until it has none and never
+// will; every thread of the CTA calls it
+template <class Src>
+__device__ void tileEngine(Src& src, unsigned stageBytes, unsigned long long copyTimeoutNs, bool persistent) {
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ ServeReq sReq[kTileStages];   // the request of each stage
-  __shared__ ServeReq sCur;                // the request being issued (thread 0), or a register tile's
+  __shared__ ServeReq sReq[kTileStages];   // the op of each stage
+  __shared__ ServeReq sCur;                // the op being issued (thread 0), or a register tile's
   __shared__ StageInfo sInfo[kTileStages];
+  __shared__ TileWork sReg;
   __shared__ int sAct;
-  __shared__ long long sRegSlot;
-  __shared__ unsigned long long sRegTile;
-  const unsigned stageBytes = a.stageBytes;
+  __shared__ long long sRegId;
   unsigned char* in = smem;
   unsigned char* out = smem + (size_t)kTileStages * stageBytes;
   uint64_t* bar = (uint64_t*)(out + 2 * (size_t)kTileOutBytes);
@@ -319,15 +425,15 @@ __device__ void work(const TileArgs& a) {
   // tiles whose completion is not yet confirmed (a tile is done once the
   // bulk-store group of its last sub-tile has completed)
   unsigned long long issued = 0, consumed = 0;
-  long long curSlot = -1;
+  long long curId = -1;
   unsigned long long curOff = 0, curEnd = 0;
   unsigned curSub = 0;
   int curB = 0, curTail = 0;
-  long long regSlot = -1;
-  unsigned long long regTile = 0;
-  unsigned curGen = 0, stageGen[kTileStages];   // which claim each stage's request copy is of
+  long long regId = -1;
+  TileWork regWork{};
+  unsigned curGen = 0, stageGen[kTileStages];   // which claim each stage's op copy is of
   for (int i = 0; i < kTileStages; i++) stageGen[i] = ~0u;
-  int doneSlot[kMaxPendingDone];
+  long long doneId[kMaxPendingDone];
   unsigned long long doneGroup[kMaxPendingDone];
   int ndone = 0;
   unsigned backoff = 64;
@@ -335,29 +441,27 @@ __device__ void work(const TileArgs& a) {
   while (true) {
     if (threadIdx.x == 0) {
       // top up the stages: issue sub-tiles of the current tile, claiming the
-      // next tile when it runs out; a register (unaligned) tile waits until
-      // the stages have drained
-      while (issued - consumed < (unsigned long long)kTileStages && regSlot < 0) {
-        if (curSlot < 0) {
+      // next tile when it runs out; a register tile waits until the stages
+      // have drained
+      while (issued - consumed < (unsigned long long)kTileStages && regId < 0) {
+        if (curId < 0) {
           unsigned long long tl = 0;
-          const long long s = claimTile(a, &tl);
-          if (s < 0) break;
-          TileState* st = &a.state[s];
-          if (!ldVol(&st->staged)) {
-            regSlot = s;
-            regTile = tl;
+          const long long id = src.claim(&tl);
+          if (id < 0) break;
+          TileWork w;
+          src.geom(id, tl, &w);
+          if (!w.staged) {
+            regId = id;
+            regWork = w;
             break;
           }
-          for (int i = 0; i < (int)(sizeof(ServeReq) / 8); i++)
-            ((unsigned long long*)&sCur)[i] = ldVol(&((const unsigned long long*)&st->req)[i]);
-          const unsigned long long perBlock = ldVol(&st->perBlock), tb = ldVol(&st->tileBytes);
-          const unsigned long long bb = ldVol(&st->blockBytes);
-          curSlot = s;
+          src.loadReq(id, &sCur);
+          curId = id;
           curGen++;
-          curB = (int)(tl / perBlock);
-          curOff = (tl % perBlock) * tb;
-          curEnd = curOff + tb < bb ? curOff + tb : bb;
-          curTail = (tl + 1 == ldVol(&st->ntiles)) && hasTail(&sCur);
+          curB = w.b;
+          curOff = w.off;
+          curEnd = w.end;
+          curTail = w.tail && hasTail(&sCur);
           const unsigned nIn = sCur.coll == kAllGather ? 1u : (unsigned)sCur.nranks;
           unsigned sub = stageBytes / nIn;
           sub = sub < kTileOutBytes ? sub : kTileOutBytes;
@@ -369,11 +473,11 @@ __device__ void work(const TileArgs& a) {
         si.off = curOff;
         si.len = len;
         si.sub = curSub;
-        si.slot = (int)curSlot;
+        si.id = (int)curId;
         si.b = curB;
         si.endOfTile = (curOff + len >= curEnd) ? 1 : 0;
         si.tail = si.endOfTile && curTail;
-        if (stageGen[stg] != curGen) {   // the stage holds another claim's request
+        if (stageGen[stg] != curGen) {   // the stage holds another claim's op
           sReq[stg] = sCur;
           stageGen[stg] = curGen;
         }
@@ -384,15 +488,15 @@ __device__ void work(const TileArgs& a) {
           bulkLoad(dst, (const char*)r.send[curB] + curOff, len, &bar[stg]);
         } else {
           const unsigned long long esz = (r.dtype == kF16 || r.dtype == kBF16) ? 2 : 4;
-          const unsigned long long src =
+          const unsigned long long from =
               (r.coll == kReduceScatter ? (unsigned long long)curB * r.count * esz : 0ull) + curOff;
           mbarExpect(&bar[stg], len * (unsigned)r.nranks);
           for (int q = 0; q < r.nranks; q++)
-            bulkLoad(dst + (size_t)q * curSub, (const char*)r.send[q] + src, len, &bar[stg]);
+            bulkLoad(dst + (size_t)q * curSub, (const char*)r.send[q] + from, len, &bar[stg]);
         }
         issued++;
         curOff += len;
-        if (curOff >= curEnd) curSlot = -1;
+        if (curOff >= curEnd) curId = -1;
       }
       int act;
       if (issued > consumed) {
@@ -400,21 +504,19 @@ __device__ void work(const TileArgs& a) {
       } else {
         // nothing in flight: every store group may complete now
         bulkWaitAll();
-        for (int i = 0; i < ndone; i++) tileDone(a, doneSlot[i]);
+        for (int i = 0; i < ndone; i++) src.done(doneId[i]);
         ndone = 0;
-        if (regSlot >= 0) {
+        if (regId >= 0) {
           act = 2;                                 // a register tile
-          sRegSlot = regSlot;
-          sRegTile = regTile;
-          TileState* st = &a.state[regSlot];
-          for (int i = 0; i < (int)(sizeof(ServeReq) / 8); i++)
-            ((unsigned long long*)&sCur)[i] = ldVol(&((const unsigned long long*)&st->req)[i]);
-          regSlot = -1;
-        } else if (*(volatile int*)&a.q->stop) {
+          sRegId = regId;
+          sReg = regWork;
+          src.loadReq(regId, &sCur);
+          regId = -1;
+        } else if (src.finished()) {
           act = 3;                                 // stop
         } else {
           act = 0;                                 // idle
-          __nanosleep(backoff);
+          if (persistent) __nanosleep(backoff);
         }
       }
       sAct = act;
@@ -429,31 +531,24 @@ __device__ void work(const TileArgs& a) {
     }
     backoff = 64;
     if (act == 2) {
-      // a tile of an unaligned request: the register kernels' element path
-      TileState* st = &a.state[sRegSlot];
-      const unsigned long long tu = ldVol(&st->tileUnits), units = ldVol(&st->units);
-      const unsigned long long nt = ldVol(&st->ntiles);
-      const unsigned long long lo = sRegTile * tu;
-      const unsigned long long hi = lo + tu < units ? lo + tu : units;
-      runTile(&sCur, lo < hi ? lo : hi, hi, sRegTile + 1 == nt);
+      // a tile of an unaligned op: the register kernels' paths
+      runTile(&sCur, sReg.lo, sReg.hi, sReg.tail != 0);
       __threadfence();
       __syncthreads();
-      if (threadIdx.x == 0) tileDone(a, (int)sRegSlot);
+      if (threadIdx.x == 0) src.done(sRegId);
       __syncthreads();
       continue;
     }
     // act == 1: the oldest issued sub-tile
     const int stg = (int)(consumed % kTileStages);
-    const bool ok = stageWait(&bar[stg], (unsigned)((consumed / kTileStages) & 1ull), a.copyTimeoutNs);
+    const bool ok = stageWait(&bar[stg], (unsigned)((consumed / kTileStages) & 1ull), copyTimeoutNs);
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) {
         // loads still in flight must land before the CTA's shared memory is released
         for (unsigned long long j = consumed; j < issued; j++)
-          (void)stageWait(&bar[j % kTileStages], (unsigned)((j / kTileStages) & 1ull), a.copyTimeoutNs);
+          (void)stageWait(&bar[j % kTileStages], (unsigned)((j / kTileStages) & 1ull), copyTimeoutNs);
         bulkWaitAll();
-        atomicCAS((int*)&a.ctl->error, 0, (int)vTimeout);
-        atomicExch(&a.q->stop, 1);
-        __threadfence_system();
+        src.fail();
       }
       return;
     }
@@ -467,9 +562,9 @@ __device__ void work(const TileArgs& a) {
       int keep = 0;
       for (int i = 0; i < ndone; i++) {
         if (doneGroup[i] + kDoneLag + 1 <= consumed) {
-          tileDone(a, doneSlot[i]);
+          src.done(doneId[i]);
         } else {
-          doneSlot[keep] = doneSlot[i];
+          doneId[keep] = doneId[i];
           doneGroup[keep] = doneGroup[i];
           keep++;
         }
@@ -487,8 +582,12 @@ __device__ void work(const TileArgs& a) {
       if (r->coll == kReduceScatter) {
         bulkStore((char*)r->recv[si.b] + si.off, o, si.len);
       } else {
-        const unsigned long long dst = (r->coll == kAllGather ? (unsigned long long)si.b * r->count : 0ull) + si.off;
-        for (int q = 0; q < r->nranks; q++) bulkStore((char*)r->recv[q] + dst, o, si.len);
+        const bool ag = r->coll == kAllGather;
+        const unsigned long long dst = (ag ? (unsigned long long)si.b * r->count : 0ull) + si.off;
+        for (int q = 0; q < r->nranks; q++) {
+          if (ag && q == si.b && ((r->inplaceMask >> q) & 1ull)) continue;   // its own block, in place
+          bulkStore((char*)r->recv[q] + dst, o, si.len);
+        }
       }
       bulkCommit();
     }
@@ -498,12 +597,12 @@ __device__ void work(const TileArgs& a) {
       __syncthreads();
     }
     if (threadIdx.x == 0 && si.endOfTile) {
-      doneSlot[ndone] = si.slot;
+      doneId[ndone] = si.id;
       doneGroup[ndone] = consumed;
       ndone++;
     }
     consumed++;        // every thread counts the stages it has folded
-    __syncthreads();   // the stage info and request copies are free again
+    __syncthreads();   // the stage info and op copies are free again
   }
 }
 
@@ -512,12 +611,20 @@ __global__ void __launch_bounds__(kTileThreads, 1) kServeTiles(const __grid_cons
     if (threadIdx.x < 32) ingest(a);
     return;
   }
-  work(a);
+  ServeSource src{a};
+  tileEngine(src, a.stageBytes, a.copyTimeoutNs, true);
+}
+
+// a group's direct calls in one launch (one CTA per SM)
+__global__ void __launch_bounds__(kTileThreads, 1) kBatchTiles(const __grid_constant__ TileBatchArgs b) {
+  BatchSource src{b, (unsigned long long)blockIdx.x};
+  tileEngine(src, b.stageBytes, b.copyTimeoutNs, false);
 }
 
 }  // namespace
 
 const void* serveTilesKernel() { return (const void*)kServeTiles; }
+const void* batchTilesKernel() { return (const void*)kBatchTiles; }
 int serveTilesThreads() { return kTileThreads; }
 int serveTilesUnitsPerIter() { return kTileThreads * kTileNU; }
 int serveTilesStages() { return kTileStages; }
