@@ -389,179 +389,209 @@ struct BatchSource {
   }
 };
 
+// What a stage slot holds.  Every slot the engine waits on carries one of
+// these, and its mbarrier completes for each: data by the bulk loads' bytes,
+// the others by a plain arrive of thread 0.
+enum { kStageData = 0, kStageReg = 1, kStageIdle = 2, kStageStop = 3 };
+
 struct StageInfo {
-  unsigned long long off;   // byte offset in the block
-  unsigned len;             // bytes (a multiple of 16)
-  unsigned sub;             // bytes per input in the stage
+  int kind;
   int id, b;
-  int endOfTile;            // the tile's last sub-tile
-  int tail;                 // the op's last tile, with an element tail
+  int endOfTile;            // data: the tile's last sub-tile
+  int tail;                 // data: the op's last tile, with an element tail
+  unsigned len;             // data: bytes (a multiple of 16)
+  unsigned sub;             // data: bytes per input in the stage
+  unsigned long long off;   // data: byte offset in the block
+  TileWork reg;             // register tile
 };
 
 constexpr int kMaxPendingDone = kDoneLag + 4;
 
+VDEV void mbarArrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smemU32(bar)) : "memory");
+}
+
 // ---- the tile engine: take tiles from `src` until it has none and never
-// will; every thread of the CTA calls it
+// will; every thread of the CTA calls it.
+//
+// The stage slots form a ring of kTileStages; sequence index j uses slot
+// j mod kTileStages and its mbarrier's phase j / kTileStages.  Thread 0 (the
+// producer) fills index j + kTileStages as soon as index j has been folded:
+// with the next sub-tile of its current tile (bulk loads), claiming a new
+// tile when the current one is done; with a register tile (an unaligned op);
+// or, with nothing to claim, with an idle mark (persistent kernel) or the
+// stop mark.  Every thread (thread 0 too) folds the indices in order: a data
+// stage costs three barriers, and thread 0 refills after the third while the
+// others already wait for the next index.
 template <class Src>
 __device__ void tileEngine(Src& src, unsigned stageBytes, unsigned long long copyTimeoutNs, bool persistent) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ ServeReq sReq[kTileStages];   // the op of each stage
-  __shared__ ServeReq sCur;                // the op being issued (thread 0), or a register tile's
+  __shared__ ServeReq sCur;                // the op being issued (thread 0)
   __shared__ StageInfo sInfo[kTileStages];
-  __shared__ TileWork sReg;
-  __shared__ int sAct;
-  __shared__ long long sRegId;
   unsigned char* in = smem;
   unsigned char* out = smem + (size_t)kTileStages * stageBytes;
   uint64_t* bar = (uint64_t*)(out + 2 * (size_t)kTileOutBytes);
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < kTileStages; s++) mbarInit(&bar[s], 1);
-    fenceBarrierInit();
-  }
-  __syncthreads();
 
-  // `consumed`: sub-tiles folded, counted by every thread alike.  The rest
-  // is thread 0's: sub-tiles issued, the tile being issued, and the finished
-  // tiles whose completion is not yet confirmed (a tile is done once the
-  // bulk-store group of its last sub-tile has completed)
-  unsigned long long issued = 0, consumed = 0;
+  // thread 0's producer state
+  unsigned long long filled = 0;               // sequence indices filled so far
   long long curId = -1;
   unsigned long long curOff = 0, curEnd = 0;
   unsigned curSub = 0;
   int curB = 0, curTail = 0;
-  long long regId = -1;
-  TileWork regWork{};
   unsigned curGen = 0, stageGen[kTileStages];   // which claim each stage's op copy is of
   for (int i = 0; i < kTileStages; i++) stageGen[i] = ~0u;
   long long doneId[kMaxPendingDone];
   unsigned long long doneGroup[kMaxPendingDone];
   int ndone = 0;
-  unsigned backoff = 64;
+  unsigned idleNs = 64;
+  bool stopped = false;
 
-  while (true) {
-    if (threadIdx.x == 0) {
-      // top up the stages: issue sub-tiles of the current tile, claiming the
-      // next tile when it runs out; a register tile waits until the stages
-      // have drained
-      while (issued - consumed < (unsigned long long)kTileStages && regId < 0) {
-        if (curId < 0) {
-          unsigned long long tl = 0;
-          const long long id = src.claim(&tl);
-          if (id < 0) break;
-          TileWork w;
-          src.geom(id, tl, &w);
-          if (!w.staged) {
-            regId = id;
-            regWork = w;
-            break;
+  // thread 0: every pending tile completion, once all store groups are done
+  auto flushDone = [&]() {
+    bulkWaitAll();
+    for (int i = 0; i < ndone; i++) src.done(doneId[i]);
+    ndone = 0;
+  };
+  // thread 0: fill sequence index `filled` (its slot has been folded)
+  auto fill = [&]() {
+    const int stg = (int)(filled % kTileStages);
+    StageInfo& si = sInfo[stg];
+    if (stopped) return;   // the stop mark is the last index filled
+    if (curId < 0) {
+      unsigned long long tl = 0;
+      const long long id = src.claim(&tl);
+      if (id < 0) {
+        flushDone();
+        if (src.finished()) {
+          si.kind = kStageStop;
+          stopped = true;
+        } else {
+          si.kind = kStageIdle;
+          if (persistent) {
+            __nanosleep(idleNs);
+            idleNs = idleNs < 4096 ? 2 * idleNs : 4096;
           }
-          src.loadReq(id, &sCur);
-          curId = id;
-          curGen++;
-          curB = w.b;
-          curOff = w.off;
-          curEnd = w.end;
-          curTail = w.tail && hasTail(&sCur);
-          const unsigned nIn = sCur.coll == kAllGather ? 1u : (unsigned)sCur.nranks;
-          unsigned sub = stageBytes / nIn;
-          sub = sub < kTileOutBytes ? sub : kTileOutBytes;
-          curSub = sub & ~127u;
         }
-        const int stg = (int)(issued % kTileStages);
-        const unsigned len = (unsigned)(curEnd - curOff < curSub ? curEnd - curOff : curSub);
-        StageInfo& si = sInfo[stg];
-        si.off = curOff;
-        si.len = len;
-        si.sub = curSub;
-        si.id = (int)curId;
-        si.b = curB;
-        si.endOfTile = (curOff + len >= curEnd) ? 1 : 0;
-        si.tail = si.endOfTile && curTail;
-        if (stageGen[stg] != curGen) {   // the stage holds another claim's op
-          sReq[stg] = sCur;
-          stageGen[stg] = curGen;
-        }
-        const ServeReq& r = sCur;
-        unsigned char* dst = in + (size_t)stg * stageBytes;
-        if (r.coll == kAllGather) {
-          mbarExpect(&bar[stg], len);
-          bulkLoad(dst, (const char*)r.send[curB] + curOff, len, &bar[stg]);
-        } else {
-          const unsigned long long esz = (r.dtype == kF16 || r.dtype == kBF16) ? 2 : 4;
-          const unsigned long long from =
-              (r.coll == kReduceScatter ? (unsigned long long)curB * r.count * esz : 0ull) + curOff;
-          mbarExpect(&bar[stg], len * (unsigned)r.nranks);
-          for (int q = 0; q < r.nranks; q++)
-            bulkLoad(dst + (size_t)q * curSub, (const char*)r.send[q] + from, len, &bar[stg]);
-        }
-        issued++;
-        curOff += len;
-        if (curOff >= curEnd) curId = -1;
+        mbarArrive(&bar[stg]);
+        filled++;
+        return;
       }
-      int act;
-      if (issued > consumed) {
-        act = 1;                                   // fold the oldest stage
-      } else {
-        // nothing in flight: every store group may complete now
-        bulkWaitAll();
-        for (int i = 0; i < ndone; i++) src.done(doneId[i]);
-        ndone = 0;
-        if (regId >= 0) {
-          act = 2;                                 // a register tile
-          sRegId = regId;
-          sReg = regWork;
-          src.loadReq(regId, &sCur);
-          regId = -1;
-        } else if (src.finished()) {
-          act = 3;                                 // stop
-        } else {
-          act = 0;                                 // idle
-          if (persistent) __nanosleep(backoff);
-        }
+      idleNs = 64;
+      TileWork w;
+      src.geom(id, tl, &w);
+      if (!w.staged) {
+        si.kind = kStageReg;
+        si.id = (int)id;
+        si.reg = w;
+        src.loadReq(id, &sReq[stg]);   // the slot's own op copy
+        stageGen[stg] = ~0u;
+        mbarArrive(&bar[stg]);
+        filled++;
+        return;
       }
-      sAct = act;
+      src.loadReq(id, &sCur);
+      curId = id;
+      curGen++;
+      curB = w.b;
+      curOff = w.off;
+      curEnd = w.end;
+      curTail = w.tail && hasTail(&sCur);
+      const unsigned nIn = sCur.coll == kAllGather ? 1u : (unsigned)sCur.nranks;
+      unsigned sub = stageBytes / nIn;
+      sub = sub < kTileOutBytes ? sub : kTileOutBytes;
+      curSub = sub & ~127u;
     }
-    __syncthreads();
-    const int act = sAct;
-    if (act == 3) return;
-    if (act == 0) {
-      backoff = backoff < 2048 ? 2 * backoff : 2048;
-      __syncthreads();   // everyone has read sAct before thread 0 writes it again
-      continue;
+    const unsigned len = (unsigned)(curEnd - curOff < curSub ? curEnd - curOff : curSub);
+    si.kind = kStageData;
+    si.off = curOff;
+    si.len = len;
+    si.sub = curSub;
+    si.id = (int)curId;
+    si.b = curB;
+    si.endOfTile = (curOff + len >= curEnd) ? 1 : 0;
+    si.tail = si.endOfTile && curTail;
+    if (stageGen[stg] != curGen) {   // the stage holds another claim's op
+      sReq[stg] = sCur;
+      stageGen[stg] = curGen;
     }
-    backoff = 64;
-    if (act == 2) {
-      // a tile of an unaligned op: the register kernels' paths
-      runTile(&sCur, sReg.lo, sReg.hi, sReg.tail != 0);
-      __threadfence();
-      __syncthreads();
-      if (threadIdx.x == 0) src.done(sRegId);
-      __syncthreads();
-      continue;
+    const ServeReq& r = sCur;
+    unsigned char* dst = in + (size_t)stg * stageBytes;
+    if (r.coll == kAllGather) {
+      mbarExpect(&bar[stg], len);
+      bulkLoad(dst, (const char*)r.send[curB] + curOff, len, &bar[stg]);
+    } else {
+      const unsigned long long esz = (r.dtype == kF16 || r.dtype == kBF16) ? 2 : 4;
+      const unsigned long long from =
+          (r.coll == kReduceScatter ? (unsigned long long)curB * r.count * esz : 0ull) + curOff;
+      mbarExpect(&bar[stg], len * (unsigned)r.nranks);
+      for (int q = 0; q < r.nranks; q++)
+        bulkLoad(dst + (size_t)q * curSub, (const char*)r.send[q] + from, len, &bar[stg]);
     }
-    // act == 1: the oldest issued sub-tile
-    const int stg = (int)(consumed % kTileStages);
-    const bool ok = stageWait(&bar[stg], (unsigned)((consumed / kTileStages) & 1ull), copyTimeoutNs);
+    filled++;
+    curOff += len;
+    if (curOff >= curEnd) curId = -1;
+  };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kTileStages; s++) mbarInit(&bar[s], 1);
+    fenceBarrierInit();
+    for (int s = 0; s < kTileStages; s++) fill();
+  }
+  __syncthreads();
+
+  // dsn: data stages folded so far (every thread counts them alike): the
+  // output buffer and the store group of a data stage go by it
+  unsigned long long dsn = 0;
+  for (unsigned long long j = 0;; j++) {
+    const int stg = (int)(j % kTileStages);
+    const bool ok = stageWait(&bar[stg], (unsigned)((j / kTileStages) & 1ull), copyTimeoutNs);
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) {
         // loads still in flight must land before the CTA's shared memory is released
-        for (unsigned long long j = consumed; j < issued; j++)
-          (void)stageWait(&bar[j % kTileStages], (unsigned)((j / kTileStages) & 1ull), copyTimeoutNs);
+        for (unsigned long long q = j; q < filled; q++)
+          (void)stageWait(&bar[q % kTileStages], (unsigned)((q / kTileStages) & 1ull), copyTimeoutNs);
         bulkWaitAll();
         src.fail();
       }
       return;
     }
-    const int ob = (int)(consumed & 1ull);
+    const int kind = sInfo[stg].kind;
+    if (kind == kStageStop) {
+      // the data stages before the mark have committed their stores since
+      // it was filled: wait for them and report their tiles
+      if (threadIdx.x == 0) flushDone();
+      return;
+    }
+    if (kind == kStageIdle) {
+      __syncthreads();                // everyone has read the mark
+      if (threadIdx.x == 0) fill();
+      continue;
+    }
+    if (kind == kStageReg) {
+      // a tile of an unaligned op: the register kernels' paths
+      const TileWork w = sInfo[stg].reg;
+      const int id = sInfo[stg].id;
+      runTile(&sReq[stg], w.lo, w.hi, w.tail != 0);
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        src.done(id);
+        fill();
+      }
+      continue;
+    }
+    // a data stage
+    const int ob = (int)(dsn & 1ull);
     if (threadIdx.x == 0) {
-      // out[ob] was last read by the store group of sub-tile consumed - 2,
-      // which has read it once at most one group is pending; the tiles whose
-      // last group is older than the newest kDoneLag are done
+      // out[ob] was last read by the store group of data stage dsn - 2,
+      // which has read it once at most one group is pending; the tiles
+      // whose last group is older than the newest kDoneLag are done
       bulkWaitRead1();
       bulkWaitDoneLag();
       int keep = 0;
       for (int i = 0; i < ndone; i++) {
-        if (doneGroup[i] + kDoneLag + 1 <= consumed) {
+        if (doneGroup[i] + kDoneLag + 1 <= dsn) {
           src.done(doneId[i]);
         } else {
           doneId[keep] = doneId[i];
@@ -578,6 +608,11 @@ __device__ void tileEngine(Src& src, unsigned stageBytes, unsigned long long cop
     foldStageAny(r, smemU32(in + (size_t)stg * stageBytes), si.sub, smemU32(o), si.b, si.off, si.len);
     fenceProxyAsync();
     __syncthreads();   // o written; the stage read by every thread
+    if (si.tail) {     // the element tail, with ordinary loads and stores
+      tailAny(r);
+      __threadfence();
+      __syncthreads();
+    }
     if (threadIdx.x == 0) {
       if (r->coll == kReduceScatter) {
         bulkStore((char*)r->recv[si.b] + si.off, o, si.len);
@@ -590,19 +625,14 @@ __device__ void tileEngine(Src& src, unsigned stageBytes, unsigned long long cop
         }
       }
       bulkCommit();
+      if (si.endOfTile) {
+        doneId[ndone] = si.id;
+        doneGroup[ndone] = dsn;
+        ndone++;
+      }
+      fill();   // refill this slot: index j + kTileStages
     }
-    if (si.tail) {   // the element tail, with ordinary loads and stores
-      tailAny(r);
-      __threadfence();
-      __syncthreads();
-    }
-    if (threadIdx.x == 0 && si.endOfTile) {
-      doneId[ndone] = si.id;
-      doneGroup[ndone] = consumed;
-      ndone++;
-    }
-    consumed++;        // every thread counts the stages it has folded
-    __syncthreads();   // the stage info and op copies are free again
+    dsn++;
   }
 }
 
