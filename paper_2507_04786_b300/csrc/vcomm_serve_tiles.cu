@@ -93,57 +93,82 @@ __device__ void runTile(const ServeReq* q, unsigned long long lo, unsigned long 
   else mx ? tileReduce<__nv_bfloat16, OpMax>(q, lo, hi, tail) : tileReduce<__nv_bfloat16, OpSum>(q, lo, hi, tail);
 }
 
-// ---- staged path: fold one sub-tile of `len` bytes (block b, byte offset
-// off in the block) from the stage's inputs (`sub` bytes apart, shared
-// memory address in) into shared memory address o.  Explicit shared-memory
-// accesses: the fold is out of line and its pointers would otherwise be
-// generic.
-VDEV uint4 lds16(unsigned a) {
-  uint4 v;
-  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
-  return v;
-}
-VDEV void sts16(unsigned a, uint4 v) {
-  asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
-               : "memory");
-}
+// ---- staged path: fold one sub-tile of `len` bytes from the stage at
+// shared-memory byte offset `in` (inputs `sub` bytes apart) into the output
+// buffer at offset `o` (offsets into the kernel's dynamic shared memory, read
+// through the array itself so the loads are ordinary shared loads).  Unit
+// u's chain starts at rank seg[i] + 1 for the first i with u < segEnd[i]
+// (thread 0 has cut the sub-tile into its ring segments); a unit's k inputs
+// are loaded before they are folded.
+constexpr int kMaxSegRuns = 4;
 
 template <class T, class Op>
-__device__ __noinline__ void foldStage(const ServeReq* q, unsigned in, unsigned sub, unsigned o, int b,
-                                       unsigned long long off, unsigned len) {
-  const DirectView v = viewOfReq(q);
-  const int k = q->nranks;
-  constexpr unsigned long long esz = sizeof(T);
-  unsigned long long runEnd = 0;
-  int seg = 0;
+__device__ __noinline__ void foldStage(int k, unsigned in, unsigned sub, unsigned o, unsigned len,
+                                       const int* seg, const unsigned* segEnd, int nseg) {
+  extern __shared__ __align__(128) unsigned char smem[];
   for (unsigned u = threadIdx.x * 16u; u < len; u += blockDim.x * 16u) {
-    if (q->coll == kAllReduce) {
-      const unsigned long long e0 = (off + u) / esz;
-      if (e0 >= runEnd) seg = arSegment(v, e0, (int)esz, &runEnd);
-    } else {
-      seg = b;   // ReduceScatter block b: the chain starts at rank b + 1
+    int i = 0;
+    while (i + 1 < nseg && u >= segEnd[i]) i++;
+    int r = seg[i] + 1 < k ? seg[i] + 1 : 0;
+    uint4 x[kServeMaxRanks];
+#pragma unroll
+    for (int j = 0; j < kServeMaxRanks; j++) {
+      if (j < k) {
+        x[j] = *(const uint4*)(smem + in + (unsigned)r * sub + u);
+        if (++r == k) r = 0;
+      }
     }
-    int r = seg + 1 < k ? seg + 1 : 0;
-    uint4 acc = lds16(in + (unsigned)r * sub + u);
-    for (int j = 1; j < k; j++) {
-      if (++r == k) r = 0;
-      acc = combine<T, Op, uint4>(acc, lds16(in + (unsigned)r * sub + u));
-    }
-    sts16(o + u, acc);
+    uint4 acc = x[0];
+#pragma unroll
+    for (int j = 1; j < kServeMaxRanks; j++)
+      if (j < k) acc = combine<T, Op, uint4>(acc, x[j]);
+    *(uint4*)(smem + o + u) = acc;
   }
 }
 
-VDEV void foldStageAny(const ServeReq* q, unsigned in, unsigned sub, unsigned o, int b,
-                       unsigned long long off, unsigned len) {
+__device__ __noinline__ void copyStage(unsigned in, unsigned o, unsigned len) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  for (unsigned u = threadIdx.x * 16u; u < len; u += blockDim.x * 16u)
+    *(uint4*)(smem + o + u) = *(const uint4*)(smem + in + u);
+}
+
+VDEV void foldStageAny(const ServeReq* q, unsigned in, unsigned sub, unsigned o, unsigned len,
+                       const int* seg, const unsigned* segEnd, int nseg) {
   if (q->coll == kAllGather) {   // a copy: the one input as it is
-    for (unsigned u = threadIdx.x * 16u; u < len; u += blockDim.x * 16u) sts16(o + u, lds16(in + u));
+    copyStage(in, o, len);
     return;
   }
+  const int k = q->nranks;
   const bool mx = q->redop == kMax;
-  if (q->dtype == kI32) mx ? foldStage<int32_t, OpMax>(q, in, sub, o, b, off, len) : foldStage<int32_t, OpSum>(q, in, sub, o, b, off, len);
-  else if (q->dtype == kF32) mx ? foldStage<float, OpMax>(q, in, sub, o, b, off, len) : foldStage<float, OpSum>(q, in, sub, o, b, off, len);
-  else if (q->dtype == kF16) mx ? foldStage<__half, OpMax>(q, in, sub, o, b, off, len) : foldStage<__half, OpSum>(q, in, sub, o, b, off, len);
-  else mx ? foldStage<__nv_bfloat16, OpMax>(q, in, sub, o, b, off, len) : foldStage<__nv_bfloat16, OpSum>(q, in, sub, o, b, off, len);
+  if (q->dtype == kI32) mx ? foldStage<int32_t, OpMax>(k, in, sub, o, len, seg, segEnd, nseg) : foldStage<int32_t, OpSum>(k, in, sub, o, len, seg, segEnd, nseg);
+  else if (q->dtype == kF32) mx ? foldStage<float, OpMax>(k, in, sub, o, len, seg, segEnd, nseg) : foldStage<float, OpSum>(k, in, sub, o, len, seg, segEnd, nseg);
+  else if (q->dtype == kF16) mx ? foldStage<__half, OpMax>(k, in, sub, o, len, seg, segEnd, nseg) : foldStage<__half, OpSum>(k, in, sub, o, len, seg, segEnd, nseg);
+  else mx ? foldStage<__nv_bfloat16, OpMax>(k, in, sub, o, len, seg, segEnd, nseg) : foldStage<__nv_bfloat16, OpSum>(k, in, sub, o, len, seg, segEnd, nseg);
+}
+
+// thread 0: the ring segments of a sub-tile (bytes [off, off + len) of block
+// b): AllReduce segments from the partition, at most kMaxSegRuns runs (a
+// sub-tile is a few KiB, a segment a chunk); ReduceScatter block b is one run
+VDEV int cutSegments(const ServeReq* q, int b, unsigned long long off, unsigned len, int* seg, unsigned* segEnd) {
+  if (q->coll != kAllReduce) {
+    seg[0] = b;
+    segEnd[0] = len;
+    return 1;
+  }
+  const DirectView v = viewOfReq(q);
+  const unsigned long long esz = (q->dtype == kF16 || q->dtype == kBF16) ? 2 : 4;
+  unsigned u = 0;
+  int n = 0;
+  while (u < len && n < kMaxSegRuns) {
+    unsigned long long runEnd;   // in elements
+    seg[n] = arSegment(v, (off + u) / esz, (int)esz, &runEnd);
+    const unsigned long long endB = runEnd * esz - off;
+    segEnd[n] = endB < len ? (unsigned)endB : len;
+    u = segEnd[n];
+    n++;
+  }
+  if (u < len) segEnd[n - 1] = len;   // cannot happen: a sub-tile spans fewer segments
+  return n;
 }
 
 // the element tail of a staged AllReduce (count not a multiple of the units)
@@ -402,6 +427,9 @@ struct StageInfo {
   unsigned len;             // data: bytes (a multiple of 16)
   unsigned sub;             // data: bytes per input in the stage
   unsigned long long off;   // data: byte offset in the block
+  int nseg;                 // data: ring segment runs of the sub-tile
+  int seg[kMaxSegRuns];
+  unsigned segEnd[kMaxSegRuns];
   TileWork reg;             // register tile
 };
 
@@ -511,6 +539,7 @@ __device__ void tileEngine(Src& src, unsigned stageBytes, unsigned long long cop
     si.b = curB;
     si.endOfTile = (curOff + len >= curEnd) ? 1 : 0;
     si.tail = si.endOfTile && curTail;
+    si.nseg = cutSegments(&sCur, curB, curOff, len, si.seg, si.segEnd);
     if (stageGen[stg] != curGen) {   // the stage holds another claim's op
       sReq[stg] = sCur;
       stageGen[stg] = curGen;
@@ -605,7 +634,8 @@ __device__ void tileEngine(Src& src, unsigned stageBytes, unsigned long long cop
     const StageInfo si = sInfo[stg];
     const ServeReq* r = &sReq[stg];
     unsigned char* o = out + (size_t)ob * kTileOutBytes;
-    foldStageAny(r, smemU32(in + (size_t)stg * stageBytes), si.sub, smemU32(o), si.b, si.off, si.len);
+    foldStageAny(r, (unsigned)((size_t)stg * stageBytes), si.sub, (unsigned)(o - smem), si.len, si.seg,
+                 si.segEnd, si.nseg);
     fenceProxyAsync();
     __syncthreads();   // o written; the stage read by every thread
     if (si.tail) {     // the element tail, with ordinary loads and stores
