@@ -103,13 +103,24 @@ __device__ void runTile(const ServeReq* q, unsigned long long lo, unsigned long 
 constexpr int kMaxSegRuns = 4;
 
 template <class T, class Op>
-__device__ __noinline__ void foldStage(int k, unsigned in, unsigned sub, unsigned o, unsigned len,
-                                       const int* seg, const unsigned* segEnd, int nseg) {
+__device__ __noinline__ void foldStage(const ServeReq* q, unsigned in, unsigned sub, unsigned o, unsigned len,
+                                       unsigned long long off, const int* seg, const unsigned* segEnd, int nseg) {
   extern __shared__ __align__(128) unsigned char smem[];
+  const int k = q->nranks;
+  unsigned long long runEnd = 0;   // nseg == 0: each unit's segment from the partition
+  int s0 = 0;
   for (unsigned u = threadIdx.x * 16u; u < len; u += blockDim.x * 16u) {
-    int i = 0;
-    while (i + 1 < nseg && u >= segEnd[i]) i++;
-    int r = seg[i] + 1 < k ? seg[i] + 1 : 0;
+    int s;
+    if (nseg > 0) {
+      int i = 0;
+      while (i + 1 < nseg && u >= segEnd[i]) i++;
+      s = seg[i];
+    } else {
+      const unsigned long long e0 = (off + u) / sizeof(T);
+      if (e0 >= runEnd) s0 = arSegment(viewOfReq(q), e0, (int)sizeof(T), &runEnd);
+      s = s0;
+    }
+    int r = s + 1 < k ? s + 1 : 0;
     uint4 x[kServeMaxRanks];
 #pragma unroll
     for (int j = 0; j < kServeMaxRanks; j++) {
@@ -133,22 +144,26 @@ __device__ __noinline__ void copyStage(unsigned in, unsigned o, unsigned len) {
 }
 
 VDEV void foldStageAny(const ServeReq* q, unsigned in, unsigned sub, unsigned o, unsigned len,
-                       const int* seg, const unsigned* segEnd, int nseg) {
+                       unsigned long long off, const int* seg, const unsigned* segEnd, int nseg) {
   if (q->coll == kAllGather) {   // a copy: the one input as it is
     copyStage(in, o, len);
     return;
   }
-  const int k = q->nranks;
   const bool mx = q->redop == kMax;
-  if (q->dtype == kI32) mx ? foldStage<int32_t, OpMax>(k, in, sub, o, len, seg, segEnd, nseg) : foldStage<int32_t, OpSum>(k, in, sub, o, len, seg, segEnd, nseg);
-  else if (q->dtype == kF32) mx ? foldStage<float, OpMax>(k, in, sub, o, len, seg, segEnd, nseg) : foldStage<float, OpSum>(k, in, sub, o, len, seg, segEnd, nseg);
-  else if (q->dtype == kF16) mx ? foldStage<__half, OpMax>(k, in, sub, o, len, seg, segEnd, nseg) : foldStage<__half, OpSum>(k, in, sub, o, len, seg, segEnd, nseg);
-  else mx ? foldStage<__nv_bfloat16, OpMax>(k, in, sub, o, len, seg, segEnd, nseg) : foldStage<__nv_bfloat16, OpSum>(k, in, sub, o, len, seg, segEnd, nseg);
+#define VC_FOLD(T) mx ? foldStage<T, OpMax>(q, in, sub, o, len, off, seg, segEnd, nseg) \
+                      : foldStage<T, OpSum>(q, in, sub, o, len, off, seg, segEnd, nseg)
+  if (q->dtype == kI32) VC_FOLD(int32_t);
+  else if (q->dtype == kF32) VC_FOLD(float);
+  else if (q->dtype == kF16) VC_FOLD(__half);
+  else VC_FOLD(__nv_bfloat16);
+#undef VC_FOLD
 }
 
 // thread 0: the ring segments of a sub-tile (bytes [off, off + len) of block
-// b): AllReduce segments from the partition, at most kMaxSegRuns runs (a
-// sub-tile is a few KiB, a segment a chunk); ReduceScatter block b is one run
+// b): AllReduce segments from the partition (a segment is normally a chunk,
+// far longer than a sub-tile; 0 runs if the sub-tile holds more than
+// kMaxSegRuns, as the short segments of a small buffer's last loop do, and
+// the fold then looks each unit's segment up); ReduceScatter block b is one run
 VDEV int cutSegments(const ServeReq* q, int b, unsigned long long off, unsigned len, int* seg, unsigned* segEnd) {
   if (q->coll != kAllReduce) {
     seg[0] = b;
@@ -159,7 +174,8 @@ VDEV int cutSegments(const ServeReq* q, int b, unsigned long long off, unsigned 
   const unsigned long long esz = (q->dtype == kF16 || q->dtype == kBF16) ? 2 : 4;
   unsigned u = 0;
   int n = 0;
-  while (u < len && n < kMaxSegRuns) {
+  while (u < len) {
+    if (n == kMaxSegRuns) return 0;
     unsigned long long runEnd;   // in elements
     seg[n] = arSegment(v, (off + u) / esz, (int)esz, &runEnd);
     const unsigned long long endB = runEnd * esz - off;
@@ -167,7 +183,6 @@ VDEV int cutSegments(const ServeReq* q, int b, unsigned long long off, unsigned 
     u = segEnd[n];
     n++;
   }
-  if (u < len) segEnd[n - 1] = len;   // cannot happen: a sub-tile spans fewer segments
   return n;
 }
 
@@ -634,8 +649,8 @@ __device__ void tileEngine(Src& src, unsigned stageBytes, unsigned long long cop
     const StageInfo si = sInfo[stg];
     const ServeReq* r = &sReq[stg];
     unsigned char* o = out + (size_t)ob * kTileOutBytes;
-    foldStageAny(r, (unsigned)((size_t)stg * stageBytes), si.sub, (unsigned)(o - smem), si.len, si.seg,
-                 si.segEnd, si.nseg);
+    foldStageAny(r, (unsigned)((size_t)stg * stageBytes), si.sub, (unsigned)(o - smem), si.len, si.off,
+                 si.seg, si.segEnd, si.nseg);
     fenceProxyAsync();
     __syncthreads();   // o written; the stage read by every thread
     if (si.tail) {     // the element tail, with ordinary loads and stores
