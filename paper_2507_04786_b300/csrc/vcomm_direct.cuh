@@ -173,11 +173,24 @@ VDEV unsigned long long copyUnits(const DirectView& a, int E) {
   return (a.count / E) * (a.coll == kAllGather ? (unsigned long long)a.nranks : 1ull);
 }
 
+// The threads that share a range of units: every thread of the CTA (the
+// per-call kernels), or the first N (the tile engine's consumer warps; its
+// producer warp comes after them).
+struct BlockThreads {
+  static VDEV unsigned id() { return threadIdx.x; }
+  static VDEV unsigned count() { return blockDim.x; }
+};
+template <unsigned N>
+struct FirstThreads {
+  static VDEV unsigned id() { return threadIdx.x; }
+  static VDEV constexpr unsigned count() { return N; }
+};
+
 // AllReduce, ReduceScatter and Reduce over units [lo, hi) of the collective
 // (consecutive threads take consecutive units, so every warp access is one
 // coalesced 512 bytes), NU units per thread per iteration; `tail`: this CTA
 // also does the element tail of each block
-template <class T, class Op, class U, int NU>
+template <class T, class Op, class U, int NU, class TS = BlockThreads>
 VDEV void directReduce(const DirectView& a, unsigned long long lo, unsigned long long hi, bool tail) {
   const int k = a.nranks;
   constexpr int E = U::kElems;
@@ -185,13 +198,13 @@ VDEV void directReduce(const DirectView& a, unsigned long long lo, unsigned long
   const unsigned long long nunit = a.count / E;                 // full units per block
   unsigned long long runEnd = 0;   // AllReduce: the current segment's end (elements)
   int seg = 0;
-  for (unsigned long long g0 = lo + threadIdx.x; g0 < hi; g0 += (unsigned long long)NU * blockDim.x) {
+  for (unsigned long long g0 = lo + TS::id(); g0 < hi; g0 += (unsigned long long)NU * TS::count()) {
     int s[NU];
     unsigned long long off[NU];
     int nu = 0;
 #pragma unroll
     for (int u = 0; u < NU; u++) {
-      const unsigned long long g = g0 + (unsigned long long)u * blockDim.x;
+      const unsigned long long g = g0 + (unsigned long long)u * TS::count();
       s[u] = 0;
       off[u] = 0;
       if (g >= hi) continue;
@@ -222,7 +235,7 @@ VDEV void directReduce(const DirectView& a, unsigned long long lo, unsigned long
       if (a.coll == kAllReduce) {
         for (int r = 0; r < k; r++) U::store((char*)a.recv[r] + off[u], v[u]);
       } else if (a.coll == kReduceScatter) {
-        const unsigned long long g = g0 + (unsigned long long)u * blockDim.x;
+        const unsigned long long g = g0 + (unsigned long long)u * TS::count();
         U::store((char*)a.recv[s[u]] + (g % nunit) * E * esz, v[u]);
       } else {
         U::store((char*)a.recv[a.root] + off[u], v[u]);
@@ -232,7 +245,7 @@ VDEV void directReduce(const DirectView& a, unsigned long long lo, unsigned long
   const unsigned long long nt = a.count - nunit * E;   // element tail of each block
   if (E > 1 && nt && tail) {
     const unsigned long long nblk = (a.coll == kReduceScatter) ? (unsigned long long)k : 1ull;
-    for (unsigned long long t = threadIdx.x; t < nt * nblk; t += blockDim.x) {
+    for (unsigned long long t = TS::id(); t < nt * nblk; t += TS::count()) {
       const unsigned long long b = t / nt, i = nunit * E + t % nt;
       using U1 = typename U::Tail;
       if (a.coll == kAllReduce) {
@@ -257,12 +270,12 @@ VDEV void directReduce(const DirectView& a, unsigned long long lo, unsigned long
 // AllGather (block b of every output = rank b's input) and Broadcast (every
 // output = the root's input) over units [lo, hi); count in bytes.  A unit is
 // read once and written to every output that is not its own source.
-template <class U>
+template <class U, class TS = BlockThreads>
 VDEV void directCopy(const DirectView& a, unsigned long long lo, unsigned long long hi, bool tail) {
   const int k = a.nranks;
   constexpr int E = sizeof(typename U::W);
   const unsigned long long nunit = a.count / E;
-  for (unsigned long long g = lo + threadIdx.x; g < hi; g += blockDim.x) {
+  for (unsigned long long g = lo + TS::id(); g < hi; g += TS::count()) {
     const unsigned long long b = (a.coll == kAllGather) ? g / nunit : (unsigned long long)a.root;
     const unsigned long long off = (g % nunit) * E;
     const typename U::W v = U::load((const char*)a.send[b] + off);
@@ -275,7 +288,7 @@ VDEV void directCopy(const DirectView& a, unsigned long long lo, unsigned long l
   const unsigned long long nt = a.count - nunit * E;   // byte tail of each block
   if (E > 1 && nt && tail) {
     const unsigned long long nblk = (a.coll == kAllGather) ? (unsigned long long)k : 1ull;
-    for (unsigned long long t = threadIdx.x; t < nt * nblk; t += blockDim.x) {
+    for (unsigned long long t = TS::id(); t < nt * nblk; t += TS::count()) {
       const unsigned long long b = (a.coll == kAllGather) ? t / nt : (unsigned long long)a.root;
       const unsigned long long off = nunit * E + t % nt;
       const uint8_t v = U::Tail::load((const char*)a.send[b] + off);
@@ -459,12 +472,12 @@ VDEV void directReduceShifted(const DirectView& a, unsigned long long lo, unsign
 // AllGather units [lo, hi): the 16-byte units of the k blocks laid end to end
 // (count bytes each, not a multiple of 16), each written to every receive
 // buffer; `tail`: this CTA also writes the last, partial unit
-template <class M>
+template <class M, class TS = BlockThreads>
 VDEV void directCopyShifted(const DirectView& a, unsigned long long lo, unsigned long long hi, bool tail) {
   using UB = typename M::template Elem<uint8_t>;
   const int k = a.nranks;
   const unsigned long long B = a.count, total = B * (unsigned long long)k;
-  for (unsigned long long u = lo + threadIdx.x; u < hi; u += blockDim.x) {
+  for (unsigned long long u = lo + TS::id(); u < hi; u += TS::count()) {
     const unsigned long long x = u * 16ull, b = x / B, o = x - b * B;
     uint4 v;
     if (o + 16 <= B) {
@@ -482,7 +495,7 @@ VDEV void directCopyShifted(const DirectView& a, unsigned long long lo, unsigned
   }
   const unsigned long long full = total / 16ull;
   if (tail && full * 16ull < total) {
-    for (unsigned long long y = full * 16ull + threadIdx.x; y < total; y += blockDim.x) {
+    for (unsigned long long y = full * 16ull + TS::id(); y < total; y += TS::count()) {
       const unsigned long long bb = y / B;
       const uint8_t c = UB::load((const char*)a.send[bb] + (y - bb * B));
       for (int r = 0; r < k; r++) ((uint8_t*)a.recv[r])[y] = c;

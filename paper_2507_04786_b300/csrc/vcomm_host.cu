@@ -1091,7 +1091,7 @@ static vResult_t launchTileGroup(vcomm* c, std::vector<CallSpec>& ops, unsigned 
       d.nranks = k;
       d.nsub = o.plan.nchannels;
       d.root = o.root;
-      d.vec = g.vec;
+      d.vec = tg.vec;
       d.ptrBase = 2 * k * i;
       for (int r = 0; r < k; r++) {
         b->ptrs[d.ptrBase + r] = o.send[r];

@@ -255,14 +255,15 @@ struct TileOpDesc {
   int coll, dtype, redop, nranks, nsub, root, vec, ptrBase;
 };
 // The tiles of one direct-protocol op (host side, serving and groups).
-// Staged (16-byte aligned AllReduce / ReduceScatter / AllGather with whole
-// 16-byte units): byte ranges of a block, whole 4 KiB pieces.  Otherwise
+// Staged (16-byte aligned buffers; ReduceScatter blocks that are not whole
+// 16-byte units too): byte ranges of a block, whole 4 KiB pieces.  Otherwise
 // ranges of the register kernels' units, whole iterations (`iter` units) of
 // a CTA.  About two tiles per worker CTA (`workers`), and at most ~4 MiB of
 // traffic per tile so that small work never waits long for a free CTA.
 // count: elements, or bytes for AllGather / Broadcast; vec as DirectArgs::vec.
 struct TileGeometry {
   unsigned long long staged, units, tileUnits, blockBytes, tileBytes, perBlock, ntiles;
+  int vec;   // the op's DirectArgs::vec in the engine (register reductions: 0)
 };
 inline TileGeometry tileGeometry(int coll, int k, unsigned long long count, int esz, int vec,
                                  unsigned long long workers, unsigned long long iter) {
@@ -274,9 +275,11 @@ inline TileGeometry tileGeometry(int coll, int k, unsigned long long count, int 
   const unsigned long long factor = coll == kAllReduce ? 2ull * k : (unsigned long long)k + 1;
   const unsigned long long twoW = 2ull * (workers > 0 ? workers : 1);
   const unsigned long long Ev = 16 / unitBytes;   // elements (bytes) per 16-byte unit
-  const bool stageable = (coll == kAllReduce || coll == kReduceScatter || coll == kAllGather) && vec == 1;
+  // staged: aligned buffers of any collective, and ReduceScatter blocks that
+  // are not whole units (shifted windows); a block of at least one full unit
+  const bool stageable = vec == 1 || (vec == 2 && coll == kReduceScatter);
   g.blockBytes = stageable ? (count / Ev) * 16 : 0;
-  g.staged = (stageable && g.blockBytes >= 16) ? 1 : 0;
+  g.staged = (stageable && g.blockBytes >= (vec == 2 ? 32u : 16u)) ? 1 : 0;
   if (g.staged) {
     const unsigned long long piece = 4096;
     const unsigned long long maxTile = std::max<unsigned long long>(piece, (4ull << 20) / factor / piece * piece);
@@ -286,9 +289,12 @@ inline TileGeometry tileGeometry(int coll, int k, unsigned long long count, int 
     g.tileBytes = tb;
     g.perBlock = (g.blockBytes + tb - 1) / tb;
     g.ntiles = blocks * g.perBlock;
-  } else {
-    const unsigned long long E = vec ? Ev : 1;
-    g.units = (vec == 2 && copy) ? count * blocks / 16 : (count / E) * blocks;
+  }
+  // the register path folds reductions element by element, copies as given
+  g.vec = (g.staged || copy) ? vec : 0;
+  if (!g.staged) {
+    const unsigned long long E = g.vec ? Ev : 1;
+    g.units = (g.vec == 2 && copy) ? count * blocks / 16 : (count / E) * blocks;
     const unsigned long long unitTraffic = E * unitBytes * factor;
     const unsigned long long maxTile = std::max<unsigned long long>(iter, (4ull << 20) / unitTraffic / iter * iter);
     unsigned long long tu = (g.units + twoW - 1) / twoW;

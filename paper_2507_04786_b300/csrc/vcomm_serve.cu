@@ -391,6 +391,7 @@ bool postTile(vserve* s, Request& q) {
   const TileGeometry tg = tileGeometry(q.coll, q.nranks, sr.count, (int)esz, sr.vec,
                                       (unsigned long long)s->tileWorkers,
                                       (unsigned long long)serveTilesUnitsPerIter());
+  sr.vec = tg.vec;
   tr.staged = tg.staged;
   tr.units = tg.units;
   tr.tileUnits = tg.tileUnits;

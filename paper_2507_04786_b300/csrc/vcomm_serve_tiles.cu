@@ -15,14 +15,17 @@
 // GPU tile by tile in arrival order.
 //
 // Data movement.  A tile of a 16-byte aligned request is a byte range of one
-// block (AllReduce: the buffer; ReduceScatter / AllGather: block b) that moves
-// through shared memory in sub-tiles: thread 0 issues bulk asynchronous copies
-// of the sub-tile's inputs (k for a reduction, one for AllGather) into one of
-// three stages, all threads fold the stage into an output buffer, and thread 0
-// bulk-stores it to every output.  The stages run ahead across tile
-// boundaries (thread 0 claims the next tile while the current one is still
-// folding), so the loads in flight never drain between tiles.  Unaligned
-// requests take the register kernels' element-wise path, one tile at a time.
+// block (AllReduce, Reduce, Broadcast: the buffer; ReduceScatter / AllGather:
+// block b) that moves through shared memory in sub-tiles.  A producer warp
+// issues bulk asynchronous copies of a sub-tile's inputs (k for a reduction,
+// one for a copy; a lane per rank) into one of three stages; eight consumer
+// warps fold the stage into an output buffer; the producer bulk-stores it to
+// every output.  Producer and consumers meet only on mbarriers, so the producer's
+// claims, stores and completions overlap the folds, and the stages run ahead
+// across tile boundaries.  ReduceScatter blocks that are not whole 16-byte
+// units load a window one unit longer and cut each 16-byte piece out of two
+// aligned ones.  Requests that are not 16-byte aligned take the register
+// kernels' element-wise path, one tile at a time.
 //
 // No CTA waits on another: claims and completions are atomics, and the only
 // waits are the idle polls (bounded by the idle timeout and the stop word)
@@ -39,10 +42,14 @@ namespace {
 
 using namespace direct;
 
-constexpr int kTileThreads = 256;
+constexpr int kTileConsumers = 256;                   // folding threads: warps 0..7
+constexpr int kConsumerWarps = kTileConsumers / 32;
+constexpr int kTileThreads = kTileConsumers + 32;     // and one producer warp
 constexpr int kTileStages = 3;
-constexpr unsigned kTileOutBytes = 16384;   // one folded sub-tile, double buffered
-constexpr int kTileNU = 2;                  // register path: units per thread per iteration
+using Consumers = FirstThreads<kTileConsumers>;
+constexpr unsigned kTileOutBytes = 16384;   // one folded sub-tile
+constexpr int kTileOutBufs = 2;             // output buffers, used in turn
+
 
 VDEV uint64_t ldAcquireSys(const unsigned long long* p) {
   uint64_t v;
@@ -62,23 +69,22 @@ VDEV DirectView viewOfReq(const ServeReq* q) {
                     q->coll, q->nranks, q->nsub, q->root, 0};
 }
 
-// ---- register path (requests that are not 16-byte aligned; vec 2: aligned
-// buffers whose blocks are not whole 16-byte units), one body per (dtype,
-// op), out of line
+// ---- register path: ops the staged path does not take (buffers that are
+// not 16-byte aligned, blocks of less than a unit or two, AllGather blocks
+// that are not whole units).  Reductions go element by element (the host
+// gives them vec 0), copies by aligned, shifted or single bytes; one body per
+// (dtype, op), out of line, so the engine's own frame stays small.
 template <class T, class Op>
 __device__ __noinline__ void tileReduce(const ServeReq* q, unsigned long long lo, unsigned long long hi,
                                         bool tail) {
-  const DirectView v = viewOfReq(q);
-  if (q->vec == 1) directReduce<T, Op, Unit16L2<T>, kTileNU>(v, lo, hi, tail);
-  else if (q->vec == 2) directReduceShifted<T, Op, L2Mem, kTileNU>(v, lo, hi, tail);
-  else directReduce<T, Op, Unit1L2<T>, 1>(v, lo, hi, tail);
+  directReduce<T, Op, Unit1L2<T>, 1, Consumers>(viewOfReq(q), lo, hi, tail);
 }
 
 __device__ __noinline__ void tileCopy(const ServeReq* q, unsigned long long lo, unsigned long long hi, bool tail) {
   const DirectView v = viewOfReq(q);
-  if (q->vec == 1) directCopy<Unit16L2<uint8_t>>(v, lo, hi, tail);
-  else if (q->vec == 2) directCopyShifted<L2Mem>(v, lo, hi, tail);
-  else directCopy<Unit1L2<uint8_t>>(v, lo, hi, tail);
+  if (q->vec == 1) directCopy<Unit16L2<uint8_t>, Consumers>(v, lo, hi, tail);
+  else if (q->vec == 2) directCopyShifted<L2Mem, Consumers>(v, lo, hi, tail);
+  else directCopy<Unit1L2<uint8_t>, Consumers>(v, lo, hi, tail);
 }
 
 __device__ void runTile(const ServeReq* q, unsigned long long lo, unsigned long long hi, bool tail) {
@@ -93,23 +99,33 @@ __device__ void runTile(const ServeReq* q, unsigned long long lo, unsigned long 
   else mx ? tileReduce<__nv_bfloat16, OpMax>(q, lo, hi, tail) : tileReduce<__nv_bfloat16, OpSum>(q, lo, hi, tail);
 }
 
-// ---- staged path: fold one sub-tile of `len` bytes from the stage at
-// shared-memory byte offset `in` (inputs `sub` bytes apart) into the output
-// buffer at offset `o` (offsets into the kernel's dynamic shared memory, read
-// through the array itself so the loads are ordinary shared loads).  Unit
+// ---- staged path: fold one sub-tile from the stage at shared-memory byte
+// offset `in` (input q at in + q x stride) into the output buffer at offset
+// `o` (offsets into the kernel's dynamic shared memory, read through the
+// array itself so the loads are ordinary shared loads), `ulen` bytes.  Unit
 // u's chain starts at rank seg[i] + 1 for the first i with u < segEnd[i]
-// (thread 0 has cut the sub-tile into its ring segments); a unit's k inputs
-// are loaded before they are folded.
+// (thread 0 has cut the sub-tile into its ring segments; nseg == 0: look each
+// unit's segment up).  d != 0: every input piece starts d bytes into an
+// aligned unit of its window (ReduceScatter blocks that are not whole units)
+// and is cut out of two aligned units.
 constexpr int kMaxSegRuns = 4;
 
-template <class T, class Op>
-__device__ __noinline__ void foldStage(const ServeReq* q, unsigned in, unsigned sub, unsigned o, unsigned len,
-                                       unsigned long long off, const int* seg, const unsigned* segEnd, int nseg) {
+// a unit's ring segment looked up in the partition (out of line: the fold
+// needs it only for sub-tiles that hold many segments)
+__device__ __noinline__ int unitSegment(const ServeReq* q, unsigned long long e0, int esz,
+                                        unsigned long long* runEnd) {
+  return arSegment(viewOfReq(q), e0, esz, runEnd);
+}
+
+template <class T, class Op, bool kShift>
+__device__ __noinline__ void foldStage(const ServeReq* q, unsigned in, unsigned stride, unsigned o, unsigned ulen,
+                                       unsigned long long off, const int* seg, const unsigned* segEnd, int nseg,
+                                       unsigned d) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int k = q->nranks;
   unsigned long long runEnd = 0;   // nseg == 0: each unit's segment from the partition
   int s0 = 0;
-  for (unsigned u = threadIdx.x * 16u; u < len; u += blockDim.x * 16u) {
+  for (unsigned u = threadIdx.x * 16u; u < ulen; u += kTileConsumers * 16u) {
     int s;
     if (nseg > 0) {
       int i = 0;
@@ -117,41 +133,46 @@ __device__ __noinline__ void foldStage(const ServeReq* q, unsigned in, unsigned 
       s = seg[i];
     } else {
       const unsigned long long e0 = (off + u) / sizeof(T);
-      if (e0 >= runEnd) s0 = arSegment(viewOfReq(q), e0, (int)sizeof(T), &runEnd);
+      if (e0 >= runEnd) s0 = unitSegment(q, e0, (int)sizeof(T), &runEnd);
       s = s0;
     }
     int r = s + 1 < k ? s + 1 : 0;
-    uint4 x[kServeMaxRanks];
-#pragma unroll
-    for (int j = 0; j < kServeMaxRanks; j++) {
-      if (j < k) {
-        x[j] = *(const uint4*)(smem + in + (unsigned)r * sub + u);
-        if (++r == k) r = 0;
-      }
+    const unsigned char* base = smem + in + u;
+    auto piece = [&](int rr) {
+      const unsigned char* p = base + (unsigned)rr * stride;
+      if (kShift) return shiftBytes(*(const uint4*)p, *(const uint4*)(p + 16), d);
+      return *(const uint4*)p;
+    };
+    uint4 acc = piece(r);
+#pragma unroll 4
+    for (int j = 1; j < k; j++) {
+      if (++r == k) r = 0;
+      acc = combine<T, Op, uint4>(acc, piece(r));
     }
-    uint4 acc = x[0];
-#pragma unroll
-    for (int j = 1; j < kServeMaxRanks; j++)
-      if (j < k) acc = combine<T, Op, uint4>(acc, x[j]);
     *(uint4*)(smem + o + u) = acc;
   }
 }
 
-__device__ __noinline__ void copyStage(unsigned in, unsigned o, unsigned len) {
+__device__ __forceinline__ void copyStage(unsigned in, unsigned o, unsigned len) {
   extern __shared__ __align__(128) unsigned char smem[];
-  for (unsigned u = threadIdx.x * 16u; u < len; u += blockDim.x * 16u)
+  for (unsigned u = threadIdx.x * 16u; u < len; u += kTileConsumers * 16u)
     *(uint4*)(smem + o + u) = *(const uint4*)(smem + in + u);
 }
 
-VDEV void foldStageAny(const ServeReq* q, unsigned in, unsigned sub, unsigned o, unsigned len,
-                       unsigned long long off, const int* seg, const unsigned* segEnd, int nseg) {
-  if (q->coll == kAllGather) {   // a copy: the one input as it is
-    copyStage(in, o, len);
+VDEV bool copyColl(int coll) { return coll == kAllGather || coll == kBroadcast; }
+
+VDEV void foldStageAny(const ServeReq* q, unsigned in, unsigned stride, unsigned o, unsigned ulen,
+                       unsigned long long off, const int* seg, const unsigned* segEnd, int nseg, unsigned d) {
+  if (copyColl(q->coll)) {   // a copy: the one input as it is
+    copyStage(in, o, ulen);
     return;
   }
   const bool mx = q->redop == kMax;
-#define VC_FOLD(T) mx ? foldStage<T, OpMax>(q, in, sub, o, len, off, seg, segEnd, nseg) \
-                      : foldStage<T, OpSum>(q, in, sub, o, len, off, seg, segEnd, nseg)
+#define VC_FOLD(T)                                                                                  \
+  d ? (mx ? foldStage<T, OpMax, true>(q, in, stride, o, ulen, off, seg, segEnd, nseg, d)               \
+          : foldStage<T, OpSum, true>(q, in, stride, o, ulen, off, seg, segEnd, nseg, d))              \
+    : (mx ? foldStage<T, OpMax, false>(q, in, stride, o, ulen, off, seg, segEnd, nseg, d)              \
+          : foldStage<T, OpSum, false>(q, in, stride, o, ulen, off, seg, segEnd, nseg, d))
   if (q->dtype == kI32) VC_FOLD(int32_t);
   else if (q->dtype == kF32) VC_FOLD(float);
   else if (q->dtype == kF16) VC_FOLD(__half);
@@ -159,14 +180,15 @@ VDEV void foldStageAny(const ServeReq* q, unsigned in, unsigned sub, unsigned o,
 #undef VC_FOLD
 }
 
-// thread 0: the ring segments of a sub-tile (bytes [off, off + len) of block
+// producer: the ring segments of a sub-tile (bytes [off, off + len) of block
 // b): AllReduce segments from the partition (a segment is normally a chunk,
 // far longer than a sub-tile; 0 runs if the sub-tile holds more than
 // kMaxSegRuns, as the short segments of a small buffer's last loop do, and
-// the fold then looks each unit's segment up); ReduceScatter block b is one run
+// the fold then looks each unit's segment up); a ReduceScatter block b is one
+// run starting at rank b + 1, a Reduce one starting at root + 1
 VDEV int cutSegments(const ServeReq* q, int b, unsigned long long off, unsigned len, int* seg, unsigned* segEnd) {
   if (q->coll != kAllReduce) {
-    seg[0] = b;
+    seg[0] = q->coll == kReduce ? q->root : b;
     segEnd[0] = len;
     return 1;
   }
@@ -186,23 +208,47 @@ VDEV int cutSegments(const ServeReq* q, int b, unsigned long long off, unsigned 
   return n;
 }
 
-// the element tail of a staged AllReduce (count not a multiple of the units)
+// ---- the elements a staged op leaves to ordinary loads and stores, done
+// with its last tile: the element tail after the last full unit (AllReduce,
+// Reduce: of the buffer; ReduceScatter: of every block) and, for a
+// ReduceScatter of blocks that are not whole units, the last block's last
+// full unit (its window would reach past the end of the send buffers)
 template <class T, class Op>
 __device__ __noinline__ void tailReduce(const ServeReq* q) {
   const DirectView v = viewOfReq(q);
+  const int k = q->nranks;
   constexpr unsigned long long E = 16 / sizeof(T);
   const unsigned long long nunit = q->count / E;
-  const unsigned long long nt = q->count - nunit * E;
-  for (unsigned long long t = threadIdx.x; t < nt; t += blockDim.x) {
-    const unsigned long long i = nunit * E + t;
+  if (q->coll == kReduceScatter) {
+    for (int b = 0; b < k; b++) {
+      const unsigned long long from = (b == k - 1 && q->vec == 2 && nunit > 0) ? (nunit - 1) * E : nunit * E;
+      for (unsigned long long i = from + threadIdx.x; i < q->count; i += kTileConsumers) {
+        const T x = foldChain<T, Op, Unit1L2<T>>(v, b, ((unsigned long long)b * q->count + i) * sizeof(T));
+        *(T*)((char*)v.recv[b] + i * sizeof(T)) = x;
+      }
+    }
+    return;
+  }
+  for (unsigned long long i = nunit * E + threadIdx.x; i < q->count; i += kTileConsumers) {
     unsigned long long re;
-    const int s = arSegment(v, i, (int)sizeof(T), &re);
+    const int s = q->coll == kReduce ? q->root : arSegment(v, i, (int)sizeof(T), &re);
     const T x = foldChain<T, Op, Unit1L2<T>>(v, s, i * sizeof(T));
-    for (int r = 0; r < q->nranks; r++) *(T*)((char*)v.recv[r] + i * sizeof(T)) = x;
+    if (q->coll == kReduce) *(T*)((char*)v.recv[q->root] + i * sizeof(T)) = x;
+    else
+      for (int r = 0; r < k; r++) *(T*)((char*)v.recv[r] + i * sizeof(T)) = x;
   }
 }
 
 VDEV void tailAny(const ServeReq* q) {
+  if (q->coll == kBroadcast) {   // the bytes after the last full unit
+    const unsigned long long from = q->count / 16 * 16;
+    for (unsigned long long i = from + threadIdx.x; i < q->count; i += kTileConsumers) {
+      const uint8_t c = Unit1L2<uint8_t>::load((const char*)q->send[q->root] + i);
+      for (int r = 0; r < q->nranks; r++)
+        if (!(r == q->root && ((q->inplaceMask >> r) & 1ull))) ((uint8_t*)q->recv[r])[i] = c;
+    }
+    return;
+  }
   const bool mx = q->redop == kMax;
   if (q->dtype == kI32) mx ? tailReduce<int32_t, OpMax>(q) : tailReduce<int32_t, OpSum>(q);
   else if (q->dtype == kF32) mx ? tailReduce<float, OpMax>(q) : tailReduce<float, OpSum>(q);
@@ -211,7 +257,9 @@ VDEV void tailAny(const ServeReq* q) {
 }
 
 VDEV bool hasTail(const ServeReq* q) {
-  if (q->coll != kAllReduce) return false;
+  if (q->coll == kAllGather) return false;            // whole units (staged AllGather blocks)
+  if (q->coll == kBroadcast) return q->count % 16 != 0;
+  if (q->coll == kReduceScatter && q->vec == 2) return true;
   const unsigned long long E = (q->dtype == kF16 || q->dtype == kBF16) ? 8 : 4;
   return q->count % E != 0;
 }
@@ -282,7 +330,8 @@ __device__ void ingest(const TileArgs& a) {
   }
 }
 
-// ---- where tiles come from.  The engine below calls a source from thread 0:
+// ---- where tiles come from.  The engine below calls a source from lane 0
+// of its producer warp:
 //   claim(&tile)        the next tile: an op id (>= 0) and its tile index; -1: none now
 //   loadReq(id, dst)    the op's description, into shared memory
 //   geom(id, tile, &w)  the tile's work: a byte range of one block (staged),
@@ -315,6 +364,7 @@ VDEV void registerGeom(unsigned long long tile, unsigned long long tileUnits, un
 
 // the serving queues (small requests first), claimed with atomics
 struct ServeSource {
+  static constexpr bool kReportsDone = true;
   const TileArgs& a;
   VDEV long long claim(unsigned long long* tile) {
     TileQueues* q = a.q;
@@ -375,6 +425,7 @@ struct ServeSource {
 
 // a group's ops, tiles assigned statically: CTA j takes j, j + grid, ...
 struct BatchSource {
+  static constexpr bool kReportsDone = false;   // the launch's end is the group's completion
   const TileBatchArgs& b;
   unsigned long long next;
   VDEV long long claim(unsigned long long* tile) {
@@ -429,9 +480,9 @@ struct BatchSource {
   }
 };
 
-// What a stage slot holds.  Every slot the engine waits on carries one of
-// these, and its mbarrier completes for each: data by the bulk loads' bytes,
-// the others by a plain arrive of thread 0.
+// What a stage slot holds.  Every slot the consumers wait on carries one of
+// these, and its `full` mbarrier completes for each: data by the bulk loads'
+// bytes, the others by a plain arrive of the producer.
 enum { kStageData = 0, kStageReg = 1, kStageIdle = 2, kStageStop = 3 };
 
 struct StageInfo {
@@ -440,7 +491,10 @@ struct StageInfo {
   int endOfTile;            // data: the tile's last sub-tile
   int tail;                 // data: the op's last tile, with an element tail
   unsigned len;             // data: bytes (a multiple of 16)
-  unsigned sub;             // data: bytes per input in the stage
+  unsigned ulen;            // data: bytes folded and stored (len, or len - 16: the last
+                            // unit of a shifted op's last sub-tile goes with the tail)
+  unsigned stride;          // data: bytes per input in the stage
+  unsigned d;               // data: shifted inputs start d bytes into their window
   unsigned long long off;   // data: byte offset in the block
   int nseg;                 // data: ring segment runs of the sub-tile
   int seg[kMaxSegRuns];
@@ -453,232 +507,408 @@ constexpr int kMaxPendingDone = kDoneLag + 4;
 VDEV void mbarArrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smemU32(bar)) : "memory");
 }
+// every committed bulk group has finished reading its shared memory
+VDEV void bulkWaitRead0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 
-// ---- the tile engine: take tiles from `src` until it has none and never
-// will; every thread of the CTA calls it.
-//
-// The stage slots form a ring of kTileStages; sequence index j uses slot
-// j mod kTileStages and its mbarrier's phase j / kTileStages.  Thread 0 (the
-// producer) fills index j + kTileStages as soon as index j has been folded:
-// with the next sub-tile of its current tile (bulk loads), claiming a new
-// tile when the current one is done; with a register tile (an unaligned op);
-// or, with nothing to claim, with an idle mark (persistent kernel) or the
-// stop mark.  Every thread (thread 0 too) folds the indices in order: a data
-// stage costs three barriers, and thread 0 refills after the third while the
-// others already wait for the next index.
-template <class Src>
-__device__ void tileEngine(Src& src, unsigned stageBytes, unsigned long long copyTimeoutNs, bool persistent) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ ServeReq sReq[kTileStages];   // the op of each stage
-  __shared__ ServeReq sCur;                // the op being issued (thread 0)
-  __shared__ StageInfo sInfo[kTileStages];
-  unsigned char* in = smem;
-  unsigned char* out = smem + (size_t)kTileStages * stageBytes;
-  uint64_t* bar = (uint64_t*)(out + 2 * (size_t)kTileOutBytes);
-
-  // thread 0's producer state
-  unsigned long long filled = 0;               // sequence indices filled so far
-  long long curId = -1;
-  unsigned long long curOff = 0, curEnd = 0;
-  unsigned curSub = 0;
-  int curB = 0, curTail = 0;
-  unsigned curGen = 0, stageGen[kTileStages];   // which claim each stage's op copy is of
-  for (int i = 0; i < kTileStages; i++) stageGen[i] = ~0u;
-  long long doneId[kMaxPendingDone];
+// The producer's state (kept in shared memory: the thread's local memory
+// mostly lives in L2 when shared memory takes the SM's on-chip storage).
+struct Producer {
+  unsigned long long filled;                  // sequence indices filled so far
+  unsigned long long groups;                  // store groups committed (data stages retired)
+  long long curId;                            // the tile being issued (-1: none)
+  unsigned long long curOff, curEnd;
+  unsigned curSub, curStride, curD, curGen;
+  int curB, curTail;
+  unsigned stageGen[kTileStages];             // which claim each stage's op copy is of
+  long long doneId[kMaxPendingDone];          // finished tiles, completion unconfirmed
   unsigned long long doneGroup[kMaxPendingDone];
-  int ndone = 0;
-  unsigned idleNs = 64;
-  bool stopped = false;
+  int ndone;
+  unsigned idleNs;
+  int stopped;
+};
 
-  // thread 0: every pending tile completion, once all store groups are done
-  auto flushDone = [&]() {
-    bulkWaitAll();
-    for (int i = 0; i < ndone; i++) src.done(doneId[i]);
-    ndone = 0;
-  };
-  // thread 0: fill sequence index `filled` (its slot has been folded)
-  auto fill = [&]() {
-    const int stg = (int)(filled % kTileStages);
-    StageInfo& si = sInfo[stg];
-    if (stopped) return;   // the stop mark is the last index filled
-    if (curId < 0) {
-      unsigned long long tl = 0;
-      const long long id = src.claim(&tl);
-      if (id < 0) {
-        flushDone();
+struct EngineSmem {
+  ServeReq sReq[kTileStages];   // the op of each stage
+  ServeReq sCur;                // the op being issued
+  StageInfo sInfo[kTileStages];
+  Producer p;
+  uint64_t full[kTileStages];   // a slot is filled (producer / bulk loads)
+  uint64_t empty[kTileStages];  // a slot is consumed (one arrive per consumer warp)
+  uint64_t outFree[kTileOutBufs];   // an output buffer's store group has read it
+  int abort;                    // a wait ran out: everyone leaves
+};
+
+VDEV bool aborted(const EngineSmem& e) { return *(const volatile int*)&e.abort != 0; }
+VDEV void setAbort(EngineSmem& e) { *(volatile int*)&e.abort = 1; }
+
+// wait for phase `parity` of *bar; false once the engine aborts or after timeoutNs
+VDEV bool engineWait(uint64_t* bar, unsigned parity, unsigned long long timeoutNs, const EngineSmem& e) {
+  if (mbarTryWait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  while (true) {
+    if (mbarTryWait(bar, parity)) return true;
+    if (aborted(e) || globaltimer() - t0 > timeoutNs) return false;
+  }
+}
+
+// The producer is one warp.  Lane 0 makes every decision (claims, the
+// slots' contents, completions) in shared memory; the bulk copies of a slot
+// are spread over the lanes, lane q taking ranks q, q + 32, ... (a bulk
+// group belongs to the thread that commits it, so every lane commits one
+// group per data stage, and waits for its own).
+constexpr unsigned kFullMask = 0xffffffffu;
+
+// producer warp: every store group has completed; lane 0 reports the
+// pending tiles
+template <class Src>
+VDEV void flushDone(Src& src, Producer& p, int lane) {
+  bulkWaitAll();
+  fenceProxyGlobal();   // this lane's completed bulk writes, before the reports
+  __syncwarp();
+  if (lane == 0) {
+    for (int i = 0; i < p.ndone; i++) src.done(p.doneId[i]);
+    p.ndone = 0;
+  }
+  __syncwarp();
+}
+
+// producer warp: fill sequence index p.filled (its slot has been consumed)
+template <class Src>
+__device__ __noinline__ void fillStage(Src& src, EngineSmem& e, unsigned char* in, unsigned stageBytes,
+                                       bool persistent, int lane) {
+  Producer& p = e.p;
+  if (p.stopped) return;   // the stop mark is the last index filled
+  const int stg = (int)(p.filled % kTileStages);
+  StageInfo& si = e.sInfo[stg];
+  uint64_t* bar = &e.full[stg];
+  if (p.curId < 0) {
+    unsigned long long tl = 0;
+    long long id = -1;
+    if (lane == 0) id = src.claim(&tl);
+    id = (long long)__shfl_sync(kFullMask, (unsigned long long)id, 0);
+    if (id < 0) {
+      flushDone(src, p, lane);
+      if (lane == 0) {
         if (src.finished()) {
           si.kind = kStageStop;
-          stopped = true;
+          p.stopped = 1;
         } else {
           si.kind = kStageIdle;
           if (persistent) {
-            __nanosleep(idleNs);
-            idleNs = idleNs < 4096 ? 2 * idleNs : 4096;
+            __nanosleep(p.idleNs);
+            p.idleNs = p.idleNs < 4096 ? 2 * p.idleNs : 4096;
           }
         }
-        mbarArrive(&bar[stg]);
-        filled++;
-        return;
+        mbarArrive(bar);
+        p.filled++;
       }
-      idleNs = 64;
+      __syncwarp();
+      return;
+    }
+    int staged = 0;
+    if (lane == 0) {
+      p.idleNs = 64;
       TileWork w;
       src.geom(id, tl, &w);
+      staged = w.staged;
       if (!w.staged) {
         si.kind = kStageReg;
         si.id = (int)id;
         si.reg = w;
-        src.loadReq(id, &sReq[stg]);   // the slot's own op copy
-        stageGen[stg] = ~0u;
-        mbarArrive(&bar[stg]);
-        filled++;
-        return;
+        src.loadReq(id, &e.sReq[stg]);   // the slot's own op copy
+        p.stageGen[stg] = ~0u;
+        mbarArrive(bar);
+        p.filled++;
+      } else {
+        src.loadReq(id, &e.sCur);
+        p.curId = id;
+        p.curGen++;
+        p.curB = w.b;
+        p.curOff = w.off;
+        p.curEnd = w.end;
+        p.curTail = w.tail && hasTail(&e.sCur);
+        const ServeReq& r = e.sCur;
+        const unsigned nIn = copyColl(r.coll) ? 1u : (unsigned)r.nranks;
+        const unsigned pad = r.vec == 2 ? 16u : 0u;   // a shifted window is one unit longer
+        unsigned sub = stageBytes / nIn - pad;
+        sub = sub < kTileOutBytes ? sub : kTileOutBytes;
+        sub &= ~127u;
+        // sub-tiles of about equal size, whole 128-byte lines (bulk copies
+        // of aligned lines)
+        const unsigned long long tb = w.end - w.off;
+        const unsigned long long m = (tb + sub - 1) / sub;
+        const unsigned long long even = ((tb + m - 1) / m + 127) / 128 * 128;
+        p.curSub = (unsigned)(even < sub ? even : sub);
+        p.curStride = p.curSub + pad;
+        const unsigned long long esz = (r.dtype == kF16 || r.dtype == kBF16) ? 2 : 4;
+        p.curD = r.vec == 2 ? (unsigned)(((unsigned long long)w.b * r.count * esz) & 15ull) : 0u;
       }
-      src.loadReq(id, &sCur);
-      curId = id;
-      curGen++;
-      curB = w.b;
-      curOff = w.off;
-      curEnd = w.end;
-      curTail = w.tail && hasTail(&sCur);
-      const unsigned nIn = sCur.coll == kAllGather ? 1u : (unsigned)sCur.nranks;
-      unsigned sub = stageBytes / nIn;
-      sub = sub < kTileOutBytes ? sub : kTileOutBytes;
-      curSub = sub & ~127u;
     }
-    const unsigned len = (unsigned)(curEnd - curOff < curSub ? curEnd - curOff : curSub);
-    si.kind = kStageData;
-    si.off = curOff;
-    si.len = len;
-    si.sub = curSub;
-    si.id = (int)curId;
-    si.b = curB;
-    si.endOfTile = (curOff + len >= curEnd) ? 1 : 0;
-    si.tail = si.endOfTile && curTail;
-    si.nseg = cutSegments(&sCur, curB, curOff, len, si.seg, si.segEnd);
-    if (stageGen[stg] != curGen) {   // the stage holds another claim's op
-      sReq[stg] = sCur;
-      stageGen[stg] = curGen;
+    staged = __shfl_sync(kFullMask, staged, 0);
+    if (!staged) {
+      __syncwarp();
+      return;
     }
-    const ServeReq& r = sCur;
-    unsigned char* dst = in + (size_t)stg * stageBytes;
-    if (r.coll == kAllGather) {
-      mbarExpect(&bar[stg], len);
-      bulkLoad(dst, (const char*)r.send[curB] + curOff, len, &bar[stg]);
-    } else {
-      const unsigned long long esz = (r.dtype == kF16 || r.dtype == kBF16) ? 2 : 4;
-      const unsigned long long from =
-          (r.coll == kReduceScatter ? (unsigned long long)curB * r.count * esz : 0ull) + curOff;
-      mbarExpect(&bar[stg], len * (unsigned)r.nranks);
-      for (int q = 0; q < r.nranks; q++)
-        bulkLoad(dst + (size_t)q * curSub, (const char*)r.send[q] + from, len, &bar[stg]);
-    }
-    filled++;
-    curOff += len;
-    if (curOff >= curEnd) curId = -1;
-  };
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < kTileStages; s++) mbarInit(&bar[s], 1);
-    fenceBarrierInit();
-    for (int s = 0; s < kTileStages; s++) fill();
   }
-  __syncthreads();
+  const ServeReq& r = e.sCur;
+  unsigned wlen = 0;
+  if (lane == 0) {
+    const unsigned long long off = p.curOff;
+    const unsigned len = (unsigned)(p.curEnd - off < p.curSub ? p.curEnd - off : p.curSub);
+    si.kind = kStageData;
+    si.off = off;
+    si.len = len;
+    si.stride = p.curStride;
+    si.d = p.curD;
+    si.id = (int)p.curId;
+    si.b = p.curB;
+    si.endOfTile = (off + len >= p.curEnd) ? 1 : 0;
+    si.tail = si.endOfTile && p.curTail;
+    // a shifted op's very last unit: its window would reach past the end of
+    // the send buffers; the tail folds it with element loads
+    const bool skipLast = r.vec == 2 && si.tail;
+    si.ulen = skipLast ? len - 16 : len;
+    si.nseg = cutSegments(&r, si.b, off, len, si.seg, si.segEnd);
+    if (p.stageGen[stg] != p.curGen) {   // the stage holds another claim's op
+      e.sReq[stg] = r;
+      p.stageGen[stg] = p.curGen;
+    }
+    wlen = (si.d != 0 && !skipLast) ? len + 16 : len;
+    mbarExpect(bar, copyColl(r.coll) ? len : wlen * (unsigned)r.nranks);
+  }
+  wlen = __shfl_sync(kFullMask, wlen, 0);
+  __syncwarp();   // si and sCur as lane 0 wrote them
+  unsigned char* dst = in + (size_t)stg * stageBytes;
+  const unsigned long long off = si.off;
+  if (copyColl(r.coll)) {   // AllGather: block b of rank b; Broadcast: the root's buffer
+    if (lane == 0) bulkLoad(dst, (const char*)r.send[r.coll == kAllGather ? si.b : r.root] + off, si.len, bar);
+  } else {
+    const unsigned long long esz = (r.dtype == kF16 || r.dtype == kBF16) ? 2 : 4;
+    const unsigned long long from =
+        (r.coll == kReduceScatter ? (unsigned long long)si.b * r.count * esz : 0ull) + off - si.d;
+    for (int q = lane; q < r.nranks; q += 32)
+      bulkLoad(dst + (size_t)q * si.stride, (const char*)r.send[q] + from, wlen, bar);
+  }
+  __syncwarp();   // every lane has read sCur and si
+  if (lane == 0) {
+    p.filled++;
+    p.curOff = off + si.len;
+    if (p.curOff >= p.curEnd) p.curId = -1;
+  }
+  __syncwarp();
+}
 
-  // dsn: data stages folded so far (every thread counts them alike): the
-  // output buffer and the store group of a data stage go by it
-  unsigned long long dsn = 0;
-  for (unsigned long long j = 0;; j++) {
-    const int stg = (int)(j % kTileStages);
-    const bool ok = stageWait(&bar[stg], (unsigned)((j / kTileStages) & 1ull), copyTimeoutNs);
-    if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) {
-        // loads still in flight must land before the CTA's shared memory is released
-        for (unsigned long long q = j; q < filled; q++)
-          (void)stageWait(&bar[q % kTileStages], (unsigned)((q / kTileStages) & 1ull), copyTimeoutNs);
-        bulkWaitAll();
-        src.fail();
+// producer warp: sequence index i has been consumed; a data stage's output
+// buffer goes to its outputs as store group n = p.groups (returned; -1 for
+// the other kinds of slot)
+template <class Src>
+__device__ __noinline__ long long retire(Src& src, EngineSmem& e, unsigned char* out, unsigned long long i,
+                                         unsigned long long timeoutNs, int lane, bool* ok) {
+  Producer& p = e.p;
+  const int stg = (int)(i % kTileStages);
+  const bool got = engineWait(&e.empty[stg], (unsigned)((i / kTileStages) & 1ull), timeoutNs, e);
+  *ok = __all_sync(kFullMask, got);
+  if (!*ok) return -1;
+  const StageInfo& si = e.sInfo[stg];
+  if (si.kind == kStageReg) {   // the consumers fenced their stores before arriving
+    if (lane == 0) src.done(si.id);
+    __syncwarp();
+    return -1;
+  }
+  if (si.kind != kStageData) return -1;
+  const unsigned long long n = p.groups;
+  const ServeReq* r = &e.sReq[stg];
+  unsigned char* o = out + (size_t)(n % kTileOutBufs) * kTileOutBytes;
+  if (si.ulen > 0) {
+    const int c = r->coll;
+    if (c == kReduceScatter || c == kReduce) {
+      if (lane == 0) bulkStore((char*)r->recv[c == kReduce ? r->root : si.b] + si.off, o, si.ulen);
+    } else {
+      // AllReduce: every rank; AllGather: block b of every rank; Broadcast:
+      // every rank (a rank whose output is its input in place is skipped)
+      const int self = c == kAllGather ? si.b : (c == kBroadcast ? r->root : -1);
+      const unsigned long long dst = (c == kAllGather ? (unsigned long long)si.b * r->count : 0ull) + si.off;
+      for (int q = lane; q < r->nranks; q += 32) {
+        if (q == self && ((r->inplaceMask >> q) & 1ull)) continue;
+        bulkStore((char*)r->recv[q] + dst, o, si.ulen);
       }
-      return;
     }
-    const int kind = sInfo[stg].kind;
-    if (kind == kStageStop) {
-      // the data stages before the mark have committed their stores since
-      // it was filled: wait for them and report their tiles
-      if (threadIdx.x == 0) flushDone();
-      return;
+  }
+  bulkCommit();
+  __syncwarp();
+  if (lane == 0) {
+    p.groups = n + 1;
+    if (Src::kReportsDone && si.endOfTile) {
+      p.doneId[p.ndone] = si.id;
+      p.doneGroup[p.ndone] = n;
+      p.ndone++;
     }
-    if (kind == kStageIdle) {
-      __syncthreads();                // everyone has read the mark
-      if (threadIdx.x == 0) fill();
-      continue;
-    }
-    if (kind == kStageReg) {
-      // a tile of an unaligned op: the register kernels' paths
-      const TileWork w = sInfo[stg].reg;
-      const int id = sInfo[stg].id;
-      runTile(&sReq[stg], w.lo, w.hi, w.tail != 0);
-      __threadfence();
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        src.done(id);
-        fill();
-      }
-      continue;
-    }
-    // a data stage
-    const int ob = (int)(dsn & 1ull);
-    if (threadIdx.x == 0) {
-      // out[ob] was last read by the store group of data stage dsn - 2,
-      // which has read it once at most one group is pending; the tiles
-      // whose last group is older than the newest kDoneLag are done
-      bulkWaitRead1();
-      bulkWaitDoneLag();
+  }
+  __syncwarp();
+  return (long long)n;
+}
+
+// producer warp, after store group n was committed: once group
+// n + 1 - kTileOutBufs has read its buffer the consumers may write it again;
+// the tiles whose last group is older than the newest kDoneLag are reported
+template <class Src>
+__device__ __noinline__ void release(Src& src, EngineSmem& e, unsigned long long n, int lane) {
+  Producer& p = e.p;
+  // every group but the newest kTileOutBufs - 1 has read its buffer
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(kTileOutBufs - 1) : "memory");
+  __syncwarp();
+  if (lane == 0 && n + 1 >= (unsigned long long)kTileOutBufs)
+    mbarArrive(&e.outFree[(n + 1 - kTileOutBufs) % kTileOutBufs]);
+  if (Src::kReportsDone) {
+    bulkWaitDoneLag();
+    fenceProxyGlobal();
+    __syncwarp();
+    if (lane == 0) {
       int keep = 0;
-      for (int i = 0; i < ndone; i++) {
-        if (doneGroup[i] + kDoneLag + 1 <= dsn) {
-          src.done(doneId[i]);
+      for (int j = 0; j < p.ndone; j++) {
+        if (p.doneGroup[j] + kDoneLag <= n) {
+          src.done(p.doneId[j]);
         } else {
-          doneId[keep] = doneId[i];
-          doneGroup[keep] = doneGroup[i];
+          p.doneId[keep] = p.doneId[j];
+          p.doneGroup[keep] = p.doneGroup[j];
           keep++;
         }
       }
-      ndone = keep;
+      p.ndone = keep;
     }
-    __syncthreads();
-    const StageInfo si = sInfo[stg];
-    const ServeReq* r = &sReq[stg];
-    unsigned char* o = out + (size_t)ob * kTileOutBytes;
-    foldStageAny(r, (unsigned)((size_t)stg * stageBytes), si.sub, (unsigned)(o - smem), si.len, si.off,
-                 si.seg, si.segEnd, si.nseg);
-    fenceProxyAsync();
-    __syncthreads();   // o written; the stage read by every thread
-    if (si.tail) {     // the element tail, with ordinary loads and stores
-      tailAny(r);
-      __threadfence();
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-      if (r->coll == kReduceScatter) {
-        bulkStore((char*)r->recv[si.b] + si.off, o, si.len);
-      } else {
-        const bool ag = r->coll == kAllGather;
-        const unsigned long long dst = (ag ? (unsigned long long)si.b * r->count : 0ull) + si.off;
-        for (int q = 0; q < r->nranks; q++) {
-          if (ag && q == si.b && ((r->inplaceMask >> q) & 1ull)) continue;   // its own block, in place
-          bulkStore((char*)r->recv[q] + dst, o, si.len);
-        }
-      }
-      bulkCommit();
-      if (si.endOfTile) {
-        doneId[ndone] = si.id;
-        doneGroup[ndone] = dsn;
-        ndone++;
-      }
-      fill();   // refill this slot: index j + kTileStages
-    }
-    dsn++;
   }
+  __syncwarp();
+}
+
+// ---- the producer warp: fill the slots ahead of the consumers, retire each
+// slot once consumed, until the stop mark; then retire the rest and report
+// the last completions.  A wait that runs out (a bulk load that never lands,
+// consumers that left) aborts the engine: the loads still in flight land
+// before the warp leaves, and the source records the failure.
+template <class Src>
+__device__ __noinline__ void produce(Src& src, EngineSmem& e, unsigned char* in, unsigned char* out,
+                                     unsigned stageBytes, unsigned long long timeoutNs, bool persistent) {
+  const int lane = threadIdx.x & 31;
+  Producer& p = e.p;
+  if (lane == 0) {
+    p.filled = p.groups = 0;
+    p.curId = -1;
+    p.curOff = p.curEnd = 0;
+    p.curSub = p.curStride = p.curD = p.curGen = 0;
+    p.curB = p.curTail = 0;
+    for (int i = 0; i < kTileStages; i++) p.stageGen[i] = ~0u;
+    p.ndone = 0;
+    p.idleNs = 64;
+    p.stopped = 0;
+  }
+  __syncwarp();
+  unsigned long long retired = 0;
+  bool ok = true;
+  while (!p.stopped) {
+    long long n = -1;
+    if (p.filled - retired == (unsigned long long)kTileStages) {
+      n = retire(src, e, out, retired, timeoutNs, lane, &ok);
+      if (!ok) break;
+      retired++;
+    }
+    // the output buffer first: consumers may be waiting for it
+    if (n >= 0) release(src, e, (unsigned long long)n, lane);
+    fillStage(src, e, in, stageBytes, persistent, lane);
+  }
+  while (ok && retired + 1 < p.filled) {   // every index before the stop mark
+    const long long n = retire(src, e, out, retired, timeoutNs, lane, &ok);
+    if (!ok) break;
+    retired++;
+    if (n >= 0) release(src, e, (unsigned long long)n, lane);
+  }
+  if (ok) {
+    flushDone(src, p, lane);
+    return;
+  }
+  if (lane == 0) {
+    setAbort(e);
+    for (unsigned long long q = retired; q < p.filled; q++)
+      if (e.sInfo[q % kTileStages].kind == kStageData)
+        (void)stageWait(&e.full[q % kTileStages], (unsigned)((q / kTileStages) & 1ull), timeoutNs);
+  }
+  bulkWaitAll();
+  __syncwarp();
+  if (lane == 0) src.fail();
+}
+
+// ---- the consumers (warps 0 .. kConsumerWarps - 1): every sequence index in
+// order.  A data stage folds into output buffer dsn mod kTileOutBufs (once
+// the buffer's previous store group has read it); the op's last sub-tile also does
+// the element tail with ordinary loads and stores.  Each warp arrives on the
+// slot's `empty` barrier when done with it.
+__device__ __noinline__ void consume(EngineSmem& e, unsigned char* out, unsigned stageBytes, unsigned long long timeoutNs) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int lane = threadIdx.x & 31;
+  unsigned long long dsn = 0;
+  for (unsigned long long j = 0;; j++) {
+    const int stg = (int)(j % kTileStages);
+    if (!engineWait(&e.full[stg], (unsigned)((j / kTileStages) & 1ull), timeoutNs, e)) {
+      setAbort(e);
+      return;
+    }
+    const StageInfo& si = e.sInfo[stg];
+    const int kind = si.kind;
+    if (kind == kStageStop) return;
+    if (kind == kStageReg) {   // a tile the staged path does not take
+      runTile(&e.sReq[stg], si.reg.lo, si.reg.hi, si.reg.tail != 0);
+      __threadfence();
+    } else if (kind == kStageData) {
+      const unsigned long long n = dsn++;
+      const int ob = (int)(n % kTileOutBufs);
+      // the buffer's previous store group (data stage n - kTileOutBufs) has read it
+      if (n >= (unsigned long long)kTileOutBufs &&
+          !engineWait(&e.outFree[ob], (unsigned)((n / kTileOutBufs - 1) & 1ull), timeoutNs, e)) {
+        setAbort(e);
+        return;
+      }
+      const ServeReq* r = &e.sReq[stg];
+      unsigned char* o = out + (size_t)ob * kTileOutBytes;
+      foldStageAny(r, (unsigned)((size_t)stg * stageBytes), si.stride, (unsigned)(o - smem), si.ulen, si.off,
+                   si.seg, si.segEnd, si.nseg, si.d);
+      if (si.tail) {   // the element tail, with ordinary loads and stores
+        tailAny(r);
+        __threadfence();
+      }
+      fenceProxyAsync();   // this thread's output writes, before the bulk stores read them
+    }
+    __syncwarp();
+    if (lane == 0) mbarArrive(&e.empty[stg]);
+  }
+}
+
+// ---- the tile engine: take tiles from `src` until it has none and never
+// will.  The stage slots form a ring of kTileStages; sequence index j uses
+// slot j mod kTileStages and its barriers' phase j / kTileStages.  The
+// producer warp runs ahead of the consumer warps by up to
+// kTileStages indices, so bulk loads stay in flight while the consumers
+// fold and the producer's own work (claims, stores, completions) overlaps
+// theirs.
+template <class Src>
+__device__ void tileEngine(Src& src, unsigned stageBytes, unsigned long long copyTimeoutNs, bool persistent) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ EngineSmem e;
+  unsigned char* in = smem;
+  unsigned char* out = smem + (size_t)kTileStages * stageBytes;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kTileStages; i++) {
+      mbarInit(&e.full[i], 1);
+      mbarInit(&e.empty[i], kConsumerWarps);
+    }
+    for (int i = 0; i < kTileOutBufs; i++) mbarInit(&e.outFree[i], 1);
+    e.abort = 0;
+    fenceBarrierInit();
+  }
+  __syncthreads();
+  if (threadIdx.x >= kTileConsumers) {
+    produce(src, e, in, out, stageBytes, copyTimeoutNs, persistent);
+    return;
+  }
+  consume(e, out, stageBytes, copyTimeoutNs);
 }
 
 __global__ void __launch_bounds__(kTileThreads, 1) kServeTiles(const __grid_constant__ TileArgs a) {
@@ -701,11 +931,11 @@ __global__ void __launch_bounds__(kTileThreads, 1) kBatchTiles(const __grid_cons
 const void* serveTilesKernel() { return (const void*)kServeTiles; }
 const void* batchTilesKernel() { return (const void*)kBatchTiles; }
 int serveTilesThreads() { return kTileThreads; }
-int serveTilesUnitsPerIter() { return kTileThreads * kTileNU; }
+int serveTilesUnitsPerIter() { return kTileConsumers; }
 int serveTilesStages() { return kTileStages; }
 unsigned serveTilesOutBytes() { return kTileOutBytes; }
 size_t serveTilesSmem(unsigned stageBytes) {
-  return (size_t)kTileStages * stageBytes + 2 * (size_t)kTileOutBytes + 8 * (size_t)kTileStages;
+  return (size_t)kTileStages * stageBytes + (size_t)kTileOutBufs * kTileOutBytes;
 }
 
 }  // namespace vc

@@ -69,7 +69,8 @@ def test_all_gather_shifted(k, n, dtype):
 
 def test_group_of_shifted_calls():
     """ReduceScatter and AllGather calls with whole and partial units in one
-    group (one launch per (dtype, op) class and one for the copies)."""
+    group (one launch of the tile engine: staged windows for the shifted
+    ReduceScatter blocks, the register path for the shifted AllGather)."""
     k = 6
     c = Comm(k, 4, slot_bytes=SMALL_SLOTS, timeout_sec=10.0)
     c.set_plan(nchannels=4, chunk_steps=1)

@@ -1,7 +1,8 @@
 """Group calls of direct-protocol collectives as ONE launch of the tile engine
 (kBatchTiles): every call's tiles laid end to end, CTA j taking tiles j,
-j + grid, ...; aligned AllReduce / ReduceScatter / AllGather tiles move by
-bulk copies through shared memory, the rest take the register kernels' paths.
+j + grid, ...; tiles of 16-byte aligned buffers (and ReduceScatter blocks that
+are not whole 16-byte units, through shifted windows) move by bulk copies
+through shared memory, the rest take the register kernels' paths.
 
 Each result must equal the oracle's for its reported plan and the bits of the
 same group launched the older way (one register kernel per (dtype, op) class,
