@@ -255,12 +255,14 @@ struct TileOpDesc {
   int coll, dtype, redop, nranks, nsub, root, vec, ptrBase;
 };
 // The tiles of one direct-protocol op (host side, serving and groups).
-// Staged (16-byte aligned buffers; ReduceScatter blocks that are not whole
-// 16-byte units too): byte ranges of a block, whole 4 KiB pieces.  Otherwise
-// ranges of the register kernels' units, whole iterations (`iter` units) of
-// a CTA.  About two tiles per worker CTA (`workers`), and at most ~4 MiB of
-// traffic per tile so that small work never waits long for a free CTA.
+// Staged (16-byte aligned buffers; ReduceScatter / AllGather blocks that are
+// not whole 16-byte units too): byte ranges of a block, whole 4 KiB pieces.
+// Otherwise ranges of the register kernels' units, whole iterations (`iter` units) of
+// a CTA.  About two tiles per worker CTA (`workers`), and at most
+// kTileMaxTraffic bytes of traffic per tile (about 120 us of one SM's share
+// of HBM) so that small work never waits long for a free CTA.
 // count: elements, or bytes for AllGather / Broadcast; vec as DirectArgs::vec.
+constexpr unsigned long long kTileMaxTraffic = 4ull << 20;
 struct TileGeometry {
   unsigned long long staged, units, tileUnits, blockBytes, tileBytes, perBlock, ntiles;
   int vec;   // the op's DirectArgs::vec in the engine (register reductions: 0)
@@ -275,14 +277,17 @@ inline TileGeometry tileGeometry(int coll, int k, unsigned long long count, int 
   const unsigned long long factor = coll == kAllReduce ? 2ull * k : (unsigned long long)k + 1;
   const unsigned long long twoW = 2ull * (workers > 0 ? workers : 1);
   const unsigned long long Ev = 16 / unitBytes;   // elements (bytes) per 16-byte unit
-  // staged: aligned buffers of any collective, and ReduceScatter blocks that
-  // are not whole units (shifted windows); a block of at least one full unit
-  const bool stageable = vec == 1 || (vec == 2 && coll == kReduceScatter);
-  g.blockBytes = stageable ? (count / Ev) * 16 : 0;
+  // staged: aligned buffers of any collective, and ReduceScatter / AllGather
+  // blocks that are not whole units (shifted windows: a ReduceScatter block's
+  // full units; an AllGather block's aligned destination units but the last,
+  // its edge bytes going with the tail)
+  const bool stageable = vec == 1 || vec == 2;
+  g.blockBytes = !stageable ? 0 : (vec == 2 && coll == kAllGather) ? (count >= 32 ? count / 16 * 16 - 16 : 0)
+                                                                    : (count / Ev) * 16;
   g.staged = (stageable && g.blockBytes >= (vec == 2 ? 32u : 16u)) ? 1 : 0;
   if (g.staged) {
     const unsigned long long piece = 4096;
-    const unsigned long long maxTile = std::max<unsigned long long>(piece, (4ull << 20) / factor / piece * piece);
+    const unsigned long long maxTile = std::max<unsigned long long>(piece, kTileMaxTraffic / factor / piece * piece);
     unsigned long long tb = (blocks * g.blockBytes + twoW - 1) / twoW;
     tb = std::min(std::max(tb, piece), maxTile);
     tb = (tb + piece - 1) / piece * piece;
@@ -296,7 +301,7 @@ inline TileGeometry tileGeometry(int coll, int k, unsigned long long count, int 
     const unsigned long long E = g.vec ? Ev : 1;
     g.units = (g.vec == 2 && copy) ? count * blocks / 16 : (count / E) * blocks;
     const unsigned long long unitTraffic = E * unitBytes * factor;
-    const unsigned long long maxTile = std::max<unsigned long long>(iter, (4ull << 20) / unitTraffic / iter * iter);
+    const unsigned long long maxTile = std::max<unsigned long long>(iter, kTileMaxTraffic / unitTraffic / iter * iter);
     unsigned long long tu = (g.units + twoW - 1) / twoW;
     tu = std::min(std::max(tu, iter), maxTile);
     tu = (tu + iter - 1) / iter * iter;

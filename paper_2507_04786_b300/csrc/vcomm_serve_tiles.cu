@@ -27,9 +27,11 @@
 // aligned ones.  Requests that are not 16-byte aligned take the register
 // kernels' element-wise path, one tile at a time.
 //
-// No CTA waits on another: claims and completions are atomics, and the only
-// waits are the idle polls (bounded by the idle timeout and the stop word)
-// and the waits for this CTA's own bulk copies (bounded by copyTimeoutNs).
+// No CTA waits on another: claims and completions are atomics.  Within a
+// CTA every wait is bounded: the producer's idle polls by the ingest's idle
+// timeout and the stop word; a consumer's wait for a slot by the producer's
+// idle heartbeat and then copyTimeoutNs; the waits for the CTA's own bulk
+// copies by copyTimeoutNs; a wait that runs out aborts the whole CTA.
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -49,6 +51,7 @@ constexpr int kTileStages = 3;
 using Consumers = FirstThreads<kTileConsumers>;
 constexpr unsigned kTileOutBytes = 16384;   // one folded sub-tile
 constexpr int kTileOutBufs = 2;             // output buffers, used in turn
+constexpr int kTileStateWords = (int)(offsetof(TileState, next) / 8);   // request .. klass
 
 
 VDEV uint64_t ldAcquireSys(const unsigned long long* p) {
@@ -153,10 +156,15 @@ __device__ __noinline__ void foldStage(const ServeReq* q, unsigned in, unsigned 
   }
 }
 
-__device__ __forceinline__ void copyStage(unsigned in, unsigned o, unsigned len) {
+// a copy's stage into the output buffer; d != 0: each 16-byte piece starts
+// d bytes into the window (AllGather blocks that are not whole units, whose
+// destination units are aligned)
+__device__ __forceinline__ void copyStage(unsigned in, unsigned o, unsigned len, unsigned d) {
   extern __shared__ __align__(128) unsigned char smem[];
-  for (unsigned u = threadIdx.x * 16u; u < len; u += kTileConsumers * 16u)
-    *(uint4*)(smem + o + u) = *(const uint4*)(smem + in + u);
+  for (unsigned u = threadIdx.x * 16u; u < len; u += kTileConsumers * 16u) {
+    const unsigned char* p = smem + in + u;
+    *(uint4*)(smem + o + u) = d ? shiftBytes(*(const uint4*)p, *(const uint4*)(p + 16), d) : *(const uint4*)p;
+  }
 }
 
 VDEV bool copyColl(int coll) { return coll == kAllGather || coll == kBroadcast; }
@@ -164,7 +172,7 @@ VDEV bool copyColl(int coll) { return coll == kAllGather || coll == kBroadcast; 
 VDEV void foldStageAny(const ServeReq* q, unsigned in, unsigned stride, unsigned o, unsigned ulen,
                        unsigned long long off, const int* seg, const unsigned* segEnd, int nseg, unsigned d) {
   if (copyColl(q->coll)) {   // a copy: the one input as it is
-    copyStage(in, o, ulen);
+    copyStage(in, o, ulen, d);
     return;
   }
   const bool mx = q->redop == kMax;
@@ -239,7 +247,29 @@ __device__ __noinline__ void tailReduce(const ServeReq* q) {
   }
 }
 
+// the bytes of an AllGather block (count bytes, not whole units) that the
+// staged path leaves out: before its first aligned destination unit and
+// after the agStaged bytes that follow it
+VDEV unsigned long long agLead(unsigned long long b, unsigned long long count) {
+  return (16 - ((b * count) & 15)) & 15;
+}
+VDEV unsigned long long agStaged(unsigned long long count) { return count / 16 * 16 - 16; }
+
 VDEV void tailAny(const ServeReq* q) {
+  if (q->coll == kAllGather) {   // shifted blocks: each block's edge bytes
+    const unsigned long long B = q->count, W = agStaged(B);
+    const int k = q->nranks;
+    for (int b = 0; b < k; b++) {
+      const unsigned long long lead = agLead((unsigned long long)b, B);
+      const unsigned long long nedge = B - W;   // lead bytes, then the rest after lead + W
+      for (unsigned long long t = threadIdx.x; t < nedge; t += kTileConsumers) {
+        const unsigned long long x = t < lead ? t : W + t;   // source offset in block b
+        const uint8_t c = Unit1L2<uint8_t>::load((const char*)q->send[b] + x);
+        for (int r = 0; r < k; r++) ((uint8_t*)q->recv[r])[(unsigned long long)b * B + x] = c;
+      }
+    }
+    return;
+  }
   if (q->coll == kBroadcast) {   // the bytes after the last full unit
     const unsigned long long from = q->count / 16 * 16;
     for (unsigned long long i = from + threadIdx.x; i < q->count; i += kTileConsumers) {
@@ -257,7 +287,7 @@ VDEV void tailAny(const ServeReq* q) {
 }
 
 VDEV bool hasTail(const ServeReq* q) {
-  if (q->coll == kAllGather) return false;            // whole units (staged AllGather blocks)
+  if (q->coll == kAllGather) return q->vec == 2;       // staged blocks of whole units have none
   if (q->coll == kBroadcast) return q->count % 16 != 0;
   if (q->coll == kReduceScatter && q->vec == 2) return true;
   const unsigned long long E = (q->dtype == kF16 || q->dtype == kBF16) ? 8 : 4;
@@ -333,9 +363,10 @@ __device__ void ingest(const TileArgs& a) {
 // ---- where tiles come from.  The engine below calls a source from lane 0
 // of its producer warp:
 //   claim(&tile)        the next tile: an op id (>= 0) and its tile index; -1: none now
-//   loadReq(id, dst)    the op's description, into shared memory
-//   geom(id, tile, &w)  the tile's work: a byte range of one block (staged),
-//                       or a range of the register kernels' units
+//   fetch(id, tile, &w, dst, scratch, lane)
+//                       (every lane) the op's description into shared memory
+//                       and the tile's work: a byte range of one block
+//                       (staged), or a range of the register kernels' units
 //   done(id)            a tile of op `id` has completed (its stores are visible)
 //   finished()          no tile will come any more
 //   fail()              a bulk copy did not complete in time
@@ -387,16 +418,22 @@ struct ServeSource {
     }
     return -1;
   }
-  VDEV void loadReq(long long id, ServeReq* dst) {
-    const unsigned long long* src = (const unsigned long long*)&a.state[id].req;
-    for (int i = 0; i < (int)(sizeof(ServeReq) / 8); i++) ((unsigned long long*)dst)[i] = ldVol(&src[i]);
-  }
-  VDEV void geom(long long id, unsigned long long tile, TileWork* w) {
-    TileState* st = &a.state[id];
-    if (ldVol(&st->staged))
-      stagedGeom(tile, ldVol(&st->perBlock), ldVol(&st->tileBytes), ldVol(&st->blockBytes), ldVol(&st->ntiles), w);
-    else
-      registerGeom(tile, ldVol(&st->tileUnits), ldVol(&st->units), ldVol(&st->ntiles), w);
+  // every lane of the producer warp: the op's state (request and geometry)
+  // into `scratch`, a word per lane at a time, then the request into `dst`
+  // and the tile's work into `w` (lane 0)
+  VDEV void fetch(long long id, unsigned long long tile, TileWork* w, ServeReq* dst, unsigned long long* scratch,
+                  int lane) {
+    const unsigned long long* src = (const unsigned long long*)&a.state[id];
+    for (int i = lane; i < kTileStateWords; i += 32) scratch[i] = ldVol(&src[i]);
+    __syncwarp();
+    const TileState* st = (const TileState*)scratch;
+    for (int i = lane; i < (int)(sizeof(ServeReq) / 8); i += 32)
+      ((unsigned long long*)dst)[i] = ((const unsigned long long*)&st->req)[i];
+    if (lane == 0) {
+      if (st->staged) stagedGeom(tile, st->perBlock, st->tileBytes, st->blockBytes, st->ntiles, w);
+      else registerGeom(tile, st->tileUnits, st->units, st->ntiles, w);
+    }
+    __syncwarp();
   }
   // the CTA that finishes a request's last tile reports the request
   VDEV void done(long long id) {
@@ -440,30 +477,31 @@ struct BatchSource {
     next += gridDim.x;
     return lo;
   }
-  VDEV void loadReq(long long id, ServeReq* dst) {
-    const TileOpDesc& o = b.ops[id];
-    dst->coll = o.coll;
-    dst->proto = kDirect;
-    dst->dtype = o.dtype;
-    dst->redop = o.redop;
-    dst->nranks = o.nranks;
-    dst->nsub = o.nsub;
-    dst->root = o.root;
-    dst->vec = o.vec;
-    dst->count = o.count;
-    dst->chunk = o.chunk;
-    dst->slotUnits = 0;
-    dst->slotBytes = 0;
-    dst->inplaceMask = o.inplaceMask;
-    for (int r = 0; r < o.nranks; r++) {
-      dst->send[r] = b.ptrs[o.ptrBase + r];
-      dst->recv[r] = const_cast<void*>(b.ptrs[o.ptrBase + o.nranks + r]);
+  // lane 0: the op's description from the launch's parameters
+  VDEV void fetch(long long id, unsigned long long tile, TileWork* w, ServeReq* dst, unsigned long long*, int lane) {
+    if (lane == 0) {
+      const TileOpDesc& o = b.ops[id];
+      dst->coll = o.coll;
+      dst->proto = kDirect;
+      dst->dtype = o.dtype;
+      dst->redop = o.redop;
+      dst->nranks = o.nranks;
+      dst->nsub = o.nsub;
+      dst->root = o.root;
+      dst->vec = o.vec;
+      dst->count = o.count;
+      dst->chunk = o.chunk;
+      dst->slotUnits = 0;
+      dst->slotBytes = 0;
+      dst->inplaceMask = o.inplaceMask;
+      for (int r = 0; r < o.nranks; r++) {
+        dst->send[r] = b.ptrs[o.ptrBase + r];
+        dst->recv[r] = const_cast<void*>(b.ptrs[o.ptrBase + o.nranks + r]);
+      }
+      if (o.staged) stagedGeom(tile, o.perBlock, o.tileBytes, o.blockBytes, o.ntiles, w);
+      else registerGeom(tile, o.tileUnits, o.units, o.ntiles, w);
     }
-  }
-  VDEV void geom(long long id, unsigned long long tile, TileWork* w) {
-    const TileOpDesc& o = b.ops[id];
-    if (o.staged) stagedGeom(tile, o.perBlock, o.tileBytes, o.blockBytes, o.ntiles, w);
-    else registerGeom(tile, o.tileUnits, o.units, o.ntiles, w);
+    __syncwarp();
   }
   VDEV void done(long long) {}
   VDEV bool finished() { return next >= b.totalTiles; }
@@ -483,7 +521,7 @@ struct BatchSource {
 // What a stage slot holds.  Every slot the consumers wait on carries one of
 // these, and its `full` mbarrier completes for each: data by the bulk loads'
 // bytes, the others by a plain arrive of the producer.
-enum { kStageData = 0, kStageReg = 1, kStageIdle = 2, kStageStop = 3 };
+enum { kStageData = 0, kStageReg = 1, kStageStop = 2 };
 
 struct StageInfo {
   int kind;
@@ -523,19 +561,21 @@ struct Producer {
   long long doneId[kMaxPendingDone];          // finished tiles, completion unconfirmed
   unsigned long long doneGroup[kMaxPendingDone];
   int ndone;
-  unsigned idleNs;
   int stopped;
 };
 
 struct EngineSmem {
   ServeReq sReq[kTileStages];   // the op of each stage
   ServeReq sCur;                // the op being issued
+  TileWork work;                // the claimed tile's work
+  unsigned long long scratch[kTileStateWords];   // a claimed op's state, as fetched
   StageInfo sInfo[kTileStages];
   Producer p;
   uint64_t full[kTileStages];   // a slot is filled (producer / bulk loads)
   uint64_t empty[kTileStages];  // a slot is consumed (one arrive per consumer warp)
   uint64_t outFree[kTileOutBufs];   // an output buffer's store group has read it
   int abort;                    // a wait ran out: everyone leaves
+  unsigned beat;                // the producer's idle polls (it is alive, with nothing to claim)
 };
 
 VDEV bool aborted(const EngineSmem& e) { return *(const volatile int*)&e.abort != 0; }
@@ -558,6 +598,34 @@ VDEV bool engineWait(uint64_t* bar, unsigned parity, unsigned long long timeoutN
 // group per data stage, and waits for its own).
 constexpr unsigned kFullMask = 0xffffffffu;
 
+// consumers: wait for sequence index j.  While the producer has not filled
+// it (nothing to claim yet) the wait lasts as long as the producer keeps
+// polling; once filled, its bulk loads have timeoutNs to land.
+VDEV bool waitFull(EngineSmem& e, unsigned long long j, unsigned long long timeoutNs) {
+  uint64_t* bar = &e.full[j % kTileStages];
+  const unsigned parity = (unsigned)((j / kTileStages) & 1ull);
+  if (mbarTryWait(bar, parity)) return true;
+  uint64_t t0 = globaltimer();
+  unsigned beat = *(const volatile unsigned*)&e.beat;
+  bool filled = false;
+  while (true) {
+    if (mbarTryWait(bar, parity)) return true;
+    if (aborted(e)) return false;
+    const uint64_t now = globaltimer();
+    if (!filled) {
+      const unsigned b = *(const volatile unsigned*)&e.beat;
+      if (*(const volatile unsigned long long*)&e.p.filled > j) {
+        filled = true;
+        t0 = now;
+      } else if (b != beat) {
+        beat = b;
+        t0 = now;
+      }
+    }
+    if (now - t0 > timeoutNs) return false;
+  }
+}
+
 // producer warp: every store group has completed; lane 0 reports the
 // pending tiles
 template <class Src>
@@ -572,55 +640,52 @@ VDEV void flushDone(Src& src, Producer& p, int lane) {
   __syncwarp();
 }
 
-// producer warp: fill sequence index p.filled (its slot has been consumed)
+// producer warp: fill sequence index p.filled (its slot has been consumed);
+// false: nothing to claim right now (no slot filled)
 template <class Src>
-__device__ __noinline__ void fillStage(Src& src, EngineSmem& e, unsigned char* in, unsigned stageBytes,
-                                       bool persistent, int lane) {
+__device__ __noinline__ bool fillStage(Src& src, EngineSmem& e, unsigned char* in, unsigned stageBytes, int lane) {
   Producer& p = e.p;
-  if (p.stopped) return;   // the stop mark is the last index filled
+  if (p.stopped) return true;   // the stop mark is the last index filled
   const int stg = (int)(p.filled % kTileStages);
   StageInfo& si = e.sInfo[stg];
   uint64_t* bar = &e.full[stg];
   if (p.curId < 0) {
     unsigned long long tl = 0;
     long long id = -1;
-    if (lane == 0) id = src.claim(&tl);
+    int fin = 0;
+    if (lane == 0) {
+      id = src.claim(&tl);
+      if (id < 0) fin = src.finished() ? 1 : 0;
+    }
     id = (long long)__shfl_sync(kFullMask, (unsigned long long)id, 0);
+    fin = __shfl_sync(kFullMask, fin, 0);
     if (id < 0) {
+      if (!fin) return false;
       flushDone(src, p, lane);
       if (lane == 0) {
-        if (src.finished()) {
-          si.kind = kStageStop;
-          p.stopped = 1;
-        } else {
-          si.kind = kStageIdle;
-          if (persistent) {
-            __nanosleep(p.idleNs);
-            p.idleNs = p.idleNs < 4096 ? 2 * p.idleNs : 4096;
-          }
-        }
+        si.kind = kStageStop;
+        p.stopped = 1;
         mbarArrive(bar);
         p.filled++;
       }
       __syncwarp();
-      return;
+      return true;
     }
+    tl = __shfl_sync(kFullMask, tl, 0);
+    src.fetch(id, tl, &e.work, &e.sCur, e.scratch, lane);   // no staged tile is in progress
     int staged = 0;
     if (lane == 0) {
-      p.idleNs = 64;
-      TileWork w;
-      src.geom(id, tl, &w);
+      const TileWork w = e.work;
       staged = w.staged;
       if (!w.staged) {
         si.kind = kStageReg;
         si.id = (int)id;
         si.reg = w;
-        src.loadReq(id, &e.sReq[stg]);   // the slot's own op copy
+        e.sReq[stg] = e.sCur;   // the slot's own op copy
         p.stageGen[stg] = ~0u;
         mbarArrive(bar);
         p.filled++;
       } else {
-        src.loadReq(id, &e.sCur);
         p.curId = id;
         p.curGen++;
         p.curB = w.b;
@@ -641,13 +706,15 @@ __device__ __noinline__ void fillStage(Src& src, EngineSmem& e, unsigned char* i
         p.curSub = (unsigned)(even < sub ? even : sub);
         p.curStride = p.curSub + pad;
         const unsigned long long esz = (r.dtype == kF16 || r.dtype == kBF16) ? 2 : 4;
-        p.curD = r.vec == 2 ? (unsigned)(((unsigned long long)w.b * r.count * esz) & 15ull) : 0u;
+        if (r.vec != 2) p.curD = 0;
+    else if (r.coll == kAllGather) p.curD = (unsigned)agLead((unsigned long long)w.b, r.count);
+    else p.curD = (unsigned)(((unsigned long long)w.b * r.count * esz) & 15ull);
       }
     }
     staged = __shfl_sync(kFullMask, staged, 0);
     if (!staged) {
       __syncwarp();
-      return;
+      return true;
     }
   }
   const ServeReq& r = e.sCur;
@@ -664,9 +731,9 @@ __device__ __noinline__ void fillStage(Src& src, EngineSmem& e, unsigned char* i
     si.b = p.curB;
     si.endOfTile = (off + len >= p.curEnd) ? 1 : 0;
     si.tail = si.endOfTile && p.curTail;
-    // a shifted op's very last unit: its window would reach past the end of
+    // a shifted ReduceScatter's very last unit: its window would reach past the end of
     // the send buffers; the tail folds it with element loads
-    const bool skipLast = r.vec == 2 && si.tail;
+    const bool skipLast = r.vec == 2 && r.coll == kReduceScatter && si.tail;
     si.ulen = skipLast ? len - 16 : len;
     si.nseg = cutSegments(&r, si.b, off, len, si.seg, si.segEnd);
     if (p.stageGen[stg] != p.curGen) {   // the stage holds another claim's op
@@ -674,14 +741,14 @@ __device__ __noinline__ void fillStage(Src& src, EngineSmem& e, unsigned char* i
       p.stageGen[stg] = p.curGen;
     }
     wlen = (si.d != 0 && !skipLast) ? len + 16 : len;
-    mbarExpect(bar, copyColl(r.coll) ? len : wlen * (unsigned)r.nranks);
+    mbarExpect(bar, copyColl(r.coll) ? wlen : wlen * (unsigned)r.nranks);
   }
   wlen = __shfl_sync(kFullMask, wlen, 0);
   __syncwarp();   // si and sCur as lane 0 wrote them
   unsigned char* dst = in + (size_t)stg * stageBytes;
   const unsigned long long off = si.off;
   if (copyColl(r.coll)) {   // AllGather: block b of rank b; Broadcast: the root's buffer
-    if (lane == 0) bulkLoad(dst, (const char*)r.send[r.coll == kAllGather ? si.b : r.root] + off, si.len, bar);
+    if (lane == 0) bulkLoad(dst, (const char*)r.send[r.coll == kAllGather ? si.b : r.root] + off, wlen, bar);
   } else {
     const unsigned long long esz = (r.dtype == kF16 || r.dtype == kBF16) ? 2 : 4;
     const unsigned long long from =
@@ -696,6 +763,7 @@ __device__ __noinline__ void fillStage(Src& src, EngineSmem& e, unsigned char* i
     if (p.curOff >= p.curEnd) p.curId = -1;
   }
   __syncwarp();
+  return true;
 }
 
 // producer warp: sequence index i has been consumed; a data stage's output
@@ -727,7 +795,10 @@ __device__ __noinline__ long long retire(Src& src, EngineSmem& e, unsigned char*
       // AllReduce: every rank; AllGather: block b of every rank; Broadcast:
       // every rank (a rank whose output is its input in place is skipped)
       const int self = c == kAllGather ? si.b : (c == kBroadcast ? r->root : -1);
-      const unsigned long long dst = (c == kAllGather ? (unsigned long long)si.b * r->count : 0ull) + si.off;
+      // (a shifted AllGather block: from its first aligned destination unit)
+      const unsigned long long bb = (unsigned long long)si.b;
+      const unsigned long long dst =
+          (c == kAllGather ? bb * r->count + (r->vec == 2 ? agLead(bb, r->count) : 0ull) : 0ull) + si.off;
       for (int q = lane; q < r->nranks; q += 32) {
         if (q == self && ((r->inplaceMask >> q) & 1ull)) continue;
         bulkStore((char*)r->recv[q] + dst, o, si.ulen);
@@ -787,7 +858,7 @@ __device__ __noinline__ void release(Src& src, EngineSmem& e, unsigned long long
 // before the warp leaves, and the source records the failure.
 template <class Src>
 __device__ __noinline__ void produce(Src& src, EngineSmem& e, unsigned char* in, unsigned char* out,
-                                     unsigned stageBytes, unsigned long long timeoutNs, bool persistent) {
+                                     unsigned stageBytes, unsigned long long timeoutNs) {
   const int lane = threadIdx.x & 31;
   Producer& p = e.p;
   if (lane == 0) {
@@ -798,11 +869,11 @@ __device__ __noinline__ void produce(Src& src, EngineSmem& e, unsigned char* in,
     p.curB = p.curTail = 0;
     for (int i = 0; i < kTileStages; i++) p.stageGen[i] = ~0u;
     p.ndone = 0;
-    p.idleNs = 64;
     p.stopped = 0;
   }
   __syncwarp();
   unsigned long long retired = 0;
+  unsigned idleNs = 32;
   bool ok = true;
   while (!p.stopped) {
     long long n = -1;
@@ -813,7 +884,23 @@ __device__ __noinline__ void produce(Src& src, EngineSmem& e, unsigned char* in,
     }
     // the output buffer first: consumers may be waiting for it
     if (n >= 0) release(src, e, (unsigned long long)n, lane);
-    fillStage(src, e, in, stageBytes, persistent, lane);
+    if (fillStage(src, e, in, stageBytes, lane)) {
+      idleNs = 32;
+      continue;
+    }
+    // nothing to claim: retire what the consumers still hold (their stores
+    // and completions go out now), report, and poll again a little later
+    while (ok && retired < p.filled) {
+      n = retire(src, e, out, retired, timeoutNs, lane, &ok);
+      if (!ok) break;
+      retired++;
+      if (n >= 0) release(src, e, (unsigned long long)n, lane);
+    }
+    if (!ok) break;
+    flushDone(src, p, lane);
+    __nanosleep(idleNs);
+    idleNs = idleNs < 512 ? 2 * idleNs : 512;
+    if (lane == 0) *(volatile unsigned*)&e.beat = *(volatile unsigned*)&e.beat + 1;
   }
   while (ok && retired + 1 < p.filled) {   // every index before the stop mark
     const long long n = retire(src, e, out, retired, timeoutNs, lane, &ok);
@@ -847,7 +934,7 @@ __device__ __noinline__ void consume(EngineSmem& e, unsigned char* out, unsigned
   unsigned long long dsn = 0;
   for (unsigned long long j = 0;; j++) {
     const int stg = (int)(j % kTileStages);
-    if (!engineWait(&e.full[stg], (unsigned)((j / kTileStages) & 1ull), timeoutNs, e)) {
+    if (!waitFull(e, j, timeoutNs)) {
       setAbort(e);
       return;
     }
@@ -884,12 +971,13 @@ __device__ __noinline__ void consume(EngineSmem& e, unsigned char* out, unsigned
 // ---- the tile engine: take tiles from `src` until it has none and never
 // will.  The stage slots form a ring of kTileStages; sequence index j uses
 // slot j mod kTileStages and its barriers' phase j / kTileStages.  The
-// producer warp runs ahead of the consumer warps by up to
-// kTileStages indices, so bulk loads stay in flight while the consumers
-// fold and the producer's own work (claims, stores, completions) overlaps
-// theirs.
+// producer warp runs ahead of the consumer warps by up to kTileStages
+// indices, so bulk loads stay in flight while the consumers fold and the
+// producer's own work (claims, stores, completions) overlaps theirs.  With
+// nothing to claim the producer fills no slot: it retires what the
+// consumers hold, reports, and polls again, so a new tile starts at once.
 template <class Src>
-__device__ void tileEngine(Src& src, unsigned stageBytes, unsigned long long copyTimeoutNs, bool persistent) {
+__device__ void tileEngine(Src& src, unsigned stageBytes, unsigned long long copyTimeoutNs) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ EngineSmem e;
   unsigned char* in = smem;
@@ -901,11 +989,13 @@ __device__ void tileEngine(Src& src, unsigned stageBytes, unsigned long long cop
     }
     for (int i = 0; i < kTileOutBufs; i++) mbarInit(&e.outFree[i], 1);
     e.abort = 0;
+    e.beat = 0;
+    e.p.filled = 0;
     fenceBarrierInit();
   }
   __syncthreads();
   if (threadIdx.x >= kTileConsumers) {
-    produce(src, e, in, out, stageBytes, copyTimeoutNs, persistent);
+    produce(src, e, in, out, stageBytes, copyTimeoutNs);
     return;
   }
   consume(e, out, stageBytes, copyTimeoutNs);
@@ -917,13 +1007,13 @@ __global__ void __launch_bounds__(kTileThreads, 1) kServeTiles(const __grid_cons
     return;
   }
   ServeSource src{a};
-  tileEngine(src, a.stageBytes, a.copyTimeoutNs, true);
+  tileEngine(src, a.stageBytes, a.copyTimeoutNs);
 }
 
 // a group's direct calls in one launch (one CTA per SM)
 __global__ void __launch_bounds__(kTileThreads, 1) kBatchTiles(const __grid_constant__ TileBatchArgs b) {
   BatchSource src{b, (unsigned long long)blockIdx.x};
-  tileEngine(src, b.stageBytes, b.copyTimeoutNs, false);
+  tileEngine(src, b.stageBytes, b.copyTimeoutNs);
 }
 
 }  // namespace
