@@ -500,6 +500,8 @@ def run_batched(args):
     with torch.cuda.stream(stream):
         batched()                               # fixes the plans before capture
     torch.cuda.synchronize()
+    protos = [p["proto"] for p in comm.group_plans()]
+    ndirect = sum(p == "direct" for p in protos)
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=stream):
         batched()
@@ -512,6 +514,10 @@ def run_batched(args):
             "batched_graph_ms": round(batch_ms, 4), "speedup": round(plain_ms / batch_ms, 3),
             "plain_algbw_GBps": round(total / (plain_ms / 1e3) / 1e9, 2),
             "batched_algbw_GBps": round(total / (batch_ms / 1e3) / 1e9, 2),
+            "direct_calls": ndirect, "fifo_calls": len(protos) - ndirect,
+            # the group's kernels: one tile-engine launch for its direct calls,
+            # one batch kernel for its FIFO calls
+            "graph_launches": int(ndirect > 0) + int(len(protos) > ndirect),
             "tune_seconds": round(tune_s, 1), "status": err}
 
 

@@ -220,11 +220,20 @@ vResult_t vReduce(const void* const* sendbufs, void* const* recvbufs, size_t cou
  * ncclGroupStart / ncclGroupEnd (Sec. II-A-4).  Collective calls between
  * vGroupStart and vGroupEnd (on the calling host thread; groups nest) are
  * validated and planned immediately but not launched; vGroupEnd launches, per
- * communicator, ONE persistent batch kernel that runs all of that
- * communicator's calls: up to 4 gangs of (nranks x nch/G) CTAs run their
- * share of the calls (longest first) concurrently, each gang's calls one after
- * another through the same FIFOs.  Each call's result is bit-identical to the
- * same call launched alone with the plan vcommGetGroupPlans reports.  All
+ * communicator, at most two persistent kernels.  The FIFO-protocol calls run
+ * in ONE batch kernel: up to 4 gangs of (nranks x nch/G) CTAs run their share
+ * of the calls (longest first) concurrently, each gang's calls one after
+ * another through the same FIFOs.  The direct-protocol calls (Auto's choice
+ * on the ring) run in ONE launch of the tile engine on up to 16 vranks with
+ * sum / max of 32- and 16-bit types (any other direct group: one launch per
+ * (dtype, op) class, and one for the copies): every call is cut into tiles,
+ * laid end to end and shared out statically, one CTA per SM; a tile of
+ * 16-byte aligned buffers moves through shared memory by bulk copies (a
+ * producer warp issues them while eight consumer warps fold), other tiles
+ * take element-wise loads and stores.  Env VCOMM_TILE_GROUPS=0 (read at
+ * vcommInit) keeps the per-class launches.  Each call's result is
+ * bit-identical to the same call launched alone with the plan
+ * vcommGetGroupPlans reports.  All
  * calls of one communicator in a group must use the same stream.  The launch
  * is capturable in a CUDA graph once the arenas it needs exist (vcommPrepare,
  * or one uncaptured run); the batch description is a kernel parameter, so a
@@ -318,11 +327,12 @@ vResult_t vcommGetTuneTable(vcomm_t comm, int coll, vPlan_t* plans, size_t* byte
  * one resident kernel; its CTA 0 takes requests in arrival order from a ring
  * in host-mapped memory and queues them on the device, small requests
  * (< bigThreshold per rank) ahead of large ones, and every other CTA takes
- * the next tile (a range of 16-byte units, at most ~2 MiB of traffic) of the
- * first queued request that has tiles left.  So a request starts as soon as
- * a CTA is free, small requests overtake large ones at tile boundaries, and
- * the CTA that finishes a request's last tile reports its completion to host
- * memory.  Plans as in mode 1 (results bit-identical); other protocols are
+ * the next tile (a byte range of one block, at most ~4 MiB of traffic) of the
+ * first queued request that has tiles left; the tiles of 16-byte aligned
+ * buffers move through shared memory by bulk copies (the group launch's
+ * tile engine).  So a request starts as soon as a CTA is free, small
+ * requests overtake large ones at tile boundaries, and the CTA that finishes
+ * a request's last tile reports its completion to host memory.  Plans as in mode 1 (results bit-identical); other protocols are
  * refused (vUnsupported).  The kernel returns after idleTimeoutSec without
  * work and is started again by the next request.
  * While a mode-0 or mode-3 server exists its kernel occupies the SMs: do not
