@@ -1066,13 +1066,35 @@ static vResult_t launchTileGroup(vcomm* c, std::vector<CallSpec>& ops, unsigned 
     b->copyTimeoutNs = (unsigned long long)(c->timeoutSec * 1e9);
     b->errClaim = c->dClaim;
     b->err = c->dErr;
-    unsigned long long start = 0;
+    // the tiles are shared out statically (CTA j takes j, j + grid, ...):
+    // ops in order of falling traffic per tile, so that every round of
+    // `grid` tiles holds tiles of about one size and the CTAs finish together
+    struct OpTiles {
+      int idx;
+      DirectGeom g;
+      TileGeometry tg;
+      unsigned long long perTile;
+    };
+    std::vector<OpTiles> order;
     for (int i = 0; i < n; i++) {
       const CallSpec& o = ops[base + i];
-      const DirectGeom g = directGeom(o);
+      OpTiles t{i, directGeom(o), {}, 0};
       const int esz = dtypeSize(o.dtype);
-      const TileGeometry tg = tileGeometry(o.kcoll, k, o.units, esz, g.vec, (unsigned long long)c->nsm,
-                                           (unsigned long long)serveTilesUnitsPerIter());
+      t.tg = tileGeometry(o.kcoll, k, o.units, esz, t.g.vec, (unsigned long long)c->nsm,
+                          (unsigned long long)serveTilesUnitsPerIter());
+      const bool copy = o.kcoll == kAllGather || o.kcoll == kBroadcast;
+      const unsigned long long factor = o.kcoll == kAllReduce ? 2ull * k : (unsigned long long)k + 1;
+      const unsigned long long unitBytes = t.tg.vec == 0 ? (copy ? 1ull : (unsigned long long)esz) : 16ull;
+      t.perTile = (t.tg.staged ? t.tg.tileBytes : t.tg.tileUnits * unitBytes) * factor;
+      order.push_back(t);
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [](const OpTiles& a, const OpTiles& b) { return a.perTile > b.perTile; });
+    unsigned long long start = 0;
+    for (int i = 0; i < n; i++) {
+      const CallSpec& o = ops[base + order[i].idx];
+      const DirectGeom& g = order[i].g;
+      const TileGeometry& tg = order[i].tg;
       TileOpDesc& d = b->ops[i];
       d.count = o.units;
       d.chunk = g.chunk;
