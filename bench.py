@@ -401,6 +401,76 @@ def run_direct(args):
             "equals_simple": bool(same), "clocks": clk.summary(), "status": err}
 
 
+# ------------------------------------------------------------------ tile-engine group leg
+
+def run_tile_group(args):
+    """The headline workload (8 vranks x S fp32, direct protocol) as a group
+    of two AllReduce calls on the two halves of every buffer: one launch of
+    the tile engine (kBatchTiles: a producer warp issuing bulk copies, eight
+    consumer warps folding from shared memory).  2kS algorithmic bytes; the
+    output is compared bit for bit with one direct call on the whole
+    buffers."""
+    import torch
+
+    from paper_2507_04786_b300 import Comm, group
+    w = workloads.HEADLINE
+    k, S = w["nranks"], args.bytes
+    n = S // 4
+    h = n // 2
+    xs = inputs.workload(w["seed"], k, n, "fp32", w["dist"])
+    sends = [torch.from_numpy(x).cuda() for x in xs]
+    del xs
+    recvs = [torch.empty_like(t) for t in sends]
+    comm = Comm(k, w["nchannels"])
+    stream = torch.cuda.current_stream()
+
+    def grp():
+        with group():
+            comm.all_reduce([t[:h] for t in sends], [t[:h] for t in recvs], op="sum", algo="ring",
+                            proto="direct", stream=stream)
+            comm.all_reduce([t[h:] for t in sends], [t[h:] for t in recvs], op="sum", algo="ring",
+                            proto="direct", stream=stream)
+
+    grp()
+    plans = comm.group_plans()
+    torch.cuda.synchronize()
+    got = [r.clone() for r in recvs[:2]]
+    # the same halves as single calls (same plans): the group must give their bits
+    for (lo, hi), p in zip(((0, h), (h, n)), plans):
+        comm.set_plan(nchannels=p["nchannels"], chunk_steps=p["chunkSteps"])
+        comm.all_reduce([t[lo:hi] for t in sends], [t[lo:hi] for t in recvs], op="sum", algo="ring",
+                        proto="direct", stream=stream)
+    torch.cuda.synchronize()
+    same = all(torch.equal(a.view(torch.int32), b.view(torch.int32)) for a, b in zip(got, recvs[:2]))
+    del got
+    comm.clear_plan()
+    for _ in range(args.warmup):
+        grp()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        torch.cuda.synchronize()
+        grp()   # untimed: the GPU sat idle while the sampler started
+        for i in range(args.steps):
+            evs[i][0].record(stream)
+            grp()
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    err = comm.async_error()
+    comm.destroy()
+    peak, peak_kind = measured_peak()
+    alg = algorithmic_bytes(k, S, "direct")
+    achieved = alg / (ms / 1e3) / 1e9
+    return {"workload": w["name"] + "-as-2-call-group", "proto": "direct", "kernel": "kBatchTiles",
+            "ms_per_step": round(ms, 4), "busbw_GBps": round(busbw(S, k, ms / 1e3), 2),
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "algorithmic_bytes_per_launch": alg,
+                         "peak_source": peak_kind,
+                         "nominal_frac": round(achieved / NOMINAL_HBM_GBS, 4)},
+            "equals_single_calls": bool(same), "clocks": clk.summary(), "status": err}
+
+
 # ------------------------------------------------------------------ all-to-all leg
 
 def run_alltoall(args):
@@ -1071,7 +1141,7 @@ def main():
     ap.add_argument("--serve-requests-direct", type=int, default=workloads.SERVED["requests"],
                     help="requests of the default-protocol served comparison (the whole stream)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and served legs")
-    ap.add_argument("--extras", default="direct,alltoall,small,batched,served,saturation,hop",
+    ap.add_argument("--extras", default="direct,tilegroup,alltoall,small,batched,served,saturation,hop",
                     help="the extra legs to run, comma separated (profiling captures run one)")
     ap.add_argument("--sweep", default=None,
                     help="run the protocol x size x channel sweep, write JSON lines here, exit")
@@ -1180,6 +1250,8 @@ def main():
     if not args.no_extras and world == 1:
         if "direct" in legs:
             line["direct"] = run_direct(args)
+        if "tilegroup" in legs:
+            line["tile_group"] = run_tile_group(args)
         if "alltoall" in legs:
             line["alltoall"] = run_alltoall(args)
         if "small" in legs:
