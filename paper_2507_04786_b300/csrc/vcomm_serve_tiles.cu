@@ -193,22 +193,37 @@ VDEV void foldStageAny(const ServeReq* q, unsigned in, unsigned stride, unsigned
 // far longer than a sub-tile; 0 runs if the sub-tile holds more than
 // kMaxSegRuns, as the short segments of a small buffer's last loop do, and
 // the fold then looks each unit's segment up); a ReduceScatter block b is one
-// run starting at rank b + 1, a Reduce one starting at root + 1
-VDEV int cutSegments(const ServeReq* q, int b, unsigned long long off, unsigned len, int* seg, unsigned* segEnd) {
+// run starting at rank b + 1, a Reduce one starting at root + 1.  The run
+// found last is kept in `cache` ([lo, hi) bytes, segment s, for claim gen):
+// a tile's sub-tiles come in rising order, so most of them lie inside it
+// and need no partition arithmetic.
+struct SegCache {
+  unsigned long long lo, hi;
+  int s;
+  unsigned gen;
+};
+VDEV int cutSegments(const ServeReq* q, int b, unsigned long long off, unsigned len, int* seg, unsigned* segEnd,
+                     SegCache& cache, unsigned gen) {
   if (q->coll != kAllReduce) {
     seg[0] = q->coll == kReduce ? q->root : b;
     segEnd[0] = len;
     return 1;
   }
-  const DirectView v = viewOfReq(q);
   const unsigned long long esz = (q->dtype == kF16 || q->dtype == kBF16) ? 2 : 4;
   unsigned u = 0;
   int n = 0;
   while (u < len) {
     if (n == kMaxSegRuns) return 0;
-    unsigned long long runEnd;   // in elements
-    seg[n] = arSegment(v, (off + u) / esz, (int)esz, &runEnd);
-    const unsigned long long endB = runEnd * esz - off;
+    const unsigned long long x = off + u;
+    if (cache.gen != gen || x < cache.lo || x >= cache.hi) {
+      unsigned long long runEnd;   // in elements
+      cache.s = arSegment(viewOfReq(q), x / esz, (int)esz, &runEnd);
+      cache.lo = x;
+      cache.hi = runEnd * esz;
+      cache.gen = gen;
+    }
+    seg[n] = cache.s;
+    const unsigned long long endB = cache.hi - off;
     segEnd[n] = endB < len ? (unsigned)endB : len;
     u = segEnd[n];
     n++;
@@ -558,6 +573,7 @@ struct Producer {
   unsigned curSub, curStride, curD, curGen;
   int curB, curTail;
   unsigned stageGen[kTileStages];             // which claim each stage's op copy is of
+  SegCache seg;                               // the ring segment run found last
   long long doneId[kMaxPendingDone];          // finished tiles, completion unconfirmed
   unsigned long long doneGroup[kMaxPendingDone];
   int ndone;
@@ -643,7 +659,7 @@ VDEV void flushDone(Src& src, Producer& p, int lane) {
 // producer warp: fill sequence index p.filled (its slot has been consumed);
 // false: nothing to claim right now (no slot filled)
 template <class Src>
-__device__ __noinline__ bool fillStage(Src& src, EngineSmem& e, unsigned char* in, unsigned stageBytes, int lane) {
+__device__ __forceinline__ bool fillStage(Src& src, EngineSmem& e, unsigned char* in, unsigned stageBytes, int lane) {
   Producer& p = e.p;
   if (p.stopped) return true;   // the stop mark is the last index filled
   const int stg = (int)(p.filled % kTileStages);
@@ -735,7 +751,7 @@ __device__ __noinline__ bool fillStage(Src& src, EngineSmem& e, unsigned char* i
     // the send buffers; the tail folds it with element loads
     const bool skipLast = r.vec == 2 && r.coll == kReduceScatter && si.tail;
     si.ulen = skipLast ? len - 16 : len;
-    si.nseg = cutSegments(&r, si.b, off, len, si.seg, si.segEnd);
+    si.nseg = cutSegments(&r, si.b, off, len, si.seg, si.segEnd, p.seg, p.curGen);
     if (p.stageGen[stg] != p.curGen) {   // the stage holds another claim's op
       e.sReq[stg] = r;
       p.stageGen[stg] = p.curGen;
@@ -770,7 +786,7 @@ __device__ __noinline__ bool fillStage(Src& src, EngineSmem& e, unsigned char* i
 // buffer goes to its outputs as store group n = p.groups (returned; -1 for
 // the other kinds of slot)
 template <class Src>
-__device__ __noinline__ long long retire(Src& src, EngineSmem& e, unsigned char* out, unsigned long long i,
+__device__ __forceinline__ long long retire(Src& src, EngineSmem& e, unsigned char* out, unsigned long long i,
                                          unsigned long long timeoutNs, int lane, bool* ok) {
   Producer& p = e.p;
   const int stg = (int)(i % kTileStages);
@@ -823,7 +839,7 @@ __device__ __noinline__ long long retire(Src& src, EngineSmem& e, unsigned char*
 // n + 1 - kTileOutBufs has read its buffer the consumers may write it again;
 // the tiles whose last group is older than the newest kDoneLag are reported
 template <class Src>
-__device__ __noinline__ void release(Src& src, EngineSmem& e, unsigned long long n, int lane) {
+__device__ __forceinline__ void release(Src& src, EngineSmem& e, unsigned long long n, int lane) {
   Producer& p = e.p;
   // every group but the newest kTileOutBufs - 1 has read its buffer
   asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(kTileOutBufs - 1) : "memory");
@@ -868,6 +884,7 @@ __device__ __noinline__ void produce(Src& src, EngineSmem& e, unsigned char* in,
     p.curSub = p.curStride = p.curD = p.curGen = 0;
     p.curB = p.curTail = 0;
     for (int i = 0; i < kTileStages; i++) p.stageGen[i] = ~0u;
+    p.seg.gen = ~0u;
     p.ndone = 0;
     p.stopped = 0;
   }
