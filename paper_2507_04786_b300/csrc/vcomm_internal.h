@@ -221,7 +221,8 @@ struct TileState {                     // device memory, one per ring entry
 
 struct TileQueues {                    // device memory, zeroed before the first launch
   unsigned long long tail[2];          // requests published per class (the ingester only)
-  unsigned long long pad0[14];
+  unsigned long long urgent;           // the ingester: the large queue's head has waited too long
+  unsigned long long pad0[13];
   unsigned long long head[2];          // first entry per class that may still have tiles
   unsigned long long pad1[14];
   unsigned long long completed;        // requests completed (atomic)

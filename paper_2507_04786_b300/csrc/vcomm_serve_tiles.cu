@@ -309,6 +309,11 @@ VDEV bool hasTail(const ServeReq* q) {
   return q->count % E != 0;
 }
 
+// A large request whose first tile has waited this long since its ingest
+// takes the CTAs ahead of small requests (small requests go first only as
+// long as they do not starve a large one).
+constexpr unsigned long long kLargeUrgentNs = 500000;
+
 // ---- CTA 0, warp 0: ingest ring entries firstSeq, firstSeq + 1, ... in order
 __device__ void ingest(const TileArgs& a) {
   const int lane = threadIdx.x & 31;
@@ -341,6 +346,18 @@ __device__ void ingest(const TileArgs& a) {
     got = __shfl_sync(0xffffffffu, got, 0);
     if (stop) break;
     if (!got) {
+      if (lane == 0) {   // between arrivals: how long has the large queue's head waited
+        const unsigned long long h = ldVol(&q->head[1]), t = ldVol(&q->tail[1]);
+        unsigned long long urgent = 0;
+        if (h < t) {
+          const unsigned long long en = ldVol(&q->entry[1][h % kTileRing]);
+          if ((en >> 32) == (h & 0xffffffffull)) {
+            const int s = (int)(en & 0xffffffffull) - 1;
+            urgent = globaltimer() - ldVol(&a.state[s].tStart) > kLargeUrgentNs ? 1 : 0;
+          }
+        }
+        if (urgent != ldVol(&q->urgent)) stVol(&q->urgent, urgent);
+      }
       __nanosleep(256);
       continue;
     }
@@ -414,7 +431,9 @@ struct ServeSource {
   const TileArgs& a;
   VDEV long long claim(unsigned long long* tile) {
     TileQueues* q = a.q;
-    for (int c = 0; c < 2; c++) {
+    const int first = ldVol(&q->urgent) ? 1 : 0;   // the large queue first when its head starves
+    for (int i = 0; i < 2; i++) {
+      const int c = i ^ first;
       unsigned long long h = ldVol(&q->head[c]);
       const unsigned long long t = ldAcquire(&q->tail[c]);
       while (h < t) {
