@@ -735,11 +735,13 @@ def user_bytes(coll, k, S):
     return 2 * k * S if coll == "allreduce" else (k + 1) * S
 
 
-def run_saturation(args, modes=("plain", "tiles"), nreq=None, outstanding=None):
+def run_saturation(args, modes=("plain", "tiles"), nreq=None, outstanding=None, repeats=3):
     """Closed loop: the served workload's requests with `outstanding` of them
     in flight at all times (a new one is submitted as soon as one completes),
     default protocol; the largest request rate and HBM rate each mode
-    sustains, with the latency it costs."""
+    sustains, with the latency it costs.  The modes alternate over `repeats`
+    runs (a closed loop's rates swing from run to run); each figure is the
+    median over the runs, the per-run values beside it."""
     from paper_2507_04786_b300 import Server
     w = workloads.SERVED
     nreq = nreq or w["saturation_requests"]
@@ -747,39 +749,50 @@ def run_saturation(args, modes=("plain", "tiles"), nreq=None, outstanding=None):
     reqs, _ = served_requests(nreq)
     pool = served_pool()
     res = {"workload": w["name"].replace("poisson-2000rps", "closed-loop"), "requests": nreq,
-           "outstanding": outstanding, "protocol": "auto (direct)"}
+           "outstanding": outstanding, "protocol": "auto (direct)", "repeats": repeats}
+    runs = {m: [] for m in modes}
+    for _ in range(repeats):
+        for mode in modes:
+            srv = Server(mode=mode, max_ranks=w["max_ranks"], mem_budget=w["budget_bytes"],
+                         small_gangs=w["small_lanes"] if mode == "streams" else 1)
+            live = {}
+            lats = []
+            nxt = 0
+            t0 = time.monotonic_ns()
+            while nxt < min(outstanding, nreq):
+                coll, dt, k, n, S = reqs[nxt]
+                live[srv.submit(coll, pool[dt][:k], n, dt, "sum", proto="auto", release=True)] = nxt
+                nxt += 1
+            deadline = time.time() + 120
+            while live and time.time() < deadline:
+                for t in list(live):
+                    state, lat, _, _ = srv.query(t)
+                    if state in ("done", "failed"):
+                        lats.append(lat / 1e6)
+                        srv.release(t)
+                        del live[t]
+                        if nxt < nreq:
+                            coll, dt, k, n, S = reqs[nxt]
+                            live[srv.submit(coll, pool[dt][:k], n, dt, "sum", proto="auto", release=True)] = nxt
+                            nxt += 1
+            span = (time.monotonic_ns() - t0) / 1e9
+            st = srv.stats()
+            srv.destroy()
+            lats = np.array(lats)
+            total = sum(user_bytes(c, k, S) for c, _, k, _, S in reqs[:len(lats)])
+            runs[mode].append({"requests_per_s": len(lats) / span, "hbm_GBps": total / span / 1e9,
+                               "p50_ms": float(np.percentile(lats, 50)), "p99_ms": float(np.percentile(lats, 99)),
+                               "completed": int(st["completed"]), "failed": int(st["failed"])})
     for mode in modes:
-        srv = Server(mode=mode, max_ranks=w["max_ranks"], mem_budget=w["budget_bytes"],
-                     small_gangs=w["small_lanes"] if mode == "streams" else 1)
-        live = {}
-        lats = []
-        nxt = 0
-        t0 = time.monotonic_ns()
-        while nxt < min(outstanding, nreq):
-            coll, dt, k, n, S = reqs[nxt]
-            live[srv.submit(coll, pool[dt][:k], n, dt, "sum", proto="auto", release=True)] = nxt
-            nxt += 1
-        deadline = time.time() + 120
-        while live and time.time() < deadline:
-            for t in list(live):
-                state, lat, _, _ = srv.query(t)
-                if state in ("done", "failed"):
-                    lats.append(lat / 1e6)
-                    srv.release(t)
-                    del live[t]
-                    if nxt < nreq:
-                        coll, dt, k, n, S = reqs[nxt]
-                        live[srv.submit(coll, pool[dt][:k], n, dt, "sum", proto="auto", release=True)] = nxt
-                        nxt += 1
-        span = (time.monotonic_ns() - t0) / 1e9
-        st = srv.stats()
-        srv.destroy()
-        lats = np.array(lats)
-        total = sum(user_bytes(c, k, S) for c, _, k, _, S in reqs[:len(lats)])
-        res[SERVE_NAMES[mode]] = {
-            "requests_per_s": round(len(lats) / span, 1), "hbm_GBps": round(total / span / 1e9, 1),
-            "p50_ms": round(float(np.percentile(lats, 50)), 4), "p99_ms": round(float(np.percentile(lats, 99)), 4),
-            "completed": int(st["completed"]), "failed": int(st["failed"])}
+        rs = runs[mode]
+        out = {}
+        for key, nd in (("requests_per_s", 1), ("hbm_GBps", 1), ("p50_ms", 4), ("p99_ms", 4)):
+            vals = [r[key] for r in rs]
+            out[key] = round(float(np.median(vals)), nd)
+            out[key + "_runs"] = [round(v, nd) for v in vals]
+        out["completed"] = sum(r["completed"] for r in rs)
+        out["failed"] = sum(r["failed"] for r in rs)
+        res[SERVE_NAMES[mode]] = out
     del pool
     return res
 

@@ -309,9 +309,9 @@ VDEV bool hasTail(const ServeReq* q) {
   return q->count % E != 0;
 }
 
-// A large request whose first tile has waited this long since its ingest
-// takes the CTAs ahead of small requests (small requests go first only as
-// long as they do not starve a large one).
+// Small requests go first, as long as they do not starve a large one: when
+// the large queue's head was ingested this much earlier than the small
+// queue's head, the large queue goes first.
 constexpr unsigned long long kLargeUrgentNs = 500000;
 
 // ---- CTA 0, warp 0: ingest ring entries firstSeq, firstSeq + 1, ... in order
@@ -346,16 +346,16 @@ __device__ void ingest(const TileArgs& a) {
     got = __shfl_sync(0xffffffffu, got, 0);
     if (stop) break;
     if (!got) {
-      if (lane == 0) {   // between arrivals: how long has the large queue's head waited
-        const unsigned long long h = ldVol(&q->head[1]), t = ldVol(&q->tail[1]);
-        unsigned long long urgent = 0;
-        if (h < t) {
-          const unsigned long long en = ldVol(&q->entry[1][h % kTileRing]);
-          if ((en >> 32) == (h & 0xffffffffull)) {
-            const int s = (int)(en & 0xffffffffull) - 1;
-            urgent = globaltimer() - ldVol(&a.state[s].tStart) > kLargeUrgentNs ? 1 : 0;
+      if (lane == 0) {   // between arrivals: compare the two queues' heads
+        unsigned long long ts[2] = {0, 0};   // ingest times of the heads (0: none)
+        for (int c = 0; c < 2; c++) {
+          const unsigned long long h = ldVol(&q->head[c]), t = ldVol(&q->tail[c]);
+          if (h < t) {
+            const unsigned long long en = ldVol(&q->entry[c][h % kTileRing]);
+            if ((en >> 32) == (h & 0xffffffffull)) ts[c] = ldVol(&a.state[(int)(en & 0xffffffffull) - 1].tStart);
           }
         }
+        const unsigned long long urgent = (ts[0] && ts[1] && ts[1] + kLargeUrgentNs < ts[0]) ? 1 : 0;
         if (urgent != ldVol(&q->urgent)) stVol(&q->urgent, urgent);
       }
       __nanosleep(256);
