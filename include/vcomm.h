@@ -331,8 +331,8 @@ vResult_t vcommGetTuneTable(vcomm_t comm, int coll, vPlan_t* plans, size_t* byte
  * first queued request that has tiles left; the tiles of 16-byte aligned
  * buffers move through shared memory by bulk copies (the group launch's
  * tile engine).  So a request starts as soon as a CTA is free, small
- * requests overtake large ones at tile boundaries (until the first large
- * request has waited 0.5 ms: then it goes first), and the CTA that finishes
+ * requests overtake large ones at tile boundaries (unless the first large
+ * request was queued 0.5 ms before the first small one), and the CTA that finishes
  * a request's last tile reports its completion to host memory.  Plans as in mode 1 (results bit-identical); other protocols are
  * refused (vUnsupported).  The kernel returns after idleTimeoutSec without
  * work and is started again by the next request.
