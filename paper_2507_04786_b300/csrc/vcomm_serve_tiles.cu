@@ -1,17 +1,21 @@
-// vcomm_serve_tiles.cu -- serving mode 3: direct-protocol requests as tiles
-// of one resident kernel.
+// vcomm_serve_tiles.cu -- the tile engine: direct-protocol collectives cut
+// into tiles and run by resident CTAs, one per SM.  Two kernels use it:
+// kBatchTiles runs a group call's direct calls in one launch (the tiles laid
+// end to end, CTA j taking tiles j, j + grid, ...), and kServeTiles is
+// serving mode 3.
 //
-// The host appends requests to a ring in host-mapped memory.  CTA 0 of the
-// kernel (one warp) ingests them in order: it copies each entry into device
-// state and publishes it on one of two device queues, small requests and
-// large ones.  Every other CTA takes the next tile of the first request of
-// the small queue that still has tiles, else of the large queue, and folds
-// its 16-byte units exactly as the direct protocol's kernels do (each unit's
-// ring chain in the ring schedule's order, so the bits are those of a
-// per-call launch with the same plan).  The CTA that finishes a request's
-// last tile writes its completion into host-mapped memory.  A small request
-// that arrives while a large one runs takes the next free CTAs, so it waits
-// for a tile at most, never for the large request; large requests share the
+// Serving: the host appends requests to a ring in host-mapped memory.  CTA
+// 0 of the kernel (one warp) ingests them in order: it copies each entry
+// into device state and publishes it on one of two device queues, small
+// requests and large ones.  Every other CTA takes the next tile of the first
+// request of the small queue that still has tiles, else of the large queue
+// (the large queue first when its head was queued well before the small
+// queue's head), and folds its 16-byte units exactly as the direct
+// protocol's kernels do (each unit's ring chain in the ring schedule's order,
+// so the bits are those of a per-call launch with the same plan).  The CTA
+// that finishes a request's last tile writes its completion into host-mapped
+// memory.  A small request that arrives while a large one runs takes the
+// next free CTAs, so it waits for a tile at most; large requests share the
 // GPU tile by tile in arrival order.
 //
 // Data movement.  A tile of a 16-byte aligned request is a byte range of one
@@ -20,11 +24,13 @@
 // issues bulk asynchronous copies of a sub-tile's inputs (k for a reduction,
 // one for a copy; a lane per rank) into one of three stages; eight consumer
 // warps fold the stage into an output buffer; the producer bulk-stores it to
-// every output.  Producer and consumers meet only on mbarriers, so the producer's
-// claims, stores and completions overlap the folds, and the stages run ahead
-// across tile boundaries.  ReduceScatter blocks that are not whole 16-byte
-// units load a window one unit longer and cut each 16-byte piece out of two
-// aligned ones.  Requests that are not 16-byte aligned take the register
+// every output.  Producer and consumers meet only on mbarriers, so the
+// producer's claims, stores and completions overlap the folds, and the
+// stages run ahead across tile boundaries.  ReduceScatter blocks that are
+// not whole 16-byte units load a window one unit longer and cut each 16-byte
+// piece out of two aligned ones; AllGather blocks that are not whole units
+// are stored to their aligned destination units, their edge bytes with
+// ordinary stores.  Requests that are not 16-byte aligned take the register
 // kernels' element-wise path, one tile at a time.
 //
 // No CTA waits on another: claims and completions are atomics.  Within a
@@ -579,8 +585,6 @@ constexpr int kMaxPendingDone = kDoneLag + 4;
 VDEV void mbarArrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smemU32(bar)) : "memory");
 }
-// every committed bulk group has finished reading its shared memory
-VDEV void bulkWaitRead0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 
 // The producer's state (kept in shared memory: the thread's local memory
 // mostly lives in L2 when shared memory takes the SM's on-chip storage).
