@@ -398,13 +398,15 @@ __device__ void ingest(const TileArgs& a) {
   }
 }
 
-// ---- where tiles come from.  The engine below calls a source from lane 0
-// of its producer warp:
-//   claim(&tile)        the next tile: an op id (>= 0) and its tile index; -1: none now
-//   fetch(id, tile, &w, dst, scratch, lane)
-//                       (every lane) the op's description into shared memory
-//                       and the tile's work: a byte range of one block
-//                       (staged), or a range of the register kernels' units
+// ---- where tiles come from.  The engine below calls a source from its
+// producer warp:
+//   take(&w, dst, scratch, lane)
+//                       (every lane) claim the next tile: its op id (>= 0, or
+//                       -1: none now), the op's description into shared
+//                       memory (dst) and the tile's work (w): a byte range of
+//                       one block (staged), or a range of the register
+//                       kernels' units
+//   (lane 0)
 //   done(id)            a tile of op `id` has completed (its stores are visible)
 //   finished()          no tile will come any more
 //   fail()              a bulk copy did not complete in time
@@ -435,45 +437,56 @@ VDEV void registerGeom(unsigned long long tile, unsigned long long tileUnits, un
 struct ServeSource {
   static constexpr bool kReportsDone = true;
   const TileArgs& a;
-  VDEV long long claim(unsigned long long* tile) {
+  // lane 0 finds the first queued request that may have tiles left and
+  // claims a tile of it with an atomic; meanwhile every lane fetches that
+  // request's state (request and geometry) into `scratch`, a word per lane
+  // at a time, so the claim and the fetch take one round trip together.  A
+  // claim past the request's last tile moves the queue's head on and tries
+  // the next request.
+  VDEV long long take(TileWork* w, ServeReq* dst, unsigned long long* scratch, int lane) {
     TileQueues* q = a.q;
-    const int first = ldVol(&q->urgent) ? 1 : 0;   // the large queue first when its head starves
-    for (int i = 0; i < 2; i++) {
-      const int c = i ^ first;
-      unsigned long long h = ldVol(&q->head[c]);
-      const unsigned long long t = ldAcquire(&q->tail[c]);
-      while (h < t) {
-        const unsigned long long e = ldVol(&q->entry[c][h % kTileRing]);
-        if ((e >> 32) != (h & 0xffffffffull)) break;   // not this position (cannot happen after tail)
-        const int s = (int)(e & 0xffffffffull) - 1;
-        TileState* st = &a.state[s];
-        const unsigned long long tl = atomicAdd(&st->next, 1ull);
-        if (tl < ldVol(&st->ntiles)) {
-          *tile = tl;
-          return s;
+    int c = 0, tries = 0;
+    if (lane == 0) c = ldVol(&q->urgent) ? 1 : 0;   // the large queue first when its head starves
+    c = __shfl_sync(0xffffffffu, c, 0);
+    while (tries < 2) {
+      int s = -1;
+      unsigned long long h = 0, tl = 0;
+      if (lane == 0) {
+        h = ldVol(&q->head[c]);
+        const unsigned long long t = ldAcquire(&q->tail[c]);
+        if (h < t) {
+          const unsigned long long en = ldVol(&q->entry[c][h % kTileRing]);
+          if ((en >> 32) == (h & 0xffffffffull)) {   // (always, once the tail is past it)
+            s = (int)(en & 0xffffffffull) - 1;
+            tl = atomicAdd(&a.state[s].next, 1ull);
+          }
         }
-        atomicCAS(&q->head[c], h, h + 1);               // every tile of entry h is claimed
-        h++;
       }
+      s = __shfl_sync(0xffffffffu, s, 0);
+      if (s < 0) {   // this queue is empty: the other one
+        c ^= 1;
+        tries++;
+        continue;
+      }
+      const unsigned long long* src = (const unsigned long long*)&a.state[s];
+      for (int i = lane; i < kTileStateWords; i += 32) scratch[i] = ldVol(&src[i]);
+      tl = __shfl_sync(0xffffffffu, tl, 0);
+      __syncwarp();
+      const TileState* st = (const TileState*)scratch;
+      if (tl < st->ntiles) {
+        for (int i = lane; i < (int)(sizeof(ServeReq) / 8); i += 32)
+          ((unsigned long long*)dst)[i] = ((const unsigned long long*)&st->req)[i];
+        if (lane == 0) {
+          if (st->staged) stagedGeom(tl, st->perBlock, st->tileBytes, st->blockBytes, st->ntiles, w);
+          else registerGeom(tl, st->tileUnits, st->units, st->ntiles, w);
+        }
+        __syncwarp();
+        return s;
+      }
+      if (lane == 0) atomicCAS(&q->head[c], h, h + 1);   // every tile of entry h is claimed
+      __syncwarp();
     }
     return -1;
-  }
-  // every lane of the producer warp: the op's state (request and geometry)
-  // into `scratch`, a word per lane at a time, then the request into `dst`
-  // and the tile's work into `w` (lane 0)
-  VDEV void fetch(long long id, unsigned long long tile, TileWork* w, ServeReq* dst, unsigned long long* scratch,
-                  int lane) {
-    const unsigned long long* src = (const unsigned long long*)&a.state[id];
-    for (int i = lane; i < kTileStateWords; i += 32) scratch[i] = ldVol(&src[i]);
-    __syncwarp();
-    const TileState* st = (const TileState*)scratch;
-    for (int i = lane; i < (int)(sizeof(ServeReq) / 8); i += 32)
-      ((unsigned long long*)dst)[i] = ((const unsigned long long*)&st->req)[i];
-    if (lane == 0) {
-      if (st->staged) stagedGeom(tile, st->perBlock, st->tileBytes, st->blockBytes, st->ntiles, w);
-      else registerGeom(tile, st->tileUnits, st->units, st->ntiles, w);
-    }
-    __syncwarp();
   }
   // the CTA that finishes a request's last tile reports the request
   VDEV void done(long long id) {
@@ -505,22 +518,21 @@ struct BatchSource {
   static constexpr bool kReportsDone = false;   // the launch's end is the group's completion
   const TileBatchArgs& b;
   unsigned long long next;
-  VDEV long long claim(unsigned long long* tile) {
-    if (next >= b.totalTiles) return -1;
-    int lo = 0, hi = b.nops - 1;   // the op whose tiles hold `next`
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) / 2;
-      if (b.ops[mid].tileStart <= next) lo = mid;
-      else hi = mid - 1;
-    }
-    *tile = next - b.ops[lo].tileStart;
-    next += gridDim.x;
-    return lo;
-  }
-  // lane 0: the op's description from the launch's parameters
-  VDEV void fetch(long long id, unsigned long long tile, TileWork* w, ServeReq* dst, unsigned long long*, int lane) {
-    if (lane == 0) {
-      const TileOpDesc& o = b.ops[id];
+  // lane 0: the op whose tiles hold `next`, its description from the
+  // launch's parameters and the tile's work
+  VDEV long long take(TileWork* w, ServeReq* dst, unsigned long long*, int lane) {
+    long long id = -1;
+    if (lane == 0 && next < b.totalTiles) {
+      int lo = 0, hi = b.nops - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (b.ops[mid].tileStart <= next) lo = mid;
+        else hi = mid - 1;
+      }
+      id = lo;
+      const unsigned long long tile = next - b.ops[lo].tileStart;
+      next += gridDim.x;
+      const TileOpDesc& o = b.ops[lo];
       dst->coll = o.coll;
       dst->proto = kDirect;
       dst->dtype = o.dtype;
@@ -541,7 +553,9 @@ struct BatchSource {
       if (o.staged) stagedGeom(tile, o.perBlock, o.tileBytes, o.blockBytes, o.ntiles, w);
       else registerGeom(tile, o.tileUnits, o.units, o.ntiles, w);
     }
+    id = (long long)__shfl_sync(0xffffffffu, (unsigned long long)id, 0);
     __syncwarp();
+    return id;
   }
   VDEV void done(long long) {}
   VDEV bool finished() { return next >= b.totalTiles; }
@@ -689,17 +703,12 @@ __device__ __forceinline__ bool fillStage(Src& src, EngineSmem& e, unsigned char
   StageInfo& si = e.sInfo[stg];
   uint64_t* bar = &e.full[stg];
   if (p.curId < 0) {
-    unsigned long long tl = 0;
-    long long id = -1;
-    int fin = 0;
-    if (lane == 0) {
-      id = src.claim(&tl);
-      if (id < 0) fin = src.finished() ? 1 : 0;
-    }
-    id = (long long)__shfl_sync(kFullMask, (unsigned long long)id, 0);
-    fin = __shfl_sync(kFullMask, fin, 0);
+    // no staged tile is in progress: sCur is free for the next one
+    const long long id = src.take(&e.work, &e.sCur, e.scratch, lane);
     if (id < 0) {
-      if (!fin) return false;
+      int fin = 0;
+      if (lane == 0) fin = src.finished() ? 1 : 0;
+      if (!__shfl_sync(kFullMask, fin, 0)) return false;
       flushDone(src, p, lane);
       if (lane == 0) {
         si.kind = kStageStop;
@@ -710,8 +719,6 @@ __device__ __forceinline__ bool fillStage(Src& src, EngineSmem& e, unsigned char
       __syncwarp();
       return true;
     }
-    tl = __shfl_sync(kFullMask, tl, 0);
-    src.fetch(id, tl, &e.work, &e.sCur, e.scratch, lane);   // no staged tile is in progress
     int staged = 0;
     if (lane == 0) {
       const TileWork w = e.work;
