@@ -319,6 +319,7 @@ VDEV bool hasTail(const ServeReq* q) {
 // the large queue's head was ingested this much earlier than the small
 // queue's head, the large queue goes first.
 constexpr unsigned long long kLargeUrgentNs = 500000;
+constexpr unsigned long long kAgeCheckNs = 20000;   // how often the ingester compares the heads
 
 // ---- CTA 0, warp 0: ingest ring entries firstSeq, firstSeq + 1, ... in order
 __device__ void ingest(const TileArgs& a) {
@@ -326,7 +327,7 @@ __device__ void ingest(const TileArgs& a) {
   TileQueues* q = a.q;
   volatile TileCtl* ctl = a.ctl;
   unsigned long long next = a.firstSeq;
-  uint64_t idle0 = globaltimer(), drain0 = 0;
+  uint64_t idle0 = globaltimer(), drain0 = 0, lastAge = 0;
   constexpr int kWords = (int)(offsetof(TileReq, seq) / 8);   // req .. klass
   static_assert(offsetof(TileReq, seq) == offsetof(TileState, next), "TileReq / TileState layouts differ");
   while (true) {
@@ -352,7 +353,9 @@ __device__ void ingest(const TileArgs& a) {
     got = __shfl_sync(0xffffffffu, got, 0);
     if (stop) break;
     if (!got) {
-      if (lane == 0) {   // between arrivals: compare the two queues' heads
+      const uint64_t now = lane == 0 ? globaltimer() : 0;
+      if (lane == 0 && now - lastAge > kAgeCheckNs) {   // between arrivals: compare the two queues' heads
+        lastAge = now;
         unsigned long long ts[2] = {0, 0};   // ingest times of the heads (0: none)
         for (int c = 0; c < 2; c++) {
           const unsigned long long h = ldVol(&q->head[c]), t = ldVol(&q->tail[c]);
