@@ -31,7 +31,7 @@ EXPORTS = ("vcommInit", "vcommInitConfig", "vcommPrepare", "vcommDestroy", "vcom
            "vcommGetGroupPlans", "vcommTune", "vcommGetTuneTable", "vcommDebugSetSkipRank",
            "vServeCreate", "vServeSubmit", "vServeQuery", "vServeRelease", "vServeGetStats",
            "vServeDestroy", "vSend", "vRecv", "vAllToAll", "vcommAbortPending", "vcommReset",
-           "vDebugHopLatency")
+           "vDebugHopLatency", "vDebugTileGeometry")
 
 
 class VcommError(RuntimeError):
@@ -106,6 +106,8 @@ def load_library():
     L.vcommDebugSetSkipRank.argtypes = [vp, i32]
     L.vDebugHopLatency.argtypes = [i32, ctypes.POINTER(i32), i32, i32, ctypes.c_double,
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
+    L.vDebugTileGeometry.argtypes = [i32, i32, ctypes.c_uint64, i32, i32, ctypes.c_uint64, ctypes.c_uint64,
+                                     ctypes.POINTER(ctypes.c_uint64)]
     L.vServeCreate.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ServeConfig)]
     L.vServeSubmit.argtypes = [vp, i32, pp, sz, i32, i32, i32, i32, i32, ctypes.c_int64,
                                ctypes.POINTER(ctypes.c_uint64)]
@@ -439,6 +441,20 @@ def debug_hop_latency(proto: str, sms=None, n: int = 0, laps: int = 1000, timeou
     _check(load_library().vDebugHopLatency(PROTO_CODES[proto], arr, n, laps, ctypes.c_double(timeout_sec),
                                            ctypes.byref(ns), out), "vDebugHopLatency")
     return ns.value, list(out)
+
+
+TILE_COLLS = {"allreduce": 0, "reducescatter": 1, "allgather": 2, "broadcast": 3, "reduce": 4}
+
+
+def debug_tile_geometry(coll: str, nranks: int, count: int, dtype_size: int, vec: int,
+                        workers: int = 147, iter_units: int = 256) -> dict:
+    """The tiles the tile engine cuts a direct-protocol op into
+    (vDebugTileGeometry; host arithmetic, no device)."""
+    out = (ctypes.c_uint64 * 8)()
+    _check(load_library().vDebugTileGeometry(TILE_COLLS[coll], nranks, count, dtype_size, vec, workers,
+                                             iter_units, out), "vDebugTileGeometry")
+    keys = ("staged", "units", "tileUnits", "blockBytes", "tileBytes", "perBlock", "ntiles", "vec")
+    return dict(zip(keys, [int(v) for v in out]))
 
 
 def debug_encode(proto: str, src, nbytes: int, flag: int, lines, stream=None):

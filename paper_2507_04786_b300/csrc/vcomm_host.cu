@@ -1641,6 +1641,24 @@ vResult_t vcommGetTuneTable(vcomm_t c, int coll, vPlan_t* plans, size_t* bytes, 
   return vSuccess;
 }
 
+// ------------------------------------------------------------------ debug: tile geometry
+vResult_t vDebugTileGeometry(int coll, int nranks, unsigned long long count, int dtypeSize, int vec,
+                             unsigned long long workers, unsigned long long iter, unsigned long long* out) {
+  if (!out || coll < kAllReduce || coll > kReduce || nranks < 1 || nranks > kServeMaxRanks ||
+      !(dtypeSize == 1 || dtypeSize == 2 || dtypeSize == 4) || vec < 0 || vec > 2 || iter == 0)
+    return vInvalidArgument;
+  const TileGeometry g = tileGeometry(coll, nranks, count, dtypeSize, vec, workers, iter);
+  out[0] = g.staged;
+  out[1] = g.units;
+  out[2] = g.tileUnits;
+  out[3] = g.blockBytes;
+  out[4] = g.tileBytes;
+  out[5] = g.perBlock;
+  out[6] = g.ntiles;
+  out[7] = (unsigned long long)g.vec;
+  return vSuccess;
+}
+
 // ------------------------------------------------------------------ debug codecs
 static std::mutex gDbgMu;
 static int* gDbgClaim = nullptr;
