@@ -224,13 +224,22 @@ VDEV void reportFailure(const KernArgs& a, int code, int rank, int ch, int where
 // After ~1024 polls (a few microseconds: a chain's pipeline filling, not a
 // step's hand-over) the poller sleeps between polls, so that it stops taking
 // issue slots and L2 requests from a CTA moving data on the same SM.
+// *seen (if given): the value that satisfied the wait.
 VDEV bool waitGeq(const KernArgs& a, const unsigned long long* p, uint64_t v, int rank, int ch,
-                  int where) {
-  if (ldAcquire(p) >= v) return true;
+                  int where, uint64_t* seen = nullptr) {
+  uint64_t x = ldAcquire(p);
+  if (x >= v) {
+    if (seen) *seen = x;
+    return true;
+  }
   uint64_t t0 = globaltimer();
   unsigned it = 0;
   while (true) {
-    if (ldAcquire(p) >= v) return true;
+    x = ldAcquire(p);
+    if (x >= v) {
+      if (seen) *seen = x;
+      return true;
+    }
     if (it >= 1024) __nanosleep(128);
     if (((++it) & 127u) == 0) {
       if (*a.abortFlag) { reportFailure(a, vAborted, rank, ch, where); return false; }
@@ -466,6 +475,7 @@ struct Prims {
   const ConnDev* sc1;
   int nrc, nsc;
   uint64_t rstep0, rstep1, sstep0, sstep1;
+  uint64_t credit0, credit1;   // LL128, thread 0: the receivers' head last seen (slots freed)
 
   VDEV Prims(const KernArgs& args, int tid_, int nthr_, int barId_, volatile int* sAbort_, int rank_,
              int ch_, const ConnDev* r0, const ConnDev* r1, const ConnDev* s0, const ConnDev* s1)
@@ -483,6 +493,7 @@ struct Prims {
     rstep1 = rc1 ? ldAcquire(rc1->head) : 0;
     sstep0 = sc0 ? ldAcquire(sc0->tail) : 0;
     sstep1 = sc1 ? ldAcquire(sc1->tail) : 0;
+    credit0 = credit1 = 0;
   }
 
   VDEV void bar() { groupBar(barId, nthr); }
@@ -499,9 +510,19 @@ struct Prims {
         if (ok && nrc > 1) ok = waitGeq(a, rc1->tail, rstep1 + 1, rank, ch, 1);
       }
       if (doSend && ok) {
+        // a slot is free once the receiver's head has passed it; the head
+        // seen last usually covers several steps, so it is read again only
+        // when it does not
         const uint64_t ns = (uint64_t)a.nsteps;
-        if (sstep0 + 1 > ns) ok = waitGeq(a, sc0->head, sstep0 + 1 - ns, rank, ch, 2);
-        if (ok && nsc > 1 && sstep1 + 1 > ns) ok = waitGeq(a, sc1->head, sstep1 + 1 - ns, rank, ch, 2);
+        if (PROTO != kLL128) {   // Simple's steps are long; LL's kernel has no registers to spare
+          if (sstep0 + 1 > ns) ok = waitGeq(a, sc0->head, sstep0 + 1 - ns, rank, ch, 2);
+          if (ok && nsc > 1 && sstep1 + 1 > ns) ok = waitGeq(a, sc1->head, sstep1 + 1 - ns, rank, ch, 2);
+        } else {
+          if (sstep0 + 1 > ns && credit0 < sstep0 + 1 - ns)
+            ok = waitGeq(a, sc0->head, sstep0 + 1 - ns, rank, ch, 2, &credit0);
+          if (ok && nsc > 1 && sstep1 + 1 > ns && credit1 < sstep1 + 1 - ns)
+            ok = waitGeq(a, sc1->head, sstep1 + 1 - ns, rank, ch, 2, &credit1);
+        }
       }
       if (!ok) *sAbort = 1;
     }
@@ -525,8 +546,17 @@ struct Prims {
         }
       }
       if (doRecv) {
-        stRelease(rc0->head, rstep0 + 1);
-        if (nrc > 1) stRelease(rc1->head, rstep1 + 1);
+        // the slot's reads have all returned (the barrier above): Simple
+        // orders them before the credit with a release store; LL / LL128
+        // publish data through the lines' flags, so their credit needs no
+        // fence on the step's path
+        if (PROTO == kSimple) {
+          stRelease(rc0->head, rstep0 + 1);
+          if (nrc > 1) stRelease(rc1->head, rstep1 + 1);
+        } else {
+          stRelaxed(rc0->head, rstep0 + 1);
+          if (nrc > 1) stRelaxed(rc1->head, rstep1 + 1);
+        }
       }
     }
     if (doSend) { sstep0++; sstep1++; }
