@@ -824,7 +824,21 @@ static vResult_t launchSingle(CallSpec& cs) {
 
   // co-residency: every CTA of the launch spins on its peers
   int nsub = (cs.al == kTree) ? 2 * plan.nchannels : plan.nchannels;
-  const int nthrMax = std::min(c->nthreads, maxThreadsFor(cs.pr));
+  int nthrMax = std::min(c->nthreads, maxThreadsFor(cs.pr));
+  // LL / LL128 on small calls: a step moves a few KiB, and a CTA of 256
+  // threads turns its barriers and polls around faster than one of 1024
+  // (16-vrank ring AllGather at 64 KiB per rank: 49.9 -> 37.3 us); chains
+  // and trees whose steps are larger keep the wider CTA (Broadcast of 64 KiB
+  // over 8 channels: 16.2 us wide, 25.7 us narrow).  Same results.
+  if (cs.pr == kLL || cs.pr == kLL128) {
+    const unsigned long long unitB = cs.bytesUnits ? 1ull : (unsigned long long)dtypeSize(cs.dtype);
+    // the larger buffer of a vrank: ReduceScatter's send, AllGather's receive
+    const bool blocks = cs.kcoll == kReduceScatter || cs.kcoll == kAllGather;
+    const unsigned long long perRank = (blocks ? (unsigned long long)k : 1ull) * cs.units * unitB;
+    const unsigned long long perCh = perRank / (unsigned long long)std::max(1, plan.nchannels);
+    const bool ringBlocks = cs.al == kRing && blocks;
+    if ((ringBlocks && perRank <= (64ull << 10)) || perCh <= (4ull << 10)) nthrMax = std::min(nthrMax, 256);
+  }
   int nthr = nthrMax;
   while (true) {
     int per = residentPerSM(fn, nthr);
