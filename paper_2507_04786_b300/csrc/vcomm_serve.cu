@@ -11,7 +11,11 @@
 // large requests, narrow gangs the small ones.  A request's plan (protocol,
 // channels, chunk) depends only on the request, so its result is the same
 // alone and in any mix.  Mode "plain" runs the same stream of requests as one
-// ordinary collective launch each, on one stream, for comparison.
+// ordinary collective launch each, on one stream, for comparison; mode
+// "streams" launches each request on a lane of streams; mode "tiles" (the
+// direct protocol only) posts each admitted request to a ring in host-mapped
+// memory that one resident tile-engine kernel ingests, its CTAs taking the
+// requests' tiles from device queues (vcomm_serve_tiles.cu).
 #include <cuda_runtime.h>
 
 #include <algorithm>
