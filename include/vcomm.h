@@ -449,13 +449,15 @@ vResult_t vDebugDecode(vProto_t proto, const void* lines, size_t nbytes, uint64_
  * dtypeSize 1, 2 or 4; vec as the direct protocol's access kind (0 element
  * accesses, 1 aligned 16-byte units, 2 aligned buffers whose RS / AG blocks
  * are not whole units); workers: the CTAs that take tiles; iter: units per
- * register-path iteration.  out[8]: staged (1: byte ranges of a block moved
+ * register-path iteration; shared: 1 for a group launch (tiles shared out
+ * statically), 0 for serving (claimed one at a time).  out[8]: staged (1: byte ranges of a block moved
  * by bulk copies), units and tileUnits (register path), blockBytes,
  * tileBytes and perBlock (staged: bytes of a block moved by bulk copies, per
  * tile, tiles per block), ntiles, and the access kind the engine uses.
  * vInvalidArgument for out == NULL or arguments out of range. */
 vResult_t vDebugTileGeometry(int coll, int nranks, unsigned long long count, int dtypeSize, int vec,
-                             unsigned long long workers, unsigned long long iter, unsigned long long* out);
+                             unsigned long long workers, unsigned long long iter, int shared,
+                             unsigned long long* out);
 
 vResult_t vDebugHopLatency(vProto_t proto, const int* ringSms, int n, int laps, double timeoutSec,
                            double* nsPerHop, int* smOut);

@@ -106,7 +106,7 @@ def load_library():
     L.vcommDebugSetSkipRank.argtypes = [vp, i32]
     L.vDebugHopLatency.argtypes = [i32, ctypes.POINTER(i32), i32, i32, ctypes.c_double,
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
-    L.vDebugTileGeometry.argtypes = [i32, i32, ctypes.c_uint64, i32, i32, ctypes.c_uint64, ctypes.c_uint64,
+    L.vDebugTileGeometry.argtypes = [i32, i32, ctypes.c_uint64, i32, i32, ctypes.c_uint64, ctypes.c_uint64, i32,
                                      ctypes.POINTER(ctypes.c_uint64)]
     L.vServeCreate.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ServeConfig)]
     L.vServeSubmit.argtypes = [vp, i32, pp, sz, i32, i32, i32, i32, i32, ctypes.c_int64,
@@ -447,12 +447,13 @@ TILE_COLLS = {"allreduce": 0, "reducescatter": 1, "allgather": 2, "broadcast": 3
 
 
 def debug_tile_geometry(coll: str, nranks: int, count: int, dtype_size: int, vec: int,
-                        workers: int = 147, iter_units: int = 256) -> dict:
+                        workers: int = 147, iter_units: int = 256, shared: bool = False) -> dict:
     """The tiles the tile engine cuts a direct-protocol op into
-    (vDebugTileGeometry; host arithmetic, no device)."""
+    (vDebugTileGeometry; host arithmetic, no device); shared: for a group
+    launch (tiles shared out statically) rather than serving."""
     out = (ctypes.c_uint64 * 8)()
     _check(load_library().vDebugTileGeometry(TILE_COLLS[coll], nranks, count, dtype_size, vec, workers,
-                                             iter_units, out), "vDebugTileGeometry")
+                                             iter_units, int(shared), out), "vDebugTileGeometry")
     keys = ("staged", "units", "tileUnits", "blockBytes", "tileBytes", "perBlock", "ntiles", "vec")
     return dict(zip(keys, [int(v) for v in out]))
 

@@ -1095,7 +1095,7 @@ static vResult_t launchTileGroup(vcomm* c, std::vector<CallSpec>& ops, unsigned 
       OpTiles t{i, directGeom(o), {}, 0};
       const int esz = dtypeSize(o.dtype);
       t.tg = tileGeometry(o.kcoll, k, o.units, esz, t.g.vec, (unsigned long long)c->nsm,
-                          (unsigned long long)serveTilesUnitsPerIter());
+                          (unsigned long long)serveTilesUnitsPerIter(), true);
       const bool copy = o.kcoll == kAllGather || o.kcoll == kBroadcast;
       const unsigned long long factor = o.kcoll == kAllReduce ? 2ull * k : (unsigned long long)k + 1;
       const unsigned long long unitBytes = t.tg.vec == 0 ? (copy ? 1ull : (unsigned long long)esz) : 16ull;
@@ -1657,11 +1657,12 @@ vResult_t vcommGetTuneTable(vcomm_t c, int coll, vPlan_t* plans, size_t* bytes, 
 
 // ------------------------------------------------------------------ debug: tile geometry
 vResult_t vDebugTileGeometry(int coll, int nranks, unsigned long long count, int dtypeSize, int vec,
-                             unsigned long long workers, unsigned long long iter, unsigned long long* out) {
+                             unsigned long long workers, unsigned long long iter, int shared,
+                             unsigned long long* out) {
   if (!out || coll < kAllReduce || coll > kReduce || nranks < 1 || nranks > kServeMaxRanks ||
       !(dtypeSize == 1 || dtypeSize == 2 || dtypeSize == 4) || vec < 0 || vec > 2 || iter == 0)
     return vInvalidArgument;
-  const TileGeometry g = tileGeometry(coll, nranks, count, dtypeSize, vec, workers, iter);
+  const TileGeometry g = tileGeometry(coll, nranks, count, dtypeSize, vec, workers, iter, shared != 0);
   out[0] = g.staged;
   out[1] = g.units;
   out[2] = g.tileUnits;

@@ -269,7 +269,7 @@ struct TileGeometry {
   int vec;   // the op's DirectArgs::vec in the engine (register reductions: 0)
 };
 inline TileGeometry tileGeometry(int coll, int k, unsigned long long count, int esz, int vec,
-                                 unsigned long long workers, unsigned long long iter) {
+                                 unsigned long long workers, unsigned long long iter, bool shared = false) {
   TileGeometry g{};
   const bool copy = (coll == kAllGather || coll == kBroadcast);
   const unsigned long long unitBytes = copy ? 1ull : (unsigned long long)esz;
@@ -288,7 +288,13 @@ inline TileGeometry tileGeometry(int coll, int k, unsigned long long count, int 
   g.staged = (stageable && g.blockBytes >= (vec == 2 ? 32u : 16u)) ? 1 : 0;
   if (g.staged) {
     const unsigned long long piece = 4096;
-    const unsigned long long maxTile = std::max<unsigned long long>(piece, kTileMaxTraffic / factor / piece * piece);
+    // shared out statically (group calls): AllReduce tiles of at most 64 KiB,
+    // so that the CTAs sweep neighbouring bytes of every buffer together
+    // (measured 1-6 % faster than traffic-sized tiles on 4..16 vranks; with
+    // tiles claimed one at a time, as in serving, the claims cost more)
+    const unsigned long long cap = std::max<unsigned long long>(piece, kTileMaxTraffic / factor / piece * piece);
+    const unsigned long long maxTile = (shared && coll == kAllReduce) ? std::min<unsigned long long>(cap, 64ull << 10)
+                                                                        : cap;
     unsigned long long tb = (blocks * g.blockBytes + twoW - 1) / twoW;
     tb = std::min(std::max(tb, piece), maxTile);
     tb = (tb + piece - 1) / piece * piece;

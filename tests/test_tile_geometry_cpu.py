@@ -14,7 +14,8 @@ and access kinds:
   inside the block;
 * the register path covers every unit with whole iterations, and its
   reductions go element by element;
-* an op gets about two tiles per worker (whole pieces) unless the cap binds.
+* an op gets about two tiles per worker (whole pieces) unless the cap binds;
+  a group launch's AllReduce tiles are at most 64 KiB.
 """
 import numpy as np
 import pytest
@@ -68,11 +69,18 @@ def test_sweep_is_large():
 
 def test_geometry_properties():
     for case in CASES:
-        check(*case)
+        check(*case, shared=False)
 
 
-def check(coll, k, count, esz, vec):
-    g = debug_tile_geometry(coll, k, count, esz, vec, W, 256)
+def test_group_geometry_properties():
+    """Group launches share tiles out statically: the same properties, with
+    AllReduce tiles of at most 64 KiB."""
+    for case in CASES:
+        check(*case, shared=True)
+
+
+def check(coll, k, count, esz, vec, shared):
+    g = debug_tile_geometry(coll, k, count, esz, vec, W, 256, shared)
     copy = coll in COPY
     blocks = k if coll in BLOCKS else 1
     unit = 1 if copy else esz
@@ -112,7 +120,10 @@ def check(coll, k, count, esz, vec):
         # about two tiles per worker: the smallest whole-piece tile that gives
         # every worker at most two (unless the traffic cap binds first)
         share = -(-(blocks * B) // (2 * W))
-        if (share + PIECE) * factor(coll, k) <= CAP:
+        small = shared and coll == "allreduce"
+        if small:
+            assert T <= max(PIECE, 64 << 10)
+        if (share + PIECE) * factor(coll, k) <= CAP and not (small and share > (64 << 10)):
             assert T >= share and (T == PIECE or T - PIECE < share)
     else:
         assert g["vec"] == (vec if copy else 0)                  # reductions: element by element
