@@ -110,6 +110,7 @@ struct vcomm {
   int treeNode = 1;                  // vranks per node of the hierarchical tree
   // direct AllReduce: bytes per rank from which the staged kernel runs
   unsigned long long stagedMinBytes = 8ull << 20;
+  unsigned long long tileMinBytes = 64ull << 20;  // single calls the tile engine takes, from this size
   bool tileGroups = true;                     // groups of direct calls: one tile-engine launch
   Arena arena[2][3];
   ErrWord* hErr = nullptr;
@@ -210,6 +211,11 @@ vResult_t vcommInitConfig(vcomm_t* comm, int nranks, int nchannels, const vcommC
     char* end = nullptr;
     const unsigned long long v = strtoull(env, &end, 10);
     if (end && end != env && *end == 0) c->stagedMinBytes = v;
+  }
+  if (const char* env = getenv("VCOMM_TILE_MIN_BYTES")) {
+    char* end = nullptr;
+    const unsigned long long v = strtoull(env, &end, 10);
+    if (end && end != env && *end == 0) c->tileMinBytes = v;
   }
   vResult_t r = fromCuda(cudaGetDevice(&c->dev));
   if (r == vSuccess) r = fromCuda(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->dev));
@@ -777,6 +783,30 @@ static vResult_t launchCopyCollStaged(CallSpec& cs) {
   return vSuccess;
 }
 
+static unsigned tileStageBytes(int dev);
+static vResult_t launchTileGroup(vcomm* c, std::vector<CallSpec>& ops, unsigned stageBytes);
+
+// Single calls that run faster as a one-call launch of the tile engine (a
+// producer warp issuing bulk copies, eight consumer warps folding) than on
+// the per-call kernels: AllReduce on 12..16 vranks (1.08-1.12x at 64 and 128
+// MiB per rank) and ReduceScatter blocks that are not whole 16-byte units on
+// up to 8 vranks (1.09-1.23x) -- from tileMinBytes per rank (send buffer;
+// 64 MiB, env VCOMM_TILE_MIN_BYTES: at 32 MiB and below a CTA's one or two
+// tiles leave the pipeline filling and draining, and the per-call kernels
+// stay ahead), 32- and 16-bit types, sum or max.  Same fold, same bits.
+static bool useTileEngine(const CallSpec& cs, const DirectGeom& g) {
+  const int k = cs.c->k;
+  if (!cs.c->tileGroups || cs.maxCtas != 0 || cs.postDiv || k < 2 || k > kServeMaxRanks) return false;
+  if (!(cs.dtype == kI32 || cs.dtype == kF32 || cs.dtype == kF16 || cs.dtype == kBF16)) return false;
+  if (!(cs.redop == kSum || cs.redop == kMax)) return false;
+  const unsigned long long perRank =
+      (cs.kcoll == kReduceScatter ? (unsigned long long)k : 1ull) * cs.units * (unsigned long long)dtypeSize(cs.dtype);
+  if (perRank < cs.c->tileMinBytes) return false;
+  if (cs.kcoll == kAllReduce) return g.vec == 1 && k >= 12;
+  if (cs.kcoll == kReduceScatter) return g.vec == 2 && k <= 8;
+  return false;
+}
+
 // The direct protocol: a plain launch over the data, no FIFO, no waits.
 static vResult_t launchDirect(CallSpec& cs) {
   vcomm* c = cs.c;
@@ -799,6 +829,15 @@ static vResult_t launchDirect(CallSpec& cs) {
   a.root = cs.root;
   a.vec = g.vec;
   a.postDiv = cs.postDiv;
+  if (useTileEngine(cs, g)) {
+    const unsigned sb = tileStageBytes(c->dev);
+    if (sb) {
+      std::vector<CallSpec> one{cs};
+      const vResult_t r = launchTileGroup(c, one, sb);
+      if (r == vSuccess) c->last = cs.plan;
+      return r;
+    }
+  }
   if (useStaged(cs, g)) return launchStaged(cs, g, a);
   if (useCopyStaged(cs, g)) return launchCopyCollStaged(cs);
   const unsigned long long units = g.units;
