@@ -16,32 +16,33 @@
 namespace vc {
 
 #define VC_DTYPES_OF(X, P) X(P, 0) X(P, 1) X(P, 2) X(P, 3) X(P, 4) X(P, 5) X(P, 6) X(P, 7) X(P, 8) X(P, 9)
-#define VC_DECL(P, D) __device__ void batchWorker_##P##_##D(const KernArgs&, int, int, volatile int*);
+#define VC_DECL(P, D) __device__ void batchWorker_##P##_##D(const KernArgs&, int, int, WorkerShared*);
 VC_DTYPES_OF(VC_DECL, 0) VC_DTYPES_OF(VC_DECL, 1) VC_DTYPES_OF(VC_DECL, 2)
 #undef VC_DECL
 
 template <int P>
-__device__ __noinline__ void batchCopyWorker(const KernArgs& a, int r, int ch, volatile int* sAbort) {
+__device__ __noinline__ void batchCopyWorker(const KernArgs& a, int r, int ch, WorkerShared* ws) {
   if (a.coll == kCopy) localCopy<uint8_t>(a, ch);
-  else runWorker<P, uint8_t, OpNone>(a, r, ch, sAbort);
+  else runWorker<P, uint8_t, OpNone>(a, r, ch, ws);
 }
 
 __device__ __forceinline__ void dispatchOp(const KernArgs& a, int proto, int dtype, bool bytes,
-                                           int r, int ch, volatile int* sAbort) {
+                                           int r, int ch, WorkerShared* ws) {
   if (bytes) {
-    if (proto == kSimple) batchCopyWorker<kSimple>(a, r, ch, sAbort);
-    else if (proto == kLL) batchCopyWorker<kLL>(a, r, ch, sAbort);
-    else batchCopyWorker<kLL128>(a, r, ch, sAbort);
+    if (proto == kSimple) batchCopyWorker<kSimple>(a, r, ch, ws);
+    else if (proto == kLL) batchCopyWorker<kLL>(a, r, ch, ws);
+    else batchCopyWorker<kLL128>(a, r, ch, ws);
     return;
   }
-#define VC_CASE(P, D) if (proto == P && dtype == D) { batchWorker_##P##_##D(a, r, ch, sAbort); return; }
+#define VC_CASE(P, D) if (proto == P && dtype == D) { batchWorker_##P##_##D(a, r, ch, ws); return; }
   VC_DTYPES_OF(VC_CASE, 0) VC_DTYPES_OF(VC_CASE, 1) VC_DTYPES_OF(VC_CASE, 2)
 #undef VC_CASE
 }
 
 __global__ void __launch_bounds__(512, 1) kBatch(const __grid_constant__ BatchArgs b) {
   __shared__ KernArgs sa;
-  __shared__ int sAbort[2];
+  __shared__ WorkerShared ws;
+  volatile int* sAbort = ws.abort;
   const int k = b.nranks;
   const int per = k * b.cpg;
   const int gang = blockIdx.x / per;
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(512, 1) kBatch(const __grid_constant__ BatchAr
     __syncthreads();
     const bool bytes = (o.coll == kAllGather || o.coll == kBroadcast ||
                         (o.coll == kCopy && o.dtype < 0));
-    dispatchOp(sa, o.proto, o.dtype, bytes, r, ch, sAbort);
+    dispatchOp(sa, o.proto, o.dtype, bytes, r, ch, &ws);
     __syncthreads();
     if (sAbort[0] || sAbort[1]) return;  // a wait failed: the error word says where
   }
@@ -144,7 +145,8 @@ __device__ void dispatchDirect(const ServeReq* q, unsigned long long local, unsi
 
 __global__ void __launch_bounds__(512, 1) kServe(const __grid_constant__ ServeArgs s) {
   __shared__ KernArgs sa;
-  __shared__ int sAbort[2];
+  __shared__ WorkerShared ws;
+  volatile int* sAbort = ws.abort;
   __shared__ int sStop;
   __shared__ int sUse;
   __shared__ int sCh;
@@ -244,7 +246,7 @@ __global__ void __launch_bounds__(512, 1) kServe(const __grid_constant__ ServeAr
       const int dtype = ((const volatile ServeReq*)&G->req)->dtype;
       const bool bytes = (sa.coll == kAllGather || sa.coll == kBroadcast ||
                           (sa.coll == kCopy && dtype < 0));
-      dispatchOp(sa, proto, dtype, bytes, r, ch, sAbort);
+      dispatchOp(sa, proto, dtype, bytes, r, ch, &ws);
     }
     __syncthreads();
     if (threadIdx.x == 0) {

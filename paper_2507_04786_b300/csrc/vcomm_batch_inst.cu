@@ -20,19 +20,19 @@ using VcT = typename DTypeOf<VC_DTYPE>::T;
 // allocation (templated on the protocol and type too: this unit is linked as
 // relocatable device code with its siblings, so the name must be unique)
 template <int P, class T, class Op>
-__device__ __noinline__ void opWorker(const KernArgs& a, int r, int ch, volatile int* sAbort) {
-  runWorker<P, T, Op>(a, r, ch, sAbort);
+__device__ __noinline__ void opWorker(const KernArgs& a, int r, int ch, WorkerShared* ws) {
+  runWorker<P, T, Op>(a, r, ch, ws);
 }
 
 // one op of a batch on CTA (r, ch) of its gang; `a` lives in shared memory
 __device__ __noinline__ void VC_BNAME(VC_PROTO, VC_DTYPE)(const KernArgs& a, int r, int ch,
-                                                         volatile int* sAbort) {
+                                                         WorkerShared* ws) {
   if (a.coll == kCopy) localCopy<VcT>(a, ch);
-  else if (a.redop == kSum) opWorker<VC_PROTO, VcT, OpSum>(a, r, ch, sAbort);
-  else if (a.redop == kMax) opWorker<VC_PROTO, VcT, OpMax>(a, r, ch, sAbort);
-  else if (a.redop == kProd) opWorker<VC_PROTO, VcT, OpProd>(a, r, ch, sAbort);
-  else if (a.redop == kMin) opWorker<VC_PROTO, VcT, OpMin>(a, r, ch, sAbort);
-  else opWorker<VC_PROTO, VcT, OpAvg>(a, r, ch, sAbort);
+  else if (a.redop == kSum) opWorker<VC_PROTO, VcT, OpSum>(a, r, ch, ws);
+  else if (a.redop == kMax) opWorker<VC_PROTO, VcT, OpMax>(a, r, ch, ws);
+  else if (a.redop == kProd) opWorker<VC_PROTO, VcT, OpProd>(a, r, ch, ws);
+  else if (a.redop == kMin) opWorker<VC_PROTO, VcT, OpMin>(a, r, ch, ws);
+  else opWorker<VC_PROTO, VcT, OpAvg>(a, r, ch, ws);
 }
 
 }  // namespace vc

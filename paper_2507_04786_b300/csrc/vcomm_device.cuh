@@ -458,47 +458,86 @@ VDEV bool llReady(const KernArgs& a, const char* slot, unsigned long long p, uin
 }
 
 // ------------------------------------------------------------------ primitives
+// One worker's connections, copied once per launch into shared memory, so
+// that a step's bookkeeping reads no connection descriptor from global memory
+// (the memory clobbers of the flag and counter accesses make the compiler
+// re-read such fields at every step, on the step's critical path).  Index i:
+// receive connections 0, 1, then send connections 0, 1.
+struct ConnCache {
+  char* buf[4];                        // the connection's nsteps slots
+  unsigned long long* mine[4];         // the counter this worker advances: head (receive), tail (send)
+  const unsigned long long* peer[4];   // the counter it waits on: tail (receive), head (send)
+  uint64_t credit[2];                  // thread 0: each send connection's head last seen (slots freed)
+};
+
+// Shared memory of one CTA's FIFO workers: an abort word per worker group
+// (the tree's reduce and broadcast groups stop separately) and a connection
+// cache per barrier id (0: the ring worker or tree root; 1, 2: the tree's
+// reduce and broadcast groups).
+struct WorkerShared {
+  int abort[2];
+  ConnCache cc[3];
+};
+
 // A Prims object is one worker's view of its connections: up to two receive
 // connections (all read by a recv* primitive) and up to two send connections
 // (all written by a *send primitive).  The seven primitives of Sec. V-B are
-// the combinations of (receive?, local input?, send?, user output?).  State
-// is kept in scalars so that it stays in registers.
+// the combinations of (receive?, local input?, send?, user output?).  The
+// FIFO positions are kept in scalars so that they stay in registers, and the
+// slot each connection's next step uses in one packed word (byte i for
+// connection i), advanced with a wrap instead of a modulo.
 template <int PROTO, class T, class Op>
 struct Prims {
   const KernArgs& a;
   int tid, nthr, barId;
   volatile int* sAbort;
+  ConnCache* cc;
   int rank, ch;
-  const ConnDev* rc0;
-  const ConnDev* rc1;
-  const ConnDev* sc0;
-  const ConnDev* sc1;
   int nrc, nsc;
+  uint32_t slots;
   uint64_t rstep0, rstep1, sstep0, sstep1;
-  uint64_t credit0, credit1;   // LL128, thread 0: the receivers' head last seen (slots freed)
 
-  VDEV Prims(const KernArgs& args, int tid_, int nthr_, int barId_, volatile int* sAbort_, int rank_,
-             int ch_, const ConnDev* r0, const ConnDev* r1, const ConnDev* s0, const ConnDev* s1)
-      : a(args), tid(tid_), nthr(nthr_), barId(barId_), sAbort(sAbort_), rank(rank_), ch(ch_) {
+  VDEV Prims(const KernArgs& args, int tid_, int nthr_, int barId_, volatile int* sAbort_, ConnCache* cc_,
+             int rank_, int ch_, const ConnDev* r0, const ConnDev* r1, const ConnDev* s0, const ConnDev* s1)
+      : a(args), tid(tid_), nthr(nthr_), barId(barId_), sAbort(sAbort_), cc(cc_), rank(rank_), ch(ch_) {
     // compact the connection lists: r0/s0 are filled first
-    rc0 = r0 ? r0 : r1;
-    rc1 = r0 ? r1 : nullptr;
-    sc0 = s0 ? s0 : s1;
-    sc1 = s0 ? s1 : nullptr;
-    nrc = (rc0 ? 1 : 0) + (rc1 ? 1 : 0);
-    nsc = (sc0 ? 1 : 0) + (sc1 ? 1 : 0);
+    const ConnDev* c[4] = {r0 ? r0 : r1, r0 ? r1 : nullptr, s0 ? s0 : s1, s0 ? s1 : nullptr};
+    nrc = (c[0] ? 1 : 0) + (c[1] ? 1 : 0);
+    nsc = (c[2] ? 1 : 0) + (c[3] ? 1 : 0);
     // a worker is the only writer of its send conns' tail and its receive
     // conns' head, so their current values are its position in each FIFO
-    rstep0 = rc0 ? ldAcquire(rc0->head) : 0;
-    rstep1 = rc1 ? ldAcquire(rc1->head) : 0;
-    sstep0 = sc0 ? ldAcquire(sc0->tail) : 0;
-    sstep1 = sc1 ? ldAcquire(sc1->tail) : 0;
-    credit0 = credit1 = 0;
+    rstep0 = c[0] ? ldAcquire(c[0]->head) : 0;
+    rstep1 = c[1] ? ldAcquire(c[1]->head) : 0;
+    sstep0 = c[2] ? ldAcquire(c[2]->tail) : 0;
+    sstep1 = c[3] ? ldAcquire(c[3]->tail) : 0;
+    const uint64_t ns = (uint64_t)a.nsteps;
+    slots = (uint32_t)(rstep0 % ns) | ((uint32_t)(rstep1 % ns) << 8) | ((uint32_t)(sstep0 % ns) << 16) |
+            ((uint32_t)(sstep1 % ns) << 24);
+    // the other threads of the worker read the cache after the first step's
+    // barrier (bar.sync orders shared memory among its threads)
+    if (tid == 0) {
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        cc->buf[i] = c[i] ? c[i]->buf : nullptr;
+        cc->mine[i] = c[i] ? (i < 2 ? c[i]->head : c[i]->tail) : nullptr;
+        cc->peer[i] = c[i] ? (i < 2 ? c[i]->tail : c[i]->head) : nullptr;
+      }
+      cc->credit[0] = cc->credit[1] = 0;
+    }
   }
 
   VDEV void bar() { groupBar(barId, nthr); }
-  VDEV char* slotOf(const ConnDev* c, uint64_t step) const {
-    return c->buf + (step % (uint64_t)a.nsteps) * a.slotBytes;
+  // connection i's slot for its next step
+  VDEV char* slotOf(int i) const {
+    return cc->buf[i] + (size_t)((slots >> (8 * i)) & 0xffu) * a.slotBytes;
+  }
+  // advance the slot indices of connections i and i + 1 by one step
+  VDEV void bumpSlots(int i) {
+    const uint32_t ns = (uint32_t)a.nsteps;
+    uint32_t x = ((slots >> (8 * i)) & 0xffu) + 1, y = ((slots >> (8 * i + 8)) & 0xffu) + 1;
+    if (x == ns) x = 0;
+    if (y == ns) y = 0;
+    slots = (slots & ~(0xffffu << (8 * i))) | (x << (8 * i)) | (y << (8 * i + 8));
   }
 
   // wait for data (Simple only) and for send credits, then a group barrier
@@ -506,23 +545,18 @@ struct Prims {
     if (tid == 0) {
       bool ok = true;
       if (PROTO == kSimple && doRecv) {
-        ok = waitGeq(a, rc0->tail, rstep0 + 1, rank, ch, 1);
-        if (ok && nrc > 1) ok = waitGeq(a, rc1->tail, rstep1 + 1, rank, ch, 1);
+        ok = waitGeq(a, cc->peer[0], rstep0 + 1, rank, ch, 1);
+        if (ok && nrc > 1) ok = waitGeq(a, cc->peer[1], rstep1 + 1, rank, ch, 1);
       }
       if (doSend && ok) {
         // a slot is free once the receiver's head has passed it; the head
         // seen last usually covers several steps, so it is read again only
         // when it does not
         const uint64_t ns = (uint64_t)a.nsteps;
-        if (PROTO != kLL128) {   // Simple's steps are long; LL's kernel has no registers to spare
-          if (sstep0 + 1 > ns) ok = waitGeq(a, sc0->head, sstep0 + 1 - ns, rank, ch, 2);
-          if (ok && nsc > 1 && sstep1 + 1 > ns) ok = waitGeq(a, sc1->head, sstep1 + 1 - ns, rank, ch, 2);
-        } else {
-          if (sstep0 + 1 > ns && credit0 < sstep0 + 1 - ns)
-            ok = waitGeq(a, sc0->head, sstep0 + 1 - ns, rank, ch, 2, &credit0);
-          if (ok && nsc > 1 && sstep1 + 1 > ns && credit1 < sstep1 + 1 - ns)
-            ok = waitGeq(a, sc1->head, sstep1 + 1 - ns, rank, ch, 2, &credit1);
-        }
+        if (sstep0 + 1 > ns && cc->credit[0] < sstep0 + 1 - ns)
+          ok = waitGeq(a, cc->peer[2], sstep0 + 1 - ns, rank, ch, 2, &cc->credit[0]);
+        if (ok && nsc > 1 && sstep1 + 1 > ns && cc->credit[1] < sstep1 + 1 - ns)
+          ok = waitGeq(a, cc->peer[3], sstep1 + 1 - ns, rank, ch, 2, &cc->credit[1]);
       }
       if (!ok) *sAbort = 1;
     }
@@ -538,11 +572,11 @@ struct Prims {
     if (tid == 0) {
       if (doSend) {
         if (PROTO == kSimple) {
-          stRelease(sc0->tail, sstep0 + 1);
-          if (nsc > 1) stRelease(sc1->tail, sstep1 + 1);
+          stRelease(cc->mine[2], sstep0 + 1);
+          if (nsc > 1) stRelease(cc->mine[3], sstep1 + 1);
         } else {
-          stRelaxed(sc0->tail, sstep0 + 1);
-          if (nsc > 1) stRelaxed(sc1->tail, sstep1 + 1);
+          stRelaxed(cc->mine[2], sstep0 + 1);
+          if (nsc > 1) stRelaxed(cc->mine[3], sstep1 + 1);
         }
       }
       if (doRecv) {
@@ -551,16 +585,16 @@ struct Prims {
         // publish data through the lines' flags, so their credit needs no
         // fence on the step's path
         if (PROTO == kSimple) {
-          stRelease(rc0->head, rstep0 + 1);
-          if (nrc > 1) stRelease(rc1->head, rstep1 + 1);
+          stRelease(cc->mine[0], rstep0 + 1);
+          if (nrc > 1) stRelease(cc->mine[1], rstep1 + 1);
         } else {
-          stRelaxed(rc0->head, rstep0 + 1);
-          if (nrc > 1) stRelaxed(rc1->head, rstep1 + 1);
+          stRelaxed(cc->mine[0], rstep0 + 1);
+          if (nrc > 1) stRelaxed(cc->mine[1], rstep1 + 1);
         }
       }
     }
-    if (doSend) { sstep0++; sstep1++; }
-    if (doRecv) { rstep0++; rstep1++; }
+    if (doSend) { sstep0++; sstep1++; bumpSlots(2); }
+    if (doRecv) { rstep0++; rstep1++; bumpSlots(0); }
     return true;
   }
 
@@ -581,14 +615,14 @@ struct Prims {
         s0 = (const char*)local;
         ns = 1;
         if (doRecv) {
-          s1 = slotOf(rc0, rstep0);
+          s1 = slotOf(0);
           ns = 2;
-          if (nrc > 1) { s2 = slotOf(rc1, rstep1); ns = 3; }
+          if (nrc > 1) { s2 = slotOf(1); ns = 3; }
         }
       } else {
-        s0 = slotOf(rc0, rstep0);
+        s0 = slotOf(0);
         ns = 1;
-        if (nrc > 1) { s1 = slotOf(rc1, rstep1); ns = 2; }
+        if (nrc > 1) { s1 = slotOf(1); ns = 2; }
       }
       char* d0 = nullptr;
       char* d1 = nullptr;
@@ -596,8 +630,8 @@ struct Prims {
       int nd = 0;
       if (doOut) { d0 = (char*)out; nd = 1; }
       if (doSend) {
-        char* t0 = slotOf(sc0, sstep0);
-        char* t1 = nsc > 1 ? slotOf(sc1, sstep1) : nullptr;
+        char* t0 = slotOf(2);
+        char* t1 = nsc > 1 ? slotOf(3) : nullptr;
         if (nd == 0) { d0 = t0; d1 = t1; } else { d1 = t0; d2 = t1; }
         nd += nsc;
       }
@@ -609,10 +643,10 @@ struct Prims {
       // loads of the round are issued before the first flag check
       constexpr int U = 4;
       const uint32_t npairs = (nbytes + 7) / 8;
-      const char* rs0 = doRecv ? slotOf(rc0, rstep0) : nullptr;
-      const char* rs1 = (doRecv && nrc > 1) ? slotOf(rc1, rstep1) : nullptr;
-      char* ss0 = doSend ? slotOf(sc0, sstep0) : nullptr;
-      char* ss1 = (doSend && nsc > 1) ? slotOf(sc1, sstep1) : nullptr;
+      const char* rs0 = doRecv ? slotOf(0) : nullptr;
+      const char* rs1 = (doRecv && nrc > 1) ? slotOf(1) : nullptr;
+      char* ss0 = doSend ? slotOf(2) : nullptr;
+      char* ss1 = (doSend && nsc > 1) ? slotOf(3) : nullptr;
       const uint32_t rf0 = (uint32_t)(rstep0 + 1), rf1 = (uint32_t)(rstep1 + 1);
       const uint32_t sf0 = (uint32_t)(sstep0 + 1), sf1 = (uint32_t)(sstep1 + 1);
       bool fail = false;
@@ -671,10 +705,10 @@ struct Prims {
       const uint32_t nquads = (nlines + 3) / 4;
       const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
       const int j = lane & 7;
-      const char* rs0 = doRecv ? slotOf(rc0, rstep0) : nullptr;
-      const char* rs1 = (doRecv && nrc > 1) ? slotOf(rc1, rstep1) : nullptr;
-      char* ss0 = doSend ? slotOf(sc0, sstep0) : nullptr;
-      char* ss1 = (doSend && nsc > 1) ? slotOf(sc1, sstep1) : nullptr;
+      const char* rs0 = doRecv ? slotOf(0) : nullptr;
+      const char* rs1 = (doRecv && nrc > 1) ? slotOf(1) : nullptr;
+      char* ss0 = doSend ? slotOf(2) : nullptr;
+      char* ss1 = (doSend && nsc > 1) ? slotOf(3) : nullptr;
       const uint64_t rf0 = rstep0 + 1, rf1 = rstep1 + 1, sf0 = sstep0 + 1, sf1 = sstep1 + 1;
       uint32_t q0 = warp;
       // Fast path for rounds of UF full line quads when the user pointers
@@ -881,11 +915,13 @@ struct Desc {
 enum Role : int { kRoleRing = 0, kRoleTreeRoot = 1, kRoleTreeUp = 2, kRoleTreeDown = 3 };
 
 // The step tables of Sec. V-E as an iterator over primitive invocations.
+// The ring collectives' block index (r - t - 1) mod k, or (r - t) mod k for
+// AllGather, is kept in `blk` and stepped down with a wrap as t advances.
 struct Sched {
   int coll, k, r, role, pos;
   bool leaf, inplace;
   unsigned long long count, chunk, end, off, c;
-  int t;
+  int t, blk;
 
   VDEV void init(const KernArgs& a, int r_, int ch, int role_, bool leaf_, int unitBytes) {
     coll = a.coll;
@@ -901,6 +937,7 @@ struct Sched {
     off = start;
     end = start + len;
     t = 0;
+    blk = 0;
     c = 0;
     pos = 0;
     if (coll == kBroadcast) pos = modk(r - a.root, k);
@@ -916,10 +953,13 @@ struct Sched {
 
   VDEV bool next(Desc& d, int unitBytes) {
     if (off >= end) return false;
+    if (t == 0) blk = (coll == kAllGather) ? r : (r == 0 ? k - 1 : r - 1);
+    const int b = blk;   // (r - t - 1) mod k, AllGather (r - t) mod k
+    blk = (blk == 0) ? k - 1 : blk - 1;
     if (role == kRoleRing && coll == kAllReduce) {
       // Table "Ring AllReduce": rank r handles segment (r - t - 1) mod k
       if (t == 0) c = ringLoopChunk(off, end, k, chunk, unitBytes);
-      const int s = modk(r - t - 1, k);
+      const int s = b;
       unsigned long long sa = off + (unsigned long long)s * c;
       if (sa > end) sa = end;
       unsigned long long sb = sa + c;
@@ -939,7 +979,7 @@ struct Sched {
     d.n = n;
     if (role == kRoleRing && coll == kReduceScatter) {
       // Table "Ring ReduceScatter": block (r - t - 1) mod k, lands on rank r at t = k-1
-      d.lo = (unsigned long long)modk(r - t - 1, k) * count + off;
+      d.lo = (unsigned long long)b * count + off;
       d.oo = off;
       if (t == 0) set(d, false, true, true, false);                 // send
       else if (t <= k - 2) set(d, true, true, true, false);         // recvReduceSend
@@ -950,7 +990,7 @@ struct Sched {
     if (role == kRoleRing && coll == kAllGather) {
       // Table "Ring AllGather": block (r - t) mod k arrives at step t
       d.lo = off;
-      d.oo = (unsigned long long)modk(r - t, k) * count + off;
+      d.oo = (unsigned long long)b * count + off;
       if (t == 0) set(d, false, true, true, !inplace);              // send / copySend
       else if (t <= k - 2) set(d, true, false, true, true);         // recvCopySend
       else set(d, true, false, false, true);                        // recv
@@ -992,7 +1032,7 @@ struct Sched {
 // root) and a broadcast group (recvCopySend / recv from the root), so the two
 // phases stream concurrently.  The data movement has a single call site.
 template <int P, class T, class Op>
-VDEV void runWorker(const KernArgs& a, int r, int ch, volatile int* sAbort) {
+VDEV void runWorker(const KernArgs& a, int r, int ch, WorkerShared* ws) {
   if (r == a.skipRank) return;   // injected fault: this vrank never takes part
   const int k = a.nranks;
   const ConnDev* r0 = nullptr;
@@ -1001,7 +1041,7 @@ VDEV void runWorker(const KernArgs& a, int r, int ch, volatile int* sAbort) {
   const ConnDev* s1 = nullptr;
   int tid = threadIdx.x, nthr = blockDim.x, barId = 0, role = kRoleRing;
   bool leaf = false;
-  volatile int* ab = sAbort;
+  volatile int* ab = ws->abort;
   if (a.algo == kTree) {
     const int t = ch & 1;
     int parent, c0, c1;
@@ -1027,7 +1067,7 @@ VDEV void runWorker(const KernArgs& a, int r, int ch, volatile int* sAbort) {
       tid = threadIdx.x - a.upThreads;
       nthr = blockDim.x - a.upThreads;
       barId = 2;
-      ab = sAbort + 1;
+      ab = ws->abort + 1;
       r0 = &down[r];
       s0 = c0 >= 0 ? &down[c0] : nullptr;
       s1 = c1 >= 0 ? &down[c1] : nullptr;
@@ -1047,7 +1087,7 @@ VDEV void runWorker(const KernArgs& a, int r, int ch, volatile int* sAbort) {
     s0 = hasSend ? &ring[r] : nullptr;
     r0 = hasRecv ? &ring[modk(r - 1, k)] : nullptr;
   }
-  Prims<P, T, Op> pr(a, tid, nthr, barId, ab, r, ch, r0, r1, s0, s1);
+  Prims<P, T, Op> pr(a, tid, nthr, barId, ab, &ws->cc[barId], r, ch, r0, r1, s0, s1);
   Sched sc;
   sc.init(a, r, ch, role, leaf, (int)sizeof(T));
   const T* x = (const T*)a.send[r];

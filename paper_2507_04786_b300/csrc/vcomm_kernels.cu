@@ -14,14 +14,13 @@ namespace vc {
 
 template <int P>
 __global__ void __launch_bounds__(maxThreadsFor(P), 1) kCopyColl(const __grid_constant__ KernArgs a) {
-  __shared__ int sAbort[2];
-  if (threadIdx.x < 2) sAbort[threadIdx.x] = 0;
+  __shared__ WorkerShared ws;
+  if (threadIdx.x < 2) ws.abort[threadIdx.x] = 0;
   __syncthreads();
   const int r = blockIdx.x % a.nranks;
   const int ch = blockIdx.x / a.nranks;
-  volatile int* sa = sAbort;
   if (a.coll == kCopy) localCopy<uint8_t>(a, ch);
-  else runWorker<P, uint8_t, OpNone>(a, r, ch, sa);
+  else runWorker<P, uint8_t, OpNone>(a, r, ch, &ws);
 }
 
 // ---- protocol encoders exposed for tests: one thread per LL line pair / one

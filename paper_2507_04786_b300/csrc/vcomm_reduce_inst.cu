@@ -13,14 +13,13 @@ namespace vc {
 
 template <int P, class T, class Op>
 __global__ void __launch_bounds__(maxThreadsFor(P), 1) kReduceColl(const __grid_constant__ KernArgs a) {
-  __shared__ int sAbort[2];
-  if (threadIdx.x < 2) sAbort[threadIdx.x] = 0;
+  __shared__ WorkerShared ws;
+  if (threadIdx.x < 2) ws.abort[threadIdx.x] = 0;
   __syncthreads();
   const int r = blockIdx.x % a.nranks;
   const int ch = blockIdx.x / a.nranks;
-  volatile int* sa = sAbort;
   if (a.coll == kCopy) localCopy<T>(a, ch);
-  else runWorker<P, T, Op>(a, r, ch, sa);
+  else runWorker<P, T, Op>(a, r, ch, &ws);
 }
 
 using VcT = typename DTypeOf<VC_DTYPE>::T;
