@@ -564,9 +564,12 @@ struct Prims {
     return *sAbort == 0;
   }
 
-  // publish the step: tail for sends, head for receives
+  // publish the step: tail for sends, head for receives.  Simple: every
+  // thread's slot writes (and reads) are ordered before thread 0's release
+  // store by the block barrier (CTA scope) and carried to the device scope by
+  // the release's cumulativity; the receiver acquires the tail and passes its
+  // own barrier before any thread reads the slot.  No per-thread fence.
   VDEV bool release(bool doRecv, bool doSend) {
-    if (PROTO == kSimple) __threadfence();
     bar();
     if (*sAbort) return false;
     if (tid == 0) {
