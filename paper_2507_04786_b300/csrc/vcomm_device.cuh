@@ -3,16 +3,18 @@
 // One CTA (or one warp group of a CTA) is the worker of one (vrank, channel).
 // Workers exchange data only through connection FIFOs in HBM.  The three
 // protocols of Sec. III differ in how a FIFO slot is filled and signalled:
-//   Simple : plain 16-byte stores into the slot, a gpu-scope fence, then a
-//            release store of the connection's `tail` counter; the receiver
-//            acquires `tail` before it reads the slot (Sec. III-A).
+//   Simple : plain 16-byte stores into the slot, the block barrier, then one
+//            thread's gpu-scope release fence and store of the connection's
+//            `tail` counter; the receiver acquires `tail` before it reads the
+//            slot (Sec. III-A).
 //   LL     : 8-byte lines {4 data bytes, 4-byte flag} written with one 8-byte
 //            store each; the reader polls the flag of every line (Sec. III-B).
 //   LL128  : 128-byte lines of 120 data bytes + an 8-byte flag, written by 8
 //            threads in one warp-wide 16-byte store instruction; the reader
 //            loads the whole line and checks the flag (Sec. III-C).
-// All three return a slot to the sender with a release store of `head`
-// (credits), so the FIFO holds at most `nsteps` steps in flight (Sec. V-C).
+// All three return a slot to the sender by advancing `head` (credits: after a
+// release fence for Simple, a relaxed store for LL / LL128, whose data the
+// flags publish), so the FIFO holds at most `nsteps` steps in flight (Sec. V-C).
 // Every wait is bounded by %globaltimer; on expiry (or on the host abort word)
 // the worker records the failure and returns -- no trap, no endless loop.
 #pragma once
@@ -41,6 +43,7 @@ VDEV uint64_t ldAcquire(const unsigned long long* p) {
 VDEV void stRelease(unsigned long long* p, uint64_t v) {
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+VDEV void fenceAcqRel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 VDEV void stRelaxed(unsigned long long* p, uint64_t v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
@@ -573,27 +576,21 @@ struct Prims {
     bar();
     if (*sAbort) return false;
     if (tid == 0) {
+      // Simple: one release fence, then every counter of the step with a
+      // strong relaxed store (a release pattern for each of them: the slot
+      // writes of a send and the slot reads of a receive, ordered before the
+      // fence by the barrier above, are seen before the counter).  One fence
+      // instead of a release store per counter, whose fences would each wait
+      // for the store before it.  LL / LL128 publish data through the lines'
+      // flags, so their counters need no fence on the step's path.
+      if (PROTO == kSimple) fenceAcqRel();
       if (doSend) {
-        if (PROTO == kSimple) {
-          stRelease(cc->mine[2], sstep0 + 1);
-          if (nsc > 1) stRelease(cc->mine[3], sstep1 + 1);
-        } else {
-          stRelaxed(cc->mine[2], sstep0 + 1);
-          if (nsc > 1) stRelaxed(cc->mine[3], sstep1 + 1);
-        }
+        stRelaxed(cc->mine[2], sstep0 + 1);
+        if (nsc > 1) stRelaxed(cc->mine[3], sstep1 + 1);
       }
       if (doRecv) {
-        // the slot's reads have all returned (the barrier above): Simple
-        // orders them before the credit with a release store; LL / LL128
-        // publish data through the lines' flags, so their credit needs no
-        // fence on the step's path
-        if (PROTO == kSimple) {
-          stRelease(cc->mine[0], rstep0 + 1);
-          if (nrc > 1) stRelease(cc->mine[1], rstep1 + 1);
-        } else {
-          stRelaxed(cc->mine[0], rstep0 + 1);
-          if (nrc > 1) stRelaxed(cc->mine[1], rstep1 + 1);
-        }
+        stRelaxed(cc->mine[0], rstep0 + 1);
+        if (nrc > 1) stRelaxed(cc->mine[1], rstep1 + 1);
       }
     }
     if (doSend) { sstep0++; sstep1++; bumpSlots(2); }
