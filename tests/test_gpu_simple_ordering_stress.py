@@ -1,4 +1,4 @@
-"""Simple FIFO publication order under load.
+"""Simple and LL FIFO publication order under load.
 
 A Simple step (Sec. III-A) publishes its slot without a fence in every
 thread: the step's threads write the slot, meet at the block barrier, and
@@ -9,6 +9,11 @@ thread reads the slot.  The barrier orders every thread's slot writes before
 thread 0's fence, and the fence's cumulativity carries them to device scope;
 a mistake in that chain would let a receiver read a slot before all of its
 bytes had landed, or let a sender overwrite a slot still being read.
+
+LL (Sec. III-B) returns its slots the same way but without the fence: its
+data is published by the lines' flags, and the receiver's head is a relaxed
+store after the barrier that follows the step's reads.  Both protocols run
+here.
 
 This test puts the chain under stress: the smallest slots the library takes
 (256 and 512 bytes, so a call takes hundreds of steps), FIFOs of 2, 3 and 8
@@ -37,13 +42,14 @@ CALLS = 400       # per communicator
 RING = 4          # output sets per communicator, checked every RING calls
 
 
-def test_simple_slots_publish_in_order_under_load():
+@pytest.mark.parametrize("proto", ["simple", "ll"])
+def test_slots_publish_in_order_under_load(proto):
     setups = []
     for i, (k, C, n, dt, algo, slot, ns) in enumerate(COMMS):
         sets = [inputs.workload(900 + 10 * i + j, k, n, dt, "normal") for j in range(2)]
-        ch = chunk_for("simple", dt, {"simple": slot}, 1)
+        ch = chunk_for(proto, dt, {proto: slot}, 1)
         want = [oracle.all_reduce(xs, dt, "sum", C, ch, algo) for xs in sets]
-        c = Comm(k, C, slot_bytes={"simple": slot}, nsteps=ns, timeout_sec=10.0)
+        c = Comm(k, C, slot_bytes={proto: slot}, nsteps=ns, timeout_sec=10.0)
         c.set_plan(nchannels=C, chunk_steps=1)
         dev_in = [[to_dev(x) for x in xs] for xs in sets]
         dev_want = [[to_dev(w) for w in ws] for ws in want]
@@ -56,7 +62,7 @@ def test_simple_slots_publish_in_order_under_load():
         for su in setups:
             with torch.cuda.stream(su["stream"]):
                 su["c"].all_reduce(su["ins"][it % 2], su["outs"][it % RING], op="sum", algo=su["algo"],
-                                   proto="simple", stream=su["stream"])
+                                   proto=proto, stream=su["stream"])
         if it % RING == RING - 1:
             torch.cuda.synchronize()
             for ci, su in enumerate(setups):
@@ -81,6 +87,6 @@ def test_simple_slots_publish_in_order_under_load():
         assert_same(to_np(su["outs"][call % RING][r], su["dt"]), su["host_want"][call % 2][r],
                     f"communicator {ci} call {call} rank {r} ({len(bad)} bad outputs)")
     for su in setups:
-        assert su["c"].last_plan()["proto"] == "simple"
+        assert su["c"].last_plan()["proto"] == proto
         su["c"].destroy()
     assert not bad
